@@ -1,0 +1,263 @@
+"""Seeded synthetic scenes for the batched trajectory optimizer.
+
+This module only draws inputs: problem descriptions (horizon, duration, start,
+goal), obstacle sets and initial coefficient sets. It holds none of the
+method's arithmetic, and both the CUDA path and the CPU oracle consume what it
+returns. Every floating-point array that the GPU receives in FP32 is rounded
+through float32 here, so that the FP64 oracle sees bit-identical inputs.
+
+The paper's benchmarks (crowd simulator scenes, the BARN dataset, Gazebo
+worlds) are not available; these generators stand in for them with the
+shapes the thesis describes: a holonomic point robot, Bernstein degree-10
+coefficients per axis, moving axis-aligned elliptical obstacles (Paper II
+problem statement) and sphere obstacles on box surfaces that emulate the
+down-sampled point clouds of the PRIEST experiments.
+
+Data layout of a ``Batch`` (all numpy):
+  dim            2 or 3
+  n_steps[P]     int32, horizon n_p of each problem
+  duration[P]    float64, horizon length T in seconds
+  start[P,dim]   float64, goal[P,dim] float64
+  offsets[P+1]   int32, CSR offsets of each problem's obstacles
+  centers[N,dim], semi_axes[N,dim], velocities[N,dim]   float32-exact float64
+  traj_problem[B] int32, problem index of each trajectory
+  xi0[B,dim,11]  float32-exact float64, initial coefficients
+  vmax, amax, rho  scalars
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+N_COEFF = 11  # Bernstein degree 10
+
+
+def f32(x):
+    """Round through float32 and return float64 (bit-identical inputs)."""
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+@dataclasses.dataclass
+class Batch:
+    dim: int
+    n_steps: np.ndarray
+    duration: np.ndarray
+    start: np.ndarray
+    goal: np.ndarray
+    offsets: np.ndarray
+    centers: np.ndarray
+    semi_axes: np.ndarray
+    velocities: np.ndarray
+    traj_problem: np.ndarray
+    xi0: np.ndarray
+    vmax: float
+    amax: float
+    rho: float = 1.0
+    name: str = ""
+
+    @property
+    def n_problems(self) -> int:
+        return int(self.n_steps.shape[0])
+
+    @property
+    def n_traj(self) -> int:
+        return int(self.traj_problem.shape[0])
+
+    def n_obstacles(self, p: int) -> int:
+        return int(self.offsets[p + 1] - self.offsets[p])
+
+    def obstacles(self, p: int):
+        s, e = int(self.offsets[p]), int(self.offsets[p + 1])
+        return self.centers[s:e], self.semi_axes[s:e], self.velocities[s:e]
+
+    def subset(self, traj_idx) -> "Batch":
+        """Same problems, a subset of the trajectories (in the given order)."""
+        traj_idx = np.asarray(traj_idx, dtype=np.int64)
+        return dataclasses.replace(self, traj_problem=self.traj_problem[traj_idx].copy(),
+                                   xi0=self.xi0[traj_idx].copy())
+
+    def select_problems(self, probs) -> "Batch":
+        """Keep only the listed problems and their trajectories (re-indexed)."""
+        probs = [int(p) for p in probs]
+        remap = {p: k for k, p in enumerate(probs)}
+        cen, ax, vel, offs = [], [], [], [0]
+        for p in probs:
+            c, a, v = self.obstacles(p)
+            cen.append(c); ax.append(a); vel.append(v); offs.append(offs[-1] + c.shape[0])
+        keep = np.array([k for k in range(self.n_traj) if int(self.traj_problem[k]) in remap],
+                        dtype=np.int64)
+        tp = np.array([remap[int(self.traj_problem[k])] for k in keep], dtype=np.int32)
+        d = self.dim
+        return dataclasses.replace(
+            self, n_steps=self.n_steps[probs].copy(), duration=self.duration[probs].copy(),
+            start=self.start[probs].copy(), goal=self.goal[probs].copy(),
+            offsets=np.array(offs, dtype=np.int32),
+            centers=np.concatenate(cen) if cen else np.zeros((0, d)),
+            semi_axes=np.concatenate(ax) if ax else np.zeros((0, d)),
+            velocities=np.concatenate(vel) if vel else np.zeros((0, d)),
+            traj_problem=tp, xi0=self.xi0[keep].copy())
+
+
+def straight_line_coeffs(start, goal) -> np.ndarray:
+    """Bernstein coefficients of the constant-velocity segment start->goal.
+
+    c_i = start + (goal - start) * i / 10, one row per axis: shape [dim, 11].
+    Used only to centre the random initial guesses (an input, not a result).
+    """
+    start = np.asarray(start, dtype=np.float64)
+    goal = np.asarray(goal, dtype=np.float64)
+    i = np.arange(N_COEFF, dtype=np.float64) / (N_COEFF - 1)
+    return start[:, None] + (goal - start)[:, None] * i[None, :]
+
+
+def _inside(point, center, axes) -> bool:
+    return float(np.sum(((np.asarray(point) - center) / axes) ** 2)) <= 1.0
+
+
+# ---------------------------------------------------------------------------
+# Config 1: 2D, 8 static circles, B=16, n_p=50, T=5 s (1' uses T=12 s).
+# ---------------------------------------------------------------------------
+def config1(seed: int = 0, feasible: bool = False) -> Batch:
+    rng = np.random.default_rng(seed)
+    radii = rng.uniform(0.3, 0.6, 8)
+    centers = rng.uniform(1.0, 9.0, (8, 2))
+    noise = rng.normal(0.0, 0.5, (16, 2, N_COEFF))
+    start = np.array([0.0, 0.0]); goal = np.array([10.0, 10.0])
+    T = 12.0 if feasible else 5.0
+    xi0 = straight_line_coeffs(start, goal)[None] + noise
+    return Batch(dim=2, n_steps=np.array([50], np.int32), duration=np.array([T]),
+                 start=start[None].copy(), goal=goal[None].copy(),
+                 offsets=np.array([0, 8], np.int32), centers=f32(centers),
+                 semi_axes=f32(np.stack([radii, radii], 1)),
+                 velocities=np.zeros((8, 2)), traj_problem=np.zeros(16, np.int32),
+                 xi0=f32(xi0), vmax=1.5, amax=2.0, rho=1.0,
+                 name="config1_feasible" if feasible else "config1")
+
+
+# ---------------------------------------------------------------------------
+# Moving ellipses (config 2 / config 4 / config 5 scenes).
+# ---------------------------------------------------------------------------
+def _draw_ellipses(rng, n_o, lo, hi, start, goal, T):
+    cen, vel, ax = [], [], []
+    while len(cen) < n_o:
+        a = rng.uniform(0.2, 0.8, 2)
+        c = rng.uniform(lo, hi, 2)
+        speed = rng.uniform(0.0, 1.0)
+        heading = rng.uniform(0.0, 2.0 * math.pi)
+        v = speed * np.array([math.cos(heading), math.sin(heading)])
+        # reject obstacles covering the start at t=0 or the goal at t=T
+        if _inside(start, c, a) or _inside(goal, c + v * T, a):
+            continue
+        cen.append(c); vel.append(v); ax.append(a)
+    return np.array(cen).reshape(-1, 2), np.array(ax).reshape(-1, 2), np.array(vel).reshape(-1, 2)
+
+
+def config2(seed: int = 0, n_scenes: int = 128, inits: int = 8, n_obstacles: int = 50,
+            n_steps: int = 100) -> Batch:
+    """2D, n_p=100 over T=10 s, 50 constant-velocity ellipses, start (0,0), goal (8,8)."""
+    rng = np.random.default_rng(seed)
+    start = np.array([0.0, 0.0]); goal = np.array([8.0, 8.0]); T = 0.1 * n_steps
+    line = straight_line_coeffs(start, goal)
+    cen, ax, vel, xi0, tp, offs = [], [], [], [], [], [0]
+    for s in range(n_scenes):
+        c, a, v = _draw_ellipses(rng, n_obstacles, 0.0, 8.0, start, goal, T)
+        cen.append(c); ax.append(a); vel.append(v); offs.append(offs[-1] + n_obstacles)
+        xi0.append(line[None] + rng.normal(0.0, 0.5, (inits, 2, N_COEFF)))
+        tp.extend([s] * inits)
+    P = n_scenes
+    return Batch(dim=2, n_steps=np.full(P, n_steps, np.int32), duration=np.full(P, T),
+                 start=np.tile(start, (P, 1)), goal=np.tile(goal, (P, 1)),
+                 offsets=np.array(offs, np.int32), centers=f32(np.concatenate(cen)),
+                 semi_axes=f32(np.concatenate(ax)), velocities=f32(np.concatenate(vel)),
+                 traj_problem=np.array(tp, np.int32), xi0=f32(np.concatenate(xi0)),
+                 vmax=1.5, amax=2.0, rho=1.0, name=f"config2_seed{seed}")
+
+
+def config4(seed: int = 0, n_problems: int = 2048, inits: int = 8) -> Batch:
+    """Uneven batch: n_o log-uniform in [4,256], n_p in {50,75,100,150}, T = 0.1 n_p."""
+    rng = np.random.default_rng(seed)
+    vmax = 1.5
+    n_steps, dur, st, gl, cen, ax, vel, xi0, tp, offs = [], [], [], [], [], [], [], [], [], [0]
+    for p in range(n_problems):
+        n_o = int(round(math.exp(rng.uniform(math.log(4.0), math.log(256.0)))))
+        n_p = int(rng.choice([50, 75, 100, 150]))
+        T = 0.1 * n_p
+        heading = rng.uniform(0.0, 2.0 * math.pi)
+        dist = 0.55 * vmax * T
+        start = np.zeros(2)
+        goal = dist * np.array([math.cos(heading), math.sin(heading)])
+        lo = np.minimum(start, goal) - 1.0; hi = np.maximum(start, goal) + 1.0
+        c, a, v = _draw_ellipses(rng, n_o, lo, hi, start, goal, T)
+        line = straight_line_coeffs(start, goal)
+        n_steps.append(n_p); dur.append(T); st.append(start); gl.append(goal)
+        cen.append(c); ax.append(a); vel.append(v); offs.append(offs[-1] + n_o)
+        xi0.append(line[None] + rng.normal(0.0, 0.5, (inits, 2, N_COEFF)))
+        tp.extend([p] * inits)
+    return Batch(dim=2, n_steps=np.array(n_steps, np.int32), duration=np.array(dur),
+                 start=np.array(st), goal=f32(np.array(gl)), offsets=np.array(offs, np.int32),
+                 centers=f32(np.concatenate(cen)), semi_axes=f32(np.concatenate(ax)),
+                 velocities=f32(np.concatenate(vel)), traj_problem=np.array(tp, np.int32),
+                 xi0=f32(np.concatenate(xi0)), vmax=vmax, amax=2.0, rho=1.0,
+                 name=f"config4_seed{seed}")
+
+
+# ---------------------------------------------------------------------------
+# Config 3: 3D, 256 spheres on the surfaces of 12 random boxes in 20x20x5 m.
+# ---------------------------------------------------------------------------
+def _box_surface_points(rng, lo, hi, n):
+    """Uniform points on the union of box surfaces (box by area, face by area)."""
+    size = hi - lo
+    faces = []  # (box, axis, side, area)
+    for b in range(lo.shape[0]):
+        sx, sy, sz = size[b]
+        for axis, area in ((0, sy * sz), (1, sx * sz), (2, sx * sy)):
+            for side in (0, 1):
+                faces.append((b, axis, side, area))
+    areas = np.array([f[3] for f in faces])
+    prob = areas / areas.sum()
+    pts = np.empty((n, 3))
+    for k in range(n):
+        b, axis, side, _ = faces[int(rng.choice(len(faces), p=prob))]
+        u = rng.uniform(0.0, 1.0, 3)
+        p = lo[b] + u * size[b]
+        p[axis] = hi[b, axis] if side else lo[b, axis]
+        pts[k] = p
+    return pts
+
+
+def config3(seed: int = 0, n_traj: int = 4096, n_spheres: int = 256) -> dict:
+    """Scene and sampler settings for the projection-guided sampler (3D)."""
+    rng = np.random.default_rng(seed)
+    start = np.array([1.0, 1.0, 1.0]); goal = np.array([19.0, 19.0, 4.0])
+    ws_lo = np.array([0.0, 0.0, 0.0]); ws_hi = np.array([20.0, 20.0, 5.0])
+    c = np.concatenate([rng.uniform(2.0, 18.0, (12, 2)), rng.uniform(0.0, 5.0, (12, 1))], 1)
+    s = np.concatenate([rng.uniform(1.0, 4.0, (12, 2)), rng.uniform(1.0, 5.0, (12, 1))], 1)
+    lo = np.clip(c - s / 2, ws_lo, ws_hi); hi = np.clip(c + s / 2, ws_lo, ws_hi)
+    cen, rad = [], []
+    while len(cen) < n_spheres:
+        p = _box_surface_points(rng, lo, hi, 1)[0]
+        r = rng.uniform(0.1, 0.3)
+        if np.linalg.norm(p - start) <= r or np.linalg.norm(p - goal) <= r:
+            continue
+        cen.append(p); rad.append(r)
+    cen = np.array(cen); rad = np.array(rad)
+    batch = Batch(dim=3, n_steps=np.array([100], np.int32), duration=np.array([20.0]),
+                  start=start[None].copy(), goal=goal[None].copy(),
+                  offsets=np.array([0, n_spheres], np.int32), centers=f32(cen),
+                  semi_axes=f32(np.stack([rad, rad, rad], 1)),
+                  velocities=np.zeros((n_spheres, 3)),
+                  traj_problem=np.zeros(n_traj, np.int32),
+                  xi0=np.zeros((n_traj, 3, N_COEFF)), vmax=2.0, amax=2.0, rho=1.0,
+                  name=f"config3_seed{seed}")
+    mu0 = straight_line_coeffs(start, goal).reshape(-1)
+    sigma0 = 4.0 * np.eye(3 * N_COEFF)
+    return dict(batch=batch, mu0=f32(mu0), sigma0=f32(sigma0), n_outer=10, n_inner=20,
+                n_proj=int(math.ceil(0.73 * n_traj)), n_elite=int(math.ceil(0.10 * n_traj)))
+
+
+def normal_draws(seed: int, shape) -> np.ndarray:
+    """Host-side standard normal draws (float32-exact) for sampler parity runs."""
+    rng = np.random.default_rng(seed)
+    return f32(rng.standard_normal(shape))

@@ -1,0 +1,156 @@
+"""Pins of the oracle's AM loop (Algorithm 2) by invariants and special cases.
+
+- Obstacle-free, bounds inactive: the iteration's fixed point is the
+  brute-force solution of the equality-constrained QP (eq. qp_cost / qp_sol),
+  computed here by the null-space method with an independent basis (BPoly).
+- Projection mode (eq. projection_cost) without obstacles: the Euclidean
+  projection onto {A xi = b}, a textbook closed form.
+- A xi = b holds at every iterate.
+- A feasible QP optimum is a fixed point: r = 0, lambda = 0, xi unchanged.
+- Multiplier sign: a single penetrating obstacle is pushed out and the
+  residual goes to zero only with lambda <- lambda - rho F^T r.
+- Early stop: the first k >= 1 whose three residuals are all <= tol.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+from scipy.interpolate import BPoly
+from scipy.linalg import null_space
+
+from oracle import am
+from paper_2408_10731_b300 import scenes
+
+
+def _tables(n_p, T):
+    t = np.linspace(0.0, T, n_p)
+    P = np.zeros((n_p, 11)); Pd = np.zeros_like(P); Pdd = np.zeros_like(P)
+    for i in range(11):
+        c = np.zeros((11, 1)); c[i, 0] = 1.0
+        bp = BPoly(c, [0.0, T])
+        P[:, i] = bp(t); Pd[:, i] = bp.derivative()(t); Pdd[:, i] = bp.derivative(2)(t)
+    return P, Pd, Pdd
+
+
+def _single_problem(start, goal, n_p, T, centers, axes, vel=None, B=1, xi0=None, vmax=1e6,
+                    amax=1e6, rho=1.0):
+    dim = len(start)
+    centers = np.asarray(centers, float).reshape(-1, dim)
+    n_o = centers.shape[0]
+    return scenes.Batch(
+        dim=dim, n_steps=np.array([n_p], np.int32), duration=np.array([T]),
+        start=np.asarray(start, float)[None], goal=np.asarray(goal, float)[None],
+        offsets=np.array([0, n_o], np.int32), centers=centers,
+        semi_axes=np.asarray(axes, float).reshape(-1, dim),
+        velocities=np.zeros((n_o, dim)) if vel is None else np.asarray(vel, float).reshape(-1, dim),
+        traj_problem=np.zeros(B, np.int32),
+        xi0=np.zeros((B, dim, 11)) if xi0 is None else np.asarray(xi0, float),
+        vmax=vmax, amax=amax, rho=rho)
+
+
+def _qp_bruteforce(Q, q, A, b):
+    xp = np.linalg.lstsq(A, b, rcond=None)[0]
+    N = null_space(A)
+    z = -np.linalg.solve(N.T @ Q @ N, N.T @ (Q @ xp + q))
+    return xp + N @ z
+
+
+def test_obstacle_free_fixed_point_is_the_qp_optimum():
+    n_p, T = 50, 5.0
+    start, goal = np.array([0.0, 1.0]), np.array([4.0, -2.0])
+    rng = np.random.default_rng(0)
+    xi0 = scenes.straight_line_coeffs(start, goal)[None] + rng.normal(0, 0.5, (3, 2, 11))
+    b = _single_problem(start, goal, n_p, T, np.zeros((0, 2)), np.zeros((0, 2)), B=3, xi0=xi0,
+                        rho=0.05)
+    out = am.solve(b, 6000, tol=-1.0)
+    P, Pd, Pdd = _tables(n_p, T)
+    Q = Pdd.T @ Pdd + P.T @ P
+    A = np.stack([P[0], Pd[0], Pdd[0], P[-1]])
+    tau = np.linspace(0, 1, n_p)
+    for a in range(2):
+        xdes = start[a] + (goal[a] - start[a]) * tau
+        ref = _qp_bruteforce(Q, -P.T @ xdes, A, np.array([start[a], 0, 0, goal[a]]))
+        np.testing.assert_allclose(out["xi"][:, a], np.broadcast_to(ref, (3, 11)), atol=1e-10)
+    np.testing.assert_allclose(out["residual"], 0.0, atol=1e-12)
+
+
+def test_projection_mode_without_obstacles_is_affine_projection():
+    n_p, T = 60, 6.0
+    start, goal = np.array([1.0, 2.0, 0.5]), np.array([5.0, -1.0, 2.0])
+    rng = np.random.default_rng(1)
+    xi0 = rng.normal(0, 1.0, (4, 3, 11))
+    b = _single_problem(start, goal, n_p, T, np.zeros((0, 3)), np.zeros((0, 3)), B=4, xi0=xi0,
+                        rho=0.01)
+    # the proximal iteration converges to the projection; run it to its fixed point
+    out = am.solve(b, 20000, tol=-1.0, cost_mode=1)
+    P, Pd, Pdd = _tables(n_p, T)
+    A = np.stack([P[0], Pd[0], Pdd[0], P[-1]])
+    for a in range(3):
+        bb = np.array([start[a], 0, 0, goal[a]])
+        x = xi0[:, a]
+        ref = x - (A.T @ np.linalg.solve(A @ A.T, A @ x.T - bb[:, None])).T
+        np.testing.assert_allclose(out["xi"][:, a], ref, atol=1e-11)
+
+
+def test_boundary_equalities_hold_at_every_iterate():
+    b = scenes.config2(3, n_scenes=2, inits=3)
+    P, Pd, Pdd = _tables(100, 10.0)
+    for k in (1, 4, 17):
+        out = am.solve(b, k, iters_fixed=np.full(b.n_traj, k))
+        xi = out["xi"]
+        np.testing.assert_allclose(xi @ P[0], b.start[b.traj_problem], atol=1e-10)
+        np.testing.assert_allclose(xi @ Pd[0], 0.0, atol=1e-10)
+        np.testing.assert_allclose(xi @ Pdd[0], 0.0, atol=1e-10)
+        np.testing.assert_allclose(xi @ P[-1], b.goal[b.traj_problem], atol=1e-10)
+
+
+def test_feasible_qp_optimum_is_a_fixed_point():
+    n_p, T = 50, 10.0
+    start, goal = np.array([0.0, 0.0]), np.array([5.0, 3.0])
+    P, Pd, Pdd = _tables(n_p, T)
+    Q = Pdd.T @ Pdd + P.T @ P
+    A = np.stack([P[0], Pd[0], Pdd[0], P[-1]])
+    tau = np.linspace(0, 1, n_p)
+    xi_star = np.stack([_qp_bruteforce(Q, -P.T @ (start[a] + (goal[a] - start[a]) * tau), A,
+                                       np.array([start[a], 0, 0, goal[a]])) for a in range(2)])
+    # obstacles well away from the optimum; bounds satisfied (1.5 m/s, 2 m/s^2)
+    centers = [[0.0, 4.0], [4.0, -2.0], [1.0, 3.0]]
+    b = _single_problem(start, goal, n_p, T, centers, [[0.5, 0.4]] * 3, B=1,
+                        xi0=xi_star[None], vmax=1.5, amax=2.0)
+    out = am.solve(b, 25, tol=-1.0, want_lambda=True)
+    np.testing.assert_allclose(out["xi"][0], xi_star, atol=1e-10)
+    np.testing.assert_allclose(out["lam"], 0.0, atol=1e-10)
+    np.testing.assert_allclose(out["residual"], 0.0, atol=1e-12)
+
+
+def test_multiplier_sign_pushes_out_of_a_single_obstacle():
+    n_p, T = 50, 10.0
+    start, goal = np.array([0.0, 0.0]), np.array([6.0, 0.0])
+    line = scenes.straight_line_coeffs(start, goal)[None]
+    # one circle sitting on the straight line, slightly off-axis so the push is +y
+    b = _single_problem(start, goal, n_p, T, [[3.0, -0.05]], [[0.5, 0.5]], B=1, xi0=line,
+                        vmax=1.5, amax=2.0)
+    out = am.solve(b, 400, tol=-1.0, want_hist=True)
+    h = out["hist"][0, :, 0]
+    assert h[0] > 0.4 and h[1] > 0.0
+    assert h[50] < 0.5 * h[1]
+    assert h[-1] < 1e-3
+    # every iterate after the first moves the midpoint further from the centre (+y)
+    ys = []
+    for k in (1, 2, 5, 20):
+        xi = am.solve(b, k, iters_fixed=[k])["xi"][0]
+        P, _, _ = _tables(n_p, T)
+        ys.append((P @ xi[1])[n_p // 2])
+    assert all(np.diff(ys) > 0), ys
+
+
+def test_early_stop_is_first_iteration_under_tolerance():
+    b = scenes.config2(0, n_scenes=2, inits=4)
+    tol = 1e-3
+    out = am.solve(b, 300, tol=tol, want_hist=True)
+    for k in range(b.n_traj):
+        h = out["hist"][k]
+        under = np.nonzero(np.all(h[1:] <= tol, axis=1))[0]
+        expect = (under[0] + 1) if under.size else 300
+        assert out["iters"][k] == expect
+        np.testing.assert_array_equal(out["residual"][k], h[out["iters"][k]])
