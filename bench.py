@@ -1,0 +1,270 @@
+#!/usr/bin/env python
+"""Benchmark: solved trajectories/sec at residual <= 1e-3 m on the 2D moving-ellipse
+workload (n_p = 100 over 10 s, 50 constant-velocity ellipses, 128 scenes x 8
+initialisations = 1024 trajectories, iteration cap 500), one batch solve per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|mixed]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Prints one JSON line (rank 0). Under torchrun each rank solves its own seeded
+batch (independent problems, no data-path collective: weak scaling); the
+barrier and the max over ranks are the only cross-rank steps.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("solved trajectories/sec at residual ≤1e-3 m; ms per batch solve vs plain FP32 GPU")
+UNIT = "solved trajectories/s"
+WORKLOAD = ("2D moving ellipses: n_p=100 over T=10 s, 50 constant-velocity axis-aligned "
+            "ellipses (semi-axes U(0.2,0.8) m, speed U(0,1) m/s), start (0,0) goal (8,8), "
+            "128 scenes x 8 initialisations N(straight line, 0.5 m) = 1024 trajectories, "
+            "vmax 1.5 m/s, amax 2 m/s^2, rho 1, cap 500 iterations, tol 1e-3")
+
+
+def algorithmic_ops(batch, iters):
+    """FP32 lane operations the method must execute for the given iteration counts.
+
+    Per obstacle-timestep pair (dense containment test, every pair every
+    iteration): Delta = p - (c + v t) [FMA + SUB per axis], u = Delta / a [MUL per
+    axis], s = |u|^2 [MUL + (dim-1) FMA], compare: 2D 9, 3D 13.
+    Per timestep: evaluate p, pdot, pddot [3 * 11 * dim FMA], velocity and
+    acceleration bound tests [2 * (dim + 1)], contraction F^T r [3 * 11 * dim FMA].
+    Per trajectory-iteration: the QP step [2 * 11 * 11 * dim FMA].
+    The initial projection counts as one more evaluate/project/contract pass.
+    """
+    dim = batch.dim
+    pair = 9 if dim == 2 else 13
+    per_t = 3 * 11 * dim + 2 * (dim + 1) + 3 * 11 * dim
+    qp = 2 * 11 * 11 * dim
+    n_o = np.diff(batch.offsets)[batch.traj_problem]
+    n_p = batch.n_steps[batch.traj_problem]
+    proj = n_o * n_p * pair + n_p * per_t
+    it = np.asarray(iters, np.int64)
+    return float(np.sum((it + 1) * proj + it * qp))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush(); self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(seed=0, n_scenes=16, inits=8, max_iters=500, tol=1e-3):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+    from oracle import am
+    from paper_2408_10731_b300 import scenes
+    b = scenes.config2(seed, n_scenes=n_scenes, inits=inits)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    out = am.solve(b, max_iters, tol=tol, n_threads=cores)
+    dt = time.perf_counter() - t0
+    solved = int(np.sum(np.all(out["residual"] <= tol, axis=1) & (out["iters"] < max_iters + 1)))
+    return {"value": solved / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{b.n_traj} trajectories ({n_scenes} scenes x {inits} inits) of the same "
+                      f"workload, full solve (cap {max_iters}, tol {tol}), FP64, OpenMP over "
+                      f"trajectories; {solved} solved in {dt:.2f} s",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(args.seed, n_scenes=2, inits=8)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline(args.seed, n_scenes=2, inits=8)
+        vals.append(r["value"]); secs.append(r["seconds"])
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD,
+                                            "sample": "16 trajectories (2 scenes x 8 inits) per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "16 trajectories (2 scenes x 8 inits) per step, full solve"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--max-iters", type=int, default=500)
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2408_10731_b300 import build as cuda_build, scenes, trajbatch
+
+    cuda_build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    batch = scenes.config2(args.seed + rank)
+    h = trajbatch.from_batch(batch, precision=args.precision)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        h.solve(args.max_iters, args.tol)
+    fp32_peak = trajbatch.measure_fp32_peak(5) if rank == 0 else None
+
+    sampler = ClockSampler(local)
+    barrier()
+    step_ms, kern_ms, solved = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = h.solve(args.max_iters, args.tol)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1)); kern_ms.append(st["gpu_ms"]); solved.append(st["n_solved"])
+    barrier()
+    clocks = sampler.stop()
+    out = h.get_trajectories()
+
+    # end to end through the public API with pinned host buffers
+    xi0_h = torch.from_numpy(batch.xi0.astype(np.float32)).pin_memory()
+    tp_h = batch.traj_problem.astype(np.int32)
+    res = {k: torch.empty(s, dtype=d).pin_memory() for k, s, d in (
+        ("coeffs", (batch.n_traj, batch.dim, 11), torch.float32),
+        ("residual", (batch.n_traj, 3), torch.float32), ("iters", (batch.n_traj,), torch.int32),
+        ("status", (batch.n_traj,), torch.int8))}
+    e2e_s, e2e_solved = [], []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1.0); torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.set_initial(tp_h, xi0_h)
+        h.solve(args.max_iters, args.tol, stats=False)
+        h.get_trajectories(res["coeffs"], res["residual"], res["iters"], res["status"])
+        e2e_s.append(time.perf_counter() - t0)
+        e2e_solved.append(int((res["status"].numpy() == 0).sum()))
+    h2d = xi0_h.numel() * 4 + tp_h.nbytes
+    d2h = sum(t.numel() * t.element_size() for t in res.values())
+
+    total_ms = float(np.sum(step_ms))
+    n_solved = float(np.sum(solved))
+    e2e_val = float(np.mean(e2e_solved)) / float(np.mean(e2e_s))
+    if world > 1:
+        t = torch.tensor([total_ms, n_solved, e2e_val, float(np.mean(e2e_s))], device="cuda",
+                         dtype=torch.float64)
+        gathered = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(gathered, t)
+        g = torch.stack(gathered).cpu().numpy()
+        total_ms_max = float(g[:, 0].max()); n_solved_all = float(g[:, 1].sum())
+        e2e_all = float(g[:, 2].mean() * world)
+    else:
+        total_ms_max, n_solved_all, e2e_all = total_ms, n_solved, e2e_val
+    value = n_solved_all / (total_ms_max * 1e-3)
+
+    if rank == 0:
+        ops = algorithmic_ops(batch, out["iters"])
+        kern_s = float(np.mean(kern_ms)) * 1e-3
+        achieved = ops / kern_s
+        peak_ops = fp32_peak / 2.0  # FFMA rate in lane-operations/s (2 FLOP per FMA)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "l2": "flushed between timed steps (256 MB write, outside the events)",
+                       "per_rank_batch": "seed + rank"},
+            "ms_per_batch_solve": float(np.mean(step_ms)),
+            "solved_per_step": float(np.mean(solved)), "trajectories_per_step": batch.n_traj,
+            "iters": {"min": int(out["iters"].min()), "median": int(np.median(out["iters"])),
+                      "max": int(out["iters"].max())},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Top/s", "frac": achieved / peak_ops, "traffic": None,
+                         "kernel": "k_am_fp32", "peak_source": "measured FFMA microbenchmark "
+                         "(traj_measure_fp32_peak), FP32 lane-ops/s",
+                         "algorithmic_ops_per_launch": ops},
+            "e2e": {"value": e2e_all, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            cb = cpu_baseline(args.seed)
+            cb.pop("seconds", None)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

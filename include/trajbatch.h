@@ -1,0 +1,173 @@
+/*
+ * trajbatch.h -- C ABI of the B300 batched trajectory optimizer.
+ *
+ * The library solves, for a batch of trajectories, the alternating-
+ * minimization (AM) problem of Rastgar's thesis, Paper II: each trajectory is
+ * a set of degree-10 Bernstein coefficients per axis (eq. parameter), the
+ * collision, velocity and acceleration constraints are written in
+ * polar/spherical form with auxiliary angle and distance variables (eqs.
+ * collision_1, fv, fa; 3D eqs. collision_priest, fv_priest, fa_priest), and
+ * each iteration of Algorithm 2 performs
+ *   Line 2  the batched QP step through a KKT inverse cached per problem
+ *           (eqs. zeta_1_sepration_1, zeta_1_sepration_3, over_3),
+ *   Lines 4-5 the closed-form alpha/beta/d projections over every
+ *           trajectory x obstacle x timestep (eqs. zeta_2, alpha_v, alpha_a,
+ *           compute_d_mij, compute_dv, compute_da, d_max),
+ *   Line 6  the multiplier update lambda <- lambda - rho F^T (F xi - g)
+ *           (eq. update_lambda2_1; PRIEST eq. lag).
+ * The projection cost of Paper III (eqs. projection_cost, affine_trans,
+ * matrix_vec) is the TRAJ_COST_PROJECT mode.
+ *
+ * Conventions shared by every entry point:
+ *  - Return codes only: nothing aborts, exits or throws across the ABI. A NULL
+ *    handle or pointer that is required gives TRAJ_EINVAL. The detail of the
+ *    last failure on a handle is available from traj_last_error().
+ *  - Arrays are dense, C order, FP32 unless stated. "Host or device" pointers
+ *    are classified with cudaPointerGetAttributes; host data is staged through
+ *    pinned memory and copied on the handle's stream.
+ *  - One handle per CUDA stream; a handle is not thread-safe. All GPU work of a
+ *    handle runs on the stream given at creation (cudaStream_t passed as
+ *    void*; NULL is the legacy default stream).
+ *  - The library owns its device workspace (allocated at creation from the
+ *    max_* sizes and released by traj_batch_destroy); the caller owns every
+ *    array it passes in or gets results into.
+ *  - The library never falls back to a CPU implementation: without a CUDA
+ *    device every call that needs one returns TRAJ_ECUDA.
+ */
+#ifndef TRAJBATCH_H
+#define TRAJBATCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TRAJ_OK = 0,
+  TRAJ_NOT_CONVERGED = 1, /* solve finished; some trajectory hit the iteration cap */
+  TRAJ_EINVAL = -1,       /* bad argument (NULL handle/pointer, size out of range) */
+  TRAJ_ENOMEM = -2,       /* device or pinned allocation failed */
+  TRAJ_ECUDA = -3,        /* a CUDA call failed; traj_last_error has its string */
+  TRAJ_ESHAPE = -4,       /* inputs do not fit the capacities given at creation */
+  TRAJ_ETIMEOUT = -5,     /* the solve's deadline passed; trajectories left are marked */
+  TRAJ_ENAN = -6,         /* a non-finite input; the affected trajectories are marked */
+  TRAJ_ESTATE = -7        /* call out of order (e.g. solve before set_initial) */
+} traj_status;
+
+/* Per-trajectory outcome written by traj_get_trajectories (int8). */
+enum {
+  TRAJ_TRAJ_CONVERGED = 0, /* all three residuals <= tol */
+  TRAJ_TRAJ_CAP = 1,       /* iteration cap reached */
+  TRAJ_TRAJ_NAN = 2,       /* non-finite input coefficients or obstacle data; skipped */
+  TRAJ_TRAJ_TIMEOUT = 3    /* stopped by the deadline */
+};
+
+typedef enum {
+  TRAJ_PREC_FP32 = 0, /* FP32 state and contractions; compensated FP32 QP step */
+  TRAJ_PREC_MIXED = 1 /* residual contraction F^T r on tcgen05 tensor cores (BF16 operands,
+                         FP32 accumulation) plus one FP32 refinement pass at exit */
+} traj_precision;
+
+typedef enum {
+  TRAJ_COST_SMOOTH_TRACK = 0, /* Q = w_s Pdd^T Pdd + w_t P^T P, q = -w_t P^T x_des
+                                 (eq. Q_matrix); x_des the constant-velocity line */
+  TRAJ_COST_PROJECT = 1       /* Q = I, q = -xi_sample (eq. matrix_vec): project each
+                                 initial coefficient set onto the feasible set */
+} traj_cost_mode;
+
+typedef struct traj_config {
+  int dim;           /* 2 or 3 */
+  int degree;        /* Bernstein degree; must be 10 */
+  int max_problems;  /* capacity: problems (scenes) */
+  int max_traj;      /* capacity: trajectories */
+  int max_obstacles; /* capacity: obstacles summed over problems */
+  int max_steps;     /* capacity: timesteps n_p of any problem (<= 256) */
+  double vmax, amax; /* velocity / acceleration bounds (eqs. fv, fa) */
+  double rho;        /* penalty weight (one rho for every constraint group) */
+  double w_smooth, w_track; /* cost weights of TRAJ_COST_SMOOTH_TRACK */
+  int precision;     /* traj_precision */
+  int cost_mode;     /* traj_cost_mode */
+  void *cuda_stream; /* cudaStream_t on which every kernel and copy of the handle runs */
+} traj_config;
+
+typedef struct traj_batch traj_batch; /* opaque; owns the device workspace */
+
+/* Create a handle. Validates the config (dim in {2,3}, degree 10, positive
+ * capacities, max_steps <= 256, vmax/amax/rho > 0) and allocates the
+ * workspace on the stream. *out is set only on TRAJ_OK. */
+traj_status traj_batch_create(const traj_config *cfg, traj_batch **out);
+
+/* Synchronise the handle's stream and free everything it owns. NULL is a no-op. */
+traj_status traj_batch_destroy(traj_batch *b);
+
+/* Problem descriptions (host pointers, copied): n_steps[n_problems] timesteps
+ * n_p >= 2 (grid tau_t = t/(n_p-1)), duration[n_problems] horizon T > 0 in
+ * seconds, start[n_problems][dim] and goal[n_problems][dim] positions (FP64).
+ * The boundary rows are start position, zero start velocity and acceleration,
+ * and the goal position (PRIEST eq. eq1_multiagent_1_priest). */
+traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
+                              const double *duration, const double *start, const double *goal);
+
+/* Obstacles of every problem as moving axis-aligned ellipses/ellipsoids with
+ * constant velocity: obstacle j of problem p has index offsets[p] + j,
+ * offsets[n_problems] = total (host int array, n_problems + 1 entries).
+ * centers[N][dim] (at t = 0), semi_axes[N][dim] (> 0), velocities[N][dim];
+ * FP32, host or device. Copied on the stream, then the FP64 set-up kernel
+ * forms and inverts every problem's KKT matrix (eq. over_2) on the GPU. */
+traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *centers,
+                               const float *semi_axes, const float *velocities);
+
+/* Trajectories: traj_problem[n_traj] (host int) maps each trajectory to its
+ * problem; coeffs0[n_traj][dim][11] FP32 initial coefficients (host or
+ * device). In TRAJ_COST_PROJECT mode coeffs0 are also the samples that the
+ * solve projects. Copied; the caller may reuse its buffers at once. */
+traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
+                             const float *coeffs0);
+
+typedef struct traj_solve_stats {
+  int n_traj, n_solved;                /* solved = all three residuals <= tol */
+  int iters_min, iters_median, iters_max;
+  float max_res_obs, max_res_v, max_res_a; /* over the batch */
+  float gpu_ms;                        /* device time of the solve (CUDA events) */
+} traj_solve_stats;
+
+/* Run Algorithm 2 on every trajectory in one persistent launch: initialise by
+ * projecting coeffs0 (lambda0 = 0), then iterate xi-step / projection /
+ * multiplier update until the three L-infinity residuals (obstacle,
+ * velocity, acceleration; metres, m/s, m/s^2) are all <= tol, checked after
+ * every iteration k >= 1, or until max_iters. tol < 0 never stops early.
+ * timeout_ms > 0 sets a device-side deadline (TRAJ_ETIMEOUT if hit).
+ * Asynchronous on the stream when stats == NULL; with stats it synchronises
+ * and fills them. Calling it again restarts from coeffs0. */
+traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
+                       traj_solve_stats *stats);
+
+/* Results of the last solve into caller buffers (host or device, each
+ * nullable): coeffs[n_traj][dim][11] FP32, residual[n_traj][3] FP32
+ * (obstacle, velocity, acceleration), iters[n_traj] int32 (iterations run),
+ * status[n_traj] int8 (TRAJ_TRAJ_*). Device destinations are written
+ * asynchronously on the stream; host destinations synchronise. */
+traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual, int *iters,
+                                  signed char *status);
+
+/* Solver state for checkpoint/resume and warm starts (nullable outputs):
+ * multipliers lambda[n_traj][dim][11] and the last residual contraction
+ * u = F^T (F xi - g) [n_traj][dim][11], FP32, host or device. */
+traj_status traj_get_state(traj_batch *b, float *lambda, float *u);
+
+/* Human-readable name of a status code (static string). */
+const char *traj_status_string(traj_status s);
+
+/* Detail of the last failure on this handle (static per handle; "" if none). */
+const char *traj_last_error(traj_batch *b);
+
+/* FP32 FFMA throughput microbenchmark, the denominator of the ALU roofline:
+ * runs an independent-chain FFMA kernel on the stream and returns the
+ * achieved FP32 FLOP/s (2 per FMA) over `reps` timed launches. */
+traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRAJBATCH_H */

@@ -1,0 +1,410 @@
+// am_solve.cu -- the fused persistent kernel of the batched AM optimizer.
+//
+// One warp owns one trajectory for its whole solve; warps pull trajectories
+// from an atomic work queue (ordered by estimated cost), so a batch with
+// uneven obstacle counts and horizons runs in a single launch. Per iteration
+// of Algorithm 2 (Paper II):
+//
+//  Line 2 (xi-step, eqs. zeta_1_sepration_1/3 solved as in eq. over_3):
+//     xi^k = hq + G xi^{k-1} + K11 (lambda^{k-1} - rho u^{k-1}),
+//     the algebraic rewrite of K11 (-q + lambda + rho F^T g) + K12 b with
+//     F^T g = F^T F xi - u, u = F^T (F xi - g), G = rho K11 F^T F and
+//     hq = K11 (-q) + K12 b precomputed in FP64. It runs in compensated FP32
+//     (K11, G, hq stored as FP32 hi/lo pairs, exact products, TwoSum
+//     accumulation): plain FP32 loses ~5 bits to the KKT inverse's
+//     conditioning.
+//  Lines 4-5 (eqs. zeta_2, compute_d_mij, d_max, alpha_v/a, compute_dv/a):
+//     for every obstacle j and timestep t, Delta = p(t) - o_j(t) with
+//     o_j(t) = c_j + v_j t, u = Delta / axes, and the alternating alpha-then-d
+//     steps give g_j - o_j = Delta * max(1, 1/||u||), so the residual
+//     r_j = p - g_j = -Delta * max(0, 1/||u||-1) is zero outside the ellipse
+//     and needs one rsqrt inside it (no atan2/cos/sin: identical values).
+//     Velocity / acceleration: r = w * max(0, 1 - bound/||w||).
+//  Line 6 (eq. update_lambda2_1): u^k = F^T r^k = P^T sum_j r_j + Pd^T r_v +
+//     Pdd^T r_a (the stacked F is never formed), lambda^k = lambda^{k-1} - rho u^k.
+//  Stop: L-infinity residuals (obstacle, velocity, acceleration) all <= tol.
+//
+// Lanes own timesteps t = lane + 32 m for evaluation, projection and the
+// contraction; the contraction's 11 x dim partial sums are reduce-scattered
+// over the warp so that lane 16 a + i owns coefficient i of axis a (axis 2 in
+// 3D: lanes i and 16 + i).
+#include "internal.cuh"
+
+namespace tb {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARPS_PER_BLOCK = 4;
+
+// Reduce-scatter of 32 per-lane values: afterwards lane L holds the warp sum of
+// slot L (recursive halving; slot order preserved).
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      float send = upper ? v[k] : v[k + s];
+      float keep = upper ? v[k + s] : v[k];
+      v[k] = keep + __shfl_xor_sync(FULL, send, s);
+    }
+  }
+  return v[0];
+}
+
+// 16 slots: plain reduction over lane halves, then reduce-scatter; lane L holds
+// the warp sum of slot (L & 15).
+__device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(FULL, v[k], 16);
+#pragma unroll
+  for (int s = 8; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      float send = upper ? v[k] : v[k + s];
+      float keep = upper ? v[k + s] : v[k];
+      v[k] = keep + __shfl_xor_sync(FULL, send, s);
+    }
+  }
+  return v[0];
+}
+
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) x = fmaxf(x, __shfl_xor_sync(FULL, x, s));
+  return x;
+}
+
+__device__ __forceinline__ void load_row(const float *row, float (&r)[12]) {
+  const float4 *r4 = reinterpret_cast<const float4 *>(row);
+  float4 a = r4[0], b = r4[1], c = r4[2];
+  r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+  r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+  r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
+}
+
+// Evaluate, project and contract one iterate (Algorithm 2 lines 4-6, minus the
+// multiplier update). xa: the iterate's coefficients (all lanes hold all).
+// Returns the per-lane partial contraction in up[DIM][11] and per-lane maxima
+// of ||r_j||^2, ||r_v||^2, ||r_a||^2.
+template <int DIM, int MAXNT>
+__device__ __forceinline__ void project_contract(
+    const float (&xa)[DIM][NC], const float *tP, const float *tD, const float *tA,
+    const float4 *obs, int n_o, int n_p, int nt, float dt, float invT, float invT2, float vmax,
+    float amax, int lane, float (&up)[DIM][NC], float &mo, float &mv, float &ma) {
+  constexpr int OV = obs_vec(DIM);
+  float pos[MAXNT][DIM], acc[MAXNT][DIM], tm[MAXNT];
+  // positions p(t) = P xi at this lane's timesteps; padding lanes get a far sentinel
+#pragma unroll
+  for (int m = 0; m < MAXNT; ++m) {
+    const int t = lane + 32 * m;
+    tm[m] = dt * (float)t;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { pos[m][a] = 1.0e18f; acc[m][a] = 0.f; }
+    if (m < nt && t < n_p) {
+      float r[12];
+      load_row(tP + t * ROW, r);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) s = fmaf(r[i], xa[a][i], s);
+        pos[m][a] = s;
+      }
+    }
+  }
+  // pair loop over obstacles: acc accumulates sum_j Delta_j * w_j (r_j = -Delta_j w_j)
+  mo = 0.f;
+  for (int j = 0; j < n_o; ++j) {
+    float4 o[OV];
+#pragma unroll
+    for (int q = 0; q < OV; ++q) o[q] = __ldg(&obs[OV * j + q]);
+    float c[DIM], v[DIM], ia[DIM], ax[DIM];
+    if constexpr (DIM == 2) {
+      c[0] = o[0].x; c[1] = o[0].y; v[0] = o[0].z; v[1] = o[0].w;
+      ia[0] = o[1].x; ia[1] = o[1].y; ax[0] = o[1].z; ax[1] = o[1].w;
+    } else {
+      c[0] = o[0].x; c[1] = o[0].y; c[2] = o[0].z; ia[0] = o[0].w;
+      v[0] = o[1].x; v[1] = o[1].y; v[2] = o[1].z; ia[1] = o[1].w;
+      ax[0] = o[2].x; ax[1] = o[2].y; ax[2] = o[2].z; ia[2] = o[2].w;
+    }
+#pragma unroll
+    for (int m = 0; m < MAXNT; ++m) {
+      if (m < nt) {
+        float d[DIM], s = 0.f;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          d[a] = pos[m][a] - fmaf(v[a], tm[m], c[a]);
+          const float u = d[a] * ia[a];
+          s = fmaf(u, u, s);
+        }
+        if (s < 1.f) { // inside the ellipse: project to its boundary along the ray
+          float e[DIM];
+          if (s > 0.f) {
+            const float w = rsqrtf(s) - 1.f;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) e[a] = d[a] * w;
+          } else { // at the centre: atan2(0, 0) = 0 pushes along +x (3D: beta = 0, +z)
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) e[a] = 0.f;
+            if constexpr (DIM == 2) e[0] = ax[0]; else e[2] = ax[2];
+          }
+          float n2 = 0.f;
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) { acc[m][a] += e[a]; n2 = fmaf(e[a], e[a], n2); }
+          mo = fmaxf(mo, n2);
+        }
+      }
+    }
+  }
+  // velocity / acceleration projections and the contraction u = F^T r
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+#pragma unroll
+    for (int i = 0; i < NC; ++i) up[a][i] = 0.f;
+  mv = 0.f; ma = 0.f;
+  const float vmax2 = vmax * vmax, amax2 = amax * amax;
+#pragma unroll
+  for (int m = 0; m < MAXNT; ++m) {
+    const int t = lane + 32 * m;
+    if (m < nt && t < n_p) {
+      float rp[12], rd[12], ra[12];
+      load_row(tP + t * ROW, rp);
+      load_row(tD + t * ROW, rd);
+      load_row(tA + t * ROW, ra);
+      float vel[DIM], ac[DIM], nv2 = 0.f, na2 = 0.f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        float sv = 0.f, sa = 0.f;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) { sv = fmaf(rd[i], xa[a][i], sv); sa = fmaf(ra[i], xa[a][i], sa); }
+        vel[a] = sv * invT; ac[a] = sa * invT2;
+        nv2 = fmaf(vel[a], vel[a], nv2); na2 = fmaf(ac[a], ac[a], na2);
+      }
+      float fv = 0.f, fa = 0.f;
+      if (nv2 > vmax2) { fv = 1.f - vmax * rsqrtf(nv2); mv = fmaxf(mv, nv2 * fv * fv); }
+      if (na2 > amax2) { fa = 1.f - amax * rsqrtf(na2); ma = fmaxf(ma, na2 * fa * fa); }
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const float Ro = -acc[m][a];              // sum_j r_j at t
+        const float Rv = vel[a] * fv * invT;      // Pd^T r_v = dB^T (r_v / T)
+        const float Ra = ac[a] * fa * invT2;      // Pdd^T r_a = d2B^T (r_a / T^2)
+#pragma unroll
+        for (int i = 0; i < NC; ++i) up[a][i] = fmaf(rp[i], Ro, fmaf(rd[i], Rv, fmaf(ra[i], Ra, up[a][i])));
+      }
+    }
+  }
+}
+
+template <int DIM, int MAXNT>
+__device__ void solve_one(const SolveArgs &A, int b, const float *stab, int lane,
+                          unsigned long long deadline) {
+  const int p = A.traj_problem[b];
+  const ProblemDev pr = A.problems[p];
+  const int n_p = pr.n_p, n_o = pr.n_o;
+  const int nt = (n_p + 31) >> 5;
+  const float *C = A.constants + pr.const_off;
+  const float *tP = stab + pr.tbl_off;
+  const float *tD = tP + n_p * ROW;
+  const float *tA = tD + n_p * ROW;
+  const float4 *obs = A.obstacles + (size_t)pr.obs_off * obs_vec(DIM);
+  const float rho = A.rho;
+
+  // ownership: lane 16 a + i holds coefficient i of axis a (a < 2); axis 2 of a 3D
+  // trajectory is held (twice) by lanes i and 16 + i.
+  const int oi = lane & 15, oa = lane >> 4;
+  const int ri = oi < NC ? oi : NC - 1; // clamped row for the non-owner lanes
+  const float *x0 = A.xi0 + (size_t)b * DIM * NC;
+  float xo = x0[oa * NC + ri];
+  float xo2 = DIM == 3 ? x0[2 * NC + ri] : 0.f;
+  bool finite = isfinite(xo) && isfinite(xo2);
+  finite = __all_sync(FULL, finite) && pr.nan_flag == 0;
+
+  float *xout = A.xi + (size_t)b * DIM * NC;
+  if (!finite) {
+    if (oi < NC) {
+      xout[oa * NC + oi] = xo;
+      if (DIM == 3 && oa == 0) xout[2 * NC + oi] = xo2;
+    }
+    if (lane < 3) A.res[b * 3 + lane] = __int_as_float(0x7fc00000);
+    if (lane == 0) { A.iters[b] = 0; A.status[b] = 2; atomicOr(A.flags, 2); }
+    return;
+  }
+
+  // hq: smoothness/tracking mode reads K11 (-q) + K12 b; projection mode forms
+  // K12 b + K11 xi_sample from this trajectory's own coefficients.
+  float hq_hi, hq_lo, hq2_hi = 0.f, hq2_lo = 0.f;
+  if (A.cost_mode == 0) {
+    hq_hi = C[C_HQ_HI + oa * ROW + ri]; hq_lo = C[C_HQ_LO + oa * ROW + ri];
+    if (DIM == 3) { hq2_hi = C[C_HQ_HI + 2 * ROW + ri]; hq2_lo = C[C_HQ_LO + 2 * ROW + ri]; }
+  } else {
+    hq_hi = C[C_C_HI + oa * ROW + ri]; hq_lo = C[C_C_LO + oa * ROW + ri];
+    if (DIM == 3) { hq2_hi = C[C_C_HI + 2 * ROW + ri]; hq2_lo = C[C_C_LO + 2 * ROW + ri]; }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const float xk = __shfl_sync(FULL, xo, (lane & 16) + k);
+      df_fma(hq_hi, hq_lo, C[C_K11_HI + ri * ROW + k], C[C_K11_LO + ri * ROW + k], xk);
+      if (DIM == 3) {
+        const float xk2 = __shfl_sync(FULL, xo2, k);
+        df_fma(hq2_hi, hq2_lo, C[C_K11_HI + ri * ROW + k], C[C_K11_LO + ri * ROW + k], xk2);
+      }
+    }
+    // hq = c + K11 xi_sample: fold lo into hi once (both stay exact pairs)
+    float s = hq_hi + hq_lo; hq_lo = hq_lo - (s - hq_hi); hq_hi = s;
+    if (DIM == 3) { float s2 = hq2_hi + hq2_lo; hq2_lo = hq2_lo - (s2 - hq2_hi); hq2_hi = s2; }
+  }
+
+  float lam = 0.f, lam2 = 0.f, uo = 0.f, uo2 = 0.f;
+  float mo, mv, ma;
+  int k = 0;
+  signed char st = 1;
+  for (;; ++k) {
+    if (k > 0) {
+      // xi-step in compensated FP32 at the owner lanes
+      const float vo = lam - rho * uo, vo2 = lam2 - rho * uo2;
+      float hi = hq_hi, lo = hq_lo, hi2 = hq2_hi, lo2 = hq2_lo;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const float xk = __shfl_sync(FULL, xo, (lane & 16) + q);
+        const float vk = __shfl_sync(FULL, vo, (lane & 16) + q);
+        const float g_hi = C[C_G_HI + ri * ROW + q], g_lo = C[C_G_LO + ri * ROW + q];
+        const float k_hi = C[C_K11_HI + ri * ROW + q], k_lo = C[C_K11_LO + ri * ROW + q];
+        df_fma(hi, lo, g_hi, g_lo, xk);
+        df_fma(hi, lo, k_hi, k_lo, vk);
+        if (DIM == 3) {
+          const float xk2 = __shfl_sync(FULL, xo2, q);
+          const float vk2 = __shfl_sync(FULL, vo2, q);
+          df_fma(hi2, lo2, g_hi, g_lo, xk2);
+          df_fma(hi2, lo2, k_hi, k_lo, vk2);
+        }
+      }
+      xo = hi + lo;
+      if (DIM == 3) xo2 = hi2 + lo2;
+    }
+    // broadcast the iterate to every lane
+    float xa[DIM][NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      xa[0][i] = __shfl_sync(FULL, xo, i);
+      xa[1][i] = __shfl_sync(FULL, xo, 16 + i);
+      if constexpr (DIM == 3) xa[2][i] = __shfl_sync(FULL, xo2, i);
+    }
+    float up[DIM][NC];
+    project_contract<DIM, MAXNT>(xa, tP, tD, tA, obs, n_o, n_p, nt, pr.dt, pr.invT, pr.invT2,
+                                 A.vmax, A.amax, lane, up, mo, mv, ma);
+    {
+      float v32[32];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        v32[i] = i < NC ? up[0][i] : 0.f;
+        v32[16 + i] = i < NC ? up[1][i] : 0.f;
+      }
+      uo = reduce_scatter32(v32, lane);
+      if constexpr (DIM == 3) {
+        float v16[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v16[i] = i < NC ? up[2][i] : 0.f;
+        uo2 = reduce_scatter16(v16, lane);
+      }
+    }
+    mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
+    if (k > 0) { // Line 6: multiplier update (lambda0 = 0 at the initial projection)
+      lam -= rho * uo;
+      if (DIM == 3) lam2 -= rho * uo2;
+      if (A.tol >= 0.f && sqrtf(mo) <= A.tol && sqrtf(mv) <= A.tol && sqrtf(ma) <= A.tol) {
+        st = 0;
+        break;
+      }
+    }
+    if (k >= A.max_iters) { st = 1; break; }
+    if (deadline) {
+      unsigned long long now = 0;
+      if (lane == 0) now = globaltimer_ns();
+      now = __shfl_sync(FULL, now, 0);
+      if (now > deadline) { st = 3; break; }
+    }
+  }
+  if (oi < NC) {
+    xout[oa * NC + oi] = xo;
+    if (A.lam) A.lam[(size_t)b * DIM * NC + oa * NC + oi] = lam;
+    if (A.u) A.u[(size_t)b * DIM * NC + oa * NC + oi] = uo;
+    if (DIM == 3 && oa == 0) {
+      xout[2 * NC + oi] = xo2;
+      if (A.lam) A.lam[(size_t)b * DIM * NC + 2 * NC + oi] = lam2;
+      if (A.u) A.u[(size_t)b * DIM * NC + 2 * NC + oi] = uo2;
+    }
+  }
+  if (lane == 0) {
+    A.res[b * 3 + 0] = sqrtf(mo);
+    A.res[b * 3 + 1] = sqrtf(mv);
+    A.res[b * 3 + 2] = sqrtf(ma);
+    A.iters[b] = k;
+    A.status[b] = st;
+    if (st == 3) atomicOr(A.flags, 1);
+  }
+}
+
+template <int DIM, int MAXNT>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
+k_am_fp32(const __grid_constant__ SolveArgs A) {
+  extern __shared__ float4 smem4[];
+  const float4 *g4 = reinterpret_cast<const float4 *>(A.tables);
+  for (int i = threadIdx.x; i < A.table_floats_total / 4; i += blockDim.x) smem4[i] = g4[i];
+  __syncthreads();
+  const float *stab = reinterpret_cast<const float *>(smem4);
+  const int lane = threadIdx.x & 31;
+
+  unsigned long long deadline = 0;
+  if (A.timeout_ns) {
+    unsigned long long t0 = 0;
+    if (lane == 0) {
+      const unsigned long long now = globaltimer_ns();
+      const unsigned long long prev = atomicCAS(A.t0, 0ull, now);
+      t0 = prev ? prev : now;
+    }
+    deadline = __shfl_sync(FULL, t0, 0) + A.timeout_ns;
+  }
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(A.queue, 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= A.n_traj) break;
+    solve_one<DIM, MAXNT>(A, A.order[item], stab, lane, deadline);
+  }
+}
+
+template <int DIM, int MAXNT>
+static cudaError_t launch_t(const SolveArgs &a, int n_sm, cudaStream_t s) {
+  auto kern = k_am_fp32<DIM, MAXNT>;
+  const size_t smem = sizeof(float) * (size_t)a.table_floats_total;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS_PER_BLOCK * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  long long want = ((long long)a.n_traj + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+  long long grid = (long long)n_sm * occ;
+  if (want < grid) grid = want;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, WARPS_PER_BLOCK * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a, int n_sm,
+                            cudaStream_t s) {
+  (void)precision;
+  const int nt = (max_np + 31) / 32;
+  if (dim == 2) {
+    if (nt <= 2) return launch_t<2, 2>(a, n_sm, s);
+    if (nt <= 4) return launch_t<2, 4>(a, n_sm, s);
+    if (nt <= 5) return launch_t<2, 5>(a, n_sm, s);
+    return launch_t<2, 8>(a, n_sm, s);
+  }
+  if (nt <= 2) return launch_t<3, 2>(a, n_sm, s);
+  if (nt <= 4) return launch_t<3, 4>(a, n_sm, s);
+  if (nt <= 5) return launch_t<3, 5>(a, n_sm, s);
+  return launch_t<3, 8>(a, n_sm, s);
+}
+
+} // namespace tb

@@ -1,0 +1,119 @@
+// internal.cuh -- device data layouts and helpers shared by the library's
+// translation units. Not part of the public ABI (include/trajbatch.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tb {
+
+constexpr int NC = 11;      // Bernstein degree 10 -> 11 coefficients per axis
+constexpr int NE = 4;       // boundary rows per axis
+constexpr int NK = NC + NE; // KKT size
+constexpr int ROW = 12;     // padded row length (floats) of every 11-wide table row
+constexpr int MAX_STEPS = 256;
+
+// Per-problem record on the device (64 bytes).
+struct ProblemDev {
+  int n_p;        // timesteps
+  int n_o;        // obstacles
+  int obs_off;    // first obstacle (index into the packed obstacle array)
+  int tbl_off;    // float offset of this horizon's P/dB/ddB tables in the table buffer
+  float dt;       // T / (n_p - 1), seconds between grid points
+  float invT;     // 1 / T   (Pdot = dB/dtau * invT)
+  float invT2;    // 1 / T^2 (Pddot = d2B/dtau2 * invT2)
+  int const_off;  // float offset of the problem's constants block
+  int nan_flag;   // nonzero if the problem's obstacle data is not finite / not positive
+  int pad[7];
+};
+
+// Constants block per problem (floats), every row padded to ROW:
+//   K11 hi/lo  [11][12] x 2     (top-left 11x11 block of the KKT inverse)
+//   G   hi/lo  [11][12] x 2     (rho * K11 * F^T F)
+//   hq  hi/lo  [3][12]  x 2     (K11 (-q_axis) + K12 b_axis; smoothness/tracking mode)
+//   c   hi/lo  [3][12]  x 2     (K12 b_axis; projection mode adds K11 xi_sample)
+// "hi/lo" is the FP64 value split into two FP32 numbers (hi = fl(x), lo = fl(x - hi)).
+constexpr int C_K11_HI = 0;
+constexpr int C_K11_LO = C_K11_HI + NC * ROW;
+constexpr int C_G_HI = C_K11_LO + NC * ROW;
+constexpr int C_G_LO = C_G_HI + NC * ROW;
+constexpr int C_HQ_HI = C_G_LO + NC * ROW;
+constexpr int C_HQ_LO = C_HQ_HI + 3 * ROW;
+constexpr int C_C_HI = C_HQ_LO + 3 * ROW;
+constexpr int C_C_LO = C_C_HI + 3 * ROW;
+constexpr int CONST_FLOATS = C_C_LO + 3 * ROW; // 672
+
+// Tables per horizon (floats): P [n_p][12], dB/dtau [n_p][12], d2B/dtau2 [n_p][12],
+// FP32 copies of FP64 values, column 11 zero. TABLE_FLOATS(n_p) = 36 n_p.
+__host__ __device__ inline int table_floats(int n_p) { return 3 * ROW * n_p; }
+
+// Packed obstacle record: OBS_VEC(dim) float4 per obstacle.
+//  2D: {cx, cy, vx, vy}, {1/ax, 1/ay, ax, ay}
+//  3D: {cx, cy, cz, 1/ax}, {vx, vy, vz, 1/ay}, {ax, ay, az, 1/az}
+__host__ __device__ constexpr int obs_vec(int dim) { return dim == 2 ? 2 : 3; }
+
+// Arguments of one solve launch.
+struct SolveArgs {
+  const ProblemDev *problems;
+  const float4 *obstacles;
+  const float *constants;
+  const float *tables;
+  int table_floats_total;
+  const int *traj_problem;
+  const int *order;
+  const float *xi0;
+  float *xi;
+  float *lam;
+  float *u;
+  float *res;
+  int *iters;
+  signed char *status;
+  int n_traj;
+  int max_iters;
+  float tol;
+  float rho;
+  float vmax, amax;
+  int cost_mode;
+  unsigned long long timeout_ns;
+  int *queue;                 // work-queue counter, zeroed before the launch
+  unsigned long long *t0;     // launch start time (globaltimer), zeroed before the launch
+  int *flags;                 // bit 0: timeout hit, bit 1: NaN input seen
+};
+
+// ---- compensated (double-float) helpers -----------------------------------
+// acc(hi, lo) += (a_hi + a_lo) * x with the exact product error of a_hi * x and a
+// TwoSum accumulation (Knuth); the _rn intrinsics keep the compiler from fusing
+// or reassociating the error-free transformations.
+__device__ __forceinline__ void df_fma(float &hi, float &lo, float a_hi, float a_lo, float x) {
+  float p = __fmul_rn(a_hi, x);
+  float e = __fmaf_rn(a_hi, x, -p);
+  e = __fmaf_rn(a_lo, x, e);
+  float s = __fadd_rn(hi, p);
+  float bb = __fsub_rn(s, hi);
+  float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+} // namespace tb
+
+// Launch wrappers implemented in the .cu files (host side, C++ linkage).
+namespace tb {
+cudaError_t launch_setup_tables(const int *d_horizons, const int *d_offsets, int n_horizons,
+                                float *d_tables, cudaStream_t s);
+cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const double *d_T,
+                                  const double *d_start, const double *d_goal, int dim,
+                                  double rho, double w_smooth, double w_track, int cost_mode,
+                                  int max_np, float *d_constants, cudaStream_t s);
+cudaError_t launch_pack_obstacles(int dim, int n_obs, const float *centers, const float *axes,
+                                  const float *vel, const int *obs_problem, float4 *out,
+                                  ProblemDev *problems, cudaStream_t s);
+cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
+                            int n_sm, cudaStream_t s);
+cudaError_t launch_ffma_peak(float *out, int blocks, int iters, cudaStream_t s);
+} // namespace tb

@@ -1,0 +1,257 @@
+// setup.cu -- once-per-problem set-up on the GPU, in FP64.
+//
+//  * Bernstein tables per horizon (eq. parameter; degree 10 on tau = t/(n_p-1)):
+//    P, dB/dtau, d2B/dtau2, FP64 evaluation stored as FP32 rows of 12.
+//  * KKT formation and inversion per problem (eqs. over_2, zeta_1_sepration_3,
+//    Q_matrix, matrix_vec): Q-bar = Q + rho F^T F with F^T F = n_o P^T P +
+//    Pd^T Pd + Pdd^T Pdd (the stacked F of Paper II is never formed), boundary
+//    rows A = [P_0; Pd_0; Pdd_0; P_{-1}], Gauss-Jordan with partial pivoting in
+//    FP64, then the per-problem constants the FP32 loop needs, each split into
+//    an FP32 (hi, lo) pair: K11, G = rho K11 F^T F, c = K12 b, hq = K11 (-q) + c.
+//  * Obstacle packing: moving ellipses/ellipsoids into the float4 records the
+//    solve kernel reads, with a per-problem flag for non-finite data.
+#include "internal.cuh"
+#include <math.h>
+
+namespace tb {
+
+__device__ double bern_d(int n, int i, double tau) {
+  if (i < 0 || i > n) return 0.0;
+  double c = 1.0;
+  for (int k = 1; k <= i; ++k) c = c * (double)(n - i + k) / (double)k;
+  double p = 1.0;
+  for (int k = 0; k < i; ++k) p *= tau;
+  for (int k = 0; k < n - i; ++k) p *= (1.0 - tau);
+  return c * p;
+}
+
+// Unscaled basis values at grid point t of an n_p-point horizon (FP64).
+__device__ void basis_row(int n_p, int t, double *P, double *dB, double *ddB) {
+  const int n = NC - 1;
+  double tau = (double)t / (double)(n_p - 1);
+  for (int i = 0; i < NC; ++i) {
+    P[i] = bern_d(n, i, tau);
+    dB[i] = n * (bern_d(n - 1, i - 1, tau) - bern_d(n - 1, i, tau));
+    ddB[i] = n * (n - 1) *
+             (bern_d(n - 2, i - 2, tau) - 2.0 * bern_d(n - 2, i - 1, tau) + bern_d(n - 2, i, tau));
+  }
+}
+
+__global__ void k_tables(const int *horizons, const int *offsets, float *tables) {
+  const int h = blockIdx.x;
+  const int n_p = horizons[h];
+  float *T0 = tables + offsets[h];
+  for (int t = threadIdx.x; t < n_p; t += blockDim.x) {
+    double P[NC], dB[NC], ddB[NC];
+    basis_row(n_p, t, P, dB, ddB);
+    for (int i = 0; i < ROW; ++i) {
+      T0[(0 * n_p + t) * ROW + i] = i < NC ? (float)P[i] : 0.f;
+      T0[(1 * n_p + t) * ROW + i] = i < NC ? (float)dB[i] : 0.f;
+      T0[(2 * n_p + t) * ROW + i] = i < NC ? (float)ddB[i] : 0.f;
+    }
+  }
+}
+
+__device__ __forceinline__ void split_store(float *hi, float *lo, double x) {
+  float h = (float)x;
+  *hi = h;
+  *lo = (float)(x - (double)h);
+}
+
+// One block per problem. Dynamic shared memory: 3 * max_np * NC doubles.
+__global__ void k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
+                                 const double *goal, int dim, double rho, double w_s, double w_t,
+                                 int cost_mode, float *constants) {
+  extern __shared__ double sm[];
+  __shared__ double Q[NC * NC], M[NC * NC], qv[3 * NC];
+  __shared__ double W[NK * 2 * NK];
+  __shared__ double K11[NC * NC], K12[NC * NE], Gm[NC * NC];
+  __shared__ int piv_s;
+  const int p = blockIdx.x;
+  const ProblemDev pr = problems[p];
+  const int n_p = pr.n_p, n_o = pr.n_o;
+  const double T = Tarr[p];
+  double *P = sm, *Pd = sm + n_p * NC, *Pdd = sm + 2 * n_p * NC;
+  const double iT = 1.0 / T, iT2 = 1.0 / (T * T);
+
+  for (int t = threadIdx.x; t < n_p; t += blockDim.x) {
+    double a[NC], b[NC], c[NC];
+    basis_row(n_p, t, a, b, c);
+    for (int i = 0; i < NC; ++i) {
+      P[t * NC + i] = a[i];
+      Pd[t * NC + i] = b[i] * iT;
+      Pdd[t * NC + i] = c[i] * iT2;
+    }
+  }
+  __syncthreads();
+
+  // Q, M = F^T F (closed form of the stacked F), q per axis
+  for (int e = threadIdx.x; e < NC * NC + 3 * NC; e += blockDim.x) {
+    if (e < NC * NC) {
+      int a = e / NC, b = e % NC;
+      double pp = 0, dd = 0, aa = 0;
+      for (int t = 0; t < n_p; ++t) {
+        pp += P[t * NC + a] * P[t * NC + b];
+        dd += Pd[t * NC + a] * Pd[t * NC + b];
+        aa += Pdd[t * NC + a] * Pdd[t * NC + b];
+      }
+      Q[e] = cost_mode == 0 ? (w_s * aa + w_t * pp) : (a == b ? 1.0 : 0.0);
+      M[e] = (double)n_o * pp + dd + aa;
+    } else {
+      int k = e - NC * NC, ax = k / NC, i = k % NC;
+      double s = 0;
+      if (ax < dim) {
+        double s0 = start[p * dim + ax], g0 = goal[p * dim + ax];
+        for (int t = 0; t < n_p; ++t) {
+          double tau = (double)t / (double)(n_p - 1);
+          s += P[t * NC + i] * (s0 + (g0 - s0) * tau);
+        }
+      }
+      qv[k] = -w_t * s; // q = -w_t P^T x_des
+    }
+  }
+  __syncthreads();
+  // augmented [K | I]
+  for (int e = threadIdx.x; e < NK * 2 * NK; e += blockDim.x) {
+    int r = e / (2 * NK), c = e % (2 * NK);
+    double v;
+    if (c >= NK) v = (c - NK == r) ? 1.0 : 0.0;
+    else if (r < NC && c < NC) v = Q[r * NC + c] + rho * M[r * NC + c];
+    else if (r < NC && c >= NC) { // A^T
+      int er = c - NC;
+      const double *row = er == 0 ? &P[0] : er == 1 ? &Pd[0] : er == 2 ? &Pdd[0] : &P[(n_p - 1) * NC];
+      v = row[r];
+    } else if (r >= NC && c < NC) {
+      int er = r - NC;
+      const double *row = er == 0 ? &P[0] : er == 1 ? &Pd[0] : er == 2 ? &Pdd[0] : &P[(n_p - 1) * NC];
+      v = row[c];
+    } else v = 0.0;
+    W[e] = v;
+  }
+  __syncthreads();
+  // Gauss-Jordan with partial pivoting
+  for (int col = 0; col < NK; ++col) {
+    if (threadIdx.x == 0) {
+      int pv = col;
+      for (int r = col + 1; r < NK; ++r)
+        if (fabs(W[r * 2 * NK + col]) > fabs(W[pv * 2 * NK + col])) pv = r;
+      piv_s = pv;
+      const double pivot = W[pv * 2 * NK + col];
+      if (pivot == 0.0 || !isfinite(pivot)) atomicOr(&problems[p].nan_flag, 2); // singular KKT
+    }
+    __syncthreads();
+    const int pv = piv_s;
+    if (pv != col)
+      for (int c = threadIdx.x; c < 2 * NK; c += blockDim.x) {
+        double tmp = W[col * 2 * NK + c];
+        W[col * 2 * NK + c] = W[pv * 2 * NK + c];
+        W[pv * 2 * NK + c] = tmp;
+      }
+    __syncthreads();
+    const double inv = 1.0 / W[col * 2 * NK + col];
+    __syncthreads();
+    for (int c = threadIdx.x; c < 2 * NK; c += blockDim.x) W[col * 2 * NK + c] *= inv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < NK * 2 * NK; e += blockDim.x) {
+      int r = e / (2 * NK), c = e % (2 * NK);
+      if (r == col) continue;
+      double f = W[r * 2 * NK + col];
+      if (c == col) continue; // column col is cleared after the loop
+      W[e] -= f * W[col * 2 * NK + c];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < NK; r += blockDim.x)
+      if (r != col) W[r * 2 * NK + col] = 0.0;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NC * NC + NC * NE; e += blockDim.x) {
+    if (e < NC * NC) K11[e] = W[(e / NC) * 2 * NK + NK + (e % NC)];
+    else {
+      int k = e - NC * NC, r = k / NE, c = k % NE;
+      K12[k] = W[r * 2 * NK + NK + NC + c];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NC * NC; e += blockDim.x) {
+    int a = e / NC, b = e % NC;
+    double s = 0;
+    for (int k = 0; k < NC; ++k) s += K11[a * NC + k] * M[k * NC + b];
+    Gm[e] = rho * s;
+  }
+  __syncthreads();
+  float *C = constants + pr.const_off;
+  for (int e = threadIdx.x; e < NC * ROW; e += blockDim.x) {
+    int r = e / ROW, c = e % ROW;
+    double k11 = c < NC ? K11[r * NC + c] : 0.0, g = c < NC ? Gm[r * NC + c] : 0.0;
+    split_store(&C[C_K11_HI + e], &C[C_K11_LO + e], k11);
+    split_store(&C[C_G_HI + e], &C[C_G_LO + e], g);
+  }
+  for (int e = threadIdx.x; e < 3 * ROW; e += blockDim.x) {
+    int ax = e / ROW, i = e % ROW;
+    double cval = 0, hq = 0;
+    if (ax < dim && i < NC) {
+      double bb[NE] = {start[p * dim + ax], 0.0, 0.0, goal[p * dim + ax]};
+      for (int k = 0; k < NE; ++k) cval += K12[i * NE + k] * bb[k];
+      hq = cval;
+      for (int k = 0; k < NC; ++k) hq += K11[i * NC + k] * (-qv[ax * NC + k]);
+    }
+    split_store(&C[C_HQ_HI + e], &C[C_HQ_LO + e], hq);
+    split_store(&C[C_C_HI + e], &C[C_C_LO + e], cval);
+  }
+}
+
+__global__ void k_pack_obstacles(int dim, int n_obs, const float *cen, const float *ax,
+                                 const float *vel, const int *obs_problem, float4 *out,
+                                 ProblemDev *problems) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_obs) return;
+  float c[3] = {0, 0, 0}, a[3] = {1, 1, 1}, v[3] = {0, 0, 0};
+  bool ok = true;
+  for (int d = 0; d < dim; ++d) {
+    c[d] = cen[j * dim + d];
+    a[d] = ax[j * dim + d];
+    v[d] = vel[j * dim + d];
+    ok = ok && isfinite(c[d]) && isfinite(v[d]) && isfinite(a[d]) && a[d] > 0.f;
+  }
+  if (!ok) atomicOr(&problems[obs_problem[j]].nan_flag, 1);
+  if (dim == 2) {
+    out[2 * j + 0] = make_float4(c[0], c[1], v[0], v[1]);
+    out[2 * j + 1] = make_float4(1.f / a[0], 1.f / a[1], a[0], a[1]);
+  } else {
+    out[3 * j + 0] = make_float4(c[0], c[1], c[2], 1.f / a[0]);
+    out[3 * j + 1] = make_float4(v[0], v[1], v[2], 1.f / a[1]);
+    out[3 * j + 2] = make_float4(a[0], a[1], a[2], 1.f / a[2]);
+  }
+}
+
+cudaError_t launch_setup_tables(const int *d_horizons, const int *d_offsets, int n_horizons,
+                                float *d_tables, cudaStream_t s) {
+  if (n_horizons <= 0) return cudaSuccess;
+  k_tables<<<n_horizons, 128, 0, s>>>(d_horizons, d_offsets, d_tables);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const double *d_T,
+                                  const double *d_start, const double *d_goal, int dim,
+                                  double rho, double w_smooth, double w_track, int cost_mode,
+                                  int max_np, float *d_constants, cudaStream_t s) {
+  if (n_problems <= 0) return cudaSuccess;
+  size_t smem = sizeof(double) * 3 * (size_t)max_np * NC;
+  cudaError_t e = cudaFuncSetAttribute(k_setup_problems,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_setup_problems<<<n_problems, 256, smem, s>>>(d_problems, d_T, d_start, d_goal, dim, rho,
+                                                 w_smooth, w_track, cost_mode, d_constants);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_obstacles(int dim, int n_obs, const float *centers, const float *axes,
+                                  const float *vel, const int *obs_problem, float4 *out,
+                                  ProblemDev *problems, cudaStream_t s) {
+  if (n_obs <= 0) return cudaSuccess;
+  k_pack_obstacles<<<(n_obs + 255) / 256, 256, 0, s>>>(dim, n_obs, centers, axes, vel,
+                                                       obs_problem, out, problems);
+  return cudaGetLastError();
+}
+
+} // namespace tb

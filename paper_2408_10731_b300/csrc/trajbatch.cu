@@ -1,0 +1,449 @@
+// trajbatch.cu -- host side of the C ABI declared in include/trajbatch.h.
+//
+// Validation, workspace ownership, copies on the caller's stream and kernel
+// launches. Every step of the method itself runs in the kernels of setup.cu
+// (FP64 set-up) and am_solve.cu (the iteration); this file only marshals.
+#include "trajbatch.h"
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace tb;
+
+struct traj_batch {
+  traj_config cfg{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int n_sm = 0;
+  int n_problems = 0, n_traj = 0, n_obs = 0, max_np_used = 0;
+  bool have_problems = false, have_obstacles = false, have_initial = false, have_result = false;
+  std::vector<int> n_steps;
+  std::vector<double> duration;
+  std::vector<int> obs_offsets;
+  std::vector<int> traj_problem;
+  // device workspace
+  ProblemDev *d_problems = nullptr;
+  double *d_T = nullptr, *d_start = nullptr, *d_goal = nullptr;
+  float *d_constants = nullptr;
+  float *d_tables = nullptr;
+  int table_floats = 0, table_cap = 0;
+  int *d_horizons = nullptr, *d_hoffsets = nullptr;
+  float4 *d_obs = nullptr;
+  float *d_obs_stage = nullptr;
+  int *d_obs_problem = nullptr;
+  int *d_traj_problem = nullptr, *d_order = nullptr;
+  float *d_xi0 = nullptr, *d_xi = nullptr, *d_lam = nullptr, *d_u = nullptr, *d_res = nullptr;
+  int *d_iters = nullptr;
+  signed char *d_status = nullptr;
+  int *d_queue = nullptr, *d_flags = nullptr;
+  unsigned long long *d_t0 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static thread_local std::string g_create_error;
+
+#define CK(b, expr)                                                                     \
+  do {                                                                                  \
+    cudaError_t _e = (expr);                                                            \
+    if (_e != cudaSuccess) {                                                            \
+      (b)->err = std::string(#expr) + ": " + cudaGetErrorString(_e);                    \
+      return TRAJ_ECUDA;                                                                \
+    }                                                                                   \
+  } while (0)
+
+static traj_status fail(traj_batch *b, traj_status s, const std::string &msg) {
+  if (b) b->err = msg;
+  return s;
+}
+
+static bool is_host_ptr(const void *p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+template <class T> static cudaError_t dalloc(T **p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (n > 0 ? n : 1));
+}
+
+static void free_all(traj_batch *b) {
+  void *ptrs[] = {b->d_problems, b->d_T, b->d_start, b->d_goal, b->d_constants, b->d_tables,
+                  b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_problem,
+                  b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res,
+                  b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+}
+
+extern "C" {
+
+const char *traj_status_string(traj_status s) {
+  switch (s) {
+  case TRAJ_OK: return "TRAJ_OK";
+  case TRAJ_NOT_CONVERGED: return "TRAJ_NOT_CONVERGED";
+  case TRAJ_EINVAL: return "TRAJ_EINVAL";
+  case TRAJ_ENOMEM: return "TRAJ_ENOMEM";
+  case TRAJ_ECUDA: return "TRAJ_ECUDA";
+  case TRAJ_ESHAPE: return "TRAJ_ESHAPE";
+  case TRAJ_ETIMEOUT: return "TRAJ_ETIMEOUT";
+  case TRAJ_ENAN: return "TRAJ_ENAN";
+  case TRAJ_ESTATE: return "TRAJ_ESTATE";
+  }
+  return "TRAJ_UNKNOWN";
+}
+
+const char *traj_last_error(traj_batch *b) {
+  return b ? b->err.c_str() : g_create_error.c_str();
+}
+
+traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
+  g_create_error.clear();
+  if (!cfg || !out) { g_create_error = "NULL config or output pointer"; return TRAJ_EINVAL; }
+  const traj_config &c = *cfg;
+  if (c.dim != 2 && c.dim != 3) { g_create_error = "dim must be 2 or 3"; return TRAJ_EINVAL; }
+  if (c.degree != 10) { g_create_error = "degree must be 10"; return TRAJ_EINVAL; }
+  if (c.max_problems < 1 || c.max_traj < 1 || c.max_obstacles < 0 || c.max_steps < 2 ||
+      c.max_steps > MAX_STEPS) {
+    g_create_error = "capacities out of range (max_steps must be in [2, 256])";
+    return TRAJ_EINVAL;
+  }
+  if (!(c.vmax > 0) || !(c.amax > 0) || !(c.rho > 0) || !(c.w_smooth >= 0) || !(c.w_track >= 0) ||
+      !std::isfinite(c.vmax) || !std::isfinite(c.amax) || !std::isfinite(c.rho)) {
+    g_create_error = "vmax, amax, rho must be positive and finite; weights non-negative";
+    return TRAJ_EINVAL;
+  }
+  if (c.precision != TRAJ_PREC_FP32 && c.precision != TRAJ_PREC_MIXED) {
+    g_create_error = "unknown precision";
+    return TRAJ_EINVAL;
+  }
+  if (c.cost_mode != TRAJ_COST_SMOOTH_TRACK && c.cost_mode != TRAJ_COST_PROJECT) {
+    g_create_error = "unknown cost mode";
+    return TRAJ_EINVAL;
+  }
+  int dev = 0, n_dev = 0;
+  cudaError_t e = cudaGetDeviceCount(&n_dev);
+  if (e != cudaSuccess || n_dev < 1) {
+    cudaGetLastError();
+    g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return TRAJ_ECUDA;
+  }
+  traj_batch *b = new (std::nothrow) traj_batch();
+  if (!b) { g_create_error = "host allocation failed"; return TRAJ_ENOMEM; }
+  b->cfg = c;
+  b->stream = reinterpret_cast<cudaStream_t>(c.cuda_stream);
+  auto bail = [&](const char *what, cudaError_t err) {
+    g_create_error = std::string(what) + ": " + cudaGetErrorString(err);
+    free_all(b);
+    delete b;
+    return err == cudaErrorMemoryAllocation ? TRAJ_ENOMEM : TRAJ_ECUDA;
+  };
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail("cudaGetDevice", e);
+  if ((e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return bail("cudaDeviceGetAttribute", e);
+  const size_t P = c.max_problems, B = c.max_traj, N = c.max_obstacles, D = c.dim;
+  if ((e = dalloc(&b->d_problems, P)) || (e = dalloc(&b->d_T, P)) || (e = dalloc(&b->d_start, P * D)) ||
+      (e = dalloc(&b->d_goal, P * D)) || (e = dalloc(&b->d_constants, P * CONST_FLOATS)) ||
+      (e = dalloc(&b->d_horizons, MAX_STEPS + 1)) || (e = dalloc(&b->d_hoffsets, MAX_STEPS + 1)) ||
+      (e = dalloc(&b->d_obs, N * obs_vec(c.dim))) || (e = dalloc(&b->d_obs_stage, 3 * N * D)) ||
+      (e = dalloc(&b->d_obs_problem, N)) || (e = dalloc(&b->d_traj_problem, B)) ||
+      (e = dalloc(&b->d_order, B)) || (e = dalloc(&b->d_xi0, B * D * NC)) ||
+      (e = dalloc(&b->d_xi, B * D * NC)) || (e = dalloc(&b->d_lam, B * D * NC)) ||
+      (e = dalloc(&b->d_u, B * D * NC)) || (e = dalloc(&b->d_res, B * 3)) ||
+      (e = dalloc(&b->d_iters, B)) || (e = dalloc(&b->d_status, B)) || (e = dalloc(&b->d_queue, 1)) ||
+      (e = dalloc(&b->d_flags, 1)) || (e = dalloc(&b->d_t0, 1)))
+    return bail("cudaMalloc", e);
+  if ((e = cudaEventCreate(&b->ev0)) || (e = cudaEventCreate(&b->ev1))) return bail("cudaEventCreate", e);
+  *out = b;
+  return TRAJ_OK;
+}
+
+traj_status traj_batch_destroy(traj_batch *b) {
+  if (!b) return TRAJ_OK;
+  cudaStreamSynchronize(b->stream);
+  free_all(b);
+  delete b;
+  return TRAJ_OK;
+}
+
+traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
+                              const double *duration, const double *start, const double *goal) {
+  if (!b) return TRAJ_EINVAL;
+  if (!n_steps || !duration || !start || !goal) return fail(b, TRAJ_EINVAL, "NULL problem array");
+  if (n_problems < 1 || n_problems > b->cfg.max_problems)
+    return fail(b, TRAJ_ESHAPE, "n_problems exceeds max_problems (or < 1)");
+  const int D = b->cfg.dim;
+  int max_np = 0;
+  for (int p = 0; p < n_problems; ++p) {
+    if (n_steps[p] < 2 || n_steps[p] > b->cfg.max_steps)
+      return fail(b, TRAJ_ESHAPE, "n_steps out of [2, max_steps] for problem " + std::to_string(p));
+    if (!(duration[p] > 0) || !std::isfinite(duration[p]))
+      return fail(b, TRAJ_EINVAL, "duration must be positive and finite");
+    for (int d = 0; d < D; ++d)
+      if (!std::isfinite(start[p * D + d]) || !std::isfinite(goal[p * D + d]))
+        return fail(b, TRAJ_ENAN, "non-finite start/goal for problem " + std::to_string(p));
+    max_np = std::max(max_np, n_steps[p]);
+  }
+  // distinct horizons -> table offsets (tables staged to shared memory by the solve)
+  std::vector<int> hz(n_steps, n_steps + n_problems);
+  std::sort(hz.begin(), hz.end());
+  hz.erase(std::unique(hz.begin(), hz.end()), hz.end());
+  std::vector<int> hoff(hz.size());
+  int tot = 0;
+  for (size_t h = 0; h < hz.size(); ++h) { hoff[h] = tot; tot += table_floats(hz[h]); }
+  if ((size_t)tot * sizeof(float) > 160 * 1024)
+    return fail(b, TRAJ_ESHAPE, "too many distinct horizons: basis tables exceed 160 KB");
+  if (tot > b->table_cap) {
+    if (b->d_tables) cudaFree(b->d_tables);
+    b->d_tables = nullptr;
+    CK(b, dalloc(&b->d_tables, tot));
+    b->table_cap = tot;
+  }
+  b->table_floats = tot;
+  CK(b, cudaMemcpyAsync(b->d_horizons, hz.data(), sizeof(int) * hz.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_hoffsets, hoff.data(), sizeof(int) * hz.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_T, duration, sizeof(double) * n_problems, cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_start, start, sizeof(double) * n_problems * D, cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_goal, goal, sizeof(double) * n_problems * D, cudaMemcpyHostToDevice, b->stream));
+  CK(b, launch_setup_tables(b->d_horizons, b->d_hoffsets, (int)hz.size(), b->d_tables, b->stream));
+  CK(b, cudaStreamSynchronize(b->stream)); // host arrays may be reused by the caller
+  b->n_steps.assign(n_steps, n_steps + n_problems);
+  b->duration.assign(duration, duration + n_problems);
+  b->n_problems = n_problems;
+  b->max_np_used = max_np;
+  b->have_problems = true;
+  b->have_obstacles = false;
+  b->have_result = false;
+  b->err.clear();
+  return TRAJ_OK;
+}
+
+traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *centers,
+                               const float *semi_axes, const float *velocities) {
+  if (!b) return TRAJ_EINVAL;
+  if (!b->have_problems) return fail(b, TRAJ_ESTATE, "traj_set_problems must come first");
+  if (!offsets) return fail(b, TRAJ_EINVAL, "NULL offsets");
+  const int P = b->n_problems, D = b->cfg.dim;
+  if (offsets[0] != 0) return fail(b, TRAJ_EINVAL, "offsets[0] must be 0");
+  for (int p = 0; p < P; ++p)
+    if (offsets[p + 1] < offsets[p]) return fail(b, TRAJ_EINVAL, "offsets must be non-decreasing");
+  const int N = offsets[P];
+  if (N > b->cfg.max_obstacles) return fail(b, TRAJ_ESHAPE, "obstacle count exceeds max_obstacles");
+  if (N > 0 && (!centers || !semi_axes || !velocities))
+    return fail(b, TRAJ_EINVAL, "NULL obstacle array");
+  std::vector<int> obs_problem(N);
+  for (int p = 0; p < P; ++p)
+    for (int j = offsets[p]; j < offsets[p + 1]; ++j) obs_problem[j] = p;
+  // tables offsets per horizon (same order as in set_problems)
+  std::vector<int> hz(b->n_steps);
+  std::sort(hz.begin(), hz.end());
+  hz.erase(std::unique(hz.begin(), hz.end()), hz.end());
+  std::vector<ProblemDev> recs(P);
+  for (int p = 0; p < P; ++p) {
+    ProblemDev r{};
+    r.n_p = b->n_steps[p];
+    r.n_o = offsets[p + 1] - offsets[p];
+    r.obs_off = offsets[p];
+    int off = 0;
+    for (int h : hz) { if (h == r.n_p) break; off += table_floats(h); }
+    r.tbl_off = off;
+    const double T = b->duration[p];
+    r.dt = (float)(T / (double)(r.n_p - 1));
+    r.invT = (float)(1.0 / T);
+    r.invT2 = (float)(1.0 / (T * T));
+    r.const_off = p * CONST_FLOATS;
+    r.nan_flag = 0;
+    recs[p] = r;
+  }
+  float *st_c = b->d_obs_stage, *st_a = st_c + (size_t)N * D, *st_v = st_a + (size_t)N * D;
+  if (N > 0) {
+    CK(b, cudaMemcpyAsync(st_c, centers, sizeof(float) * N * D, cudaMemcpyDefault, b->stream));
+    CK(b, cudaMemcpyAsync(st_a, semi_axes, sizeof(float) * N * D, cudaMemcpyDefault, b->stream));
+    CK(b, cudaMemcpyAsync(st_v, velocities, sizeof(float) * N * D, cudaMemcpyDefault, b->stream));
+    CK(b, cudaMemcpyAsync(b->d_obs_problem, obs_problem.data(), sizeof(int) * N, cudaMemcpyHostToDevice, b->stream));
+  }
+  CK(b, cudaMemcpyAsync(b->d_problems, recs.data(), sizeof(ProblemDev) * P, cudaMemcpyHostToDevice, b->stream));
+  CK(b, launch_pack_obstacles(D, N, st_c, st_a, st_v, b->d_obs_problem, b->d_obs, b->d_problems, b->stream));
+  CK(b, launch_setup_problems(b->d_problems, P, b->d_T, b->d_start, b->d_goal, D, b->cfg.rho,
+                              b->cfg.w_smooth, b->cfg.w_track, b->cfg.cost_mode, b->max_np_used,
+                              b->d_constants, b->stream));
+  CK(b, cudaStreamSynchronize(b->stream));
+  b->obs_offsets.assign(offsets, offsets + P + 1);
+  b->n_obs = N;
+  b->have_obstacles = true;
+  b->have_result = false;
+  b->err.clear();
+  return TRAJ_OK;
+}
+
+traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
+                             const float *coeffs0) {
+  if (!b) return TRAJ_EINVAL;
+  if (!b->have_obstacles) return fail(b, TRAJ_ESTATE, "traj_set_obstacles must come first");
+  if (!traj_problem || !coeffs0) return fail(b, TRAJ_EINVAL, "NULL trajectory array");
+  if (n_traj < 1 || n_traj > b->cfg.max_traj) return fail(b, TRAJ_ESHAPE, "n_traj exceeds max_traj (or < 1)");
+  for (int k = 0; k < n_traj; ++k)
+    if (traj_problem[k] < 0 || traj_problem[k] >= b->n_problems)
+      return fail(b, TRAJ_EINVAL, "traj_problem entry out of range");
+  // work-queue order: most expensive (n_o * n_p) first, stable
+  std::vector<int> order(n_traj);
+  for (int k = 0; k < n_traj; ++k) order[k] = k;
+  std::vector<long long> cost(b->n_problems);
+  for (int p = 0; p < b->n_problems; ++p)
+    cost[p] = (long long)(b->obs_offsets[p + 1] - b->obs_offsets[p] + 2) * b->n_steps[p];
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return cost[traj_problem[x]] > cost[traj_problem[y]];
+  });
+  CK(b, cudaMemcpyAsync(b->d_xi0, coeffs0, sizeof(float) * n_traj * b->cfg.dim * NC, cudaMemcpyDefault, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_traj_problem, traj_problem, sizeof(int) * n_traj, cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * n_traj, cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaStreamSynchronize(b->stream));
+  b->traj_problem.assign(traj_problem, traj_problem + n_traj);
+  b->n_traj = n_traj;
+  b->have_initial = true;
+  b->have_result = false;
+  b->err.clear();
+  return TRAJ_OK;
+}
+
+traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
+                       traj_solve_stats *stats) {
+  if (!b) return TRAJ_EINVAL;
+  if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
+  if (max_iters < 0) return fail(b, TRAJ_EINVAL, "max_iters must be >= 0");
+  if (std::isnan(tol) || !(timeout_ms >= 0)) return fail(b, TRAJ_EINVAL, "bad tol or timeout");
+  SolveArgs a{};
+  a.problems = b->d_problems;
+  a.obstacles = b->d_obs;
+  a.constants = b->d_constants;
+  a.tables = b->d_tables;
+  a.table_floats_total = b->table_floats;
+  a.traj_problem = b->d_traj_problem;
+  a.order = b->d_order;
+  a.xi0 = b->d_xi0;
+  a.xi = b->d_xi;
+  a.lam = b->d_lam;
+  a.u = b->d_u;
+  a.res = b->d_res;
+  a.iters = b->d_iters;
+  a.status = b->d_status;
+  a.n_traj = b->n_traj;
+  a.max_iters = max_iters;
+  a.tol = tol;
+  a.rho = (float)b->cfg.rho;
+  a.vmax = (float)b->cfg.vmax;
+  a.amax = (float)b->cfg.amax;
+  a.cost_mode = b->cfg.cost_mode;
+  a.timeout_ns = timeout_ms > 0 ? (unsigned long long)(timeout_ms * 1e6) : 0ull;
+  a.queue = b->d_queue;
+  a.t0 = b->d_t0;
+  a.flags = b->d_flags;
+  CK(b, cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream));
+  CK(b, cudaMemsetAsync(b->d_flags, 0, sizeof(int), b->stream));
+  CK(b, cudaMemsetAsync(b->d_t0, 0, sizeof(unsigned long long), b->stream));
+  CK(b, cudaEventRecord(b->ev0, b->stream));
+  CK(b, launch_am_solve(b->cfg.dim, b->max_np_used, b->cfg.precision, a, b->n_sm, b->stream));
+  CK(b, cudaEventRecord(b->ev1, b->stream));
+  b->have_result = true;
+  if (!stats) return TRAJ_OK;
+  CK(b, cudaStreamSynchronize(b->stream));
+  const int B = b->n_traj;
+  std::vector<int> it(B);
+  std::vector<float> res((size_t)B * 3);
+  std::vector<signed char> st(B);
+  int flags = 0;
+  CK(b, cudaMemcpy(it.data(), b->d_iters, sizeof(int) * B, cudaMemcpyDeviceToHost));
+  CK(b, cudaMemcpy(res.data(), b->d_res, sizeof(float) * B * 3, cudaMemcpyDeviceToHost));
+  CK(b, cudaMemcpy(st.data(), b->d_status, B, cudaMemcpyDeviceToHost));
+  CK(b, cudaMemcpy(&flags, b->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+  float ms = 0.f;
+  CK(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  traj_solve_stats s{};
+  s.n_traj = B;
+  std::vector<int> sorted = it;
+  std::sort(sorted.begin(), sorted.end());
+  s.iters_min = sorted.front();
+  s.iters_max = sorted.back();
+  s.iters_median = sorted[B / 2];
+  for (int k = 0; k < B; ++k) {
+    if (st[k] == TRAJ_TRAJ_CONVERGED) ++s.n_solved;
+    if (st[k] == TRAJ_TRAJ_NAN) continue;
+    s.max_res_obs = std::max(s.max_res_obs, res[k * 3 + 0]);
+    s.max_res_v = std::max(s.max_res_v, res[k * 3 + 1]);
+    s.max_res_a = std::max(s.max_res_a, res[k * 3 + 2]);
+  }
+  s.gpu_ms = ms;
+  *stats = s;
+  if (flags & 1) return fail(b, TRAJ_ETIMEOUT, "deadline reached");
+  if (flags & 2) return fail(b, TRAJ_ENAN, "non-finite input in some trajectories");
+  return s.n_solved == B ? TRAJ_OK : TRAJ_NOT_CONVERGED;
+}
+
+traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual, int *iters,
+                                  signed char *status) {
+  if (!b) return TRAJ_EINVAL;
+  if (!b->have_result) return fail(b, TRAJ_ESTATE, "no solve has run");
+  const size_t B = b->n_traj, D = b->cfg.dim;
+  bool host = false;
+  if (coeffs) { CK(b, cudaMemcpyAsync(coeffs, b->d_xi, sizeof(float) * B * D * NC, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(coeffs); }
+  if (residual) { CK(b, cudaMemcpyAsync(residual, b->d_res, sizeof(float) * B * 3, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(residual); }
+  if (iters) { CK(b, cudaMemcpyAsync(iters, b->d_iters, sizeof(int) * B, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(iters); }
+  if (status) { CK(b, cudaMemcpyAsync(status, b->d_status, B, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(status); }
+  if (host) CK(b, cudaStreamSynchronize(b->stream));
+  return TRAJ_OK;
+}
+
+traj_status traj_get_state(traj_batch *b, float *lambda, float *u) {
+  if (!b) return TRAJ_EINVAL;
+  if (!b->have_result) return fail(b, TRAJ_ESTATE, "no solve has run");
+  const size_t n = (size_t)b->n_traj * b->cfg.dim * NC;
+  bool host = false;
+  if (lambda) { CK(b, cudaMemcpyAsync(lambda, b->d_lam, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(lambda); }
+  if (u) { CK(b, cudaMemcpyAsync(u, b->d_u, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(u); }
+  if (host) CK(b, cudaStreamSynchronize(b->stream));
+  return TRAJ_OK;
+}
+
+traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_per_s) {
+  if (!flops_per_s || reps < 1) return TRAJ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TRAJ_ECUDA;
+  }
+  float *out = nullptr;
+  cudaEvent_t e0, e1;
+  if (cudaMalloc(&out, sizeof(float) * n_sm * 8) != cudaSuccess) return TRAJ_ENOMEM;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = n_sm * 8, iters = 4096;
+  const double flops = 2.0 * 8 * 16 * (double)iters * 256.0 * blocks;
+  double best = 0.0;
+  traj_status rc = TRAJ_OK;
+  for (int r = 0; r <= reps && rc == TRAJ_OK; ++r) {
+    cudaEventRecord(e0, s);
+    if (tb::launch_ffma_peak(out, blocks, iters, s) != cudaSuccess) rc = TRAJ_ECUDA;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = TRAJ_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0 && ms > 0) best = std::max(best, flops / (ms * 1e-3));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *flops_per_s = best;
+  return rc;
+}
+
+} // extern "C"

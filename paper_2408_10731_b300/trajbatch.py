@@ -1,0 +1,227 @@
+"""Python binding of libtrajbatch.so (include/trajbatch.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels. There is no CPU
+fallback: if the shared library is missing, or no CUDA device is present,
+the calls raise.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); they are
+passed to the C ABI as raw pointers. The stream defaults to torch's current
+CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_c_int, _c_double, _c_void_p, _c_float = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_float
+
+STATUS_NAMES = {0: "TRAJ_OK", 1: "TRAJ_NOT_CONVERGED", -1: "TRAJ_EINVAL", -2: "TRAJ_ENOMEM",
+                -3: "TRAJ_ECUDA", -4: "TRAJ_ESHAPE", -5: "TRAJ_ETIMEOUT", -6: "TRAJ_ENAN",
+                -7: "TRAJ_ESTATE"}
+TRAJ_CONVERGED, TRAJ_CAP, TRAJ_NAN, TRAJ_TIMEOUT = 0, 1, 2, 3
+PRECISION = {"fp32": 0, "mixed": 1}
+COST_MODE = {"smooth_track": 0, "project": 1}
+
+
+class TrajConfig(ctypes.Structure):
+    _fields_ = [("dim", _c_int), ("degree", _c_int), ("max_problems", _c_int),
+                ("max_traj", _c_int), ("max_obstacles", _c_int), ("max_steps", _c_int),
+                ("vmax", _c_double), ("amax", _c_double), ("rho", _c_double),
+                ("w_smooth", _c_double), ("w_track", _c_double), ("precision", _c_int),
+                ("cost_mode", _c_int), ("cuda_stream", _c_void_p)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("n_traj", _c_int), ("n_solved", _c_int), ("iters_min", _c_int),
+                ("iters_median", _c_int), ("iters_max", _c_int), ("max_res_obs", _c_float),
+                ("max_res_v", _c_float), ("max_res_a", _c_float), ("gpu_ms", _c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TrajBatchError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Load the in-tree shared library; raise loudly if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtrajbatch.so is not built ({path}); run "
+                           "paper_2408_10731_b300.build.build() or __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    lib.traj_batch_create.argtypes = [ctypes.POINTER(TrajConfig), ctypes.POINTER(_vp)]
+    lib.traj_batch_destroy.argtypes = [_vp]
+    lib.traj_set_problems.argtypes = [_vp, _c_int, _vp, _vp, _vp, _vp]
+    lib.traj_set_obstacles.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    lib.traj_set_initial.argtypes = [_vp, _c_int, _vp, _vp]
+    lib.traj_solve.argtypes = [_vp, _c_int, _c_float, _c_double, ctypes.POINTER(SolveStats)]
+    lib.traj_get_trajectories.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    lib.traj_get_state.argtypes = [_vp, _vp, _vp]
+    lib.traj_status_string.argtypes = [_c_int]
+    lib.traj_status_string.restype = ctypes.c_char_p
+    lib.traj_last_error.argtypes = [_vp]
+    lib.traj_last_error.restype = ctypes.c_char_p
+    lib.traj_measure_fp32_peak.argtypes = [_vp, _c_int, ctypes.POINTER(_c_double)]
+    for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
+                 "traj_set_obstacles", "traj_set_initial", "traj_solve",
+                 "traj_get_trajectories", "traj_get_state", "traj_measure_fp32_peak"):
+        getattr(lib, name).restype = _c_int
+    _LIB = lib
+    return lib
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive) of a numpy array or torch tensor, checked for dtype/contiguity."""
+    if x is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+                   np.int8: torch.int8}[dtype]
+            if x.dtype != tdt or not x.is_contiguous():
+                raise TypeError(f"tensor must be contiguous {tdt}, got {x.dtype}")
+            return x.data_ptr(), x
+    except ImportError:
+        pass
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+        x = np.ascontiguousarray(x, dtype=dtype)
+    return x.ctypes.data, x
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def measure_fp32_peak(reps: int = 5, stream=None) -> float:
+    lib = load_library()
+    out = ctypes.c_double(0.0)
+    rc = lib.traj_measure_fp32_peak(stream if stream is not None else _default_stream(), reps,
+                                    ctypes.byref(out))
+    if rc != 0:
+        raise TrajBatchError(rc, "FFMA microbenchmark failed")
+    return out.value
+
+
+class TrajBatch:
+    """Handle of one batch (C struct traj_batch); mirrors the C entry points."""
+
+    def __init__(self, dim, max_problems, max_traj, max_obstacles, max_steps, vmax, amax,
+                 rho=1.0, w_smooth=1.0, w_track=1.0, precision="fp32", cost_mode="smooth_track",
+                 stream=None):
+        self._lib = load_library()
+        self.dim = dim
+        self.stream = stream if stream is not None else _default_stream()
+        cfg = TrajConfig(dim, 10, max_problems, max_traj, max_obstacles, max_steps, vmax, amax,
+                         rho, w_smooth, w_track, PRECISION[precision], COST_MODE[cost_mode],
+                         self.stream)
+        h = _vp()
+        rc = self._lib.traj_batch_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != 0:
+            raise TrajBatchError(rc, self._lib.traj_last_error(None).decode())
+        self._h = h
+        self.n_traj = 0
+
+    def _check(self, rc, ok=(0,)):
+        if rc not in ok:
+            raise TrajBatchError(rc, self._lib.traj_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.traj_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_problems(self, n_steps, duration, start, goal):
+        n, kn = _ptr(np.asarray(n_steps), np.int32)
+        d, kd = _ptr(np.asarray(duration), np.float64)
+        s, ks = _ptr(np.asarray(start), np.float64)
+        g, kg = _ptr(np.asarray(goal), np.float64)
+        self._check(self._lib.traj_set_problems(self._h, int(np.asarray(n_steps).shape[0]), n, d, s, g))
+
+    def set_obstacles(self, offsets, centers, semi_axes, velocities):
+        o, ko = _ptr(np.asarray(offsets), np.int32)
+        c, kc = _ptr(centers, np.float32)
+        a, ka = _ptr(semi_axes, np.float32)
+        v, kv = _ptr(velocities, np.float32)
+        self._check(self._lib.traj_set_obstacles(self._h, o, c, a, v))
+
+    def set_initial(self, traj_problem, coeffs0):
+        tp, kt = _ptr(np.asarray(traj_problem), np.int32)
+        x, kx = _ptr(coeffs0, np.float32)
+        n = int(np.asarray(traj_problem).shape[0])
+        self._check(self._lib.traj_set_initial(self._h, n, tp, x))
+        self.n_traj = n
+
+    def solve(self, max_iters, tol=1e-3, timeout_ms=0.0, stats=True):
+        st = SolveStats()
+        rc = self._lib.traj_solve(self._h, int(max_iters), float(tol), float(timeout_ms),
+                                  ctypes.byref(st) if stats else None)
+        self._check(rc, ok=(0, 1) if stats else (0,))
+        return st.as_dict() if stats else None
+
+    def get_trajectories(self, coeffs=None, residual=None, iters=None, status=None):
+        """Into the given buffers (host or device); allocates numpy arrays if all are None."""
+        alloc = coeffs is None and residual is None and iters is None and status is None
+        if alloc:
+            coeffs = np.zeros((self.n_traj, self.dim, 11), np.float32)
+            residual = np.zeros((self.n_traj, 3), np.float32)
+            iters = np.zeros(self.n_traj, np.int32)
+            status = np.zeros(self.n_traj, np.int8)
+        c, kc = _ptr(coeffs, np.float32)
+        r, kr = _ptr(residual, np.float32)
+        i, ki = _ptr(iters, np.int32)
+        s, ks = _ptr(status, np.int8)
+        self._check(self._lib.traj_get_trajectories(self._h, c, r, i, s))
+        return dict(xi=coeffs, residual=residual, iters=iters, status=status)
+
+    def get_state(self):
+        lam = np.zeros((self.n_traj, self.dim, 11), np.float32)
+        u = np.zeros((self.n_traj, self.dim, 11), np.float32)
+        self._check(self._lib.traj_get_state(self._h, _ptr(lam, np.float32)[0],
+                                             _ptr(u, np.float32)[0]))
+        return dict(lam=lam, u=u)
+
+
+def from_batch(batch, precision="fp32", cost_mode="smooth_track", w_smooth=1.0, w_track=1.0,
+               stream=None, max_traj=None) -> TrajBatch:
+    """Create a handle sized for a scenes.Batch and load its problems, obstacles and xi0."""
+    tb = TrajBatch(batch.dim, batch.n_problems, max_traj or batch.n_traj,
+                   max(1, int(batch.offsets[-1])), int(batch.n_steps.max()), batch.vmax,
+                   batch.amax, batch.rho, w_smooth, w_track, precision, cost_mode, stream)
+    tb.set_problems(batch.n_steps, batch.duration, batch.start, batch.goal)
+    tb.set_obstacles(batch.offsets, batch.centers.astype(np.float32),
+                     batch.semi_axes.astype(np.float32), batch.velocities.astype(np.float32))
+    tb.set_initial(batch.traj_problem, batch.xi0.astype(np.float32))
+    return tb
