@@ -55,20 +55,32 @@ def algorithmic_ops(batch, iters):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms; mark() brackets the
+    timed region so that only the samples taken inside it are summarised."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, gpu_id):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.marks = []
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 10 and self._lines() == 0 and self.p.poll() is None:
+            time.sleep(0.05)
+
+    def _lines(self):
+        with open(self.f.name) as fh:
+            return sum(1 for _ in fh)
+
+    def mark(self):
+        self.marks.append(self._lines())
 
     def stop(self):
         if self.p is None:
@@ -78,10 +90,13 @@ class ClockSampler:
             self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
-        self.f.flush(); self.f.seek(0)
+        with open(self.f.name) as fh:
+            lines = fh.read().splitlines()
+        os.unlink(self.f.name)
+        lo, hi = (self.marks + [0, len(lines)])[:2] if len(self.marks) >= 2 else (0, len(lines))
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
+        for line in lines[lo:hi]:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -92,10 +107,17 @@ class ClockSampler:
             for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
-        os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _pci_id(torch, dev):
+    p = torch.cuda.get_device_properties(dev)
+    try:
+        return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+    except AttributeError:
+        return str(dev)
 
 
 def cpu_baseline(seed=0, n_scenes=16, inits=8, max_iters=500, tol=1e-3):
@@ -140,8 +162,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
     ap.add_argument("--max-iters", type=int, default=500)
@@ -175,13 +197,14 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    sampler = ClockSampler(_pci_id(torch, local))
     for _ in range(args.warmup):
         flush.fill_(1.0)
         h.solve(args.max_iters, args.tol)
     fp32_peak = trajbatch.measure_fp32_peak(5) if rank == 0 else None
 
-    sampler = ClockSampler(local)
     barrier()
+    sampler.mark()
     step_ms, kern_ms, solved = [], [], []
     for _ in range(args.steps):
         flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
@@ -192,6 +215,7 @@ def main():
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1)); kern_ms.append(st["gpu_ms"]); solved.append(st["n_solved"])
     barrier()
+    sampler.mark()
     clocks = sampler.stop()
     out = h.get_trajectories()
 
@@ -203,7 +227,7 @@ def main():
         ("residual", (batch.n_traj, 3), torch.float32), ("iters", (batch.n_traj,), torch.int32),
         ("status", (batch.n_traj,), torch.int8))}
     e2e_s, e2e_solved = [], []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(max(3, min(50, args.steps // 2))):
         flush.fill_(1.0); torch.cuda.synchronize()
         t0 = time.perf_counter()
         h.set_initial(tp_h, xi0_h)

@@ -162,9 +162,10 @@ const char *traj_status_string(traj_status s);
 /* Detail of the last failure on this handle (static per handle; "" if none). */
 const char *traj_last_error(traj_batch *b);
 
-/* FP32 FFMA throughput microbenchmark, the denominator of the ALU roofline:
- * runs an independent-chain FFMA kernel on the stream and returns the
- * achieved FP32 FLOP/s (2 per FMA) over `reps` timed launches. */
+/* FP32 FMA throughput microbenchmark, the denominator of the ALU roofline:
+ * runs independent-chain kernels of scalar FMA and of packed two-lane FMA
+ * (f32x2) on the stream and returns the better achieved FP32 FLOP/s (2 per
+ * FMA), best of `reps` timed launches each. No paper counterpart (measurement). */
 traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_per_s);
 
 #ifdef __cplusplus

@@ -113,46 +113,79 @@ __device__ __forceinline__ void project_contract(
       }
     }
   }
-  // pair loop over obstacles: acc accumulates sum_j Delta_j * w_j (r_j = -Delta_j w_j)
+  // pair loop over obstacles: acc accumulates sum_j Delta_j * w_j (r_j = -Delta_j w_j).
+  // The containment tests of a pair of obstacles against all of a lane's
+  // timesteps are computed branch-free (x and y packed in f32x2 lanes) and
+  // combined with one min; only when one of them contains a point does the
+  // warp take the projection branch (rare once the iterates are outside).
   mo = 0.f;
-  for (int j = 0; j < n_o; ++j) {
-    float4 o[OV];
+  for (int j = 0; j < n_o; j += 2) {
+    float4 o[2][OV];
 #pragma unroll
-    for (int q = 0; q < OV; ++q) o[q] = __ldg(&obs[OV * j + q]);
-    float c[DIM], v[DIM], ia[DIM], ax[DIM];
-    if constexpr (DIM == 2) {
-      c[0] = o[0].x; c[1] = o[0].y; v[0] = o[0].z; v[1] = o[0].w;
-      ia[0] = o[1].x; ia[1] = o[1].y; ax[0] = o[1].z; ax[1] = o[1].w;
-    } else {
-      c[0] = o[0].x; c[1] = o[0].y; c[2] = o[0].z; ia[0] = o[0].w;
-      v[0] = o[1].x; v[1] = o[1].y; v[2] = o[1].z; ia[1] = o[1].w;
-      ax[0] = o[2].x; ax[1] = o[2].y; ax[2] = o[2].z; ia[2] = o[2].w;
-    }
+    for (int h = 0; h < 2; ++h) {
+      if (j + h < n_o) {
 #pragma unroll
-    for (int m = 0; m < MAXNT; ++m) {
-      if (m < nt) {
-        float d[DIM], s = 0.f;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          d[a] = pos[m][a] - fmaf(v[a], tm[m], c[a]);
-          const float u = d[a] * ia[a];
-          s = fmaf(u, u, s);
+        for (int q = 0; q < OV; ++q) o[h][q] = __ldg(&obs[OV * (j + h) + q]);
+      } else { // tail sentinel: static, 1e18 m away, unit axes: never inside
+        if constexpr (DIM == 2) {
+          o[h][0] = make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
+          o[h][1] = make_float4(1.f, 1.f, 1.f, 1.f);
+        } else {
+          o[h][0] = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 1.f);
+          o[h][1] = make_float4(0.f, 0.f, 0.f, 1.f);
+          o[h][2] = make_float4(1.f, 1.f, 1.f, 1.f);
         }
-        if (s < 1.f) { // inside the ellipse: project to its boundary along the ray
-          float e[DIM];
-          if (s > 0.f) {
-            const float w = rsqrtf(s) - 1.f;
+      }
+    }
+    float d[2][MAXNT][DIM], s[2][MAXNT];
+    float smin = 3.0e38f;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) e[a] = d[a] * w;
-          } else { // at the centre: atan2(0, 0) = 0 pushes along +x (3D: beta = 0, +z)
+    for (int h = 0; h < 2; ++h) {
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) e[a] = 0.f;
-            if constexpr (DIM == 2) e[0] = ax[0]; else e[2] = ax[2];
+      for (int m = 0; m < MAXNT; ++m) {
+        if constexpr (DIM == 2) {
+          const float2 nc = make_float2(o[h][0].x, o[h][0].y), nv = make_float2(o[h][0].z, o[h][0].w);
+          const float2 ia = make_float2(o[h][1].x, o[h][1].y);
+          const float2 pc = __fadd2_rn(make_float2(pos[m][0], pos[m][1]), nc);
+          const float2 dd = __ffma2_rn(nv, make_float2(tm[m], tm[m]), pc);
+          const float2 uu = __fmul2_rn(dd, ia);
+          d[h][m][0] = dd.x; d[h][m][1] = dd.y;
+          s[h][m] = fmaf(uu.y, uu.y, uu.x * uu.x);
+        } else {
+          const float2 nc = make_float2(o[h][0].x, o[h][0].y), nv = make_float2(o[h][1].x, o[h][1].y);
+          const float2 ia = make_float2(o[h][0].w, o[h][1].w);
+          const float2 pc = __fadd2_rn(make_float2(pos[m][0], pos[m][1]), nc);
+          const float2 dd = __ffma2_rn(nv, make_float2(tm[m], tm[m]), pc);
+          const float2 uu = __fmul2_rn(dd, ia);
+          const float dz = fmaf(o[h][1].z, tm[m], pos[m][2] + o[h][0].z);
+          const float uz = dz * o[h][2].w;
+          d[h][m][0] = dd.x; d[h][m][1] = dd.y; d[h][m][2] = dz;
+          s[h][m] = fmaf(uz, uz, fmaf(uu.y, uu.y, uu.x * uu.x));
+        }
+        smin = fminf(smin, s[h][m]);
+      }
+    }
+    if (smin < 1.f) { // some timestep is inside one of the two ellipses
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int m = 0; m < MAXNT; ++m) {
+          if (s[h][m] < 1.f) {
+            float e[DIM];
+            if (s[h][m] > 0.f) { // project along the ray: target offset Delta / ||u||
+              const float w = rsqrtf(s[h][m]) - 1.f;
+#pragma unroll
+              for (int a = 0; a < DIM; ++a) e[a] = d[h][m][a] * w;
+            } else { // at the centre: atan2(0, 0) = 0 pushes along +x (3D: beta = 0, +z)
+#pragma unroll
+              for (int a = 0; a < DIM; ++a) e[a] = 0.f;
+              if constexpr (DIM == 2) e[0] = o[h][1].z; else e[2] = o[h][2].z;
+            }
+            float n2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) { acc[m][a] += e[a]; n2 = fmaf(e[a], e[a], n2); }
+            mo = fmaxf(mo, n2);
           }
-          float n2 = 0.f;
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) { acc[m][a] += e[a]; n2 = fmaf(e[a], e[a], n2); }
-          mo = fmaxf(mo, n2);
         }
       }
     }

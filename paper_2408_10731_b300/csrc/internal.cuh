@@ -46,9 +46,10 @@ constexpr int CONST_FLOATS = C_C_LO + 3 * ROW; // 672
 // FP32 copies of FP64 values, column 11 zero. TABLE_FLOATS(n_p) = 36 n_p.
 __host__ __device__ inline int table_floats(int n_p) { return 3 * ROW * n_p; }
 
-// Packed obstacle record: OBS_VEC(dim) float4 per obstacle.
-//  2D: {cx, cy, vx, vy}, {1/ax, 1/ay, ax, ay}
-//  3D: {cx, cy, cz, 1/ax}, {vx, vy, vz, 1/ay}, {ax, ay, az, 1/az}
+// Packed obstacle record: OBS_VEC(dim) float4 per obstacle (centre c and
+// velocity v stored negated).
+//  2D: {-cx, -cy, -vx, -vy}, {1/ax, 1/ay, ax, ay}
+//  3D: {-cx, -cy, -cz, 1/ax}, {-vx, -vy, -vz, 1/ay}, {ax, ay, az, 1/az}
 __host__ __device__ constexpr int obs_vec(int dim) { return dim == 2 ? 2 : 3; }
 
 // Arguments of one solve launch.
@@ -116,4 +117,5 @@ cudaError_t launch_pack_obstacles(int dim, int n_obs, const float *centers, cons
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             int n_sm, cudaStream_t s);
 cudaError_t launch_ffma_peak(float *out, int blocks, int iters, cudaStream_t s);
+cudaError_t launch_ffma2_peak(float *out, int blocks, int iters, cudaStream_t s);
 } // namespace tb

@@ -214,12 +214,14 @@ __global__ void k_pack_obstacles(int dim, int n_obs, const float *cen, const flo
     ok = ok && isfinite(c[d]) && isfinite(v[d]) && isfinite(a[d]) && a[d] > 0.f;
   }
   if (!ok) atomicOr(&problems[obs_problem[j]].nan_flag, 1);
+  // centre and velocity are stored negated: the solve forms p - c - v t as
+  // fma(-v, t, p + (-c)) with packed two-lane arithmetic
   if (dim == 2) {
-    out[2 * j + 0] = make_float4(c[0], c[1], v[0], v[1]);
+    out[2 * j + 0] = make_float4(-c[0], -c[1], -v[0], -v[1]);
     out[2 * j + 1] = make_float4(1.f / a[0], 1.f / a[1], a[0], a[1]);
   } else {
-    out[3 * j + 0] = make_float4(c[0], c[1], c[2], 1.f / a[0]);
-    out[3 * j + 1] = make_float4(v[0], v[1], v[2], 1.f / a[1]);
+    out[3 * j + 0] = make_float4(-c[0], -c[1], -c[2], 1.f / a[0]);
+    out[3 * j + 1] = make_float4(-v[0], -v[1], -v[2], 1.f / a[1]);
     out[3 * j + 2] = make_float4(a[0], a[1], a[2], 1.f / a[2]);
   }
 }
