@@ -156,6 +156,42 @@ traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual,
  * u = F^T (F xi - g) [n_traj][dim][11], FP32, host or device. */
 traj_status traj_get_state(traj_batch *b, float *lambda, float *u);
 
+/* Solve without allocating any memory, for callers that cannot allocate
+ * device memory: code running under an allocator or memory pool owned by
+ * another framework, plugins that may only use the buffers they are handed,
+ * or real-time paths where an allocation could stall. Such callers cannot
+ * create a traj_batch (its workspace is allocated), so this entry point runs
+ * the same set-up and solve kernels with every intermediate kept in one
+ * fixed-size device array (about 1.4 MB) that the library reserves at load
+ * time in every GPU that loads it, until the process exits. The paper has no
+ * counterpart; this is an interface for constrained callers.
+ *  - cfg: as for traj_batch_create (capacity fields ignored; precision must
+ *    be TRAJ_PREC_FP32); its stream carries all the work.
+ *  - Host arrays: n_steps, duration, start, goal (as traj_set_problems) and
+ *    obs_offsets[n_problems + 1] (as traj_set_obstacles).
+ *  - Device arrays (FP32 unless stated): centers, semi_axes, velocities
+ *    [N][dim]; traj_problem[n_traj] (int32); coeffs0[n_traj][dim][11]; and
+ *    the outputs coeffs[n_traj][dim][11], residual[n_traj][3],
+ *    iters[n_traj] (int32), status[n_traj] (int8), as traj_get_trajectories.
+ *  - Limits: n_problems <= 256, N <= 8192 obstacles, n_traj <= 8192, n_p <=
+ *    256, basis tables of the distinct horizons <= 160 KB; beyond them the
+ *    call returns TRAJ_ESHAPE with the limit named in traj_last_error(NULL).
+ *  - Synchronous: returns after the solve has finished on the stream. The
+ *    first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress), so make that first call before any stream capture.
+ *  - Every call shares the one array: calls that overlap on the GPU (other
+ *    threads, other streams) race and corrupt each other. Each call rewrites
+ *    the parts it uses and clears its counters, so nothing leaks between calls
+ *    that run one after another.
+ *  - Calls no cudaMalloc, cudaFree or other allocating routine. */
+traj_status traj_solve_noalloc(const traj_config *cfg, int n_problems, const int *n_steps,
+                               const double *duration, const double *start, const double *goal,
+                               const int *obs_offsets, const float *centers,
+                               const float *semi_axes, const float *velocities, int n_traj,
+                               const int *traj_problem, const float *coeffs0, int max_iters,
+                               float tol, float *coeffs, float *residual, int *iters,
+                               signed char *status);
+
 /* Human-readable name of a status code (static string). */
 const char *traj_status_string(traj_status s);
 

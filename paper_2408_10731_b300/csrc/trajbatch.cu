@@ -46,6 +46,11 @@ struct traj_batch {
 
 static thread_local std::string g_create_error;
 
+namespace tb {
+// Error detail of calls that have no handle (creation, traj_solve_noalloc).
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+} // namespace tb
+
 #define CK(b, expr)                                                                     \
   do {                                                                                  \
     cudaError_t _e = (expr);                                                            \

@@ -81,9 +81,13 @@ def load_library():
     lib.traj_last_error.argtypes = [_vp]
     lib.traj_last_error.restype = ctypes.c_char_p
     lib.traj_measure_fp32_peak.argtypes = [_vp, _c_int, ctypes.POINTER(_c_double)]
+    lib.traj_solve_noalloc.argtypes = [ctypes.POINTER(TrajConfig), _c_int, _vp, _vp, _vp, _vp,
+                                       _vp, _vp, _vp, _vp, _c_int, _vp, _vp, _c_int, _c_float,
+                                       _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
                  "traj_set_obstacles", "traj_set_initial", "traj_solve",
-                 "traj_get_trajectories", "traj_get_state", "traj_measure_fp32_peak"):
+                 "traj_get_trajectories", "traj_get_state", "traj_measure_fp32_peak",
+                 "traj_solve_noalloc"):
         getattr(lib, name).restype = _c_int
     _LIB = lib
     return lib
@@ -212,6 +216,33 @@ class TrajBatch:
         self._check(self._lib.traj_get_state(self._h, _ptr(lam, np.float32)[0],
                                              _ptr(u, np.float32)[0]))
         return dict(lam=lam, u=u)
+
+
+def solve_noalloc(dim, vmax, amax, rho, n_steps, duration, start, goal, obs_offsets, centers,
+                  semi_axes, velocities, traj_problem, coeffs0, max_iters, tol, coeffs, residual,
+                  iters, status, w_smooth=1.0, w_track=1.0, cost_mode="smooth_track", stream=None):
+    """traj_solve_noalloc: the allocation-free solve. Obstacles, traj_problem, coeffs0 and
+    the four outputs must be CUDA tensors; the problem arrays are host arrays."""
+    lib = load_library()
+    cfg = TrajConfig(dim, 10, 0, 0, 0, 0, vmax, amax, rho, w_smooth, w_track, 0,
+                     COST_MODE[cost_mode], stream if stream is not None else _default_stream())
+    n, kn = _ptr(np.asarray(n_steps), np.int32)
+    d, kd = _ptr(np.asarray(duration), np.float64)
+    s, ks = _ptr(np.asarray(start), np.float64)
+    g, kg = _ptr(np.asarray(goal), np.float64)
+    o, ko = _ptr(np.asarray(obs_offsets), np.int32)
+    args = [_ptr(x, dt)[0] for x, dt in ((centers, np.float32), (semi_axes, np.float32),
+                                         (velocities, np.float32))]
+    tp = _ptr(traj_problem, np.int32)[0]
+    x0 = _ptr(coeffs0, np.float32)[0]
+    outs = [_ptr(x, dt)[0] for x, dt in ((coeffs, np.float32), (residual, np.float32),
+                                         (iters, np.int32), (status, np.int8))]
+    rc = lib.traj_solve_noalloc(ctypes.byref(cfg), int(np.asarray(n_steps).shape[0]), n, d, s, g,
+                                o, *args, int(traj_problem.shape[0]), tp, x0, int(max_iters),
+                                float(tol), *outs)
+    if rc != 0:
+        raise TrajBatchError(rc, lib.traj_last_error(None).decode())
+    return rc
 
 
 def from_batch(batch, precision="fp32", cost_mode="smooth_track", w_smooth=1.0, w_track=1.0,
