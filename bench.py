@@ -30,6 +30,10 @@ WORKLOAD = ("2D moving ellipses: n_p=100 over T=10 s, 50 constant-velocity axis-
             "ellipses (semi-axes U(0.2,0.8) m, speed U(0,1) m/s), start (0,0) goal (8,8), "
             "128 scenes x 8 initialisations N(straight line, 0.5 m) = 1024 trajectories, "
             "vmax 1.5 m/s, amax 2 m/s^2, rho 1, cap 500 iterations, tol 1e-3")
+WORKLOAD_UNEVEN = ("uneven 2D batch: 2048 problems, obstacle counts log-uniform 4-256, horizons "
+                   "n_p in {50,75,100,150} over T=0.1 n_p s, goal 0.55 vmax T away, 8 "
+                   "initialisations each = 16384 trajectories in one persistent launch "
+                   "(CUDA graph, autotuned CTA shape), cap 500 iterations, tol 1e-3")
 
 
 def algorithmic_ops(batch, iters):
@@ -169,6 +173,7 @@ def main():
     ap.add_argument("--max-iters", type=int, default=500)
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workload", default="config2", choices=["config2", "uneven"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -192,8 +197,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    batch = scenes.config2(args.seed + rank)
+    from paper_2408_10731_b300 import autotune
+    if args.workload == "uneven":
+        batch = scenes.config4(args.seed + rank)
+    else:
+        batch = scenes.config2(args.seed + rank)
     h = trajbatch.from_batch(batch, precision=args.precision)
+    shape = autotune.tuned(h, batch, args.precision, iters=200)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -263,7 +273,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision,
+            "config": {"workload": WORKLOAD if args.workload == "config2" else WORKLOAD_UNEVEN,
+                       "precision": args.precision, "launch_shape": shape,
                        "l2": "flushed between timed steps (256 MB write, outside the events)",
                        "per_rank_batch": "seed + rank"},
             "ms_per_batch_solve": float(np.mean(step_ms)),
@@ -280,7 +291,7 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == "config2":
             cb = cpu_baseline(args.seed)
             cb.pop("seconds", None)
             line["cpu_baseline"] = cb

@@ -132,7 +132,9 @@ typedef struct traj_solve_stats {
   float gpu_ms;                        /* device time of the solve (CUDA events) */
 } traj_solve_stats;
 
-/* Run Algorithm 2 on every trajectory in one persistent launch: initialise by
+/* Run Algorithm 2 on every trajectory in one persistent launch, captured once
+ * as a CUDA graph (counter clears + kernel) and replayed while max_iters, tol,
+ * timeout, the batch and the launch shape are unchanged: initialise by
  * projecting coeffs0 (lambda0 = 0), then iterate xi-step / projection /
  * multiplier update until the three L-infinity residuals (obstacle,
  * velocity, acceleration; metres, m/s, m/s^2) are all <= tol, checked after
@@ -191,6 +193,24 @@ traj_status traj_solve_noalloc(const traj_config *cfg, int n_problems, const int
                                const int *traj_problem, const float *coeffs0, int max_iters,
                                float tol, float *coeffs, float *residual, int *iters,
                                signed char *status);
+
+/* CTA shape of the persistent solve launch: warps per block (1..8, one
+ * trajectory per warp at a time) and a cap on resident blocks per SM (0 =
+ * as many as occupancy allows). The grid never exceeds what the batch needs. */
+typedef struct traj_launch_shape {
+  int warps_per_block;
+  int blocks_per_sm;
+} traj_launch_shape;
+
+/* Use this launch shape for later solves (default: 4 warps, occupancy-bound). */
+traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape);
+
+/* Autotuner: times every candidate shape (warps per block in {1,2,4,8} x
+ * blocks per SM in {occupancy,1,2,4}) on this handle's own batch with `iters`
+ * fixed iterations, keeps the fastest for later solves and reports it in
+ * *chosen and its time per solve in *best_ms (both nullable). Synchronises;
+ * the previous solve's results are discarded. No paper counterpart. */
+traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, float *best_ms);
 
 /* Human-readable name of a status code (static string). */
 const char *traj_status_string(traj_status s);

@@ -33,7 +33,7 @@
 namespace tb {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int WARPS_PER_BLOCK = 4;
+constexpr int MAX_WARPS_PER_BLOCK = 8;
 
 // Reduce-scatter of 32 per-lane values: afterwards lane L holds the warp sum of
 // slot L (recursive halving; slot order preserved).
@@ -230,8 +230,8 @@ __device__ __forceinline__ void project_contract(
 }
 
 template <int DIM, int MAXNT>
-__device__ void solve_one(const SolveArgs &A, int b, const float *stab, int lane,
-                          unsigned long long deadline) {
+__device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *stab, int lane,
+                                       unsigned long long deadline) {
   const int p = A.traj_problem[b];
   const ProblemDev pr = A.problems[p];
   const int n_p = pr.n_p, n_o = pr.n_o;
@@ -377,8 +377,21 @@ __device__ void solve_one(const SolveArgs &A, int b, const float *stab, int lane
   }
 }
 
+// Per-trajectory specialisation on the number of 32-step timestep slots, so a
+// short horizon in an uneven batch does not pay for the longest one's slots.
+template <int DIM, int NT, int MAXNT>
+__device__ __forceinline__ void solve_nt(const SolveArgs &A, int b, const float *stab, int lane,
+                                         unsigned long long deadline, int nt) {
+  if constexpr (NT >= MAXNT) {
+    solve_one<DIM, MAXNT>(A, b, stab, lane, deadline);
+  } else {
+    if (nt <= NT) solve_one<DIM, NT>(A, b, stab, lane, deadline);
+    else solve_nt<DIM, NT + 1, MAXNT>(A, b, stab, lane, deadline, nt);
+  }
+}
+
 template <int DIM, int MAXNT>
-__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32)
 k_am_fp32(const __grid_constant__ SolveArgs A) {
   extern __shared__ float4 smem4[];
   const float4 *g4 = reinterpret_cast<const float4 *>(A.tables);
@@ -402,42 +415,47 @@ k_am_fp32(const __grid_constant__ SolveArgs A) {
     if (lane == 0) item = atomicAdd(A.queue, 1);
     item = __shfl_sync(FULL, item, 0);
     if (item >= A.n_traj) break;
-    solve_one<DIM, MAXNT>(A, A.order[item], stab, lane, deadline);
+    const int b = A.order[item];
+    const int nt = (A.problems[A.traj_problem[b]].n_p + 31) >> 5;
+    solve_nt<DIM, 1, MAXNT>(A, b, stab, lane, deadline, nt);
   }
 }
 
 template <int DIM, int MAXNT>
-static cudaError_t launch_t(const SolveArgs &a, int n_sm, cudaStream_t s) {
+static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_sm,
+                            cudaStream_t s, LaunchShape *used) {
   auto kern = k_am_fp32<DIM, MAXNT>;
+  const int warps = shape.warps_per_block > 0 ? shape.warps_per_block : 4;
+  if (warps > MAX_WARPS_PER_BLOCK) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * (size_t)a.table_floats_total;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS_PER_BLOCK * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  long long want = ((long long)a.n_traj + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+  if (shape.blocks_per_sm > 0 && shape.blocks_per_sm < occ) occ = shape.blocks_per_sm;
+  long long want = ((long long)a.n_traj + warps - 1) / warps;
   long long grid = (long long)n_sm * occ;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, WARPS_PER_BLOCK * 32, smem, s>>>(a);
+  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; }
+  kern<<<(unsigned)grid, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a, int n_sm,
-                            cudaStream_t s) {
+cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
+                            const LaunchShape &shape, int n_sm, cudaStream_t s, LaunchShape *used) {
   (void)precision;
   const int nt = (max_np + 31) / 32;
   if (dim == 2) {
-    if (nt <= 2) return launch_t<2, 2>(a, n_sm, s);
-    if (nt <= 4) return launch_t<2, 4>(a, n_sm, s);
-    if (nt <= 5) return launch_t<2, 5>(a, n_sm, s);
-    return launch_t<2, 8>(a, n_sm, s);
+    if (nt <= 4) return launch_t<2, 4>(a, shape, n_sm, s, used);
+    if (nt <= 5) return launch_t<2, 5>(a, shape, n_sm, s, used);
+    return launch_t<2, 8>(a, shape, n_sm, s, used);
   }
-  if (nt <= 2) return launch_t<3, 2>(a, n_sm, s);
-  if (nt <= 4) return launch_t<3, 4>(a, n_sm, s);
-  if (nt <= 5) return launch_t<3, 5>(a, n_sm, s);
-  return launch_t<3, 8>(a, n_sm, s);
+  if (nt <= 4) return launch_t<3, 4>(a, shape, n_sm, s, used);
+  if (nt <= 5) return launch_t<3, 5>(a, shape, n_sm, s, used);
+  return launch_t<3, 8>(a, shape, n_sm, s, used);
 }
 
 } // namespace tb

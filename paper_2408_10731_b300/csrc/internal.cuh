@@ -114,8 +114,16 @@ cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const 
 cudaError_t launch_pack_obstacles(int dim, int n_obs, const float *centers, const float *axes,
                                   const float *vel, const int *obs_problem, float4 *out,
                                   ProblemDev *problems, cudaStream_t s);
+// CTA shape of the persistent solve launch (the autotuner's search space);
+// zero fields take the defaults (4 warps, occupancy-limited blocks per SM).
+struct LaunchShape {
+  int warps_per_block;
+  int blocks_per_sm;
+  int grid; // filled in by the launcher
+};
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
-                            int n_sm, cudaStream_t s);
+                            const LaunchShape &shape, int n_sm, cudaStream_t s,
+                            LaunchShape *used);
 cudaError_t launch_ffma_peak(float *out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_ffma2_peak(float *out, int blocks, int iters, cudaStream_t s);
 } // namespace tb

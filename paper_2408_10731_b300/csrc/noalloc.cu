@@ -230,7 +230,7 @@ extern "C" traj_status traj_solve_noalloc(
   a.queue = d_words;
   a.flags = d_words + 1;
   a.t0 = reinterpret_cast<unsigned long long *>(d_words + 2);
-  NA_CK(launch_am_solve(D, max_np, TRAJ_PREC_FP32, a, n_sm, s));
+  NA_CK(launch_am_solve(D, max_np, TRAJ_PREC_FP32, a, LaunchShape{4, 0, 0}, n_sm, s, nullptr));
   // the host-side sources above live on this stack frame: finish before returning
   NA_CK(cudaStreamSynchronize(s));
   int flags = 0;

@@ -42,6 +42,15 @@ struct traj_batch {
   int *d_queue = nullptr, *d_flags = nullptr;
   unsigned long long *d_t0 = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // launch shape of the solve (set by traj_autotune / traj_set_launch_shape)
+  LaunchShape shape{4, 0, 0};
+  // the solve captured as a CUDA graph, replayed while its key is unchanged
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  bool graph_valid = false;
+  int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1;
+  float g_tol = 0.f;
+  unsigned long long g_timeout = 0;
 };
 
 static thread_local std::string g_create_error;
@@ -87,6 +96,14 @@ static void free_all(traj_batch *b) {
     if (p) cudaFree(p);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+}
+
+static void invalidate_graph(traj_batch *b) {
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  b->graph_exec = nullptr;
+  b->graph_valid = false;
 }
 
 extern "C" {
@@ -167,6 +184,8 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
       (e = dalloc(&b->d_flags, 1)) || (e = dalloc(&b->d_t0, 1)))
     return bail("cudaMalloc", e);
   if ((e = cudaEventCreate(&b->ev0)) || (e = cudaEventCreate(&b->ev1))) return bail("cudaEventCreate", e);
+  if ((e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking)))
+    return bail("cudaStreamCreateWithFlags", e);
   *out = b;
   return TRAJ_OK;
 }
@@ -225,6 +244,7 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
   b->n_problems = n_problems;
   b->max_np_used = max_np;
   b->have_problems = true;
+  invalidate_graph(b);
   b->have_obstacles = false;
   b->have_result = false;
   b->err.clear();
@@ -284,6 +304,7 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
   b->obs_offsets.assign(offsets, offsets + P + 1);
   b->n_obs = N;
   b->have_obstacles = true;
+  invalidate_graph(b);
   b->have_result = false;
   b->err.clear();
   return TRAJ_OK;
@@ -314,6 +335,7 @@ traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
   b->traj_problem.assign(traj_problem, traj_problem + n_traj);
   b->n_traj = n_traj;
   b->have_initial = true;
+  invalidate_graph(b);
   b->have_result = false;
   b->err.clear();
   return TRAJ_OK;
@@ -351,11 +373,34 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   a.queue = b->d_queue;
   a.t0 = b->d_t0;
   a.flags = b->d_flags;
-  CK(b, cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream));
-  CK(b, cudaMemsetAsync(b->d_flags, 0, sizeof(int), b->stream));
-  CK(b, cudaMemsetAsync(b->d_t0, 0, sizeof(unsigned long long), b->stream));
+  const bool same = b->graph_valid && b->g_max_iters == max_iters && b->g_tol == tol &&
+                    b->g_timeout == a.timeout_ns && b->g_n_traj == b->n_traj &&
+                    b->g_warps == b->shape.warps_per_block && b->g_bps == b->shape.blocks_per_sm;
+  if (!same) {
+    // capture {clear counters; persistent solve} on the handle's capture stream
+    invalidate_graph(b);
+    cudaStream_t cs = b->capture_stream;
+    CK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaMemsetAsync(b->d_queue, 0, sizeof(int), cs);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_flags, 0, sizeof(int), cs);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_t0, 0, sizeof(unsigned long long), cs);
+    if (ce == cudaSuccess)
+      ce = launch_am_solve(b->cfg.dim, b->max_np_used, b->cfg.precision, a, b->shape, b->n_sm, cs, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->graph_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      invalidate_graph(b);
+      return fail(b, TRAJ_ECUDA, std::string("solve graph capture: ") + cudaGetErrorString(ce));
+    }
+    b->graph_valid = true;
+    b->g_max_iters = max_iters; b->g_tol = tol; b->g_timeout = a.timeout_ns;
+    b->g_n_traj = b->n_traj; b->g_warps = b->shape.warps_per_block; b->g_bps = b->shape.blocks_per_sm;
+  }
   CK(b, cudaEventRecord(b->ev0, b->stream));
-  CK(b, launch_am_solve(b->cfg.dim, b->max_np_used, b->cfg.precision, a, b->n_sm, b->stream));
+  CK(b, cudaGraphLaunch(b->graph_exec, b->stream));
   CK(b, cudaEventRecord(b->ev1, b->stream));
   b->have_result = true;
   if (!stats) return TRAJ_OK;
@@ -415,6 +460,45 @@ traj_status traj_get_state(traj_batch *b, float *lambda, float *u) {
   if (u) { CK(b, cudaMemcpyAsync(u, b->d_u, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(u); }
   if (host) CK(b, cudaStreamSynchronize(b->stream));
   return TRAJ_OK;
+}
+
+traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape) {
+  if (!b || !shape) return TRAJ_EINVAL;
+  if (shape->warps_per_block < 1 || shape->warps_per_block > 8 || shape->blocks_per_sm < 0)
+    return fail(b, TRAJ_EINVAL, "warps_per_block must be in [1, 8], blocks_per_sm >= 0");
+  b->shape = LaunchShape{shape->warps_per_block, shape->blocks_per_sm, 0};
+  invalidate_graph(b);
+  return TRAJ_OK;
+}
+
+traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, float *best_ms) {
+  if (!b) return TRAJ_EINVAL;
+  if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
+  if (iters < 1) return fail(b, TRAJ_EINVAL, "iters must be >= 1");
+  static const int cand_w[] = {1, 2, 4, 8};
+  static const int cand_b[] = {0, 1, 2, 4};
+  LaunchShape best{4, 0, 0};
+  float best_t = 1e30f;
+  for (int w : cand_w)
+    for (int bps : cand_b) {
+      b->shape = LaunchShape{w, bps, 0};
+      invalidate_graph(b);
+      float tot = 0.f;
+      bool ok = true;
+      for (int r = 0; r < 3 && ok; ++r) { // first run captures the graph, then two timed replays
+        traj_solve_stats st{};
+        traj_status rc = traj_solve(b, iters, -1.0f, 0.0, &st);
+        if (rc != TRAJ_OK && rc != TRAJ_NOT_CONVERGED) ok = false;
+        else if (r > 0) tot += st.gpu_ms;
+      }
+      if (ok && tot < best_t) { best_t = tot; best = b->shape; }
+    }
+  b->shape = best;
+  invalidate_graph(b);
+  b->have_result = false;
+  if (chosen) { chosen->warps_per_block = best.warps_per_block; chosen->blocks_per_sm = best.blocks_per_sm; }
+  if (best_ms) *best_ms = best_t / 2.f;
+  return best_t < 1e30f ? TRAJ_OK : fail(b, TRAJ_ECUDA, "no launch shape ran");
 }
 
 traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_per_s) {

@@ -44,6 +44,10 @@ class SolveStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class LaunchShape(ctypes.Structure):
+    _fields_ = [("warps_per_block", _c_int), ("blocks_per_sm", _c_int)]
+
+
 class TrajBatchError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -81,13 +85,16 @@ def load_library():
     lib.traj_last_error.argtypes = [_vp]
     lib.traj_last_error.restype = ctypes.c_char_p
     lib.traj_measure_fp32_peak.argtypes = [_vp, _c_int, ctypes.POINTER(_c_double)]
+    lib.traj_set_launch_shape.argtypes = [_vp, ctypes.POINTER(LaunchShape)]
+    lib.traj_autotune.argtypes = [_vp, _c_int, ctypes.POINTER(LaunchShape),
+                                  ctypes.POINTER(_c_float)]
     lib.traj_solve_noalloc.argtypes = [ctypes.POINTER(TrajConfig), _c_int, _vp, _vp, _vp, _vp,
                                        _vp, _vp, _vp, _vp, _c_int, _vp, _vp, _c_int, _c_float,
                                        _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
                  "traj_set_obstacles", "traj_set_initial", "traj_solve",
                  "traj_get_trajectories", "traj_get_state", "traj_measure_fp32_peak",
-                 "traj_solve_noalloc"):
+                 "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune"):
         getattr(lib, name).restype = _c_int
     _LIB = lib
     return lib
@@ -209,6 +216,18 @@ class TrajBatch:
         s, ks = _ptr(status, np.int8)
         self._check(self._lib.traj_get_trajectories(self._h, c, r, i, s))
         return dict(xi=coeffs, residual=residual, iters=iters, status=status)
+
+    def set_launch_shape(self, warps_per_block, blocks_per_sm=0):
+        self._check(self._lib.traj_set_launch_shape(
+            self._h, ctypes.byref(LaunchShape(int(warps_per_block), int(blocks_per_sm)))))
+
+    def autotune(self, iters=20):
+        """Time the candidate launch shapes on this batch; keep and return the fastest."""
+        shape, ms = LaunchShape(), _c_float(0.0)
+        self._check(self._lib.traj_autotune(self._h, int(iters), ctypes.byref(shape),
+                                            ctypes.byref(ms)))
+        return dict(warps_per_block=shape.warps_per_block, blocks_per_sm=shape.blocks_per_sm,
+                    ms=ms.value)
 
     def get_state(self):
         lam = np.zeros((self.n_traj, self.dim, 11), np.float32)

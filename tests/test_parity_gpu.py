@@ -187,3 +187,30 @@ def test_deadline_stops_every_trajectory():
     g = gpu_solve(b, 100000, tol=-1.0, timeout_ms=1e-6)
     assert g["stats"].get("error") == -5
     assert np.all(g["status"] == 3) and np.all(g["iters"] < 100000)
+
+
+def test_launch_shape_graph_replay_and_autotune_do_not_change_results():
+    """Uneven batch in one persistent launch: every launch shape, a replayed
+    CUDA graph and the autotuned shape give bitwise the same trajectories."""
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = reduced_config4(16, seed=4, inits=3)
+    h = tb.from_batch(b)
+    try:
+        ref = None
+        for w, bps in ((1, 0), (4, 1), (8, 2), (2, 0)):
+            h.set_launch_shape(w, bps)
+            for _ in range(2):  # capture, then replay
+                h.solve(25, tol=-1.0)
+                out = h.get_trajectories()
+                if ref is None:
+                    ref = out
+                np.testing.assert_array_equal(out["xi"], ref["xi"])
+                np.testing.assert_array_equal(out["iters"], ref["iters"])
+        choice = h.autotune(5)
+        assert 1 <= choice["warps_per_block"] <= 8 and choice["ms"] > 0
+        h.solve(25, tol=-1.0)
+        np.testing.assert_array_equal(h.get_trajectories()["xi"], ref["xi"])
+    finally:
+        h.close()
+    o = am.solve(b, 25, tol=-1.0)
+    assert position_error(b, ref["xi"], o["xi"]).max() <= POS_TOL
