@@ -212,6 +212,40 @@ traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape)
  * the previous solve's results are discarded. No paper counterpart. */
 traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, float *best_ms);
 
+/* ---- Projection-guided sampler (Paper III, Algorithm 3) ---------------------
+ * Settings of one outer iteration. Samples are drawn from N(mu, Sigma + eps I);
+ * n_inner projection iterations (Algorithm 2 order with Q = I, q = -sample,
+ * eq. matrix_vec); r = the worst of the three L-infinity residuals; the
+ * n_proj lowest r form the ConstraintEliteSet, the n_elite lowest
+ * c_aug = sum_t ||p''(t)||^2 + w_res * r among them the EliteSet; weights
+ * exp(-(c_aug - min c_aug) / gamma); mean and covariance move by sigma_lr
+ * toward the weighted elite mean/covariance (eqs. update_mean,
+ * update_covariance; the covariance about the new mean). */
+typedef struct traj_sampler_config {
+  int n_inner, n_proj, n_elite;
+  float gamma, sigma_lr, eps, w_res;
+  unsigned long long seed; /* Philox4x32-10 key (counter = sample, iteration, pair, 0) */
+} traj_sampler_config;
+
+/* Optional device copies of one step's intermediates (each nullable):
+ * samples and projected [n_traj][dim*11], residual and cost_aug [n_traj],
+ * proj_idx [n_proj] and elite_idx [n_elite] (ascending by key, ties by index). */
+typedef struct traj_sampler_trace {
+  float *samples, *projected, *residual, *cost_aug;
+  int *proj_idx, *elite_idx;
+} traj_sampler_trace;
+
+/* One outer iteration of Algorithm 3 on problem 0 of a TRAJ_COST_PROJECT
+ * handle whose n_traj trajectories (<= 8192) all belong to problem 0.
+ * mu [dim*11] and sigma [(dim*11)^2] are device arrays updated in place
+ * (coefficient order [axis][11]); z is a device array [n_traj][dim*11] of
+ * standard normal draws, or NULL to draw them on the device with Philox and
+ * Box-Muller; best [dim*11 + 1] receives the lowest-c_aug elite and its c_aug.
+ * Asynchronous on the handle's stream. */
+traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *cfg, int iteration,
+                              float *mu, float *sigma, const float *z, float *best,
+                              const traj_sampler_trace *trace);
+
 /* Human-readable name of a status code (static string). */
 const char *traj_status_string(traj_status s);
 

@@ -124,6 +124,15 @@ struct LaunchShape {
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s,
                             LaunchShape *used);
+cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int B, float eps,
+                                 const float *z, unsigned long long seed, int iteration,
+                                 float *L_scratch, int *flag, float *xi0, float *samples_out,
+                                 cudaStream_t s);
+cudaError_t launch_sampler_back(const float *xi, const float *res, const float *tables,
+                                int tbl_off, int n_p, float invT2, int dim, int B, float w_r,
+                                int n_proj, int n_elite, float gamma, float sig, float *r_out,
+                                float *caug_out, int *proj_idx, int *elite_idx, float *mu,
+                                float *sigma, float *best, cudaStream_t s);
 cudaError_t launch_ffma_peak(float *out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_ffma2_peak(float *out, int blocks, int iters, cudaStream_t s);
 } // namespace tb

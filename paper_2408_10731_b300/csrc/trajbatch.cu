@@ -51,6 +51,10 @@ struct traj_batch {
   int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1;
   float g_tol = 0.f;
   unsigned long long g_timeout = 0;
+  std::vector<int> tbl_off; // per problem, float offset of its basis tables
+  // sampler scratch (allocated at creation from max_traj)
+  float *d_L = nullptr, *d_r = nullptr, *d_caug = nullptr;
+  int *d_proj = nullptr, *d_elite = nullptr, *d_sflag = nullptr;
 };
 
 static thread_local std::string g_create_error;
@@ -91,7 +95,8 @@ static void free_all(traj_batch *b) {
   void *ptrs[] = {b->d_problems, b->d_T, b->d_start, b->d_goal, b->d_constants, b->d_tables,
                   b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_problem,
                   b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res,
-                  b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0};
+                  b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0, b->d_L, b->d_r,
+                  b->d_caug, b->d_proj, b->d_elite, b->d_sflag};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (b->ev0) cudaEventDestroy(b->ev0);
@@ -181,7 +186,9 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
       (e = dalloc(&b->d_xi, B * D * NC)) || (e = dalloc(&b->d_lam, B * D * NC)) ||
       (e = dalloc(&b->d_u, B * D * NC)) || (e = dalloc(&b->d_res, B * 3)) ||
       (e = dalloc(&b->d_iters, B)) || (e = dalloc(&b->d_status, B)) || (e = dalloc(&b->d_queue, 1)) ||
-      (e = dalloc(&b->d_flags, 1)) || (e = dalloc(&b->d_t0, 1)))
+      (e = dalloc(&b->d_flags, 1)) || (e = dalloc(&b->d_t0, 1)) || (e = dalloc(&b->d_L, 48 * 48)) ||
+      (e = dalloc(&b->d_r, B)) || (e = dalloc(&b->d_caug, B)) || (e = dalloc(&b->d_proj, B)) ||
+      (e = dalloc(&b->d_elite, B)) || (e = dalloc(&b->d_sflag, 1)))
     return bail("cudaMalloc", e);
   if ((e = cudaEventCreate(&b->ev0)) || (e = cudaEventCreate(&b->ev1))) return bail("cudaEventCreate", e);
   if ((e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking)))
@@ -272,6 +279,7 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
   std::sort(hz.begin(), hz.end());
   hz.erase(std::unique(hz.begin(), hz.end()), hz.end());
   std::vector<ProblemDev> recs(P);
+  std::vector<int> tbl_host(P);
   for (int p = 0; p < P; ++p) {
     ProblemDev r{};
     r.n_p = b->n_steps[p];
@@ -280,6 +288,7 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
     int off = 0;
     for (int h : hz) { if (h == r.n_p) break; off += table_floats(h); }
     r.tbl_off = off;
+    tbl_host[p] = off;
     const double T = b->duration[p];
     r.dt = (float)(T / (double)(r.n_p - 1));
     r.invT = (float)(1.0 / T);
@@ -302,6 +311,7 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
                               b->d_constants, b->stream));
   CK(b, cudaStreamSynchronize(b->stream));
   b->obs_offsets.assign(offsets, offsets + P + 1);
+  b->tbl_off = tbl_host;
   b->n_obs = N;
   b->have_obstacles = true;
   invalidate_graph(b);
@@ -499,6 +509,42 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
   if (chosen) { chosen->warps_per_block = best.warps_per_block; chosen->blocks_per_sm = best.blocks_per_sm; }
   if (best_ms) *best_ms = best_t / 2.f;
   return best_t < 1e30f ? TRAJ_OK : fail(b, TRAJ_ECUDA, "no launch shape ran");
+}
+
+traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *sc, int iteration,
+                              float *mu, float *sigma, const float *z, float *best,
+                              const traj_sampler_trace *trace) {
+  if (!b) return TRAJ_EINVAL;
+  if (!sc || !mu || !sigma || !best) return fail(b, TRAJ_EINVAL, "NULL sampler argument");
+  if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
+  if (b->cfg.cost_mode != TRAJ_COST_PROJECT)
+    return fail(b, TRAJ_ESTATE, "the sampler needs a handle in TRAJ_COST_PROJECT mode");
+  const int B = b->n_traj, D = b->cfg.dim * NC;
+  for (int k = 0; k < B; ++k)
+    if (b->traj_problem[k] != 0) return fail(b, TRAJ_EINVAL, "sampler trajectories must all belong to problem 0");
+  if (B > 8192) return fail(b, TRAJ_ESHAPE, "sampler batch must be <= 8192");
+  if (sc->n_inner < 0 || sc->n_proj < 1 || sc->n_proj > B || sc->n_elite < 1 ||
+      sc->n_elite > sc->n_proj || !(sc->gamma > 0) || !(sc->sigma_lr > 0) || sc->sigma_lr > 1 ||
+      !(sc->eps >= 0) || !(sc->w_res >= 0))
+    return fail(b, TRAJ_EINVAL, "sampler config out of range");
+  CK(b, launch_sampler_front(mu, sigma, D, B, sc->eps, z, sc->seed, iteration, b->d_L, b->d_sflag,
+                             b->d_xi0, trace ? trace->samples : nullptr, b->stream));
+  traj_status rc = traj_solve(b, sc->n_inner, -1.0f, 0.0, nullptr);
+  if (rc != TRAJ_OK) return rc;
+  const int n_p = b->n_steps[0];
+  const double T = b->duration[0];
+  CK(b, launch_sampler_back(b->d_xi, b->d_res, b->d_tables, b->tbl_off[0], n_p, (float)(1.0 / (T * T)),
+                            b->cfg.dim, B, sc->w_res, sc->n_proj, sc->n_elite, sc->gamma,
+                            sc->sigma_lr, b->d_r, b->d_caug, b->d_proj, b->d_elite, mu, sigma, best,
+                            b->stream));
+  if (trace) {
+    if (trace->projected) CK(b, cudaMemcpyAsync(trace->projected, b->d_xi, sizeof(float) * B * D, cudaMemcpyDeviceToDevice, b->stream));
+    if (trace->residual) CK(b, cudaMemcpyAsync(trace->residual, b->d_r, sizeof(float) * B, cudaMemcpyDeviceToDevice, b->stream));
+    if (trace->cost_aug) CK(b, cudaMemcpyAsync(trace->cost_aug, b->d_caug, sizeof(float) * B, cudaMemcpyDeviceToDevice, b->stream));
+    if (trace->proj_idx) CK(b, cudaMemcpyAsync(trace->proj_idx, b->d_proj, sizeof(int) * sc->n_proj, cudaMemcpyDeviceToDevice, b->stream));
+    if (trace->elite_idx) CK(b, cudaMemcpyAsync(trace->elite_idx, b->d_elite, sizeof(int) * sc->n_elite, cudaMemcpyDeviceToDevice, b->stream));
+  }
+  return TRAJ_OK;
 }
 
 traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_per_s) {

@@ -48,6 +48,17 @@ class LaunchShape(ctypes.Structure):
     _fields_ = [("warps_per_block", _c_int), ("blocks_per_sm", _c_int)]
 
 
+class SamplerConfig(ctypes.Structure):
+    _fields_ = [("n_inner", _c_int), ("n_proj", _c_int), ("n_elite", _c_int), ("gamma", _c_float),
+                ("sigma_lr", _c_float), ("eps", _c_float), ("w_res", _c_float),
+                ("seed", ctypes.c_ulonglong)]
+
+
+class SamplerTrace(ctypes.Structure):
+    _fields_ = [("samples", _c_void_p), ("projected", _c_void_p), ("residual", _c_void_p),
+                ("cost_aug", _c_void_p), ("proj_idx", _c_void_p), ("elite_idx", _c_void_p)]
+
+
 class TrajBatchError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -88,13 +99,16 @@ def load_library():
     lib.traj_set_launch_shape.argtypes = [_vp, ctypes.POINTER(LaunchShape)]
     lib.traj_autotune.argtypes = [_vp, _c_int, ctypes.POINTER(LaunchShape),
                                   ctypes.POINTER(_c_float)]
+    lib.traj_sampler_step.argtypes = [_vp, ctypes.POINTER(SamplerConfig), _c_int, _vp, _vp, _vp,
+                                      _vp, ctypes.POINTER(SamplerTrace)]
     lib.traj_solve_noalloc.argtypes = [ctypes.POINTER(TrajConfig), _c_int, _vp, _vp, _vp, _vp,
                                        _vp, _vp, _vp, _vp, _c_int, _vp, _vp, _c_int, _c_float,
                                        _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
                  "traj_set_obstacles", "traj_set_initial", "traj_solve",
                  "traj_get_trajectories", "traj_get_state", "traj_measure_fp32_peak",
-                 "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune"):
+                 "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune",
+                 "traj_sampler_step"):
         getattr(lib, name).restype = _c_int
     _LIB = lib
     return lib
@@ -228,6 +242,21 @@ class TrajBatch:
                                             ctypes.byref(ms)))
         return dict(warps_per_block=shape.warps_per_block, blocks_per_sm=shape.blocks_per_sm,
                     ms=ms.value)
+
+    def sampler_step(self, cfg: dict, iteration, mu, sigma, best, z=None, trace=None):
+        """One outer iteration of the projection-guided sampler (device tensors)."""
+        sc = SamplerConfig(int(cfg["n_inner"]), int(cfg["n_proj"]), int(cfg["n_elite"]),
+                           float(cfg["gamma"]), float(cfg["sigma_lr"]), float(cfg["eps"]),
+                           float(cfg.get("w_res", 1.0)), int(cfg.get("seed", 0)))
+        tr = None
+        if trace is not None:
+            tr = SamplerTrace(*[_ptr(trace.get(k), dt)[0] for k, dt in (
+                ("samples", np.float32), ("projected", np.float32), ("residual", np.float32),
+                ("cost_aug", np.float32), ("proj_idx", np.int32), ("elite_idx", np.int32))])
+        self._check(self._lib.traj_sampler_step(
+            self._h, ctypes.byref(sc), int(iteration), _ptr(mu, np.float32)[0],
+            _ptr(sigma, np.float32)[0], _ptr(z, np.float32)[0], _ptr(best, np.float32)[0],
+            ctypes.byref(tr) if tr is not None else None))
 
     def get_state(self):
         lam = np.zeros((self.n_traj, self.dim, 11), np.float32)

@@ -1,0 +1,122 @@
+"""GPU parity of the projection-guided sampler (Algorithm 3) against the oracle.
+
+Every stage of every outer iteration is compared with the oracle run on the
+GPU's own inputs to that stage, so that a discrete decision (which samples are
+elites) is always taken on the same FP32 keys on both sides.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import am, priest
+from paper_2408_10731_b300 import scenes
+from tests.gpu_helpers import POS_TOL, position_error
+
+pytestmark = pytest.mark.gpu
+
+
+def _handle(B, seed=0):
+    from paper_2408_10731_b300 import trajbatch as tb
+    c3 = scenes.config3(seed, n_traj=B)
+    b = c3["batch"]
+    return c3, b, tb.from_batch(b, cost_mode="project")
+
+
+def _cuda(x, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype or torch.float32, device="cuda")
+
+
+def test_philox_box_muller_draws_match_oracle():
+    import torch
+    c3, b, h = _handle(64)
+    try:
+        D = 33
+        mu, sigma, best = _cuda(np.zeros(D)), _cuda(np.eye(D)), _cuda(np.zeros(D + 1))
+        samples = torch.zeros(64, D, device="cuda")
+        cfg = dict(n_inner=0, n_proj=64, n_elite=8, gamma=1.0, sigma_lr=0.5, eps=0.0, seed=1234)
+        h.sampler_step(cfg, 3, mu, sigma, best, trace=dict(samples=samples))
+        z = priest.philox_normals(64, D, 1234, 3)
+        np.testing.assert_allclose(samples.cpu().numpy(), z, atol=2e-5, rtol=2e-6)
+    finally:
+        h.close()
+
+
+def test_sampler_steps_match_oracle_stagewise():
+    import torch
+    B = 256
+    c3, b, h = _handle(B)
+    D = 33
+    cfg = dict(n_inner=20, n_proj=math.ceil(0.73 * B), n_elite=math.ceil(0.10 * B), gamma=1.0,
+               sigma_lr=0.5, eps=1e-6, w_res=1.0, seed=0)
+    mu, sigma, best = _cuda(c3["mu0"]), _cuda(c3["sigma0"]), _cuda(np.zeros(D + 1))
+    try:
+        for it in range(3):
+            z = scenes.normal_draws(100 + it, (B, D))
+            mu_in = mu.cpu().numpy().astype(np.float64)
+            sig_in = sigma.cpu().numpy().astype(np.float64)
+            tr = dict(samples=torch.zeros(B, D, device="cuda"),
+                      projected=torch.zeros(B, D, device="cuda"),
+                      residual=torch.zeros(B, device="cuda"), cost_aug=torch.zeros(B, device="cuda"),
+                      proj_idx=torch.zeros(cfg["n_proj"], dtype=torch.int32, device="cuda"),
+                      elite_idx=torch.zeros(cfg["n_elite"], dtype=torch.int32, device="cuda"))
+            h.sampler_step(cfg, it, mu, sigma, best, z=_cuda(z), trace=tr)
+            g = {k: v.cpu().numpy() for k, v in tr.items()}
+            # draw
+            ref = priest.sample(mu_in, sig_in, z, cfg["eps"])
+            np.testing.assert_allclose(g["samples"], ref, atol=5e-5, rtol=1e-5)
+            # projection (Algorithm 2 in projection mode) from the GPU's samples
+            xs = g["samples"].astype(np.float64).reshape(B, 3, 11)
+            o = am.solve(b, cfg["n_inner"], tol=-1.0, cost_mode=1, xi0=xs)
+            err = position_error(b, g["projected"].reshape(B, 3, 11), o["xi"])
+            assert err.max() <= POS_TOL, err.max()
+            # residuals and costs of the GPU's projected trajectories
+            r_o, c_o = priest.costs(b, g["projected"].astype(np.float64), o["residual"])
+            np.testing.assert_allclose(g["residual"], r_o, atol=2e-5, rtol=1e-4)
+            np.testing.assert_allclose(g["cost_aug"], c_o, atol=1e-4, rtol=2e-5)
+            # selections on the GPU's own FP32 keys: exact
+            p_o, e_o = priest.select(g["residual"], g["cost_aug"], cfg["n_proj"], cfg["n_elite"])
+            np.testing.assert_array_equal(g["proj_idx"], p_o)
+            np.testing.assert_array_equal(g["elite_idx"], e_o)
+            # mean / covariance update from the GPU's elites
+            m_o, s_o, best_o, bc_o = priest.refit(g["projected"].astype(np.float64),
+                                                  g["cost_aug"].astype(np.float64), e_o, mu_in,
+                                                  sig_in, cfg["gamma"], cfg["sigma_lr"])
+            np.testing.assert_allclose(mu.cpu().numpy(), m_o, rtol=1e-4, atol=1e-4)
+            np.testing.assert_allclose(sigma.cpu().numpy(), s_o, rtol=1e-3, atol=1e-4)
+            np.testing.assert_array_equal(best.cpu().numpy()[:D], g["projected"][e_o[0]])
+    finally:
+        h.close()
+
+
+def test_full_size_sampler_run_invariants():
+    """The 3D workload at full size: 4096 samples, 10 outer x 20 inner iterations,
+    on-device Philox draws."""
+    import torch
+    B = 4096
+    c3, b, h = _handle(B)
+    D = 33
+    cfg = dict(n_inner=c3["n_inner"], n_proj=c3["n_proj"], n_elite=c3["n_elite"], gamma=1.0,
+               sigma_lr=0.5, eps=1e-6, w_res=1.0, seed=7)
+    mu, sigma, best = _cuda(c3["mu0"]), _cuda(c3["sigma0"]), _cuda(np.zeros(D + 1))
+    caug = torch.zeros(B, device="cuda")
+    elite = torch.zeros(cfg["n_elite"], dtype=torch.int32, device="cuda")
+    try:
+        for it in range(c3["n_outer"]):
+            h.sampler_step(cfg, it, mu, sigma, best, trace=dict(cost_aug=caug, elite_idx=elite))
+        torch.cuda.synchronize()
+        S = sigma.cpu().numpy(); e = elite.cpu().numpy(); c = caug.cpu().numpy()
+        assert np.all(np.isfinite(S)) and np.all(np.isfinite(mu.cpu().numpy()))
+        np.testing.assert_allclose(S, S.T, rtol=1e-5, atol=1e-6)
+        assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > -1e-4
+        assert len(set(e.tolist())) == len(e) and e.min() >= 0 and e.max() < B
+        assert np.all(np.diff(c[e]) >= 0)
+        assert best.cpu().numpy()[D] == c[e[0]]
+        # the best elite is a projected trajectory: boundary rows hold
+        P, Pd, Pdd = am.bernstein(100, 20.0)
+        xb = best.cpu().numpy()[:D].reshape(3, 11).astype(np.float64)
+        np.testing.assert_allclose(xb @ P[0], b.start[0], atol=1e-3)
+        np.testing.assert_allclose(xb @ P[-1], b.goal[0], atol=1e-3)
+    finally:
+        h.close()
