@@ -246,6 +246,15 @@ traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *cfg, int
                               float *mu, float *sigma, const float *z, float *best,
                               const traj_sampler_trace *trace);
 
+/* BF16 tensor-core GEMM, the building block of the warm-start network:
+ * C[M][N] = A[M][K] * B[N][K]^T with FP32 accumulation (tcgen05, TMA-staged
+ * operands). A, B: device BF16, row-major, K % 8 == 0, 16-byte aligned; C:
+ * device FP32 [M][N]; err: device int whose bit 0 is set if a pipeline wait
+ * expired (the result is then incomplete). Asynchronous on the stream. No
+ * paper counterpart. */
+traj_status traj_gemm_bf16(int M, int N, int K, const void *A, const void *B, float *C, int *err,
+                           void *cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char *traj_status_string(traj_status s);
 

@@ -1,0 +1,275 @@
+// gemm_tc.cu -- BF16 GEMM on the 5th-generation tensor cores (tcgen05) with
+// TMA-staged operands, for the warm-start network's training and inference.
+//
+//   C[M x N] = A[M x K] * B[N x K]^T,   A, B row-major BF16 (K contiguous),
+//   FP32 accumulation in tensor memory, fused epilogues (bias, GELU, GELU').
+//
+// One CTA computes one 128 x 128 tile with 4 warps: warp 0 lane 0 streams
+// 128 x 64 A and B tiles into shared memory with TMA (128-byte swizzle, a
+// 4-stage ring of mbarriers), warp 1 lane 0 issues tcgen05.mma (kind::f16,
+// M = 128, N = 128, K = 16 per instruction) into a 128-column FP32
+// accumulator in TMEM and commits each stage back to the producer, and all
+// four warps read the accumulator with tcgen05.ld (warp w owns rows
+// 32w..32w+31) for the epilogue. Every mbarrier wait is bounded: on
+// expiry the CTA sets the error flag, skips the remaining work, still frees
+// its TMEM and returns.
+#include "internal.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math.h>
+#include <mutex>
+
+namespace tb {
+
+constexpr int GM_BM = 128, GM_BN = 128, GM_BK = 64, GM_STAGES = 4;
+constexpr int GM_TILE_A = GM_BM * GM_BK * 2;
+constexpr int GM_TILE_B = GM_BN * GM_BK * 2;
+constexpr int GM_SMEM = GM_STAGES * (GM_TILE_A + GM_TILE_B) + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t GM_WAIT_LIMIT = 1u << 22;
+
+struct GemmArgs {
+  int M, N, K;
+  float *out_f32;           // EPI_F32 / EPI_BIAS_F32: C; EPI_BIAS_GELU: pre-activation Z
+  __nv_bfloat16 *out_bf16;  // EPI_BIAS_GELU: GELU(Z); EPI_GELU_BWD: dZ = C * GELU'(Z)
+  int ldo;                  // row stride of the outputs (elements)
+  const float *bias;        // [N] (bias epilogues)
+  const float *aux;         // EPI_GELU_BWD: Z [M][ldo]
+  int *err;                 // bit 0 set if a wait expired
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < GM_WAIT_LIMIT; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+// Shared-memory matrix descriptor: K-major tile written by TMA with the
+// 128-byte swizzle (8-row atoms of 1024 B): start address, LBO 16 B (unused
+// for this layout), SBO 1024 B between 8-row groups, descriptor version 1,
+// layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float gelu_tanh(float z) {
+  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+  return 0.5f * z * (1.f + tanhf(k0 * (z + k1 * z * z * z)));
+}
+
+__device__ __forceinline__ float gelu_tanh_grad(float z) {
+  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+  const float t = tanhf(k0 * (z + k1 * z * z * z));
+  return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * k0 * (1.f + 3.f * k1 * z * z);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128, 1)
+k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ GemmArgs g) {
+  extern __shared__ uint8_t gm_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gm_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + GM_STAGES * GM_TILE_A;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sB + GM_STAGES * GM_TILE_B);
+  uint64_t *empty = full + GM_STAGES;
+  uint64_t *done = empty + GM_STAGES;
+  uint32_t *taddr_s = reinterpret_cast<uint32_t *>(done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * GM_BM, n0 = blockIdx.y * GM_BN;
+  const int KT = (g.K + GM_BK - 1) / GM_BK;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(taddr_s)), "r"((uint32_t)GM_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < GM_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(done)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *taddr_s;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % GM_STAGES;
+      if (kt >= GM_STAGES && !mbar_wait(smem_u32(&empty[s]), ((kt / GM_STAGES) - 1) & 1)) {
+        atomicOr(g.err, 1);
+        break;
+      }
+      const uint32_t fb = smem_u32(&full[s]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                   :: "r"(fb), "r"((uint32_t)(GM_TILE_A + GM_TILE_B)) : "memory");
+      asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                   " [%0], [%1, {%2, %3}], [%4];"
+                   :: "r"(smem_u32(sA + s * GM_TILE_A)), "l"(reinterpret_cast<uint64_t>(&tmA)),
+                      "r"(kt * GM_BK), "r"(m0), "r"(fb) : "memory");
+      asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                   " [%0], [%1, {%2, %3}], [%4];"
+                   :: "r"(smem_u32(sB + s * GM_TILE_B)), "l"(reinterpret_cast<uint64_t>(&tmB)),
+                      "r"(kt * GM_BK), "r"(n0), "r"(fb) : "memory");
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(GM_BM, GM_BN);
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % GM_STAGES;
+      if (!mbar_wait(smem_u32(&full[s]), (kt / GM_STAGES) & 1)) { atomicOr(g.err, 1); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint64_t da = sdesc_sw128(smem_u32(sA + s * GM_TILE_A));
+      const uint64_t db = sdesc_sw128(smem_u32(sB + s * GM_TILE_B));
+#pragma unroll
+      for (int ks = 0; ks < GM_BK / 16; ++ks) {
+        const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                     :: "r"(tmem), "l"(da + 2 * ks), "l"(db + 2 * ks), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&empty[s])) : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(done)) : "memory");
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(smem_u32(done), 0);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (!ok) {
+    if (lane == 0) atomicOr(g.err, 1);
+  } else {
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < GM_BN; c += 16) {
+      uint32_t r[16];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,"
+                   "%11,%12,%13,%14,%15}, [%16];"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                     "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                     "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                   : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < g.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c + j;
+          if (col >= g.N) continue;
+          const float v = __uint_as_float(r[j]);
+          const size_t o = (size_t)row * g.ldo + col;
+          if constexpr (EPI == 0) {
+            g.out_f32[o] = v;
+          } else if constexpr (EPI == 1) {
+            const float z = v + g.bias[col];
+            if (g.out_f32) g.out_f32[o] = z;
+            g.out_bf16[o] = __float2bfloat16_rn(gelu_tanh(z));
+          } else if constexpr (EPI == 2) {
+            g.out_f32[o] = v + g.bias[col];
+          } else {
+            g.out_bf16[o] = __float2bfloat16_rn(v * gelu_tanh_grad(g.aux[o]));
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem), "r"((uint32_t)GM_BN));
+}
+
+// ---- host ----------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Row-major BF16 matrix [rows][cols] (cols contiguous, cols % 8 == 0, 16-byte aligned base)
+// as a 2D tensor map with 64 x 128 boxes and the 128-byte swizzle; out-of-range
+// elements of a box read as zero.
+static cudaError_t make_map(CUtensorMap *m, const void *ptr, int rows, int cols) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if ((cols % 8) != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)GM_BK, (cuuint32_t)GM_BM};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemm_bf16(int epi, const void *A, const void *B, int M, int N, int K,
+                             float *out_f32, void *out_bf16, int ldo, const float *bias,
+                             const float *aux, int *err, cudaStream_t s) {
+  if (M < 1 || N < 1 || K < 1) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  cudaError_t e = make_map(&ma, A, M, K);
+  if (e != cudaSuccess) return e;
+  if ((e = make_map(&mb, B, N, K)) != cudaSuccess) return e;
+  GemmArgs g{M, N, K, out_f32, reinterpret_cast<__nv_bfloat16 *>(out_bf16), ldo, bias, aux, err};
+  dim3 grid((M + GM_BM - 1) / GM_BM, (N + GM_BN - 1) / GM_BN);
+  switch (epi) {
+  case 0:
+    cudaFuncSetAttribute(k_gemm_bf16<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM);
+    k_gemm_bf16<0><<<grid, 128, GM_SMEM, s>>>(ma, mb, g);
+    break;
+  case 1:
+    cudaFuncSetAttribute(k_gemm_bf16<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM);
+    k_gemm_bf16<1><<<grid, 128, GM_SMEM, s>>>(ma, mb, g);
+    break;
+  case 2:
+    cudaFuncSetAttribute(k_gemm_bf16<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM);
+    k_gemm_bf16<2><<<grid, 128, GM_SMEM, s>>>(ma, mb, g);
+    break;
+  case 3:
+    cudaFuncSetAttribute(k_gemm_bf16<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM);
+    k_gemm_bf16<3><<<grid, 128, GM_SMEM, s>>>(ma, mb, g);
+    break;
+  default:
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+} // namespace tb

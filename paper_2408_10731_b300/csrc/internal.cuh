@@ -133,6 +133,11 @@ cudaError_t launch_sampler_back(const float *xi, const float *res, const float *
                                 int n_proj, int n_elite, float gamma, float sig, float *r_out,
                                 float *caug_out, int *proj_idx, int *elite_idx, float *mu,
                                 float *sigma, float *best, cudaStream_t s);
+// tcgen05 BF16 GEMM C = A B^T (gemm_tc.cu); epi: 0 FP32 store, 1 bias+GELU (Z f32 and
+// GELU(Z) bf16), 2 bias FP32, 3 C * GELU'(aux) -> bf16.
+cudaError_t launch_gemm_bf16(int epi, const void *A, const void *B, int M, int N, int K,
+                             float *out_f32, void *out_bf16, int ldo, const float *bias,
+                             const float *aux, int *err, cudaStream_t s);
 cudaError_t launch_ffma_peak(float *out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_ffma2_peak(float *out, int blocks, int iters, cudaStream_t s);
 } // namespace tb

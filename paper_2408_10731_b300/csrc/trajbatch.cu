@@ -547,6 +547,15 @@ traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *sc, int 
   return TRAJ_OK;
 }
 
+traj_status traj_gemm_bf16(int M, int N, int K, const void *A, const void *B, float *C, int *err,
+                           void *cuda_stream) {
+  if (!A || !B || !C || !err || M < 1 || N < 1 || K < 1 || (K % 8) != 0) return TRAJ_EINVAL;
+  cudaError_t e = launch_gemm_bf16(0, A, B, M, N, K, C, nullptr, N, nullptr, nullptr, err,
+                                   reinterpret_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) { g_create_error = cudaGetErrorString(e); return TRAJ_ECUDA; }
+  return TRAJ_OK;
+}
+
 traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_per_s) {
   if (!flops_per_s || reps < 1) return TRAJ_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);

@@ -101,6 +101,7 @@ def load_library():
                                   ctypes.POINTER(_c_float)]
     lib.traj_sampler_step.argtypes = [_vp, ctypes.POINTER(SamplerConfig), _c_int, _vp, _vp, _vp,
                                       _vp, ctypes.POINTER(SamplerTrace)]
+    lib.traj_gemm_bf16.argtypes = [_c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _vp]
     lib.traj_solve_noalloc.argtypes = [ctypes.POINTER(TrajConfig), _c_int, _vp, _vp, _vp, _vp,
                                        _vp, _vp, _vp, _vp, _c_int, _vp, _vp, _c_int, _c_float,
                                        _vp, _vp, _vp, _vp]
@@ -108,7 +109,7 @@ def load_library():
                  "traj_set_obstacles", "traj_set_initial", "traj_solve",
                  "traj_get_trajectories", "traj_get_state", "traj_measure_fp32_peak",
                  "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune",
-                 "traj_sampler_step"):
+                 "traj_sampler_step", "traj_gemm_bf16"):
         getattr(lib, name).restype = _c_int
     _LIB = lib
     return lib
@@ -264,6 +265,19 @@ class TrajBatch:
         self._check(self._lib.traj_get_state(self._h, _ptr(lam, np.float32)[0],
                                              _ptr(u, np.float32)[0]))
         return dict(lam=lam, u=u)
+
+
+def gemm_bf16(A, B, C, err, stream=None):
+    """C = A B^T on the tensor cores (A [M,K], B [N,K] bf16 CUDA tensors, C [M,N] fp32)."""
+    import torch
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and C.dtype == torch.float32
+    M, K = A.shape
+    N = B.shape[0]
+    rc = load_library().traj_gemm_bf16(M, N, K, A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                                       err.data_ptr(),
+                                       stream if stream is not None else _default_stream())
+    if rc != 0:
+        raise TrajBatchError(rc, load_library().traj_last_error(None).decode())
 
 
 def solve_noalloc(dim, vmax, amax, rho, n_steps, duration, start, goal, obs_offsets, centers,
