@@ -121,7 +121,9 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
 /* Trajectories: traj_problem[n_traj] (host int) maps each trajectory to its
  * problem; coeffs0[n_traj][dim][11] FP32 initial coefficients (host or
  * device). In TRAJ_COST_PROJECT mode coeffs0 are also the samples that the
- * solve projects. Copied; the caller may reuse its buffers at once. */
+ * solve projects. Copied; the caller may reuse its buffers at once.
+ * With traj_problem == NULL and the same n_traj as the previous call, only the
+ * coefficients are replaced (asynchronously for a device source). */
 traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
                              const float *coeffs0);
 
@@ -152,6 +154,10 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
  * asynchronously on the stream; host destinations synchronise. */
 traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual, int *iters,
                                   signed char *status);
+
+/* Smoothness cost of the last solve's trajectories, c_1 = sum_t ||p''(t)||^2
+ * over the grid (PRIEST's acceleration cost), FP32 [n_traj], host or device. */
+traj_status traj_get_accel_cost(traj_batch *b, float *cost);
 
 /* Solver state for checkpoint/resume and warm starts (nullable outputs):
  * multipliers lambda[n_traj][dim][11] and the last residual contraction
@@ -254,6 +260,50 @@ traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *cfg, int
  * paper counterpart. */
 traj_status traj_gemm_bf16(int M, int N, int K, const void *A, const void *B, float *C, int *err,
                            void *cuda_stream);
+
+/* ---- Learned warm start (no paper counterpart: the thesis lists learning-
+ * based methods as future work) ------------------------------------------------
+ * An MLP 388 -> 256 -> 256 -> 256 -> 176 (GELU, tanh form) maps a scene's
+ * features to K = 8 proposal coefficient sets, read as offsets from the
+ * straight-line coefficients. BF16 weights and activations on the tcgen05
+ * tensor cores with FP32 accumulation; FP32 master weights and AdamW
+ * (beta 0.9/0.999, eps 1e-8, decoupled decay on the weight matrices).
+ * Features (388 per scene, stored BF16 in rows of 400): start and goal
+ * relative to the start, x0.1; then the 64 obstacles whose t = 0 centre is
+ * nearest to the start->goal segment (ascending distance, ties by index),
+ * each (cx, cy) relative to the start x0.1, semi-axes (a, b), velocity
+ * (vx, vy); absent slots are zero. 2D only.
+ * Parameters (public flat FP32 order): W1[256][388], b1[256], W2[256][256],
+ * b2, W3[256][256], b3, W4[176][256], b4[176].
+ * Loss: for each solved label t_m of a scene (offsets from the line, up to 8),
+ * min_k ||y_k - t_m||^2 + 0.05 * mean_k ||y_k - t_m||^2, averaged over all
+ * labels of the batch. Rows of a batch: a multiple of 8, <= max_rows. */
+typedef struct traj_warmstart traj_warmstart;
+int traj_warmstart_num_params(void);
+traj_status traj_warmstart_create(int max_rows, void *cuda_stream, traj_warmstart **out);
+traj_status traj_warmstart_destroy(traj_warmstart *w);
+/* params: host or device FP32 [num_params]; resets the optimizer state */
+traj_status traj_warmstart_set_params(traj_warmstart *w, const float *params);
+traj_status traj_warmstart_get_params(traj_warmstart *w, float *params);
+/* start, goal [n][2] FP64 and offsets [n + 1] host; obstacles device FP32 [N][2];
+ * features: device BF16 [n][400]; line: device FP32 [n][22] straight-line coefficients */
+traj_status traj_warmstart_features(traj_warmstart *w, int n_scenes, const double *start,
+                                    const double *goal, const int *offsets, const float *centers,
+                                    const float *semi_axes, const float *velocities,
+                                    void *features, float *line);
+/* proposals: device FP32 [rows][8][2][11] = line + network output */
+traj_status traj_warmstart_forward(traj_warmstart *w, int rows, const void *features,
+                                   const float *line, float *proposals);
+/* targets: device FP32 [rows][8][22] label offsets; n_labels: device int [rows];
+ * loss: device FP32 scalar; grads (nullable): FP32 [num_params], host or device */
+traj_status traj_warmstart_gradients(traj_warmstart *w, int rows, const void *features,
+                                     const float *targets, const int *n_labels, float *grads,
+                                     float *loss);
+traj_status traj_warmstart_train_step(traj_warmstart *w, int rows, const void *features,
+                                      const float *targets, const int *n_labels, float lr,
+                                      float weight_decay, float *loss);
+/* synchronise; TRAJ_ECUDA if a GEMM pipeline wait expired since creation */
+traj_status traj_warmstart_sync(traj_warmstart *w);
 
 /* Human-readable name of a status code (static string). */
 const char *traj_status_string(traj_status s);

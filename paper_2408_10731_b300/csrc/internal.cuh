@@ -138,6 +138,8 @@ cudaError_t launch_sampler_back(const float *xi, const float *res, const float *
 cudaError_t launch_gemm_bf16(int epi, const void *A, const void *B, int M, int N, int K,
                              float *out_f32, void *out_bf16, int ldo, const float *bias,
                              const float *aux, int *err, cudaStream_t s);
+cudaError_t launch_accel_cost(const float *xi, const int *traj_problem, const ProblemDev *problems,
+                              const float *tables, int dim, int B, float *out, cudaStream_t s);
 cudaError_t launch_ffma_peak(float *out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_ffma2_peak(float *out, int blocks, int iters, cudaStream_t s);
 } // namespace tb

@@ -208,6 +208,33 @@ __global__ void k_refit(const float *xi, const float *caug, const int *elite, in
   if (threadIdx.x == 0) best[D] = delta;
 }
 
+// c_1 = sum_t ||p''(t)||^2 of every trajectory of a batch (each with its own problem).
+__global__ void k_accel_cost(const float *xi, const int *traj_problem, const ProblemDev *problems,
+                             const float *tables, int dim, int B, float *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  const ProblemDev pr = problems[traj_problem[i]];
+  const float *tA = tables + pr.tbl_off + 2 * pr.n_p * ROW;
+  float c1 = 0.f;
+  for (int t = 0; t < pr.n_p; ++t) {
+    float a2 = 0.f;
+    for (int a = 0; a < dim; ++a) {
+      float s = 0.f;
+      for (int k = 0; k < NC; ++k) s = fmaf(tA[t * ROW + k], xi[((size_t)i * dim + a) * NC + k], s);
+      s *= pr.invT2;
+      a2 = fmaf(s, s, a2);
+    }
+    c1 += a2;
+  }
+  out[i] = c1;
+}
+
+cudaError_t launch_accel_cost(const float *xi, const int *traj_problem, const ProblemDev *problems,
+                              const float *tables, int dim, int B, float *out, cudaStream_t s) {
+  k_accel_cost<<<(B + 127) / 128, 128, 0, s>>>(xi, traj_problem, problems, tables, dim, B, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int B, float eps,
                                  const float *z, unsigned long long seed, int iteration,
                                  float *L_scratch, int *flag, float *xi0, float *samples_out,

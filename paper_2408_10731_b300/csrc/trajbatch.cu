@@ -324,6 +324,14 @@ traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
                              const float *coeffs0) {
   if (!b) return TRAJ_EINVAL;
   if (!b->have_obstacles) return fail(b, TRAJ_ESTATE, "traj_set_obstacles must come first");
+  if (!traj_problem && coeffs0 && b->have_initial && n_traj == b->n_traj) {
+    // coefficients only: keep the trajectory -> problem map and the work order
+    CK(b, cudaMemcpyAsync(b->d_xi0, coeffs0, sizeof(float) * n_traj * b->cfg.dim * NC,
+                          cudaMemcpyDefault, b->stream));
+    if (is_host_ptr(coeffs0)) CK(b, cudaStreamSynchronize(b->stream));
+    b->have_result = false;
+    return TRAJ_OK;
+  }
   if (!traj_problem || !coeffs0) return fail(b, TRAJ_EINVAL, "NULL trajectory array");
   if (n_traj < 1 || n_traj > b->cfg.max_traj) return fail(b, TRAJ_ESHAPE, "n_traj exceeds max_traj (or < 1)");
   for (int k = 0; k < n_traj; ++k)
@@ -458,6 +466,16 @@ traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual,
   if (iters) { CK(b, cudaMemcpyAsync(iters, b->d_iters, sizeof(int) * B, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(iters); }
   if (status) { CK(b, cudaMemcpyAsync(status, b->d_status, B, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(status); }
   if (host) CK(b, cudaStreamSynchronize(b->stream));
+  return TRAJ_OK;
+}
+
+traj_status traj_get_accel_cost(traj_batch *b, float *cost) {
+  if (!b || !cost) return TRAJ_EINVAL;
+  if (!b->have_result) return fail(b, TRAJ_ESTATE, "no solve has run");
+  CK(b, launch_accel_cost(b->d_xi, b->d_traj_problem, b->d_problems, b->d_tables, b->cfg.dim,
+                          b->n_traj, b->d_r, b->stream));
+  CK(b, cudaMemcpyAsync(cost, b->d_r, sizeof(float) * b->n_traj, cudaMemcpyDefault, b->stream));
+  if (is_host_ptr(cost)) CK(b, cudaStreamSynchronize(b->stream));
   return TRAJ_OK;
 }
 

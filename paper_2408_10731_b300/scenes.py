@@ -175,6 +175,47 @@ def config2(seed: int = 0, n_scenes: int = 128, inits: int = 8, n_obstacles: int
                  vmax=1.5, amax=2.0, rho=1.0, name=f"config2_seed{seed}")
 
 
+def ellipse_scenes(seed: int, n_scenes: int, n_obstacles: int = 50, inits: int = 0,
+                   n_steps: int = 100) -> Batch:
+    """Many config-2-style scenes drawn in bulk (warm-start training and held-out sets).
+
+    Same distributions as config2 (semi-axes U(0.2,0.8), centres U([0,8]^2), speed
+    U(0,1), heading U(0,2pi), start/goal covering rejected), drawn per scene in
+    vectorised rounds of candidates; the first n_obstacles accepted candidates of
+    each scene are kept. `inits` random initialisations N(straight line, 0.5 m).
+    """
+    rng = np.random.default_rng(seed)
+    start = np.array([0.0, 0.0]); goal = np.array([8.0, 8.0]); T = 0.1 * n_steps
+    S, n = n_scenes, n_obstacles
+    cen = np.zeros((S, n, 2)); ax = np.zeros((S, n, 2)); vel = np.zeros((S, n, 2))
+    have = np.zeros(S, np.int64)
+    while np.any(have < n):
+        todo = np.nonzero(have < n)[0]
+        m = 2 * n
+        a = rng.uniform(0.2, 0.8, (todo.size, m, 2))
+        c = rng.uniform(0.0, 8.0, (todo.size, m, 2))
+        speed = rng.uniform(0.0, 1.0, (todo.size, m))
+        head = rng.uniform(0.0, 2.0 * math.pi, (todo.size, m))
+        v = speed[..., None] * np.stack([np.cos(head), np.sin(head)], -1)
+        bad = (((start - c) / a) ** 2).sum(-1) <= 1.0
+        bad |= (((goal - (c + v * T)) / a) ** 2).sum(-1) <= 1.0
+        for r, sidx in enumerate(todo):
+            ok = np.nonzero(~bad[r])[0][: n - have[sidx]]
+            k0 = have[sidx]
+            cen[sidx, k0:k0 + ok.size] = c[r, ok]; ax[sidx, k0:k0 + ok.size] = a[r, ok]
+            vel[sidx, k0:k0 + ok.size] = v[r, ok]
+            have[sidx] += ok.size
+    line = straight_line_coeffs(start, goal)
+    xi0 = (line[None] + rng.normal(0.0, 0.5, (S * inits, 2, N_COEFF))) if inits else \
+        np.zeros((0, 2, N_COEFF))
+    return Batch(dim=2, n_steps=np.full(S, n_steps, np.int32), duration=np.full(S, T),
+                 start=np.tile(start, (S, 1)), goal=np.tile(goal, (S, 1)),
+                 offsets=np.arange(S + 1, dtype=np.int32) * n, centers=f32(cen.reshape(-1, 2)),
+                 semi_axes=f32(ax.reshape(-1, 2)), velocities=f32(vel.reshape(-1, 2)),
+                 traj_problem=np.repeat(np.arange(S, dtype=np.int32), inits), xi0=f32(xi0),
+                 vmax=1.5, amax=2.0, rho=1.0, name=f"ellipses_seed{seed}")
+
+
 def config4(seed: int = 0, n_problems: int = 2048, inits: int = 8) -> Batch:
     """Uneven batch: n_o log-uniform in [4,256], n_p in {50,75,100,150}, T = 0.1 n_p."""
     rng = np.random.default_rng(seed)

