@@ -220,6 +220,7 @@ def main():
     ap.add_argument("--workload", default="config2", choices=["config2", "uneven", "priest"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warmstart", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--ws-scenes", type=int, default=200000)
     args = ap.parse_args()
 
@@ -260,46 +261,58 @@ def main():
 
     # forms: the plain FP32 form from N(straight line, 0.5 m) initialisations, and the
     # learned warm start (network proposals computed inside every timed step)
-    forms = {"plain_fp32": None}
+    handles = {"fp32": h}
+    if args.workload == "config2" and not args.no_mixed:
+        handles["mixed"] = trajbatch.from_batch(batch, precision="mixed")
+    forms = {"plain_fp32": ("fp32", None)}
+    if "mixed" in handles:
+        forms["plain_mixed"] = ("mixed", None)
     ws = None
     if args.workload == "config2" and not args.no_warmstart:
         from paper_2408_10731_b300 import warmstart
         ws, ws_info = warmstart.trained(seed=1000, n_scenes=args.ws_scenes, epochs=20)
-        def ws_init():
+
+        def ws_init(hh):
             X, line = ws.features(batch)
             prop = ws.forward(X, line).reshape(batch.n_traj, 2, 11)
-            h.set_initial(None, prop)
-        forms["warmstart_fp32"] = ws_init
+            hh.set_initial(None, prop)
+        forms["warmstart_fp32"] = ("fp32", ws_init)
+        if "mixed" in handles:
+            forms["warmstart_mixed"] = ("mixed", ws_init)
     xi0_dev = torch.as_tensor(batch.xi0, dtype=torch.float32, device="cuda")
 
-    def run_form(init, steps, timed):
+    def run_form(form, steps, timed):
+        prec, init = form
+        hh = handles[prec]
         if init is None:
-            h.set_initial(None, xi0_dev)
+            hh.set_initial(None, xi0_dev)
         step_ms, kern_ms, solved = [], [], []
         for _ in range(steps):
             flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if init is not None:
-                init()
-            st = h.solve(args.max_iters, args.tol)
+                init(hh)
+            st = hh.solve(args.max_iters, args.tol)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1)); kern_ms.append(st["gpu_ms"]); solved.append(st["n_solved"])
-        return step_ms, kern_ms, solved, h.get_trajectories()
+        return step_ms, kern_ms, solved, hh.get_trajectories()
 
     results = {}
     barrier()
     sampler.mark()
-    for name, init in forms.items():
-        run_form(init, args.warmup, False)
+    for name, form in forms.items():
+        run_form(form, args.warmup, False)
         barrier()
-        results[name] = run_form(init, args.steps, True)
+        results[name] = run_form(form, args.steps, True)
     barrier()
     sampler.mark()
     clocks = sampler.stop()
-    headline = "warmstart_fp32" if "warmstart_fp32" in results else "plain_fp32"
-    step_ms, kern_ms, solved, out = results[headline]
+    headline = next(f for f in ("warmstart_mixed", "warmstart_fp32", "plain_fp32") if f in results)
+    step_ms, kern_ms, solved, out = results["plain_fp32"]
+    h_step_ms, h_kern_ms, h_solved, h_out = results[headline]
+    hh = handles[forms[headline][0]]
 
     # end to end through the public API with pinned host buffers (headline form)
     tp_h = batch.traj_problem.astype(np.int32)
@@ -312,24 +325,24 @@ def main():
     for _ in range(max(3, min(50, args.steps // 2))):
         flush.fill_(1.0); torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if headline == "warmstart_fp32":
+        if headline.startswith("warmstart"):
             # features copy the scene (obstacles, start, goal, offsets) host -> device
             Xw, lw = ws.features(batch)
             prop = ws.forward(Xw, lw).reshape(batch.n_traj, 2, 11)
-            h.set_initial(None, prop)
+            hh.set_initial(None, prop)
         else:
-            h.set_initial(tp_h, xi0_h)
-        h.solve(args.max_iters, args.tol, stats=False)
-        h.get_trajectories(res["coeffs"], res["residual"], res["iters"], res["status"])
+            hh.set_initial(tp_h, xi0_h)
+        hh.solve(args.max_iters, args.tol, stats=False)
+        hh.get_trajectories(res["coeffs"], res["residual"], res["iters"], res["status"])
         e2e_s.append(time.perf_counter() - t0)
         e2e_solved.append(int((res["status"].numpy() == 0).sum()))
     scene_bytes = 3 * batch.centers.size * 4 + batch.start.nbytes + batch.goal.nbytes + \
         batch.offsets.astype(np.int32).nbytes
-    h2d = scene_bytes if headline == "warmstart_fp32" else xi0_h.numel() * 4 + tp_h.nbytes
+    h2d = scene_bytes if headline.startswith("warmstart") else xi0_h.numel() * 4 + tp_h.nbytes
     d2h = sum(t.numel() * t.element_size() for t in res.values())
 
-    total_ms = float(np.sum(step_ms))
-    n_solved = float(np.sum(solved))
+    total_ms = float(np.sum(h_step_ms))
+    n_solved = float(np.sum(h_solved))
     e2e_val = float(np.mean(e2e_solved)) / float(np.mean(e2e_s))
     if world > 1:
         t = torch.tensor([total_ms, n_solved, e2e_val, float(np.mean(e2e_s))], device="cuda",
@@ -350,11 +363,15 @@ def main():
                               "solve_kernel_ms": float(np.mean(km)),
                               "solved_per_step": float(np.mean(sv)),
                               "scenes_with_a_solution": float(ok.reshape(batch.n_problems, -1).any(1).mean()),
-                              "iters_median_solved": float(np.median(o["iters"][ok])) if ok.any() else None}
+                              "iters_median_solved": float(np.median(o["iters"][ok])) if ok.any() else None,
+                              "solve_roofline_frac": (algorithmic_ops(batch, o["iters"]) /
+                                                      (float(np.mean(km)) * 1e-3) /
+                                                      (fp32_peak / 2.0)) if fp32_peak else None}
 
     if rank == 0:
-        ops = algorithmic_ops(batch, out["iters"])
-        kern_s = float(np.mean(kern_ms)) * 1e-3
+        # roofline of the headline step's dominant kernel (the solve)
+        ops = algorithmic_ops(batch, h_out["iters"])
+        kern_s = float(np.mean(h_kern_ms)) * 1e-3
         achieved = ops / kern_s
         peak_ops = fp32_peak / 2.0  # FFMA rate in lane-operations/s (2 FLOP per FMA)
         line = {
@@ -366,18 +383,20 @@ def main():
                        "precision": args.precision, "launch_shape": shape,
                        "l2": "flushed between timed steps (256 MB write, outside the events)",
                        "per_rank_batch": "seed + rank"},
-            "ms_per_batch_solve": float(np.mean(step_ms)),
-            "solved_per_step": float(np.mean(solved)), "trajectories_per_step": batch.n_traj,
-            "iters": {"min": int(out["iters"].min()), "median": int(np.median(out["iters"])),
-                      "max": int(out["iters"].max())},
+            "ms_per_batch_solve": float(np.mean(h_step_ms)),
+            "ms_per_batch_solve_plain_fp32": float(np.mean(step_ms)),
+            "solved_per_step": float(np.mean(h_solved)), "trajectories_per_step": batch.n_traj,
+            "iters": {"min": int(h_out["iters"].min()), "median": int(np.median(h_out["iters"])),
+                      "max": int(h_out["iters"].max())},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Top/s", "frac": achieved / peak_ops, "traffic": None,
-                         "kernel": "k_am_fp32", "peak_source": "measured FFMA microbenchmark "
+                         "kernel": "k_am_mixed" if forms[headline][0] == "mixed" else "k_am_fp32",
+                         "peak_source": "measured FFMA microbenchmark "
                          "(traj_measure_fp32_peak), FP32 lane-ops/s",
                          "algorithmic_ops_per_launch": ops},
             "e2e": {"value": e2e_all, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": args.steps * (7 if headline == "warmstart_fp32" else 1),
+            "gpu_launches": args.steps * (7 if headline.startswith("warmstart") else 1),
             "clocks": clocks,
             "headline_form": headline, "forms": form_summary,
         }
@@ -386,7 +405,8 @@ def main():
             cb.pop("seconds", None)
             line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)
-    h.close()
+    for hx in handles.values():
+        hx.close()
     if world > 1:
         dist.destroy_process_group()
 

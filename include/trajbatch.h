@@ -66,7 +66,10 @@ enum {
 typedef enum {
   TRAJ_PREC_FP32 = 0, /* FP32 state and contractions; compensated FP32 QP step */
   TRAJ_PREC_MIXED = 1 /* residual contraction F^T r on tcgen05 tensor cores (BF16 operands,
-                         FP32 accumulation) plus one FP32 refinement pass at exit */
+                         FP32 accumulation in TMEM) plus one FP32 refinement pass when the
+                         residuals first meet the tolerance (the refined iterate must meet it
+                         too; it may add one iteration past the cap); residuals are always
+                         FP32. Needs one horizon (n_steps) for every problem of a batch. */
 } traj_precision;
 
 typedef enum {

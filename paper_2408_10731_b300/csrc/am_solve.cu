@@ -29,205 +29,11 @@
 // over the warp so that lane 16 a + i owns coefficient i of axis a (axis 2 in
 // 3D: lanes i and 16 + i).
 #include "internal.cuh"
+#include "am_device.cuh"
 
 namespace tb {
 
-constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_WARPS_PER_BLOCK = 8;
-
-// Reduce-scatter of 32 per-lane values: afterwards lane L holds the warp sum of
-// slot L (recursive halving; slot order preserved).
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const bool upper = (lane & s) != 0;
-#pragma unroll
-    for (int k = 0; k < s; ++k) {
-      float send = upper ? v[k] : v[k + s];
-      float keep = upper ? v[k + s] : v[k];
-      v[k] = keep + __shfl_xor_sync(FULL, send, s);
-    }
-  }
-  return v[0];
-}
-
-// 16 slots: plain reduction over lane halves, then reduce-scatter; lane L holds
-// the warp sum of slot (L & 15).
-__device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
-#pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(FULL, v[k], 16);
-#pragma unroll
-  for (int s = 8; s >= 1; s >>= 1) {
-    const bool upper = (lane & s) != 0;
-#pragma unroll
-    for (int k = 0; k < s; ++k) {
-      float send = upper ? v[k] : v[k + s];
-      float keep = upper ? v[k + s] : v[k];
-      v[k] = keep + __shfl_xor_sync(FULL, send, s);
-    }
-  }
-  return v[0];
-}
-
-__device__ __forceinline__ float warp_max(float x) {
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) x = fmaxf(x, __shfl_xor_sync(FULL, x, s));
-  return x;
-}
-
-__device__ __forceinline__ void load_row(const float *row, float (&r)[12]) {
-  const float4 *r4 = reinterpret_cast<const float4 *>(row);
-  float4 a = r4[0], b = r4[1], c = r4[2];
-  r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
-  r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
-  r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
-}
-
-// Evaluate, project and contract one iterate (Algorithm 2 lines 4-6, minus the
-// multiplier update). xa: the iterate's coefficients (all lanes hold all).
-// Returns the per-lane partial contraction in up[DIM][11] and per-lane maxima
-// of ||r_j||^2, ||r_v||^2, ||r_a||^2.
-template <int DIM, int MAXNT>
-__device__ __forceinline__ void project_contract(
-    const float (&xa)[DIM][NC], const float *tP, const float *tD, const float *tA,
-    const float4 *obs, int n_o, int n_p, int nt, float dt, float invT, float invT2, float vmax,
-    float amax, int lane, float (&up)[DIM][NC], float &mo, float &mv, float &ma) {
-  constexpr int OV = obs_vec(DIM);
-  float pos[MAXNT][DIM], acc[MAXNT][DIM], tm[MAXNT];
-  // positions p(t) = P xi at this lane's timesteps; padding lanes get a far sentinel
-#pragma unroll
-  for (int m = 0; m < MAXNT; ++m) {
-    const int t = lane + 32 * m;
-    tm[m] = dt * (float)t;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) { pos[m][a] = 1.0e18f; acc[m][a] = 0.f; }
-    if (m < nt && t < n_p) {
-      float r[12];
-      load_row(tP + t * ROW, r);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < NC; ++i) s = fmaf(r[i], xa[a][i], s);
-        pos[m][a] = s;
-      }
-    }
-  }
-  // pair loop over obstacles: acc accumulates sum_j Delta_j * w_j (r_j = -Delta_j w_j).
-  // The containment tests of a pair of obstacles against all of a lane's
-  // timesteps are computed branch-free (x and y packed in f32x2 lanes) and
-  // combined with one min; only when one of them contains a point does the
-  // warp take the projection branch (rare once the iterates are outside).
-  mo = 0.f;
-  for (int j = 0; j < n_o; j += 2) {
-    float4 o[2][OV];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (j + h < n_o) {
-#pragma unroll
-        for (int q = 0; q < OV; ++q) o[h][q] = __ldg(&obs[OV * (j + h) + q]);
-      } else { // tail sentinel: static, 1e18 m away, unit axes: never inside
-        if constexpr (DIM == 2) {
-          o[h][0] = make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
-          o[h][1] = make_float4(1.f, 1.f, 1.f, 1.f);
-        } else {
-          o[h][0] = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 1.f);
-          o[h][1] = make_float4(0.f, 0.f, 0.f, 1.f);
-          o[h][2] = make_float4(1.f, 1.f, 1.f, 1.f);
-        }
-      }
-    }
-    float d[2][MAXNT][DIM], s[2][MAXNT];
-    float smin = 3.0e38f;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-#pragma unroll
-      for (int m = 0; m < MAXNT; ++m) {
-        if constexpr (DIM == 2) {
-          const float2 nc = make_float2(o[h][0].x, o[h][0].y), nv = make_float2(o[h][0].z, o[h][0].w);
-          const float2 ia = make_float2(o[h][1].x, o[h][1].y);
-          const float2 pc = __fadd2_rn(make_float2(pos[m][0], pos[m][1]), nc);
-          const float2 dd = __ffma2_rn(nv, make_float2(tm[m], tm[m]), pc);
-          const float2 uu = __fmul2_rn(dd, ia);
-          d[h][m][0] = dd.x; d[h][m][1] = dd.y;
-          s[h][m] = fmaf(uu.y, uu.y, uu.x * uu.x);
-        } else {
-          const float2 nc = make_float2(o[h][0].x, o[h][0].y), nv = make_float2(o[h][1].x, o[h][1].y);
-          const float2 ia = make_float2(o[h][0].w, o[h][1].w);
-          const float2 pc = __fadd2_rn(make_float2(pos[m][0], pos[m][1]), nc);
-          const float2 dd = __ffma2_rn(nv, make_float2(tm[m], tm[m]), pc);
-          const float2 uu = __fmul2_rn(dd, ia);
-          const float dz = fmaf(o[h][1].z, tm[m], pos[m][2] + o[h][0].z);
-          const float uz = dz * o[h][2].w;
-          d[h][m][0] = dd.x; d[h][m][1] = dd.y; d[h][m][2] = dz;
-          s[h][m] = fmaf(uz, uz, fmaf(uu.y, uu.y, uu.x * uu.x));
-        }
-        smin = fminf(smin, s[h][m]);
-      }
-    }
-    if (smin < 1.f) { // some timestep is inside one of the two ellipses
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-#pragma unroll
-        for (int m = 0; m < MAXNT; ++m) {
-          if (s[h][m] < 1.f) {
-            float e[DIM];
-            if (s[h][m] > 0.f) { // project along the ray: target offset Delta / ||u||
-              const float w = rsqrtf(s[h][m]) - 1.f;
-#pragma unroll
-              for (int a = 0; a < DIM; ++a) e[a] = d[h][m][a] * w;
-            } else { // at the centre: atan2(0, 0) = 0 pushes along +x (3D: beta = 0, +z)
-#pragma unroll
-              for (int a = 0; a < DIM; ++a) e[a] = 0.f;
-              if constexpr (DIM == 2) e[0] = o[h][1].z; else e[2] = o[h][2].z;
-            }
-            float n2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) { acc[m][a] += e[a]; n2 = fmaf(e[a], e[a], n2); }
-            mo = fmaxf(mo, n2);
-          }
-        }
-      }
-    }
-  }
-  // velocity / acceleration projections and the contraction u = F^T r
-#pragma unroll
-  for (int a = 0; a < DIM; ++a)
-#pragma unroll
-    for (int i = 0; i < NC; ++i) up[a][i] = 0.f;
-  mv = 0.f; ma = 0.f;
-  const float vmax2 = vmax * vmax, amax2 = amax * amax;
-#pragma unroll
-  for (int m = 0; m < MAXNT; ++m) {
-    const int t = lane + 32 * m;
-    if (m < nt && t < n_p) {
-      float rp[12], rd[12], ra[12];
-      load_row(tP + t * ROW, rp);
-      load_row(tD + t * ROW, rd);
-      load_row(tA + t * ROW, ra);
-      float vel[DIM], ac[DIM], nv2 = 0.f, na2 = 0.f;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        float sv = 0.f, sa = 0.f;
-#pragma unroll
-        for (int i = 0; i < NC; ++i) { sv = fmaf(rd[i], xa[a][i], sv); sa = fmaf(ra[i], xa[a][i], sa); }
-        vel[a] = sv * invT; ac[a] = sa * invT2;
-        nv2 = fmaf(vel[a], vel[a], nv2); na2 = fmaf(ac[a], ac[a], na2);
-      }
-      float fv = 0.f, fa = 0.f;
-      if (nv2 > vmax2) { fv = 1.f - vmax * rsqrtf(nv2); mv = fmaxf(mv, nv2 * fv * fv); }
-      if (na2 > amax2) { fa = 1.f - amax * rsqrtf(na2); ma = fmaxf(ma, na2 * fa * fa); }
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const float Ro = -acc[m][a];              // sum_j r_j at t
-        const float Rv = vel[a] * fv * invT;      // Pd^T r_v = dB^T (r_v / T)
-        const float Ra = ac[a] * fa * invT2;      // Pdd^T r_a = d2B^T (r_a / T^2)
-#pragma unroll
-        for (int i = 0; i < NC; ++i) up[a][i] = fmaf(rp[i], Ro, fmaf(rd[i], Rv, fmaf(ra[i], Ra, up[a][i])));
-      }
-    }
-  }
-}
 
 template <int DIM, int MAXNT>
 __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *stab, int lane,
@@ -446,7 +252,7 @@ static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_
 
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s, LaunchShape *used) {
-  (void)precision;
+  if (precision == 1) return launch_am_mixed(dim, max_np, a, n_sm, s);
   const int nt = (max_np + 31) / 32;
   if (dim == 2) {
     if (nt <= 4) return launch_t<2, 4>(a, shape, n_sm, s, used);

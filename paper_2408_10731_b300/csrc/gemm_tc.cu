@@ -14,6 +14,7 @@
 // expiry the CTA sets the error flag, skips the remaining work, still frees
 // its TMEM and returns.
 #include "internal.cuh"
+#include "tcgen05.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -26,7 +27,6 @@ constexpr int GM_BM = 128, GM_BN = 128, GM_BK = 64, GM_STAGES = 4;
 constexpr int GM_TILE_A = GM_BM * GM_BK * 2;
 constexpr int GM_TILE_B = GM_BN * GM_BK * 2;
 constexpr int GM_SMEM = GM_STAGES * (GM_TILE_A + GM_TILE_B) + 1024 /*align*/ + 256 /*barriers*/;
-constexpr uint32_t GM_WAIT_LIMIT = 1u << 22;
 
 struct GemmArgs {
   int M, N, K;
@@ -37,43 +37,6 @@ struct GemmArgs {
   const float *aux;         // EPI_GELU_BWD: Z [M][ldo]
   int *err;                 // bit 0 set if a wait expired
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-               " selp.u32 %0, 1, 0, p;\n}"
-               : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < GM_WAIT_LIMIT; ++i)
-    if (mbar_try(bar, parity)) return true;
-  return false;
-}
-
-// Shared-memory matrix descriptor: K-major tile written by TMA with the
-// 128-byte swizzle (8-row atoms of 1024 B): start address, LBO 16 B (unused
-// for this layout), SBO 1024 B between 8-row groups, descriptor version 1,
-// layout type 2 (128-byte swizzle).
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
 
 __device__ __forceinline__ float gelu_tanh(float z) {
   const float k0 = 0.7978845608028654f, k1 = 0.044715f;

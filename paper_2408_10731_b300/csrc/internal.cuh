@@ -77,7 +77,7 @@ struct SolveArgs {
   unsigned long long timeout_ns;
   int *queue;                 // work-queue counter, zeroed before the launch
   unsigned long long *t0;     // launch start time (globaltimer), zeroed before the launch
-  int *flags;                 // bit 0: timeout hit, bit 1: NaN input seen
+  int *flags;                 // bit 0: timeout hit, bit 1: NaN input seen, bit 3: MMA wait expired
 };
 
 // ---- compensated (double-float) helpers -----------------------------------
@@ -121,6 +121,8 @@ struct LaunchShape {
   int blocks_per_sm;
   int grid; // filled in by the launcher
 };
+// tensor-core form (am_mixed.cu); every problem of the batch has n_p steps
+cudaError_t launch_am_mixed(int dim, int n_p, const SolveArgs &a, int n_sm, cudaStream_t s);
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s,
                             LaunchShape *used);

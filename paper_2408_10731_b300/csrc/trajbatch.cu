@@ -365,6 +365,10 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
   if (max_iters < 0) return fail(b, TRAJ_EINVAL, "max_iters must be >= 0");
   if (std::isnan(tol) || !(timeout_ms >= 0)) return fail(b, TRAJ_EINVAL, "bad tol or timeout");
+  if (b->cfg.precision == TRAJ_PREC_MIXED)
+    for (int p = 1; p < b->n_problems; ++p)
+      if (b->n_steps[p] != b->n_steps[0])
+        return fail(b, TRAJ_ESHAPE, "the tensor-core form needs one horizon (n_steps) per batch");
   SolveArgs a{};
   a.problems = b->d_problems;
   a.obstacles = b->d_obs;
@@ -450,6 +454,7 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   }
   s.gpu_ms = ms;
   *stats = s;
+  if (flags & 8) return fail(b, TRAJ_ECUDA, "a tensor-core pipeline wait expired");
   if (flags & 1) return fail(b, TRAJ_ETIMEOUT, "deadline reached");
   if (flags & 2) return fail(b, TRAJ_ENAN, "non-finite input in some trajectories");
   return s.n_solved == B ? TRAJ_OK : TRAJ_NOT_CONVERGED;
