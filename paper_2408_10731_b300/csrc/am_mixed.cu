@@ -2,10 +2,12 @@
 //
 // Same persistent warp-per-trajectory scheme and FP32 state as am_solve.cu, but
 // the residual contraction u = F^T r = P^T sum_j r_j + Pd^T r_v + Pdd^T r_a of
-// all four warps of a CTA runs on the 5th-generation tensor cores:
+// all eight warps of a CTA runs on the 5th-generation tensor cores:
 //
 //   D[128 x 16] (FP32, TMEM) = A[128 x K] * B[16 x K]^T,   K = 3 n_p padded to 64,
-//   A row 32 w + a  = warp w's residuals of axis a, BF16: [sum_j r_j(t) | r_v(t)/T | r_a(t)/T^2]
+//   A row 32 (w % 4) + 16 (w / 4) + a = warp w's residuals of axis a, BF16:
+//                     [sum_j r_j(t) | r_v(t)/T | r_a(t)/T^2]  (warp w can read TMEM lanes
+//                     32 (w % 4) .. + 31 only, so each lane quarter holds two warps' rows)
 //   B row i         = coefficient i's basis column, BF16: [P(t, i) | dB(t, i) | d2B(t, i)]
 //
 // Both operands live in shared memory in the K-major 128-byte swizzle layout; the
@@ -28,7 +30,7 @@
 
 namespace tb {
 
-constexpr int MX_WARPS = 4;
+constexpr int MX_WARPS = 8;
 constexpr int MX_TILE_A = 128 * 128; // bytes of one 128-row x 64-column BF16 tile
 constexpr int MX_TILE_B = 16 * 128;  // bytes of one 16-row x 64-column BF16 tile
 
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_am_mixed(const __grid_constan
   const int oi = lane & 15, oa = lane >> 4;
   const int ri = oi < NC ? oi : NC - 1;
   const float rho = A.rho;
+  const int row0 = 32 * (warp & 3) + 16 * (warp >> 2); // this warp's first A row / TMEM lane
   // per-warp trajectory state
   int b = -1, k = 0;
   bool qdone = false, dirty = false;
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_am_mixed(const __grid_constan
         if (t < n_p) {
 #pragma unroll
           for (int a = 0; a < DIM; ++a) {
-            const int row = 32 * warp + a;
+            const int row = row0 + a;
             const float vals[3] = {Ro[m][a], Rv[m][a], Ra[m][a]};
 #pragma unroll
             for (int g = 0; g < 3; ++g) {
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_am_mixed(const __grid_constan
     } else if (dirty) { // an idle warp contributes zero rows
       for (int e = lane; e < DIM * KT * 64; e += 32) {
         const int a = e / (KT * 64), kk = e % (KT * 64);
-        *reinterpret_cast<__nv_bfloat16 *>(sA + (kk >> 6) * MX_TILE_A + sw128_offset(32 * warp + a, kk & 63)) =
+        *reinterpret_cast<__nv_bfloat16 *>(sA + (kk >> 6) * MX_TILE_A + sw128_offset(row0 + a, kk & 63)) =
             __float2bfloat16_rn(0.f);
       }
       dirty = false;
@@ -277,21 +280,22 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_am_mixed(const __grid_constan
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
                    "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
                    "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+                 : "r"(tmem + ((uint32_t)(32 * (warp & 3)) << 16)));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (!__syncthreads_and(waited)) { // the MMA never completed: give up on this CTA's work
       if (tid == 0) atomicOr(A.flags, 8);
       break;
     }
     if (active) {
-      // lane 16 a + i takes coefficient i of axis a from lane a (axis 2 from lane 2)
+      // lane 16 a + i takes coefficient i of axis a from the lane of row row0 + a
       float un = 0.f, un2 = 0.f;
+      const int src = 16 * (warp >> 2);
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        const float v0 = __shfl_sync(FULL, __uint_as_float(r[c]), oa);
+        const float v0 = __shfl_sync(FULL, __uint_as_float(r[c]), src + oa);
         if (oi == c) un = v0;
         if constexpr (DIM == 3) {
-          const float v2 = __shfl_sync(FULL, __uint_as_float(r[c]), 2);
+          const float v2 = __shfl_sync(FULL, __uint_as_float(r[c]), src + 2);
           if (oi == c) un2 = v2;
         }
       }
