@@ -38,7 +38,8 @@ def tuned(handle, batch, precision="fp32", iters=20):
     cache = _load()
     if key in cache:
         e = cache[key]
-        handle.set_launch_shape(e["warps_per_block"], e["blocks_per_sm"])
+        handle.set_launch_shape(e["warps_per_block"], e["blocks_per_sm"],
+                                e.get("warps_per_trajectory", 1))
         return dict(e, cached=True)
     e = handle.autotune(iters)
     cache = _load()

@@ -144,20 +144,21 @@ __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const 
 }
 
 // Evaluate, project and contract one iterate (Algorithm 2 lines 4-6, minus the
-// multiplier update). xa: the iterate's coefficients (all lanes hold all).
+// multiplier update). The lane's timesteps are t = lane + ts * m (the caller
+// passes its first timestep as `lane`; ts = 32 when one warp owns a trajectory). xa: the iterate's coefficients (all lanes hold all).
 // Returns the per-lane partial contraction in up[DIM][11] and per-lane maxima
 // of ||r_j||^2, ||r_v||^2, ||r_a||^2.
 template <int DIM, int MAXNT>
 __device__ __forceinline__ void project_contract(
     const float (&xa)[DIM][NC], const float *tP, const float *tD, const float *tA,
     const float4 *obs, int n_o, int n_p, int nt, float dt, float invT, float invT2, float vmax,
-    float amax, int lane, float (&up)[DIM][NC], float &mo, float &mv, float &ma) {
+    float amax, int lane, float (&up)[DIM][NC], float &mo, float &mv, float &ma, int ts = 32) {
   constexpr int OV = obs_vec(DIM);
   float pos[MAXNT][DIM], acc[MAXNT][DIM], tm[MAXNT];
   // positions p(t) = P xi at this lane's timesteps; padding lanes get a far sentinel
 #pragma unroll
   for (int m = 0; m < MAXNT; ++m) {
-    const int t = lane + 32 * m;
+    const int t = lane + ts * m;
     tm[m] = dt * (float)t;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { pos[m][a] = 1.0e18f; acc[m][a] = 0.f; }
@@ -183,7 +184,7 @@ __device__ __forceinline__ void project_contract(
   const float vmax2 = vmax * vmax, amax2 = amax * amax;
 #pragma unroll
   for (int m = 0; m < MAXNT; ++m) {
-    const int t = lane + 32 * m;
+    const int t = lane + ts * m;
     if (m < nt && t < n_p) {
       float rp[12], rd[12], ra[12];
       load_row(tP + t * ROW, rp);
@@ -222,11 +223,11 @@ __device__ __forceinline__ void project_only(
     const float (&xa)[DIM][NC], const float *tP, const float *tD, const float *tA,
     const float4 *obs, int n_o, int n_p, float dt, float invT, float invT2, float vmax, float amax,
     int lane, float (&Ro)[NT][DIM], float (&Rv)[NT][DIM], float (&Ra)[NT][DIM], float &mo,
-    float &mv, float &ma) {
+    float &mv, float &ma, int ts = 32) {
   float pos[NT][DIM], acc[NT][DIM], tm[NT];
 #pragma unroll
   for (int m = 0; m < NT; ++m) {
-    const int t = lane + 32 * m;
+    const int t = lane + ts * m;
     tm[m] = dt * (float)t;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { pos[m][a] = 1.0e18f; acc[m][a] = 0.f; }
@@ -247,7 +248,7 @@ __device__ __forceinline__ void project_only(
   const float vmax2 = vmax * vmax, amax2 = amax * amax;
 #pragma unroll
   for (int m = 0; m < NT; ++m) {
-    const int t = lane + 32 * m;
+    const int t = lane + ts * m;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { Ro[m][a] = 0.f; Rv[m][a] = 0.f; Ra[m][a] = 0.f; }
     if (t < n_p) {
@@ -282,14 +283,14 @@ template <int DIM, int NT>
 __device__ __forceinline__ void contract_fp32(const float (&Ro)[NT][DIM], const float (&Rv)[NT][DIM],
                                               const float (&Ra)[NT][DIM], const float *tP,
                                               const float *tD, const float *tA, int n_p, int lane,
-                                              float (&up)[DIM][NC]) {
+                                              float (&up)[DIM][NC], int ts = 32) {
 #pragma unroll
   for (int a = 0; a < DIM; ++a)
 #pragma unroll
     for (int i = 0; i < NC; ++i) up[a][i] = 0.f;
 #pragma unroll
   for (int m = 0; m < NT; ++m) {
-    const int t = lane + 32 * m;
+    const int t = lane + ts * m;
     if (t < n_p) {
       float rp[12], rd[12], rA[12];
       load_row(tP + t * ROW, rp);

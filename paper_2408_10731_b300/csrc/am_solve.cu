@@ -183,6 +183,223 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
   }
 }
 
+// ---- two warps per trajectory ---------------------------------------------------
+// The team's warps r = 0, 1 own timesteps t = 2 lane + r + 64 m (interleaved, so
+// both carry the same share of a ragged horizon). Each evaluates, projects and
+// contracts its timesteps; the partial contractions (after each warp's
+// reduce-scatter) and the residual maxima are exchanged through double-buffered
+// shared memory with one named barrier per iteration, and both warps add them in
+// the same order, so they hold bitwise-identical u, lambda and xi and take the
+// same decisions. The compensated QP step runs redundantly in both.
+constexpr int XCH = 72; // floats per exchange slot: u (32 lanes), u of axis 2 (32), maxima, flag
+
+__device__ __forceinline__ void team_bar(int id) {
+  asm volatile("bar.sync %0, 64;" :: "r"(id) : "memory");
+}
+
+template <int DIM, int NT>
+__device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *stab, int lane,
+                                        int r, float *xch, int bar_id,
+                                        unsigned long long deadline) {
+  const int p = A.traj_problem[b];
+  const ProblemDev pr = A.problems[p];
+  const int n_p = pr.n_p, n_o = pr.n_o;
+  const float *C = A.constants + pr.const_off;
+  const float *tP = stab + pr.tbl_off;
+  const float *tD = tP + n_p * ROW;
+  const float *tA = tD + n_p * ROW;
+  const float4 *obs = A.obstacles + (size_t)pr.obs_off * obs_vec(DIM);
+  const float rho = A.rho;
+  const int oi = lane & 15, oa = lane >> 4;
+  const int ri = oi < NC ? oi : NC - 1;
+  const float *x0 = A.xi0 + (size_t)b * DIM * NC;
+  float xo = x0[oa * NC + ri];
+  float xo2 = DIM == 3 ? x0[2 * NC + ri] : 0.f;
+  bool finite = isfinite(xo) && isfinite(xo2);
+  finite = __all_sync(FULL, finite) && pr.nan_flag == 0;
+  float *xout = A.xi + (size_t)b * DIM * NC;
+  if (!finite) {
+    if (r == 0) {
+      if (oi < NC) {
+        xout[oa * NC + oi] = xo;
+        if (DIM == 3 && oa == 0) xout[2 * NC + oi] = xo2;
+      }
+      if (lane < 3) A.res[b * 3 + lane] = __int_as_float(0x7fc00000);
+      if (lane == 0) { A.iters[b] = 0; A.status[b] = 2; atomicOr(A.flags, 2); }
+    }
+    return;
+  }
+  float hq_hi, hq_lo, hq2_hi = 0.f, hq2_lo = 0.f;
+  if (A.cost_mode == 0) {
+    hq_hi = C[C_HQ_HI + oa * ROW + ri]; hq_lo = C[C_HQ_LO + oa * ROW + ri];
+    if (DIM == 3) { hq2_hi = C[C_HQ_HI + 2 * ROW + ri]; hq2_lo = C[C_HQ_LO + 2 * ROW + ri]; }
+  } else {
+    hq_hi = C[C_C_HI + oa * ROW + ri]; hq_lo = C[C_C_LO + oa * ROW + ri];
+    if (DIM == 3) { hq2_hi = C[C_C_HI + 2 * ROW + ri]; hq2_lo = C[C_C_LO + 2 * ROW + ri]; }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const float xk = __shfl_sync(FULL, xo, (lane & 16) + q);
+      df_fma(hq_hi, hq_lo, C[C_K11_HI + ri * ROW + q], C[C_K11_LO + ri * ROW + q], xk);
+      if (DIM == 3) {
+        const float xk2 = __shfl_sync(FULL, xo2, q);
+        df_fma(hq2_hi, hq2_lo, C[C_K11_HI + ri * ROW + q], C[C_K11_LO + ri * ROW + q], xk2);
+      }
+    }
+    float s0 = hq_hi + hq_lo; hq_lo = hq_lo - (s0 - hq_hi); hq_hi = s0;
+    if (DIM == 3) { float s2 = hq2_hi + hq2_lo; hq2_lo = hq2_lo - (s2 - hq2_hi); hq2_hi = s2; }
+  }
+  float lam = 0.f, lam2 = 0.f, uo = 0.f, uo2 = 0.f;
+  float mo, mv, ma;
+  int k = 0, par = 0;
+  signed char st = 1;
+  for (;; ++k) {
+    if (k > 0) {
+      const float vo = lam - rho * uo, vo2 = lam2 - rho * uo2;
+      float hi = hq_hi, lo = hq_lo, hi2 = hq2_hi, lo2 = hq2_lo;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const float xk = __shfl_sync(FULL, xo, (lane & 16) + q);
+        const float vk = __shfl_sync(FULL, vo, (lane & 16) + q);
+        const float g_hi = C[C_G_HI + ri * ROW + q], g_lo = C[C_G_LO + ri * ROW + q];
+        const float k_hi = C[C_K11_HI + ri * ROW + q], k_lo = C[C_K11_LO + ri * ROW + q];
+        df_fma(hi, lo, g_hi, g_lo, xk);
+        df_fma(hi, lo, k_hi, k_lo, vk);
+        if (DIM == 3) {
+          const float xk2 = __shfl_sync(FULL, xo2, q);
+          const float vk2 = __shfl_sync(FULL, vo2, q);
+          df_fma(hi2, lo2, g_hi, g_lo, xk2);
+          df_fma(hi2, lo2, k_hi, k_lo, vk2);
+        }
+      }
+      xo = hi + lo;
+      if (DIM == 3) xo2 = hi2 + lo2;
+    }
+    float xa[DIM][NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      xa[0][i] = __shfl_sync(FULL, xo, i);
+      xa[1][i] = __shfl_sync(FULL, xo, 16 + i);
+      if constexpr (DIM == 3) xa[2][i] = __shfl_sync(FULL, xo2, i);
+    }
+    float up[DIM][NC];
+    project_contract<DIM, NT>(xa, tP, tD, tA, obs, n_o, n_p, NT, pr.dt, pr.invT, pr.invT2,
+                              A.vmax, A.amax, 2 * lane + r, up, mo, mv, ma, 64);
+    float part = 0.f, part2 = 0.f;
+    {
+      float v32[32];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        v32[i] = i < NC ? up[0][i] : 0.f;
+        v32[16 + i] = i < NC ? up[1][i] : 0.f;
+      }
+      part = reduce_scatter32(v32, lane);
+      if constexpr (DIM == 3) {
+        float v16[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v16[i] = i < NC ? up[2][i] : 0.f;
+        part2 = reduce_scatter16(v16, lane);
+      }
+    }
+    mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
+    // exchange with the partner warp
+    float *mine = xch + (par * 2 + r) * XCH;
+    mine[lane] = part;
+    if (DIM == 3) mine[32 + lane] = part2;
+    if (lane == 0) {
+      mine[64] = mo; mine[65] = mv; mine[66] = ma;
+      float late = 0.f;
+      if (r == 0 && deadline && globaltimer_ns() > deadline) late = 1.f;
+      mine[67] = late;
+    }
+    team_bar(bar_id);
+    const float *s0 = xch + (par * 2 + 0) * XCH, *s1 = xch + (par * 2 + 1) * XCH;
+    uo = s0[lane] + s1[lane];
+    if (DIM == 3) uo2 = s0[32 + lane] + s1[32 + lane];
+    mo = fmaxf(s0[64], s1[64]); mv = fmaxf(s0[65], s1[65]); ma = fmaxf(s0[66], s1[66]);
+    const bool late = s0[67] != 0.f;
+    par ^= 1;
+    if (k > 0) {
+      lam -= rho * uo;
+      if (DIM == 3) lam2 -= rho * uo2;
+      if (A.tol >= 0.f && sqrtf(mo) <= A.tol && sqrtf(mv) <= A.tol && sqrtf(ma) <= A.tol) {
+        st = 0;
+        break;
+      }
+    }
+    if (k >= A.max_iters) { st = 1; break; }
+    if (late) { st = 3; break; }
+  }
+  if (r == 0) {
+    if (oi < NC) {
+      xout[oa * NC + oi] = xo;
+      if (A.lam) A.lam[(size_t)b * DIM * NC + oa * NC + oi] = lam;
+      if (A.u) A.u[(size_t)b * DIM * NC + oa * NC + oi] = uo;
+      if (DIM == 3 && oa == 0) {
+        xout[2 * NC + oi] = xo2;
+        if (A.lam) A.lam[(size_t)b * DIM * NC + 2 * NC + oi] = lam2;
+        if (A.u) A.u[(size_t)b * DIM * NC + 2 * NC + oi] = uo2;
+      }
+    }
+    if (lane == 0) {
+      A.res[b * 3 + 0] = sqrtf(mo);
+      A.res[b * 3 + 1] = sqrtf(mv);
+      A.res[b * 3 + 2] = sqrtf(ma);
+      A.iters[b] = k;
+      A.status[b] = st;
+      if (st == 3) atomicOr(A.flags, 1);
+    }
+  }
+}
+
+template <int DIM, int NT, int MAXNT>
+__device__ __forceinline__ void team_nt(const SolveArgs &A, int b, const float *stab, int lane,
+                                        int r, float *xch, int bar_id,
+                                        unsigned long long deadline, int nt) {
+  if constexpr (NT >= MAXNT) {
+    solve_team<DIM, MAXNT>(A, b, stab, lane, r, xch, bar_id, deadline);
+  } else {
+    if (nt <= NT) solve_team<DIM, NT>(A, b, stab, lane, r, xch, bar_id, deadline);
+    else team_nt<DIM, NT + 1, MAXNT>(A, b, stab, lane, r, xch, bar_id, deadline, nt);
+  }
+}
+
+template <int DIM, int MAXNT>
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32)
+k_am_team(const __grid_constant__ SolveArgs A) {
+  extern __shared__ float4 smem4[];
+  const int nteam = blockDim.x / 64;
+  const float4 *g4 = reinterpret_cast<const float4 *>(A.tables);
+  for (int i = threadIdx.x; i < A.table_floats_total / 4; i += blockDim.x) smem4[i] = g4[i];
+  float *stab = reinterpret_cast<float *>(smem4);
+  float *xch_all = stab + A.table_floats_total;          // [teams][2 parities][2 warps][XCH]
+  int *sitem = reinterpret_cast<int *>(xch_all + nteam * 4 * XCH);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int team = warp >> 1, r = warp & 1, bar_id = 1 + team;
+  float *xch = xch_all + team * 4 * XCH;
+
+  unsigned long long deadline = 0;
+  if (A.timeout_ns) {
+    unsigned long long t0 = 0;
+    if (lane == 0) {
+      const unsigned long long now = globaltimer_ns();
+      const unsigned long long prev = atomicCAS(A.t0, 0ull, now);
+      t0 = prev ? prev : now;
+    }
+    deadline = __shfl_sync(FULL, t0, 0) + A.timeout_ns;
+  }
+  for (;;) {
+    if (r == 0 && lane == 0) sitem[team] = atomicAdd(A.queue, 1);
+    team_bar(bar_id);
+    const int item = sitem[team];
+    team_bar(bar_id);
+    if (item >= A.n_traj) break;
+    const int b = A.order[item];
+    const int nt = (A.problems[A.traj_problem[b]].n_p + 63) >> 6;
+    team_nt<DIM, 1, MAXNT>(A, b, stab, lane, r, xch, bar_id, deadline, nt);
+  }
+}
+
 // Per-trajectory specialisation on the number of 32-step timestep slots, so a
 // short horizon in an uneven batch does not pay for the longest one's slots.
 template <int DIM, int NT, int MAXNT>
@@ -227,13 +444,15 @@ k_am_fp32(const __grid_constant__ SolveArgs A) {
   }
 }
 
-template <int DIM, int MAXNT>
+template <int DIM, int MAXNT, bool TEAM>
 static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_sm,
                             cudaStream_t s, LaunchShape *used) {
-  auto kern = k_am_fp32<DIM, MAXNT>;
+  auto kern = TEAM ? k_am_team<DIM, (MAXNT + 1) / 2> : k_am_fp32<DIM, MAXNT>;
   const int warps = shape.warps_per_block > 0 ? shape.warps_per_block : 4;
-  if (warps > MAX_WARPS_PER_BLOCK) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float) * (size_t)a.table_floats_total;
+  if (warps > MAX_WARPS_PER_BLOCK || (TEAM && (warps & 1))) return cudaErrorInvalidValue;
+  const int per = TEAM ? 2 : 1; // warps per trajectory
+  const size_t smem = sizeof(float) * (size_t)a.table_floats_total +
+                      (TEAM ? (size_t)(warps / 2) * (4 * XCH * sizeof(float) + sizeof(int)) : 0);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -241,11 +460,11 @@ static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   if (shape.blocks_per_sm > 0 && shape.blocks_per_sm < occ) occ = shape.blocks_per_sm;
-  long long want = ((long long)a.n_traj + warps - 1) / warps;
+  long long want = ((long long)a.n_traj * per + warps - 1) / warps;
   long long grid = (long long)n_sm * occ;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
-  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; }
+  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = per; }
   kern<<<(unsigned)grid, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -254,14 +473,19 @@ cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs 
                             const LaunchShape &shape, int n_sm, cudaStream_t s, LaunchShape *used) {
   if (precision == 1) return launch_am_mixed(dim, max_np, a, n_sm, s);
   const int nt = (max_np + 31) / 32;
+  const bool team = shape.team == 2;
+#define TB_PICK(D, N)                                                                   \
+  return team ? launch_t<D, N, true>(a, shape, n_sm, s, used)                           \
+              : launch_t<D, N, false>(a, shape, n_sm, s, used)
   if (dim == 2) {
-    if (nt <= 4) return launch_t<2, 4>(a, shape, n_sm, s, used);
-    if (nt <= 5) return launch_t<2, 5>(a, shape, n_sm, s, used);
-    return launch_t<2, 8>(a, shape, n_sm, s, used);
+    if (nt <= 4) TB_PICK(2, 4);
+    if (nt <= 5) TB_PICK(2, 5);
+    TB_PICK(2, 8);
   }
-  if (nt <= 4) return launch_t<3, 4>(a, shape, n_sm, s, used);
-  if (nt <= 5) return launch_t<3, 5>(a, shape, n_sm, s, used);
-  return launch_t<3, 8>(a, shape, n_sm, s, used);
+  if (nt <= 4) TB_PICK(3, 4);
+  if (nt <= 5) TB_PICK(3, 5);
+  TB_PICK(3, 8);
+#undef TB_PICK
 }
 
 } // namespace tb

@@ -120,6 +120,7 @@ struct LaunchShape {
   int warps_per_block;
   int blocks_per_sm;
   int grid; // filled in by the launcher
+  int team; // warps per trajectory: 1 or 2
 };
 // tensor-core form (am_mixed.cu); every problem of the batch has n_p steps
 cudaError_t launch_am_mixed(int dim, int n_p, const SolveArgs &a, int n_sm, cudaStream_t s);

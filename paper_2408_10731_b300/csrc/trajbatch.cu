@@ -43,12 +43,12 @@ struct traj_batch {
   unsigned long long *d_t0 = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // launch shape of the solve (set by traj_autotune / traj_set_launch_shape)
-  LaunchShape shape{4, 0, 0};
+  LaunchShape shape{4, 0, 0, 1};
   // the solve captured as a CUDA graph, replayed while its key is unchanged
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_valid = false;
-  int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1;
+  int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1, g_team = -1;
   float g_tol = 0.f;
   unsigned long long g_timeout = 0;
   std::vector<int> tbl_off; // per problem, float offset of its basis tables
@@ -397,7 +397,8 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   a.flags = b->d_flags;
   const bool same = b->graph_valid && b->g_max_iters == max_iters && b->g_tol == tol &&
                     b->g_timeout == a.timeout_ns && b->g_n_traj == b->n_traj &&
-                    b->g_warps == b->shape.warps_per_block && b->g_bps == b->shape.blocks_per_sm;
+                    b->g_warps == b->shape.warps_per_block && b->g_bps == b->shape.blocks_per_sm &&
+                    b->g_team == b->shape.team;
   if (!same) {
     // capture {clear counters; persistent solve} on the handle's capture stream
     invalidate_graph(b);
@@ -420,6 +421,7 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
     b->graph_valid = true;
     b->g_max_iters = max_iters; b->g_tol = tol; b->g_timeout = a.timeout_ns;
     b->g_n_traj = b->n_traj; b->g_warps = b->shape.warps_per_block; b->g_bps = b->shape.blocks_per_sm;
+    b->g_team = b->shape.team;
   }
   CK(b, cudaEventRecord(b->ev0, b->stream));
   CK(b, cudaGraphLaunch(b->graph_exec, b->stream));
@@ -497,9 +499,12 @@ traj_status traj_get_state(traj_batch *b, float *lambda, float *u) {
 
 traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape) {
   if (!b || !shape) return TRAJ_EINVAL;
-  if (shape->warps_per_block < 1 || shape->warps_per_block > 8 || shape->blocks_per_sm < 0)
-    return fail(b, TRAJ_EINVAL, "warps_per_block must be in [1, 8], blocks_per_sm >= 0");
-  b->shape = LaunchShape{shape->warps_per_block, shape->blocks_per_sm, 0};
+  if (shape->warps_per_block < 1 || shape->warps_per_block > 8 || shape->blocks_per_sm < 0 ||
+      (shape->warps_per_trajectory != 1 && shape->warps_per_trajectory != 2) ||
+      (shape->warps_per_trajectory == 2 && (shape->warps_per_block & 1)))
+    return fail(b, TRAJ_EINVAL, "warps_per_block in [1, 8] (even for 2 warps per trajectory), "
+                                "blocks_per_sm >= 0, warps_per_trajectory 1 or 2");
+  b->shape = LaunchShape{shape->warps_per_block, shape->blocks_per_sm, 0, shape->warps_per_trajectory};
   invalidate_graph(b);
   return TRAJ_OK;
 }
@@ -510,11 +515,13 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
   if (iters < 1) return fail(b, TRAJ_EINVAL, "iters must be >= 1");
   static const int cand_w[] = {1, 2, 4, 8};
   static const int cand_b[] = {0, 1, 2, 4};
-  LaunchShape best{4, 0, 0};
+  LaunchShape best{4, 0, 0, 1};
   float best_t = 1e30f;
+  for (int team = 1; team <= (b->cfg.precision == TRAJ_PREC_MIXED ? 1 : 2); ++team)
   for (int w : cand_w)
     for (int bps : cand_b) {
-      b->shape = LaunchShape{w, bps, 0};
+      if (team == 2 && (w & 1)) continue;
+      b->shape = LaunchShape{w, bps, 0, team};
       invalidate_graph(b);
       float tot = 0.f;
       bool ok = true;
@@ -529,7 +536,11 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
   b->shape = best;
   invalidate_graph(b);
   b->have_result = false;
-  if (chosen) { chosen->warps_per_block = best.warps_per_block; chosen->blocks_per_sm = best.blocks_per_sm; }
+  if (chosen) {
+    chosen->warps_per_block = best.warps_per_block;
+    chosen->blocks_per_sm = best.blocks_per_sm;
+    chosen->warps_per_trajectory = best.team;
+  }
   if (best_ms) *best_ms = best_t / 2.f;
   return best_t < 1e30f ? TRAJ_OK : fail(b, TRAJ_ECUDA, "no launch shape ran");
 }

@@ -45,7 +45,8 @@ class SolveStats(ctypes.Structure):
 
 
 class LaunchShape(ctypes.Structure):
-    _fields_ = [("warps_per_block", _c_int), ("blocks_per_sm", _c_int)]
+    _fields_ = [("warps_per_block", _c_int), ("blocks_per_sm", _c_int),
+                ("warps_per_trajectory", _c_int)]
 
 
 class SamplerConfig(ctypes.Structure):
@@ -236,9 +237,10 @@ class TrajBatch:
         self._check(self._lib.traj_get_trajectories(self._h, c, r, i, s))
         return dict(xi=coeffs, residual=residual, iters=iters, status=status)
 
-    def set_launch_shape(self, warps_per_block, blocks_per_sm=0):
+    def set_launch_shape(self, warps_per_block, blocks_per_sm=0, warps_per_trajectory=1):
         self._check(self._lib.traj_set_launch_shape(
-            self._h, ctypes.byref(LaunchShape(int(warps_per_block), int(blocks_per_sm)))))
+            self._h, ctypes.byref(LaunchShape(int(warps_per_block), int(blocks_per_sm),
+                                              int(warps_per_trajectory)))))
 
     def autotune(self, iters=20):
         """Time the candidate launch shapes on this batch; keep and return the fastest."""
@@ -246,7 +248,7 @@ class TrajBatch:
         self._check(self._lib.traj_autotune(self._h, int(iters), ctypes.byref(shape),
                                             ctypes.byref(ms)))
         return dict(warps_per_block=shape.warps_per_block, blocks_per_sm=shape.blocks_per_sm,
-                    ms=ms.value)
+                    warps_per_trajectory=shape.warps_per_trajectory, ms=ms.value)
 
     def sampler_step(self, cfg: dict, iteration, mu, sigma, best, z=None, trace=None):
         """One outer iteration of the projection-guided sampler (device tensors)."""
