@@ -203,22 +203,25 @@ traj_status traj_solve_noalloc(const traj_config *cfg, int n_problems, const int
                                float tol, float *coeffs, float *residual, int *iters,
                                signed char *status);
 
-/* CTA shape of the persistent solve launch: warps per block (1..8), a cap on
- * resident blocks per SM (0 = as many as occupancy allows) and the warps that
- * share one trajectory (1, or 2: timesteps interleaved across the two warps,
- * partial contractions exchanged through shared memory; FP32 form only). The
- * grid never exceeds what the batch needs. Results do not depend on the shape. */
+/* CTA shape of the persistent solve launch: warps per block (1..8; 0 = the
+ * default of the form), a cap on resident blocks per SM (0 = as many as
+ * occupancy allows) and the warps that share one trajectory (1, 2 or 4,
+ * dividing warps_per_block: timesteps interleaved across the warps, partial
+ * contractions exchanged through shared memory; FP32 form only). The grid never exceeds what the batch needs. Results
+ * are bitwise identical across shapes with the same warps per trajectory; across
+ * those they differ only in the summation order of the contraction. */
 typedef struct traj_launch_shape {
   int warps_per_block;
   int blocks_per_sm;
   int warps_per_trajectory;
 } traj_launch_shape;
 
-/* Use this launch shape for later solves (default: 4 warps, occupancy-bound). */
+/* Use this launch shape for later solves (default: FP32 form 4 warps per block,
+ * tensor-core form the batch spread over all SMs; occupancy-bound blocks per SM). */
 traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape);
 
 /* Autotuner: times every candidate shape (warps per block in {1,2,4,8} x
- * blocks per SM in {occupancy,1,2,4} x warps per trajectory in {1,2}, the
+ * blocks per SM in {occupancy,1,2,4} x warps per trajectory in {1,2,4}, the
  * latter in the FP32 form only) on this handle's own batch with `iters`
  * fixed iterations, keeps the fastest for later solves and reports it in
  * *chosen and its time per solve in *best_ms (both nullable). Synchronises;

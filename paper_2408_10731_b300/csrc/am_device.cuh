@@ -1,7 +1,13 @@
 // am_device.cuh -- device building blocks of the AM iteration shared by the
-// FP32 solve kernel (am_solve.cu) and the tensor-core form (am_mixed.cu):
-// warp reductions, basis-row loads, the obstacle pair loop and the fused
-// evaluate / project / contract pass (Algorithm 2 lines 4-6).
+// FP32 solve kernels (am_solve.cu) and the tensor-core form (am_mixed.cu):
+// warp reductions, basis-row loads, the compensated QP step (Algorithm 2 line 2),
+// the obstacle pair loop and the fused evaluate / project / contract pass
+// (Algorithm 2 lines 4-6).
+//
+// Packed arithmetic: the 11 coefficients of an axis are held as six two-lane pairs
+// (2i, 2i + 1), the twelfth lane zero, so that evaluation and contraction run on
+// the f32x2 FMA (__ffma2_rn: two IEEE fmas per instruction), and the obstacle
+// test runs on the two obstacles of a pair record at once.
 #pragma once
 #include "internal.cuh"
 
@@ -57,250 +63,343 @@ __device__ __forceinline__ void load_row(const float *row, float (&r)[12]) {
   r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
 }
 
-// Pair loop over obstacles (Algorithm 2 lines 4-5 for the obstacle groups): acc
-// accumulates sum_j Delta_j * w_j (r_j = -Delta_j w_j) at each of the lane's
-// timesteps; mo is the lane's max ||r_j||^2.
+// Coefficient pairs of the iterate: xp[a][j] = (xi_a[2j], xi_a[2j+1]), xp[a][5].y = 0.
+// Lane 16 a + i owns coefficient i of axis a < 2; axis 2 is owned by lanes i (< 11).
+template <int DIM>
+__device__ __forceinline__ void broadcast_pairs(float xo, float xo2, float2 (&xp)[DIM][6]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      xp[a][j].x = __shfl_sync(FULL, xo, 16 * a + 2 * j);
+      xp[a][j].y = j < 5 ? __shfl_sync(FULL, xo, 16 * a + 2 * j + 1) : 0.f;
+    }
+    if constexpr (DIM == 3) {
+      xp[2][j].x = __shfl_sync(FULL, xo2, 2 * j);
+      xp[2][j].y = j < 5 ? __shfl_sync(FULL, xo2, 2 * j + 1) : 0.f;
+    }
+  }
+}
+
+// Row (12 floats, column 11 zero) dotted with a coefficient-pair vector: six
+// packed fmas over the pairs, then the two lanes added.
+__device__ __forceinline__ float dot11(const float (&r)[12], const float2 (&xp)[6]) {
+  float2 acc = __fmul2_rn(make_float2(r[0], r[1]), xp[0]);
+#pragma unroll
+  for (int j = 1; j < 6; ++j) acc = __ffma2_rn(make_float2(r[2 * j], r[2 * j + 1]), xp[j], acc);
+  return acc.x + acc.y;
+}
+
+// up[j] += (r[2j], r[2j+1]) * R, the fmas of every coefficient in the order
+// R_a (acceleration), R_v (velocity), R_o (obstacles).
+__device__ __forceinline__ void contract_row3(float2 (&up)[6], const float (&rp)[12],
+                                              const float (&rd)[12], const float (&ra)[12],
+                                              float Ro, float Rv, float Ra) {
+  const float2 o2 = make_float2(Ro, Ro), v2 = make_float2(Rv, Rv), a2 = make_float2(Ra, Ra);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    float2 t = __ffma2_rn(make_float2(ra[2 * j], ra[2 * j + 1]), a2, up[j]);
+    t = __ffma2_rn(make_float2(rd[2 * j], rd[2 * j + 1]), v2, t);
+    up[j] = __ffma2_rn(make_float2(rp[2 * j], rp[2 * j + 1]), o2, t);
+  }
+}
+
+// Reduce-scatter of the per-lane partial contraction (coefficient pairs) over the
+// warp: afterwards lane 16 a + i holds u_a[i] (axis 2 of 3D: lanes i and 16 + i).
+template <int DIM>
+__device__ __forceinline__ void scatter_pairs(const float2 (&up)[DIM][6], int lane, float &uo,
+                                              float &uo2) {
+  float v32[32];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v32[i] = i < NC ? ((i & 1) ? up[0][i >> 1].y : up[0][i >> 1].x) : 0.f;
+    v32[16 + i] = i < NC ? ((i & 1) ? up[1][i >> 1].y : up[1][i >> 1].x) : 0.f;
+  }
+  uo = reduce_scatter32(v32, lane);
+  if constexpr (DIM == 3) {
+    float v16[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v16[i] = i < NC ? ((i & 1) ? up[2][i >> 1].y : up[2][i >> 1].x) : 0.f;
+    uo2 = reduce_scatter16(v16, lane);
+  } else {
+    uo2 = 0.f;
+  }
+}
+
+// Algorithm 2 line 2 at the owner lanes, compensated FP32:
+// xi^k = hq + G xi^{k-1} + K11 (lambda^{k-1} - rho u^{k-1}).
+template <int DIM>
+__device__ __forceinline__ void qp_step(const float *C, int lane, float rho, float hq_hi,
+                                        float hq_lo, float hq2_hi, float hq2_lo, float lam,
+                                        float lam2, float uo, float uo2, float &xo, float &xo2) {
+  const int oi = lane & 15;
+  const int ri = oi < NC ? oi : NC - 1;
+  const float vo = lam - rho * uo, vo2 = lam2 - rho * uo2;
+  float hi = hq_hi, lo = hq_lo, hi2 = hq2_hi, lo2 = hq2_lo;
+  const float x_own = xo, x_own2 = xo2;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const float xk = __shfl_sync(FULL, x_own, (lane & 16) + q);
+    const float vk = __shfl_sync(FULL, vo, (lane & 16) + q);
+    const float g_hi = C[C_G_HI + ri * ROW + q], g_lo = C[C_G_LO + ri * ROW + q];
+    const float k_hi = C[C_K11_HI + ri * ROW + q], k_lo = C[C_K11_LO + ri * ROW + q];
+    df_fma(hi, lo, g_hi, g_lo, xk);
+    df_fma(hi, lo, k_hi, k_lo, vk);
+    if constexpr (DIM == 3) {
+      const float xk2 = __shfl_sync(FULL, x_own2, q);
+      const float vk2 = __shfl_sync(FULL, vo2, q);
+      df_fma(hi2, lo2, g_hi, g_lo, xk2);
+      df_fma(hi2, lo2, k_hi, k_lo, vk2);
+    }
+  }
+  xo = hi + lo;
+  if constexpr (DIM == 3) xo2 = hi2 + lo2;
+}
+
+// ---- obstacles (Algorithm 2 lines 4-5 for the obstacle groups) ---------------------
+// Component k (0..3, a compile-time constant after unrolling) of a float4.
+__device__ __forceinline__ float f4c(const float4 &v, int k) {
+  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// ||u||^2 - 1 of both obstacles of a record at one timestep (packed), with
+// u = p * ia + (nc + nv t): negative inside the ellipse / ellipsoid.
+template <int DIM>
+__device__ __forceinline__ float2 pair_sm1(const float4 (&o)[pair_vec(DIM)], const float2 (&p2)[DIM],
+                                           float2 t2) {
+  constexpr int IA = DIM; // record index of {iax0, iax1, iay0, iay1}
+  float2 ux = __ffma2_rn(make_float2(o[0].z, o[0].w), t2, make_float2(o[0].x, o[0].y));
+  ux = __ffma2_rn(make_float2(o[IA].x, o[IA].y), p2[0], ux);
+  float2 uy = __ffma2_rn(make_float2(o[1].z, o[1].w), t2, make_float2(o[1].x, o[1].y));
+  uy = __ffma2_rn(make_float2(o[IA].z, o[IA].w), p2[1], uy);
+  float2 s = __ffma2_rn(ux, ux, make_float2(-1.f, -1.f));
+  s = __ffma2_rn(uy, uy, s);
+  if constexpr (DIM == 3) {
+    float2 uz = __ffma2_rn(make_float2(o[2].z, o[2].w), t2, make_float2(o[2].x, o[2].y));
+    uz = __ffma2_rn(make_float2(o[4].x, o[4].y), p2[2], uz);
+    s = __ffma2_rn(uz, uz, s);
+  }
+  return s;
+}
+
+// Projection of one timestep onto obstacle H of a record (only called when the
+// point is inside): the alpha and d steps give g - o = Delta * max(1, 1/||u||), so
+// acc += g - p = Delta (1/||u|| - 1) with Delta = u * a; at the centre atan2(0, 0) = 0
+// pushes along +x (3D: beta = 0, along +z). mo takes the max of ||g - p||^2.
+template <int DIM, int H>
+__device__ __forceinline__ void pair_project(const float4 (&o)[pair_vec(DIM)], const float (&p)[DIM],
+                                             float t, float (&acc)[DIM], float &mo) {
+  float u[DIM], ax[DIM];
+  if constexpr (DIM == 2) {
+    u[0] = fmaf(f4c(o[2], H), p[0], fmaf(f4c(o[0], 2 + H), t, f4c(o[0], H)));
+    u[1] = fmaf(f4c(o[2], 2 + H), p[1], fmaf(f4c(o[1], 2 + H), t, f4c(o[1], H)));
+    ax[0] = f4c(o[3], H); ax[1] = f4c(o[3], 2 + H);
+  } else {
+    u[0] = fmaf(f4c(o[3], H), p[0], fmaf(f4c(o[0], 2 + H), t, f4c(o[0], H)));
+    u[1] = fmaf(f4c(o[3], 2 + H), p[1], fmaf(f4c(o[1], 2 + H), t, f4c(o[1], H)));
+    u[2] = fmaf(f4c(o[4], H), p[2], fmaf(f4c(o[2], 2 + H), t, f4c(o[2], H)));
+    ax[0] = f4c(o[4], 2 + H); ax[1] = f4c(o[5], H); ax[2] = f4c(o[5], 2 + H);
+  }
+  float s = u[0] * u[0];
+#pragma unroll
+  for (int a = 1; a < DIM; ++a) s = fmaf(u[a], u[a], s);
+  float e[DIM];
+  if (s > 0.f) {
+    const float w = fmaxf(rsqrtf(s) - 1.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) e[a] = (u[a] * ax[a]) * w;
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) e[a] = 0.f;
+    e[DIM == 2 ? 0 : 2] = ax[DIM == 2 ? 0 : 2];
+  }
+  float n2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { acc[a] += e[a]; n2 = fmaf(e[a], e[a], n2); }
+  mo = fmaxf(mo, n2);
+}
+
+// Pair loop: all of the lane's timesteps against the problem's obstacle-pair
+// records, one record (two obstacles) per step. The tests are branch-free and
+// packed; the sign bits of all ||u||^2 - 1 are OR-ed, and only when one is negative
+// (a point inside, a few percent of the steps) does the warp take the projection
+// branch.
+// acc accumulates sum_j (g_j - p) (= -sum_j r_j); mo is the lane's max ||r_j||^2.
 template <int DIM, int MAXNT>
 __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const float (&tm)[MAXNT],
                                           const float4 *obs, int n_o, float (&acc)[MAXNT][DIM],
                                           float &mo) {
-  constexpr int OV = obs_vec(DIM);
-  // The containment tests of a pair of obstacles against all of a lane's
-  // timesteps are computed branch-free (x and y packed in f32x2 lanes) and
-  // combined with one min; only when one of them contains a point does the
-  // warp take the projection branch (rare once the iterates are outside).
+  constexpr int PV = pair_vec(DIM);
+  const int n_pairs = pair_count(n_o);
+  float2 p2[MAXNT][DIM], t2[MAXNT];
+#pragma unroll
+  for (int m = 0; m < MAXNT; ++m) {
+    t2[m] = make_float2(tm[m], tm[m]);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) p2[m][a] = make_float2(pos[m][a], pos[m][a]);
+  }
   mo = 0.f;
-  for (int j = 0; j < n_o; j += 2) {
-    float4 o[2][OV];
+  for (int q = 0; q < n_pairs; ++q) {
+    float4 o[PV];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (j + h < n_o) {
+    for (int k = 0; k < PV; ++k) o[k] = __ldg(&obs[PV * q + k]);
+    float2 sm[MAXNT];
+    unsigned sign = 0u;
 #pragma unroll
-        for (int q = 0; q < OV; ++q) o[h][q] = __ldg(&obs[OV * (j + h) + q]);
-      } else { // tail sentinel: static, 1e18 m away, unit axes: never inside
-        if constexpr (DIM == 2) {
-          o[h][0] = make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
-          o[h][1] = make_float4(1.f, 1.f, 1.f, 1.f);
-        } else {
-          o[h][0] = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 1.f);
-          o[h][1] = make_float4(0.f, 0.f, 0.f, 1.f);
-          o[h][2] = make_float4(1.f, 1.f, 1.f, 1.f);
-        }
-      }
+    for (int m = 0; m < MAXNT; ++m) {
+      sm[m] = pair_sm1<DIM>(o, p2[m], t2[m]);
+      sign |= __float_as_uint(sm[m].x) | __float_as_uint(sm[m].y);
     }
-    float d[2][MAXNT][DIM], s[2][MAXNT];
-    float smin = 3.0e38f;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    if ((int)sign < 0) { // some timestep is inside one of the two obstacles
 #pragma unroll
       for (int m = 0; m < MAXNT; ++m) {
-        if constexpr (DIM == 2) {
-          const float2 nc = make_float2(o[h][0].x, o[h][0].y), nv = make_float2(o[h][0].z, o[h][0].w);
-          const float2 ia = make_float2(o[h][1].x, o[h][1].y);
-          const float2 pc = __fadd2_rn(make_float2(pos[m][0], pos[m][1]), nc);
-          const float2 dd = __ffma2_rn(nv, make_float2(tm[m], tm[m]), pc);
-          const float2 uu = __fmul2_rn(dd, ia);
-          d[h][m][0] = dd.x; d[h][m][1] = dd.y;
-          s[h][m] = fmaf(uu.y, uu.y, uu.x * uu.x);
-        } else {
-          const float2 nc = make_float2(o[h][0].x, o[h][0].y), nv = make_float2(o[h][1].x, o[h][1].y);
-          const float2 ia = make_float2(o[h][0].w, o[h][1].w);
-          const float2 pc = __fadd2_rn(make_float2(pos[m][0], pos[m][1]), nc);
-          const float2 dd = __ffma2_rn(nv, make_float2(tm[m], tm[m]), pc);
-          const float2 uu = __fmul2_rn(dd, ia);
-          const float dz = fmaf(o[h][1].z, tm[m], pos[m][2] + o[h][0].z);
-          const float uz = dz * o[h][2].w;
-          d[h][m][0] = dd.x; d[h][m][1] = dd.y; d[h][m][2] = dz;
-          s[h][m] = fmaf(uz, uz, fmaf(uu.y, uu.y, uu.x * uu.x));
-        }
-        smin = fminf(smin, s[h][m]);
-      }
-    }
-    if (smin < 1.f) { // some timestep is inside one of the two ellipses
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-#pragma unroll
-        for (int m = 0; m < MAXNT; ++m) {
-          if (s[h][m] < 1.f) {
-            float e[DIM];
-            if (s[h][m] > 0.f) { // project along the ray: target offset Delta / ||u||
-              const float w = rsqrtf(s[h][m]) - 1.f;
-#pragma unroll
-              for (int a = 0; a < DIM; ++a) e[a] = d[h][m][a] * w;
-            } else { // at the centre: atan2(0, 0) = 0 pushes along +x (3D: beta = 0, +z)
-#pragma unroll
-              for (int a = 0; a < DIM; ++a) e[a] = 0.f;
-              if constexpr (DIM == 2) e[0] = o[h][1].z; else e[2] = o[h][2].z;
-            }
-            float n2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) { acc[m][a] += e[a]; n2 = fmaf(e[a], e[a], n2); }
-            mo = fmaxf(mo, n2);
-          }
-        }
+        if (sm[m].x < 0.f) pair_project<DIM, 0>(o, pos[m], tm[m], acc[m], mo);
+        if (sm[m].y < 0.f) pair_project<DIM, 1>(o, pos[m], tm[m], acc[m], mo);
       }
     }
   }
 }
 
-// Evaluate, project and contract one iterate (Algorithm 2 lines 4-6, minus the
-// multiplier update). The lane's timesteps are t = lane + ts * m (the caller
-// passes its first timestep as `lane`; ts = 32 when one warp owns a trajectory). xa: the iterate's coefficients (all lanes hold all).
-// Returns the per-lane partial contraction in up[DIM][11] and per-lane maxima
-// of ||r_j||^2, ||r_v||^2, ||r_a||^2.
+// ---- evaluate / project / contract ---------------------------------------------------
+// Positions p(t) = P xi at the lane's timesteps t = t0 + ts m (padding slots get a far
+// sentinel, which is outside every obstacle).
 template <int DIM, int MAXNT>
-__device__ __forceinline__ void project_contract(
-    const float (&xa)[DIM][NC], const float *tP, const float *tD, const float *tA,
-    const float4 *obs, int n_o, int n_p, int nt, float dt, float invT, float invT2, float vmax,
-    float amax, int lane, float (&up)[DIM][NC], float &mo, float &mv, float &ma, int ts = 32) {
-  constexpr int OV = obs_vec(DIM);
-  float pos[MAXNT][DIM], acc[MAXNT][DIM], tm[MAXNT];
-  // positions p(t) = P xi at this lane's timesteps; padding lanes get a far sentinel
+__device__ __forceinline__ void eval_positions(const float2 (&xp)[DIM][6], const float *tP, int n_p,
+                                               int nt, float dt, int t0, int ts,
+                                               float (&pos)[MAXNT][DIM], float (&tm)[MAXNT]) {
 #pragma unroll
   for (int m = 0; m < MAXNT; ++m) {
-    const int t = lane + ts * m;
+    const int t = t0 + ts * m;
     tm[m] = dt * (float)t;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) { pos[m][a] = 1.0e18f; acc[m][a] = 0.f; }
+    for (int a = 0; a < DIM; ++a) pos[m][a] = 1.0e18f;
     if (m < nt && t < n_p) {
       float r[12];
       load_row(tP + t * ROW, r);
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < NC; ++i) s = fmaf(r[i], xa[a][i], s);
-        pos[m][a] = s;
-      }
+      for (int a = 0; a < DIM; ++a) pos[m][a] = dot11(r, xp[a]);
     }
   }
+}
+
+// Velocity / acceleration at one timestep and their projections onto the bound
+// balls: r = w max(0, 1 - bound/||w||). Returns the time-scaled residuals
+// Rv = r_v / T and Ra = r_a / T^2 (so that Pd^T r_v = dB^T Rv) and raises the maxima.
+template <int DIM>
+__device__ __forceinline__ void bound_residuals(const float2 (&xp)[DIM][6], const float (&rd)[12],
+                                                const float (&ra)[12], float invT, float invT2,
+                                                float vmax, float amax, float (&Rv)[DIM],
+                                                float (&Ra)[DIM], float &mv, float &ma) {
+  float vel[DIM], ac[DIM], nv2 = 0.f, na2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    vel[a] = dot11(rd, xp[a]) * invT;
+    ac[a] = dot11(ra, xp[a]) * invT2;
+    nv2 = fmaf(vel[a], vel[a], nv2);
+    na2 = fmaf(ac[a], ac[a], na2);
+  }
+  float fv = 0.f, fa = 0.f;
+  if (nv2 > vmax * vmax) { fv = 1.f - vmax * rsqrtf(nv2); mv = fmaxf(mv, nv2 * fv * fv); }
+  if (na2 > amax * amax) { fa = 1.f - amax * rsqrtf(na2); ma = fmaxf(ma, na2 * fa * fa); }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    Rv[a] = vel[a] * fv * invT;
+    Ra[a] = ac[a] * fa * invT2;
+  }
+}
+
+// Evaluate, project and contract one iterate (Algorithm 2 lines 4-6, minus the
+// multiplier update). The lane's timesteps are t = t0 + ts m (ts = 32 when one warp
+// owns a trajectory). Returns the per-lane partial contraction u = F^T r as
+// coefficient pairs up[DIM][6] and the lane maxima of ||r_j||^2, ||r_v||^2, ||r_a||^2.
+template <int DIM, int MAXNT>
+__device__ __forceinline__ void project_contract(
+    const float2 (&xp)[DIM][6], const float *tP, const float *tD, const float *tA,
+    const float4 *obs, int n_o, int n_p, int nt, float dt, float invT, float invT2, float vmax,
+    float amax, int t0, float2 (&up)[DIM][6], float &mo, float &mv, float &ma, int ts = 32) {
+  float pos[MAXNT][DIM], acc[MAXNT][DIM], tm[MAXNT];
+  eval_positions<DIM, MAXNT>(xp, tP, n_p, nt, dt, t0, ts, pos, tm);
+#pragma unroll
+  for (int m = 0; m < MAXNT; ++m)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) acc[m][a] = 0.f;
   pair_loop<DIM, MAXNT>(pos, tm, obs, n_o, acc, mo);
-  // velocity / acceleration projections and the contraction u = F^T r
 #pragma unroll
   for (int a = 0; a < DIM; ++a)
 #pragma unroll
-    for (int i = 0; i < NC; ++i) up[a][i] = 0.f;
+    for (int j = 0; j < 6; ++j) up[a][j] = make_float2(0.f, 0.f);
   mv = 0.f; ma = 0.f;
-  const float vmax2 = vmax * vmax, amax2 = amax * amax;
 #pragma unroll
   for (int m = 0; m < MAXNT; ++m) {
-    const int t = lane + ts * m;
+    const int t = t0 + ts * m;
     if (m < nt && t < n_p) {
       float rp[12], rd[12], ra[12];
       load_row(tP + t * ROW, rp);
       load_row(tD + t * ROW, rd);
       load_row(tA + t * ROW, ra);
-      float vel[DIM], ac[DIM], nv2 = 0.f, na2 = 0.f;
+      float Rv[DIM], Ra[DIM];
+      bound_residuals<DIM>(xp, rd, ra, invT, invT2, vmax, amax, Rv, Ra, mv, ma);
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        float sv = 0.f, sa = 0.f;
-#pragma unroll
-        for (int i = 0; i < NC; ++i) { sv = fmaf(rd[i], xa[a][i], sv); sa = fmaf(ra[i], xa[a][i], sa); }
-        vel[a] = sv * invT; ac[a] = sa * invT2;
-        nv2 = fmaf(vel[a], vel[a], nv2); na2 = fmaf(ac[a], ac[a], na2);
-      }
-      float fv = 0.f, fa = 0.f;
-      if (nv2 > vmax2) { fv = 1.f - vmax * rsqrtf(nv2); mv = fmaxf(mv, nv2 * fv * fv); }
-      if (na2 > amax2) { fa = 1.f - amax * rsqrtf(na2); ma = fmaxf(ma, na2 * fa * fa); }
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const float Ro = -acc[m][a];              // sum_j r_j at t
-        const float Rv = vel[a] * fv * invT;      // Pd^T r_v = dB^T (r_v / T)
-        const float Ra = ac[a] * fa * invT2;      // Pdd^T r_a = d2B^T (r_a / T^2)
-#pragma unroll
-        for (int i = 0; i < NC; ++i) up[a][i] = fmaf(rp[i], Ro, fmaf(rd[i], Rv, fmaf(ra[i], Ra, up[a][i])));
-      }
+      for (int a = 0; a < DIM; ++a) contract_row3(up[a], rp, rd, ra, -acc[m][a], Rv[a], Ra[a]);
     }
   }
 }
 
 // Evaluate and project one iterate without the contraction (the tensor-core form
 // contracts on the MMA): per lane and timestep slot, the residual vectors
-// Ro = sum_j r_j, Rv = r_v / T and Ra = r_a / T^2 (the time scaling folded in,
-// zero past the horizon) and the lane maxima of ||r_j||^2, ||r_v||^2, ||r_a||^2.
+// Ro = sum_j r_j, Rv = r_v / T and Ra = r_a / T^2 (zero past the horizon) and the
+// lane maxima of ||r_j||^2, ||r_v||^2, ||r_a||^2.
 template <int DIM, int NT>
 __device__ __forceinline__ void project_only(
-    const float (&xa)[DIM][NC], const float *tP, const float *tD, const float *tA,
+    const float2 (&xp)[DIM][6], const float *tP, const float *tD, const float *tA,
     const float4 *obs, int n_o, int n_p, float dt, float invT, float invT2, float vmax, float amax,
-    int lane, float (&Ro)[NT][DIM], float (&Rv)[NT][DIM], float (&Ra)[NT][DIM], float &mo,
+    int t0, float (&Ro)[NT][DIM], float (&Rv)[NT][DIM], float (&Ra)[NT][DIM], float &mo,
     float &mv, float &ma, int ts = 32) {
   float pos[NT][DIM], acc[NT][DIM], tm[NT];
+  eval_positions<DIM, NT>(xp, tP, n_p, NT, dt, t0, ts, pos, tm);
 #pragma unroll
-  for (int m = 0; m < NT; ++m) {
-    const int t = lane + ts * m;
-    tm[m] = dt * (float)t;
+  for (int m = 0; m < NT; ++m)
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) { pos[m][a] = 1.0e18f; acc[m][a] = 0.f; }
-    if (t < n_p) {
-      float r[12];
-      load_row(tP + t * ROW, r);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < NC; ++i) s = fmaf(r[i], xa[a][i], s);
-        pos[m][a] = s;
-      }
-    }
-  }
+    for (int a = 0; a < DIM; ++a) acc[m][a] = 0.f;
   pair_loop<DIM, NT>(pos, tm, obs, n_o, acc, mo);
   mv = 0.f; ma = 0.f;
-  const float vmax2 = vmax * vmax, amax2 = amax * amax;
 #pragma unroll
   for (int m = 0; m < NT; ++m) {
-    const int t = lane + ts * m;
+    const int t = t0 + ts * m;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { Ro[m][a] = 0.f; Rv[m][a] = 0.f; Ra[m][a] = 0.f; }
     if (t < n_p) {
-      float rd[12], rA[12];
+      float rd[12], ra[12];
       load_row(tD + t * ROW, rd);
-      load_row(tA + t * ROW, rA);
-      float vel[DIM], ac[DIM], nv2 = 0.f, na2 = 0.f;
+      load_row(tA + t * ROW, ra);
+      bound_residuals<DIM>(xp, rd, ra, invT, invT2, vmax, amax, Rv[m], Ra[m], mv, ma);
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        float sv = 0.f, sa = 0.f;
-#pragma unroll
-        for (int i = 0; i < NC; ++i) { sv = fmaf(rd[i], xa[a][i], sv); sa = fmaf(rA[i], xa[a][i], sa); }
-        vel[a] = sv * invT; ac[a] = sa * invT2;
-        nv2 = fmaf(vel[a], vel[a], nv2); na2 = fmaf(ac[a], ac[a], na2);
-      }
-      float fv = 0.f, fa = 0.f;
-      if (nv2 > vmax2) { fv = 1.f - vmax * rsqrtf(nv2); mv = fmaxf(mv, nv2 * fv * fv); }
-      if (na2 > amax2) { fa = 1.f - amax * rsqrtf(na2); ma = fmaxf(ma, na2 * fa * fa); }
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        Ro[m][a] = -acc[m][a];
-        Rv[m][a] = vel[a] * fv * invT;
-        Ra[m][a] = ac[a] * fa * invT2;
-      }
+      for (int a = 0; a < DIM; ++a) Ro[m][a] = -acc[m][a];
     }
   }
 }
 
 // FP32 contraction of residuals produced by project_only: per-lane partial
-// u = P^T Ro + dB^T Rv + d2B^T Ra over the lane's timesteps.
+// u = P^T Ro + dB^T Rv + d2B^T Ra over the lane's timesteps, as coefficient pairs.
 template <int DIM, int NT>
 __device__ __forceinline__ void contract_fp32(const float (&Ro)[NT][DIM], const float (&Rv)[NT][DIM],
                                               const float (&Ra)[NT][DIM], const float *tP,
-                                              const float *tD, const float *tA, int n_p, int lane,
-                                              float (&up)[DIM][NC], int ts = 32) {
+                                              const float *tD, const float *tA, int n_p, int t0,
+                                              float2 (&up)[DIM][6], int ts = 32) {
 #pragma unroll
   for (int a = 0; a < DIM; ++a)
 #pragma unroll
-    for (int i = 0; i < NC; ++i) up[a][i] = 0.f;
+    for (int j = 0; j < 6; ++j) up[a][j] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int m = 0; m < NT; ++m) {
-    const int t = lane + ts * m;
+    const int t = t0 + ts * m;
     if (t < n_p) {
-      float rp[12], rd[12], rA[12];
+      float rp[12], rd[12], ra[12];
       load_row(tP + t * ROW, rp);
       load_row(tD + t * ROW, rd);
-      load_row(tA + t * ROW, rA);
+      load_row(tA + t * ROW, ra);
 #pragma unroll
-      for (int a = 0; a < DIM; ++a)
-#pragma unroll
-        for (int i = 0; i < NC; ++i)
-          up[a][i] = fmaf(rp[i], Ro[m][a], fmaf(rd[i], Rv[m][a], fmaf(rA[i], Ra[m][a], up[a][i])));
+      for (int a = 0; a < DIM; ++a) contract_row3(up[a], rp, rd, ra, Ro[m][a], Rv[m][a], Ra[m][a]);
     }
   }
 }

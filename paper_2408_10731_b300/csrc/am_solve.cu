@@ -46,7 +46,7 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
   const float *tP = stab + pr.tbl_off;
   const float *tD = tP + n_p * ROW;
   const float *tA = tD + n_p * ROW;
-  const float4 *obs = A.obstacles + (size_t)pr.obs_off * obs_vec(DIM);
+  const float4 *obs = A.obstacles + (size_t)pr.pair_off * pair_vec(DIM);
   const float rho = A.rho;
 
   // ownership: lane 16 a + i holds coefficient i of axis a (a < 2); axis 2 of a 3D
@@ -98,54 +98,13 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
   int k = 0;
   signed char st = 1;
   for (;; ++k) {
-    if (k > 0) {
-      // xi-step in compensated FP32 at the owner lanes
-      const float vo = lam - rho * uo, vo2 = lam2 - rho * uo2;
-      float hi = hq_hi, lo = hq_lo, hi2 = hq2_hi, lo2 = hq2_lo;
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const float xk = __shfl_sync(FULL, xo, (lane & 16) + q);
-        const float vk = __shfl_sync(FULL, vo, (lane & 16) + q);
-        const float g_hi = C[C_G_HI + ri * ROW + q], g_lo = C[C_G_LO + ri * ROW + q];
-        const float k_hi = C[C_K11_HI + ri * ROW + q], k_lo = C[C_K11_LO + ri * ROW + q];
-        df_fma(hi, lo, g_hi, g_lo, xk);
-        df_fma(hi, lo, k_hi, k_lo, vk);
-        if (DIM == 3) {
-          const float xk2 = __shfl_sync(FULL, xo2, q);
-          const float vk2 = __shfl_sync(FULL, vo2, q);
-          df_fma(hi2, lo2, g_hi, g_lo, xk2);
-          df_fma(hi2, lo2, k_hi, k_lo, vk2);
-        }
-      }
-      xo = hi + lo;
-      if (DIM == 3) xo2 = hi2 + lo2;
-    }
-    // broadcast the iterate to every lane
-    float xa[DIM][NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) {
-      xa[0][i] = __shfl_sync(FULL, xo, i);
-      xa[1][i] = __shfl_sync(FULL, xo, 16 + i);
-      if constexpr (DIM == 3) xa[2][i] = __shfl_sync(FULL, xo2, i);
-    }
-    float up[DIM][NC];
-    project_contract<DIM, MAXNT>(xa, tP, tD, tA, obs, n_o, n_p, nt, pr.dt, pr.invT, pr.invT2,
+    if (k > 0) qp_step<DIM>(C, lane, rho, hq_hi, hq_lo, hq2_hi, hq2_lo, lam, lam2, uo, uo2, xo, xo2);
+    float2 xp[DIM][6];
+    broadcast_pairs<DIM>(xo, xo2, xp);
+    float2 up[DIM][6];
+    project_contract<DIM, MAXNT>(xp, tP, tD, tA, obs, n_o, n_p, nt, pr.dt, pr.invT, pr.invT2,
                                  A.vmax, A.amax, lane, up, mo, mv, ma);
-    {
-      float v32[32];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        v32[i] = i < NC ? up[0][i] : 0.f;
-        v32[16 + i] = i < NC ? up[1][i] : 0.f;
-      }
-      uo = reduce_scatter32(v32, lane);
-      if constexpr (DIM == 3) {
-        float v16[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v16[i] = i < NC ? up[2][i] : 0.f;
-        uo2 = reduce_scatter16(v16, lane);
-      }
-    }
+    scatter_pairs<DIM>(up, lane, uo, uo2);
     mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
     if (k > 0) { // Line 6: multiplier update (lambda0 = 0 at the initial projection)
       lam -= rho * uo;
@@ -183,21 +142,21 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
   }
 }
 
-// ---- two warps per trajectory ---------------------------------------------------
-// The team's warps r = 0, 1 own timesteps t = 2 lane + r + 64 m (interleaved, so
-// both carry the same share of a ragged horizon). Each evaluates, projects and
+// ---- W warps per trajectory (W = 2 or 4) ---------------------------------------------
+// The team's warps r = 0 .. W-1 own timesteps t = W lane + r + 32 W m (interleaved,
+// so all carry the same share of a ragged horizon). Each evaluates, projects and
 // contracts its timesteps; the partial contractions (after each warp's
 // reduce-scatter) and the residual maxima are exchanged through double-buffered
-// shared memory with one named barrier per iteration, and both warps add them in
-// the same order, so they hold bitwise-identical u, lambda and xi and take the
-// same decisions. The compensated QP step runs redundantly in both.
+// shared memory with one named barrier per iteration, and every warp adds them in
+// the same order (r = 0, 1, ...), so all hold bitwise-identical u, lambda and xi
+// and take the same decisions. The compensated QP step runs redundantly in each.
 constexpr int XCH = 72; // floats per exchange slot: u (32 lanes), u of axis 2 (32), maxima, flag
 
-__device__ __forceinline__ void team_bar(int id) {
-  asm volatile("bar.sync %0, 64;" :: "r"(id) : "memory");
+__device__ __forceinline__ void team_bar(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(threads) : "memory");
 }
 
-template <int DIM, int NT>
+template <int DIM, int NT, int W>
 __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *stab, int lane,
                                         int r, float *xch, int bar_id,
                                         unsigned long long deadline) {
@@ -208,7 +167,7 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
   const float *tP = stab + pr.tbl_off;
   const float *tD = tP + n_p * ROW;
   const float *tA = tD + n_p * ROW;
-  const float4 *obs = A.obstacles + (size_t)pr.obs_off * obs_vec(DIM);
+  const float4 *obs = A.obstacles + (size_t)pr.pair_off * pair_vec(DIM);
   const float rho = A.rho;
   const int oi = lane & 15, oa = lane >> 4;
   const int ri = oi < NC ? oi : NC - 1;
@@ -253,56 +212,17 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
   int k = 0, par = 0;
   signed char st = 1;
   for (;; ++k) {
-    if (k > 0) {
-      const float vo = lam - rho * uo, vo2 = lam2 - rho * uo2;
-      float hi = hq_hi, lo = hq_lo, hi2 = hq2_hi, lo2 = hq2_lo;
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const float xk = __shfl_sync(FULL, xo, (lane & 16) + q);
-        const float vk = __shfl_sync(FULL, vo, (lane & 16) + q);
-        const float g_hi = C[C_G_HI + ri * ROW + q], g_lo = C[C_G_LO + ri * ROW + q];
-        const float k_hi = C[C_K11_HI + ri * ROW + q], k_lo = C[C_K11_LO + ri * ROW + q];
-        df_fma(hi, lo, g_hi, g_lo, xk);
-        df_fma(hi, lo, k_hi, k_lo, vk);
-        if (DIM == 3) {
-          const float xk2 = __shfl_sync(FULL, xo2, q);
-          const float vk2 = __shfl_sync(FULL, vo2, q);
-          df_fma(hi2, lo2, g_hi, g_lo, xk2);
-          df_fma(hi2, lo2, k_hi, k_lo, vk2);
-        }
-      }
-      xo = hi + lo;
-      if (DIM == 3) xo2 = hi2 + lo2;
-    }
-    float xa[DIM][NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) {
-      xa[0][i] = __shfl_sync(FULL, xo, i);
-      xa[1][i] = __shfl_sync(FULL, xo, 16 + i);
-      if constexpr (DIM == 3) xa[2][i] = __shfl_sync(FULL, xo2, i);
-    }
-    float up[DIM][NC];
-    project_contract<DIM, NT>(xa, tP, tD, tA, obs, n_o, n_p, NT, pr.dt, pr.invT, pr.invT2,
-                              A.vmax, A.amax, 2 * lane + r, up, mo, mv, ma, 64);
+    if (k > 0) qp_step<DIM>(C, lane, rho, hq_hi, hq_lo, hq2_hi, hq2_lo, lam, lam2, uo, uo2, xo, xo2);
+    float2 xp[DIM][6];
+    broadcast_pairs<DIM>(xo, xo2, xp);
+    float2 up[DIM][6];
+    project_contract<DIM, NT>(xp, tP, tD, tA, obs, n_o, n_p, NT, pr.dt, pr.invT, pr.invT2,
+                              A.vmax, A.amax, W * lane + r, up, mo, mv, ma, 32 * W);
     float part = 0.f, part2 = 0.f;
-    {
-      float v32[32];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        v32[i] = i < NC ? up[0][i] : 0.f;
-        v32[16 + i] = i < NC ? up[1][i] : 0.f;
-      }
-      part = reduce_scatter32(v32, lane);
-      if constexpr (DIM == 3) {
-        float v16[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v16[i] = i < NC ? up[2][i] : 0.f;
-        part2 = reduce_scatter16(v16, lane);
-      }
-    }
+    scatter_pairs<DIM>(up, lane, part, part2);
     mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
-    // exchange with the partner warp
-    float *mine = xch + (par * 2 + r) * XCH;
+    // exchange with the partner warps
+    float *mine = xch + (par * W + r) * XCH;
     mine[lane] = part;
     if (DIM == 3) mine[32 + lane] = part2;
     if (lane == 0) {
@@ -311,11 +231,18 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
       if (r == 0 && deadline && globaltimer_ns() > deadline) late = 1.f;
       mine[67] = late;
     }
-    team_bar(bar_id);
-    const float *s0 = xch + (par * 2 + 0) * XCH, *s1 = xch + (par * 2 + 1) * XCH;
-    uo = s0[lane] + s1[lane];
-    if (DIM == 3) uo2 = s0[32 + lane] + s1[32 + lane];
-    mo = fmaxf(s0[64], s1[64]); mv = fmaxf(s0[65], s1[65]); ma = fmaxf(s0[66], s1[66]);
+    team_bar(bar_id, 32 * W);
+    const float *s0 = xch + par * W * XCH;
+    uo = s0[lane];
+    if (DIM == 3) uo2 = s0[32 + lane];
+    mo = s0[64]; mv = s0[65]; ma = s0[66];
+#pragma unroll
+    for (int w = 1; w < W; ++w) {
+      const float *sw = s0 + w * XCH;
+      uo += sw[lane];
+      if (DIM == 3) uo2 += sw[32 + lane];
+      mo = fmaxf(mo, sw[64]); mv = fmaxf(mv, sw[65]); ma = fmaxf(ma, sw[66]);
+    }
     const bool late = s0[67] != 0.f;
     par ^= 1;
     if (k > 0) {
@@ -351,32 +278,32 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
   }
 }
 
-template <int DIM, int NT, int MAXNT>
+template <int DIM, int NT, int MAXNT, int W>
 __device__ __forceinline__ void team_nt(const SolveArgs &A, int b, const float *stab, int lane,
                                         int r, float *xch, int bar_id,
                                         unsigned long long deadline, int nt) {
   if constexpr (NT >= MAXNT) {
-    solve_team<DIM, MAXNT>(A, b, stab, lane, r, xch, bar_id, deadline);
+    solve_team<DIM, MAXNT, W>(A, b, stab, lane, r, xch, bar_id, deadline);
   } else {
-    if (nt <= NT) solve_team<DIM, NT>(A, b, stab, lane, r, xch, bar_id, deadline);
-    else team_nt<DIM, NT + 1, MAXNT>(A, b, stab, lane, r, xch, bar_id, deadline, nt);
+    if (nt <= NT) solve_team<DIM, NT, W>(A, b, stab, lane, r, xch, bar_id, deadline);
+    else team_nt<DIM, NT + 1, MAXNT, W>(A, b, stab, lane, r, xch, bar_id, deadline, nt);
   }
 }
 
-template <int DIM, int MAXNT>
+template <int DIM, int MAXNT, int W>
 __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32)
 k_am_team(const __grid_constant__ SolveArgs A) {
   extern __shared__ float4 smem4[];
-  const int nteam = blockDim.x / 64;
+  const int nteam = blockDim.x / (32 * W);
   const float4 *g4 = reinterpret_cast<const float4 *>(A.tables);
   for (int i = threadIdx.x; i < A.table_floats_total / 4; i += blockDim.x) smem4[i] = g4[i];
   float *stab = reinterpret_cast<float *>(smem4);
-  float *xch_all = stab + A.table_floats_total;          // [teams][2 parities][2 warps][XCH]
-  int *sitem = reinterpret_cast<int *>(xch_all + nteam * 4 * XCH);
+  float *xch_all = stab + A.table_floats_total;          // [teams][2 parities][W warps][XCH]
+  int *sitem = reinterpret_cast<int *>(xch_all + nteam * 2 * W * XCH);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int team = warp >> 1, r = warp & 1, bar_id = 1 + team;
-  float *xch = xch_all + team * 4 * XCH;
+  const int team = warp / W, r = warp % W, bar_id = 1 + team;
+  float *xch = xch_all + team * 2 * W * XCH;
 
   unsigned long long deadline = 0;
   if (A.timeout_ns) {
@@ -390,13 +317,13 @@ k_am_team(const __grid_constant__ SolveArgs A) {
   }
   for (;;) {
     if (r == 0 && lane == 0) sitem[team] = atomicAdd(A.queue, 1);
-    team_bar(bar_id);
+    team_bar(bar_id, 32 * W);
     const int item = sitem[team];
-    team_bar(bar_id);
+    team_bar(bar_id, 32 * W);
     if (item >= A.n_traj) break;
     const int b = A.order[item];
-    const int nt = (A.problems[A.traj_problem[b]].n_p + 63) >> 6;
-    team_nt<DIM, 1, MAXNT>(A, b, stab, lane, r, xch, bar_id, deadline, nt);
+    const int nt = (A.problems[A.traj_problem[b]].n_p + 32 * W - 1) / (32 * W);
+    team_nt<DIM, 1, MAXNT, W>(A, b, stab, lane, r, xch, bar_id, deadline, nt);
   }
 }
 
@@ -414,7 +341,7 @@ __device__ __forceinline__ void solve_nt(const SolveArgs &A, int b, const float 
 }
 
 template <int DIM, int MAXNT>
-__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32)
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32, 1)
 k_am_fp32(const __grid_constant__ SolveArgs A) {
   extern __shared__ float4 smem4[];
   const float4 *g4 = reinterpret_cast<const float4 *>(A.tables);
@@ -444,15 +371,21 @@ k_am_fp32(const __grid_constant__ SolveArgs A) {
   }
 }
 
-template <int DIM, int MAXNT, bool TEAM>
+template <int W> struct TeamKernel {
+  template <int DIM, int MAXNT> static constexpr auto get() { return k_am_team<DIM, (MAXNT + W - 1) / W, W>; }
+};
+template <> struct TeamKernel<1> {
+  template <int DIM, int MAXNT> static constexpr auto get() { return k_am_fp32<DIM, MAXNT>; }
+};
+
+template <int DIM, int MAXNT, int W>
 static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_sm,
                             cudaStream_t s, LaunchShape *used) {
-  auto kern = TEAM ? k_am_team<DIM, (MAXNT + 1) / 2> : k_am_fp32<DIM, MAXNT>;
+  auto kern = TeamKernel<W>::template get<DIM, MAXNT>();
   const int warps = shape.warps_per_block > 0 ? shape.warps_per_block : 4;
-  if (warps > MAX_WARPS_PER_BLOCK || (TEAM && (warps & 1))) return cudaErrorInvalidValue;
-  const int per = TEAM ? 2 : 1; // warps per trajectory
+  if (warps > MAX_WARPS_PER_BLOCK || warps % W != 0) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * (size_t)a.table_floats_total +
-                      (TEAM ? (size_t)(warps / 2) * (4 * XCH * sizeof(float) + sizeof(int)) : 0);
+                      (W > 1 ? (size_t)(warps / W) * (2 * W * XCH * sizeof(float) + sizeof(int)) : 0);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -460,23 +393,25 @@ static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   if (shape.blocks_per_sm > 0 && shape.blocks_per_sm < occ) occ = shape.blocks_per_sm;
-  long long want = ((long long)a.n_traj * per + warps - 1) / warps;
+  long long want = ((long long)a.n_traj * W + warps - 1) / warps;
   long long grid = (long long)n_sm * occ;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
-  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = per; }
+  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = W; }
   kern<<<(unsigned)grid, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s, LaunchShape *used) {
-  if (precision == 1) return launch_am_mixed(dim, max_np, a, n_sm, s);
+  if (precision == 1) return launch_am_mixed(dim, max_np, a, shape, n_sm, s, used);
   const int nt = (max_np + 31) / 32;
-  const bool team = shape.team == 2;
+  const int team = shape.team;
+  if (team != 0 && team != 1 && team != 2 && team != 4) return cudaErrorInvalidValue;
 #define TB_PICK(D, N)                                                                   \
-  return team ? launch_t<D, N, true>(a, shape, n_sm, s, used)                           \
-              : launch_t<D, N, false>(a, shape, n_sm, s, used)
+  return team == 4 ? launch_t<D, N, 4>(a, shape, n_sm, s, used)                         \
+       : team == 2 ? launch_t<D, N, 2>(a, shape, n_sm, s, used)                         \
+                   : launch_t<D, N, 1>(a, shape, n_sm, s, used)
   if (dim == 2) {
     if (nt <= 4) TB_PICK(2, 4);
     if (nt <= 5) TB_PICK(2, 5);

@@ -16,7 +16,7 @@ constexpr int MAX_STEPS = 256;
 struct ProblemDev {
   int n_p;        // timesteps
   int n_o;        // obstacles
-  int obs_off;    // first obstacle (index into the packed obstacle array)
+  int pair_off;   // first obstacle-pair record (index into the packed pair array)
   int tbl_off;    // float offset of this horizon's P/dB/ddB tables in the table buffer
   float dt;       // T / (n_p - 1), seconds between grid points
   float invT;     // 1 / T   (Pdot = dB/dtau * invT)
@@ -46,11 +46,20 @@ constexpr int CONST_FLOATS = C_C_LO + 3 * ROW; // 672
 // FP32 copies of FP64 values, column 11 zero. TABLE_FLOATS(n_p) = 36 n_p.
 __host__ __device__ inline int table_floats(int n_p) { return 3 * ROW * n_p; }
 
-// Packed obstacle record: OBS_VEC(dim) float4 per obstacle (centre c and
-// velocity v stored negated).
-//  2D: {-cx, -cy, -vx, -vy}, {1/ax, 1/ay, ax, ay}
-//  3D: {-cx, -cy, -cz, 1/ax}, {-vx, -vy, -vz, 1/ay}, {ax, ay, az, 1/az}
-__host__ __device__ constexpr int obs_vec(int dim) { return dim == 2 ? 2 : 3; }
+// Packed obstacle-pair records: a problem's obstacles j = 2q, 2q + 1 share record q
+// (an odd count is padded with a sentinel that is never inside), each record
+// PAIR_VEC(dim) float4, every float4 holding the same quantity of both obstacles so
+// that the containment test runs on packed two-lane arithmetic. The values are
+// normalised by the semi-axes a, u = (p - c - v t) / a = p * ia + (nc + nv t), with
+// nc = -c / a, nv = -v / a, ia = 1 / a (formed in FP64, rounded once):
+//  2D: {ncx0, ncx1, nvx0, nvx1}, {ncy0, ncy1, nvy0, nvy1}, {iax0, iax1, iay0, iay1},
+//      {ax0, ax1, ay0, ay1}
+//  3D: {ncx0, ncx1, nvx0, nvx1}, {ncy0, ncy1, nvy0, nvy1}, {ncz0, ncz1, nvz0, nvz1},
+//      {iax0, iax1, iay0, iay1}, {iaz0, iaz1, ax0, ax1}, {ay0, ay1, az0, az1}
+// Sentinel half: nc = 1e18, nv = 0, ia = a = 1.
+__host__ __device__ constexpr int pair_vec(int dim) { return dim == 2 ? 4 : 6; }
+__host__ __device__ constexpr int pair_count(int n_o) { return (n_o + 1) / 2; }
+constexpr float PAIR_SENTINEL = 1.0e18f;
 
 // Arguments of one solve launch.
 struct SolveArgs {
@@ -111,19 +120,26 @@ cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const 
                                   const double *d_start, const double *d_goal, int dim,
                                   double rho, double w_smooth, double w_track, int cost_mode,
                                   int max_np, float *d_constants, cudaStream_t s);
-cudaError_t launch_pack_obstacles(int dim, int n_obs, const float *centers, const float *axes,
-                                  const float *vel, const int *obs_problem, float4 *out,
-                                  ProblemDev *problems, cudaStream_t s);
+// Obstacle-pair records of all problems: n_slots = 2 x (total pair records); offsets
+// (CSR obstacle offsets, n_problems + 1) and pair_off (first record of each problem,
+// n_problems + 1) are device arrays.
+cudaError_t launch_pack_obstacles(int dim, int n_problems, int n_slots, const int *offsets,
+                                  const int *pair_off, const float *centers, const float *axes,
+                                  const float *vel, float4 *out, ProblemDev *problems,
+                                  cudaStream_t s);
 // CTA shape of the persistent solve launch (the autotuner's search space);
-// zero fields take the defaults (4 warps, occupancy-limited blocks per SM).
+// zero fields take the defaults (FP32 form: 4 warps; tensor-core form: the batch
+// spread over all SMs; occupancy-limited blocks per SM; one warp per trajectory).
 struct LaunchShape {
   int warps_per_block;
   int blocks_per_sm;
   int grid; // filled in by the launcher
   int team; // warps per trajectory: 1 or 2
 };
-// tensor-core form (am_mixed.cu); every problem of the batch has n_p steps
-cudaError_t launch_am_mixed(int dim, int n_p, const SolveArgs &a, int n_sm, cudaStream_t s);
+// tensor-core form (am_mixed.cu); every problem of the batch has n_p steps; the
+// shape's warps per block (0: the batch spread over all SMs) and blocks per SM apply
+cudaError_t launch_am_mixed(int dim, int n_p, const SolveArgs &a, const LaunchShape &shape,
+                            int n_sm, cudaStream_t s, LaunchShape *used);
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s,
                             LaunchShape *used);

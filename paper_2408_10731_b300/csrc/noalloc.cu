@@ -48,8 +48,9 @@ constexpr size_t OFF_HZ = al(OFF_TABLES + sizeof(float) * NA_MAX_TABLE_FLOATS);
 constexpr size_t OFF_HOFF = al(OFF_HZ + sizeof(int) * (MAX_STEPS + 1));
 constexpr size_t OFF_OFFSETS = al(OFF_HOFF + sizeof(int) * (MAX_STEPS + 1));
 constexpr size_t OFF_OBS = al(OFF_OFFSETS + sizeof(int) * (NA_MAX_PROBLEMS + 1));
-constexpr size_t OFF_OBS_PROBLEM = al(OFF_OBS + sizeof(float4) * 3 * NA_MAX_OBSTACLES);
-constexpr size_t OFF_ORDER = al(OFF_OBS_PROBLEM + sizeof(int) * NA_MAX_OBSTACLES);
+constexpr size_t OFF_PAIR_OFF = al(OFF_OBS + sizeof(float4) * pair_vec(3) *
+                                             ((NA_MAX_OBSTACLES + NA_MAX_PROBLEMS) / 2 + 1));
+constexpr size_t OFF_ORDER = al(OFF_PAIR_OFF + sizeof(int) * (NA_MAX_PROBLEMS + 1));
 constexpr size_t OFF_WORDS = al(OFF_ORDER + sizeof(int) * NA_MAX_TRAJ); // queue, flags, t0
 constexpr size_t SCRATCH_BYTES = al(OFF_WORDS + 64);                    // about 1.4 MB
 
@@ -77,19 +78,10 @@ cudaError_t scratch_address(int dev, unsigned char **out) {
   return cudaSuccess;
 }
 
-// order[k] = k; obs_problem[j] = problem owning obstacle j (offsets in scratch).
-__global__ void k_noalloc_index(const int *offsets, int n_problems, int n_obs, int n_traj,
-                                int *obs_problem, int *order) {
+// order[k] = k (the queue runs the trajectories in index order).
+__global__ void k_noalloc_order(int n_traj, int *order) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_traj) order[i] = i;
-  if (i < n_obs) {
-    int lo = 0, hi = n_problems - 1;
-    while (lo < hi) { // last p with offsets[p] <= i
-      const int mid = (lo + hi + 1) >> 1;
-      if (offsets[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    obs_problem[i] = lo;
-  }
 }
 
 traj_status err(traj_status s, const std::string &msg) {
@@ -152,11 +144,15 @@ extern "C" traj_status traj_solve_noalloc(
     if (seen[n]) { hz[n_hz] = n; hoff[n_hz] = tot; tot += table_floats(n); ++n_hz; }
   if (tot > NA_MAX_TABLE_FLOATS) return err(TRAJ_ESHAPE, "too many distinct horizons (tables > 160 KB)");
   ProblemDev recs[NA_MAX_PROBLEMS];
+  int pair_off[NA_MAX_PROBLEMS + 1];
+  pair_off[0] = 0;
+  for (int p = 0; p < n_problems; ++p)
+    pair_off[p + 1] = pair_off[p] + pair_count(obs_offsets[p + 1] - obs_offsets[p]);
   for (int p = 0; p < n_problems; ++p) {
     ProblemDev r{};
     r.n_p = n_steps[p];
     r.n_o = obs_offsets[p + 1] - obs_offsets[p];
-    r.obs_off = obs_offsets[p];
+    r.pair_off = pair_off[p];
     for (int h = 0; h < n_hz; ++h)
       if (hz[h] == r.n_p) r.tbl_off = hoff[h];
     const double T = duration[p];
@@ -183,7 +179,7 @@ extern "C" traj_status traj_solve_noalloc(
   int *d_hoff = reinterpret_cast<int *>(S + OFF_HOFF);
   int *d_offsets = reinterpret_cast<int *>(S + OFF_OFFSETS);
   float4 *d_obs = reinterpret_cast<float4 *>(S + OFF_OBS);
-  int *d_obs_problem = reinterpret_cast<int *>(S + OFF_OBS_PROBLEM);
+  int *d_pair_off = reinterpret_cast<int *>(S + OFF_PAIR_OFF);
   int *d_order = reinterpret_cast<int *>(S + OFF_ORDER);
   int *d_words = reinterpret_cast<int *>(S + OFF_WORDS);
 
@@ -196,12 +192,13 @@ extern "C" traj_status traj_solve_noalloc(
   NA_CK(cudaMemcpyAsync(d_hz, hz, sizeof(int) * n_hz, cudaMemcpyHostToDevice, s));
   NA_CK(cudaMemcpyAsync(d_hoff, hoff, sizeof(int) * n_hz, cudaMemcpyHostToDevice, s));
   NA_CK(cudaMemcpyAsync(d_offsets, obs_offsets, sizeof(int) * (n_problems + 1), cudaMemcpyHostToDevice, s));
+  NA_CK(cudaMemcpyAsync(d_pair_off, pair_off, sizeof(int) * (n_problems + 1), cudaMemcpyHostToDevice, s));
   NA_CK(cudaMemsetAsync(d_words, 0, 64, s));
-  const int n_idx = std::max(N, n_traj);
-  k_noalloc_index<<<(n_idx + 255) / 256, 256, 0, s>>>(d_offsets, n_problems, N, n_traj, d_obs_problem, d_order);
+  k_noalloc_order<<<(n_traj + 255) / 256, 256, 0, s>>>(n_traj, d_order);
   NA_CK(cudaGetLastError());
   NA_CK(launch_setup_tables(d_hz, d_hoff, n_hz, d_tables, s));
-  NA_CK(launch_pack_obstacles(D, N, centers, semi_axes, velocities, d_obs_problem, d_obs, d_problems, s));
+  NA_CK(launch_pack_obstacles(D, n_problems, 2 * pair_off[n_problems], d_offsets, d_pair_off,
+                              centers, semi_axes, velocities, d_obs, d_problems, s));
   NA_CK(launch_setup_problems(d_problems, n_problems, d_T, d_start, d_goal, D, c.rho, c.w_smooth,
                               c.w_track, c.cost_mode, max_np, d_const, s));
   SolveArgs a{};

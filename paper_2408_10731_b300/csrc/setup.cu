@@ -200,30 +200,45 @@ __global__ void k_setup_problems(ProblemDev *problems, const double *Tarr, const
   }
 }
 
-__global__ void k_pack_obstacles(int dim, int n_obs, const float *cen, const float *ax,
-                                 const float *vel, const int *obs_problem, float4 *out,
-                                 ProblemDev *problems) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n_obs) return;
-  float c[3] = {0, 0, 0}, a[3] = {1, 1, 1}, v[3] = {0, 0, 0};
+// One thread per half of a pair record (see the layout in internal.cuh): problem p
+// owns records pair_off[p] .. pair_off[p + 1) - 1; the record's half h holds the
+// problem's obstacle 2 (q - pair_off[p]) + h, or the sentinel past its last obstacle.
+__global__ void k_pack_obstacles(int dim, int n_problems, int n_slots, const int *offsets,
+                                 const int *pair_off, const float *cen, const float *ax,
+                                 const float *vel, float4 *out, ProblemDev *problems) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots) return;
+  const int q = s >> 1, h = s & 1;
+  int lo = 0, hi = n_problems - 1;
+  while (lo < hi) { // last problem whose first record is <= q
+    const int mid = (lo + hi + 1) >> 1;
+    if (pair_off[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  const int p = lo;
+  const int l = 2 * (q - pair_off[p]) + h;
+  const int n_o = offsets[p + 1] - offsets[p];
+  float *rec = reinterpret_cast<float *>(out + (size_t)pair_vec(dim) * q);
+  const int B = 4 * dim;
+  if (l >= n_o) {
+    for (int d = 0; d < dim; ++d) {
+      rec[4 * d + h] = PAIR_SENTINEL;
+      rec[4 * d + 2 + h] = 0.f;
+      rec[B + 2 * d + h] = 1.f;
+      rec[B + 2 * dim + 2 * d + h] = 1.f;
+    }
+    return;
+  }
+  const int j = offsets[p] + l;
   bool ok = true;
   for (int d = 0; d < dim; ++d) {
-    c[d] = cen[j * dim + d];
-    a[d] = ax[j * dim + d];
-    v[d] = vel[j * dim + d];
-    ok = ok && isfinite(c[d]) && isfinite(v[d]) && isfinite(a[d]) && a[d] > 0.f;
+    const double c = cen[j * dim + d], a = ax[j * dim + d], v = vel[j * dim + d];
+    ok = ok && isfinite(c) && isfinite(v) && isfinite(a) && a > 0.0;
+    rec[4 * d + h] = (float)(-c / a);
+    rec[4 * d + 2 + h] = (float)(-v / a);
+    rec[B + 2 * d + h] = (float)(1.0 / a);
+    rec[B + 2 * dim + 2 * d + h] = (float)a;
   }
-  if (!ok) atomicOr(&problems[obs_problem[j]].nan_flag, 1);
-  // centre and velocity are stored negated: the solve forms p - c - v t as
-  // fma(-v, t, p + (-c)) with packed two-lane arithmetic
-  if (dim == 2) {
-    out[2 * j + 0] = make_float4(-c[0], -c[1], -v[0], -v[1]);
-    out[2 * j + 1] = make_float4(1.f / a[0], 1.f / a[1], a[0], a[1]);
-  } else {
-    out[3 * j + 0] = make_float4(-c[0], -c[1], -c[2], 1.f / a[0]);
-    out[3 * j + 1] = make_float4(-v[0], -v[1], -v[2], 1.f / a[1]);
-    out[3 * j + 2] = make_float4(a[0], a[1], a[2], 1.f / a[2]);
-  }
+  if (!ok) atomicOr(&problems[p].nan_flag, 1);
 }
 
 cudaError_t launch_setup_tables(const int *d_horizons, const int *d_offsets, int n_horizons,
@@ -247,12 +262,14 @@ cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_obstacles(int dim, int n_obs, const float *centers, const float *axes,
-                                  const float *vel, const int *obs_problem, float4 *out,
-                                  ProblemDev *problems, cudaStream_t s) {
-  if (n_obs <= 0) return cudaSuccess;
-  k_pack_obstacles<<<(n_obs + 255) / 256, 256, 0, s>>>(dim, n_obs, centers, axes, vel,
-                                                       obs_problem, out, problems);
+cudaError_t launch_pack_obstacles(int dim, int n_problems, int n_slots, const int *offsets,
+                                  const int *pair_off, const float *centers, const float *axes,
+                                  const float *vel, float4 *out, ProblemDev *problems,
+                                  cudaStream_t s) {
+  if (n_slots <= 0 || n_problems <= 0) return cudaSuccess;
+  k_pack_obstacles<<<(n_slots + 255) / 256, 256, 0, s>>>(dim, n_problems, n_slots, offsets,
+                                                        pair_off, centers, axes, vel, out,
+                                                        problems);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ struct traj_batch {
   int *d_horizons = nullptr, *d_hoffsets = nullptr;
   float4 *d_obs = nullptr;
   float *d_obs_stage = nullptr;
-  int *d_obs_problem = nullptr;
+  int *d_obs_index = nullptr; // CSR obstacle offsets [P + 1], then first pair record [P + 1]
   int *d_traj_problem = nullptr, *d_order = nullptr;
   float *d_xi0 = nullptr, *d_xi = nullptr, *d_lam = nullptr, *d_u = nullptr, *d_res = nullptr;
   int *d_iters = nullptr;
@@ -43,7 +43,7 @@ struct traj_batch {
   unsigned long long *d_t0 = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // launch shape of the solve (set by traj_autotune / traj_set_launch_shape)
-  LaunchShape shape{4, 0, 0, 1};
+  LaunchShape shape{0, 0, 0, 1};
   // the solve captured as a CUDA graph, replayed while its key is unchanged
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -93,7 +93,7 @@ template <class T> static cudaError_t dalloc(T **p, size_t n) {
 
 static void free_all(traj_batch *b) {
   void *ptrs[] = {b->d_problems, b->d_T, b->d_start, b->d_goal, b->d_constants, b->d_tables,
-                  b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_problem,
+                  b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_index,
                   b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res,
                   b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0, b->d_L, b->d_r,
                   b->d_caug, b->d_proj, b->d_elite, b->d_sflag};
@@ -180,8 +180,8 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
   if ((e = dalloc(&b->d_problems, P)) || (e = dalloc(&b->d_T, P)) || (e = dalloc(&b->d_start, P * D)) ||
       (e = dalloc(&b->d_goal, P * D)) || (e = dalloc(&b->d_constants, P * CONST_FLOATS)) ||
       (e = dalloc(&b->d_horizons, MAX_STEPS + 1)) || (e = dalloc(&b->d_hoffsets, MAX_STEPS + 1)) ||
-      (e = dalloc(&b->d_obs, N * obs_vec(c.dim))) || (e = dalloc(&b->d_obs_stage, 3 * N * D)) ||
-      (e = dalloc(&b->d_obs_problem, N)) || (e = dalloc(&b->d_traj_problem, B)) ||
+      (e = dalloc(&b->d_obs, ((N + P) / 2 + 1) * pair_vec(c.dim))) ||
+      (e = dalloc(&b->d_obs_stage, 3 * N * D)) || (e = dalloc(&b->d_obs_index, 2 * (P + 1))) || (e = dalloc(&b->d_traj_problem, B)) ||
       (e = dalloc(&b->d_order, B)) || (e = dalloc(&b->d_xi0, B * D * NC)) ||
       (e = dalloc(&b->d_xi, B * D * NC)) || (e = dalloc(&b->d_lam, B * D * NC)) ||
       (e = dalloc(&b->d_u, B * D * NC)) || (e = dalloc(&b->d_res, B * 3)) ||
@@ -271,9 +271,10 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
   if (N > b->cfg.max_obstacles) return fail(b, TRAJ_ESHAPE, "obstacle count exceeds max_obstacles");
   if (N > 0 && (!centers || !semi_axes || !velocities))
     return fail(b, TRAJ_EINVAL, "NULL obstacle array");
-  std::vector<int> obs_problem(N);
-  for (int p = 0; p < P; ++p)
-    for (int j = offsets[p]; j < offsets[p + 1]; ++j) obs_problem[j] = p;
+  // pair records: problem p owns pair_count(n_o) of them from index[P + 1 + p]
+  std::vector<int> index(2 * (P + 1));
+  for (int p = 0; p <= P; ++p) index[p] = offsets[p];
+  for (int p = 0; p < P; ++p) index[P + 2 + p] = index[P + 1 + p] + pair_count(offsets[p + 1] - offsets[p]);
   // tables offsets per horizon (same order as in set_problems)
   std::vector<int> hz(b->n_steps);
   std::sort(hz.begin(), hz.end());
@@ -284,7 +285,7 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
     ProblemDev r{};
     r.n_p = b->n_steps[p];
     r.n_o = offsets[p + 1] - offsets[p];
-    r.obs_off = offsets[p];
+    r.pair_off = index[P + 1 + p];
     int off = 0;
     for (int h : hz) { if (h == r.n_p) break; off += table_floats(h); }
     r.tbl_off = off;
@@ -302,10 +303,11 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
     CK(b, cudaMemcpyAsync(st_c, centers, sizeof(float) * N * D, cudaMemcpyDefault, b->stream));
     CK(b, cudaMemcpyAsync(st_a, semi_axes, sizeof(float) * N * D, cudaMemcpyDefault, b->stream));
     CK(b, cudaMemcpyAsync(st_v, velocities, sizeof(float) * N * D, cudaMemcpyDefault, b->stream));
-    CK(b, cudaMemcpyAsync(b->d_obs_problem, obs_problem.data(), sizeof(int) * N, cudaMemcpyHostToDevice, b->stream));
   }
   CK(b, cudaMemcpyAsync(b->d_problems, recs.data(), sizeof(ProblemDev) * P, cudaMemcpyHostToDevice, b->stream));
-  CK(b, launch_pack_obstacles(D, N, st_c, st_a, st_v, b->d_obs_problem, b->d_obs, b->d_problems, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_obs_index, index.data(), sizeof(int) * 2 * (P + 1), cudaMemcpyHostToDevice, b->stream));
+  CK(b, launch_pack_obstacles(D, P, 2 * index[2 * P + 1], b->d_obs_index, b->d_obs_index + P + 1,
+                              st_c, st_a, st_v, b->d_obs, b->d_problems, b->stream));
   CK(b, launch_setup_problems(b->d_problems, P, b->d_T, b->d_start, b->d_goal, D, b->cfg.rho,
                               b->cfg.w_smooth, b->cfg.w_track, b->cfg.cost_mode, b->max_np_used,
                               b->d_constants, b->stream));
@@ -499,11 +501,14 @@ traj_status traj_get_state(traj_batch *b, float *lambda, float *u) {
 
 traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape) {
   if (!b || !shape) return TRAJ_EINVAL;
-  if (shape->warps_per_block < 1 || shape->warps_per_block > 8 || shape->blocks_per_sm < 0 ||
-      (shape->warps_per_trajectory != 1 && shape->warps_per_trajectory != 2) ||
-      (shape->warps_per_trajectory == 2 && (shape->warps_per_block & 1)))
-    return fail(b, TRAJ_EINVAL, "warps_per_block in [1, 8] (even for 2 warps per trajectory), "
-                                "blocks_per_sm >= 0, warps_per_trajectory 1 or 2");
+  if (shape->warps_per_block < 0 || shape->warps_per_block > 8 || shape->blocks_per_sm < 0 ||
+      (shape->warps_per_trajectory != 1 && shape->warps_per_trajectory != 2 &&
+       shape->warps_per_trajectory != 4) ||
+      (shape->warps_per_block % shape->warps_per_trajectory) != 0 ||
+      (b->cfg.precision == TRAJ_PREC_MIXED && shape->warps_per_trajectory != 1))
+    return fail(b, TRAJ_EINVAL, "warps_per_block in [0, 8] (0: default; a multiple of "
+                                "warps_per_trajectory), blocks_per_sm >= 0, warps_per_trajectory "
+                                "1, 2 or 4 (1 in the tensor-core form)");
   b->shape = LaunchShape{shape->warps_per_block, shape->blocks_per_sm, 0, shape->warps_per_trajectory};
   invalidate_graph(b);
   return TRAJ_OK;
@@ -517,10 +522,10 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
   static const int cand_b[] = {0, 1, 2, 4};
   LaunchShape best{4, 0, 0, 1};
   float best_t = 1e30f;
-  for (int team = 1; team <= (b->cfg.precision == TRAJ_PREC_MIXED ? 1 : 2); ++team)
+  for (int team = 1; team <= (b->cfg.precision == TRAJ_PREC_MIXED ? 1 : 4); team *= 2)
   for (int w : cand_w)
     for (int bps : cand_b) {
-      if (team == 2 && (w & 1)) continue;
+      if (w % team != 0) continue;
       b->shape = LaunchShape{w, bps, 0, team};
       invalidate_graph(b);
       float tot = 0.f;
