@@ -11,6 +11,7 @@ batch (independent problems, no data-path collective: weak scaling); the
 barrier and the max over ranks are the only cross-rank steps.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -34,6 +35,44 @@ WORKLOAD_UNEVEN = ("uneven 2D batch: 2048 problems, obstacle counts log-uniform 
                    "n_p in {50,75,100,150} over T=0.1 n_p s, goal 0.55 vmax T away, 8 "
                    "initialisations each = 16384 trajectories in one persistent launch "
                    "(CUDA graph, autotuned CTA shape), cap 500 iterations, tol 1e-3")
+
+
+# DRAM bytes (read + write) per launch of each solve kernel on the 1024-trajectory
+# 2D workload, from one ncu capture each (profiles/), valid only for the kernel
+# sources they were taken on: kernel -> (bytes, source digest of KERNEL_SOURCES).
+# A changed source reports null until the kernel is captured again.
+KERNEL_SOURCES = {
+    "k_am_fp32": ("am_solve.cu", "am_device.cuh", "internal.cuh"),
+    "k_am_team": ("am_solve.cu", "am_device.cuh", "internal.cuh"),
+    "k_am_mixed": ("am_mixed.cu", "am_device.cuh", "internal.cuh", "tcgen05.cuh"),
+}
+MEASURED_TRAFFIC = {
+    "k_am_fp32": (736768, "af53a3a82dbe8c9b"),
+    "k_am_team": (710400, "af53a3a82dbe8c9b"),
+    "k_am_mixed": (717824, "b1c35f74ceb4999e"),
+}
+
+
+def source_digest(kernel):
+    """SHA-256 (first 16 hex digits) over the sources that build a solve kernel."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_2408_10731_b300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    entry = MEASURED_TRAFFIC.get(kernel)
+    return entry[0] if entry and entry[1] == source_digest(kernel) else None
+
+
+def kernel_name(precision, shape):
+    """The solve kernel a handle of this precision and launch shape runs."""
+    if precision == "mixed":
+        return "k_am_mixed"
+    return "k_am_team" if shape and shape.get("warps_per_trajectory", 1) > 1 else "k_am_fp32"
 
 
 def algorithmic_ops(batch, iters):
@@ -124,41 +163,55 @@ def _pci_id(torch, dev):
         return str(dev)
 
 
-def cpu_baseline(seed=0, n_scenes=16, inits=8, max_iters=500, tol=1e-3):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+def cpu_baseline(seed=0, scenes_idx=range(16), max_iters=500, tol=1e-3, workload=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload: the
+    listed scenes of the seeded 128-scene batch with all their initialisations."""
     from oracle import am
     from paper_2408_10731_b300 import scenes
-    b = scenes.config2(seed, n_scenes=n_scenes, inits=inits)
+    full = workload if workload is not None else scenes.config2(seed)
+    idx = list(scenes_idx)
+    b = full.select_problems(idx)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     out = am.solve(b, max_iters, tol=tol, n_threads=cores)
     dt = time.perf_counter() - t0
     solved = int(np.sum(np.all(out["residual"] <= tol, axis=1) & (out["iters"] < max_iters + 1)))
     return {"value": solved / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{b.n_traj} trajectories ({n_scenes} scenes x {inits} inits) of the same "
-                      f"workload, full solve (cap {max_iters}, tol {tol}), FP64, OpenMP over "
-                      f"trajectories; {solved} solved in {dt:.2f} s",
-            "seconds": dt}
+            "sample": f"{b.n_traj} trajectories (scenes {idx[0]}..{idx[-1]} of the 128 x 8 "
+                      f"workload, all initialisations), full solve (cap {max_iters}, tol {tol}), "
+                      f"FP64, OpenMP over trajectories; {solved} solved in {dt:.2f} s",
+            "seconds": dt, "solved": solved}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only). Step i
+    solves scenes 2i, 2i + 1 (mod 128) of the seeded workload with all their
+    initialisations, so that successive steps sweep the whole batch; the value is
+    the total solved over the total time of the timed steps."""
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        cpu_baseline(args.seed, n_scenes=2, inits=8)
-    vals, secs = [], []
-    for _ in range(args.steps):
-        r = cpu_baseline(args.seed, n_scenes=2, inits=8)
-        vals.append(r["value"]); secs.append(r["seconds"])
-    value = float(np.mean(vals))
+    from paper_2408_10731_b300 import scenes
+    full = scenes.config2(args.seed)
+    P = full.n_problems
+
+    def step(i):
+        return cpu_baseline(args.seed, ((2 * i) % P, (2 * i + 1) % P), workload=full)
+
+    for i in range(args.warmup):
+        step(i)
+    solved, secs = 0, []
+    for i in range(args.steps):
+        r = step(i)
+        solved += r["solved"]; secs.append(r["seconds"])
+    value = solved / float(np.sum(secs))
+    sample = (f"16 trajectories per step (scenes 2i, 2i+1 of the 128 x 8 workload, all "
+              f"initialisations), full FP64 solve; {solved} solved in {np.sum(secs):.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD,
-                                            "sample": "16 trajectories (2 scenes x 8 inits) per step"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "16 trajectories (2 scenes x 8 inits) per step, full solve"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -222,6 +275,9 @@ def main():
     ap.add_argument("--no-warmstart", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--ws-scenes", type=int, default=200000)
+    ap.add_argument("--shape", default=None,
+                    help="FP32 launch shape W,B,T (warps per block, blocks per SM, warps per "
+                         "trajectory) instead of the autotuned one")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -252,7 +308,13 @@ def main():
     else:
         batch = scenes.config2(args.seed + rank)
     h = trajbatch.from_batch(batch, precision=args.precision)
-    shape = autotune.tuned(h, batch, args.precision, iters=200)
+    if args.shape:
+        w, bps, team = (int(x) for x in args.shape.split(","))
+        h.set_launch_shape(w, bps, team)
+        shape = {"warps_per_block": w, "blocks_per_sm": bps, "warps_per_trajectory": team,
+                 "fixed": True}
+    else:
+        shape = autotune.tuned(h, batch, args.precision, iters=200)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -272,9 +334,10 @@ def main():
         from paper_2408_10731_b300 import warmstart
         ws, ws_info = warmstart.trained(seed=1000, n_scenes=args.ws_scenes, epochs=20)
 
+        staged = ws.stage(batch)  # the scenes resident on the device before the timed steps
+
         def ws_init(hh):
-            X, line = ws.features(batch)
-            prop = ws.forward(X, line).reshape(batch.n_traj, 2, 11)
+            prop = ws.propose(staged).reshape(batch.n_traj, 2, 11)
             hh.set_initial(None, prop)
         forms["warmstart_fp32"] = ("fp32", ws_init)
         if "mixed" in handles:
@@ -358,7 +421,9 @@ def main():
     form_summary = {}
     for name, (sm, km, sv, o) in results.items():
         ok = o["status"] == 0
-        form_summary[name] = {"solved_per_s": float(np.sum(sv)) / (float(np.sum(sm)) * 1e-3),
+        form_summary[name] = {"kernel": kernel_name(forms[name][0], shape if forms[name][0] ==
+                                                     args.precision else None),
+                              "solved_per_s": float(np.sum(sv)) / (float(np.sum(sm)) * 1e-3),
                               "ms_per_batch_solve": float(np.mean(sm)),
                               "solve_kernel_ms": float(np.mean(km)),
                               "solved_per_step": float(np.mean(sv)),
@@ -374,10 +439,14 @@ def main():
         kern_s = float(np.mean(h_kern_ms)) * 1e-3
         achieved = ops / kern_s
         peak_ops = fp32_peak / 2.0  # FFMA rate in lane-operations/s (2 FLOP per FMA)
+        prec_h = forms[headline][0]
+        kern = kernel_name(prec_h, shape if prec_h == args.precision else None)
+        traffic = measured_traffic(kern) if args.workload == "config2" else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+bf16" if prec_h == "mixed" else "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.workload == "config2" else WORKLOAD_UNEVEN,
                        "precision": args.precision, "launch_shape": shape,
@@ -389,8 +458,8 @@ def main():
             "iters": {"min": int(h_out["iters"].min()), "median": int(np.median(h_out["iters"])),
                       "max": int(h_out["iters"].max())},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Top/s", "frac": achieved / peak_ops, "traffic": None,
-                         "kernel": "k_am_mixed" if forms[headline][0] == "mixed" else "k_am_fp32",
+                         "unit": "Top/s", "frac": achieved / peak_ops, "traffic": traffic,
+                         "kernel": kern,
                          "peak_source": "measured FFMA microbenchmark "
                          "(traj_measure_fp32_peak), FP32 lane-ops/s",
                          "algorithmic_ops_per_launch": ops},
@@ -399,10 +468,11 @@ def main():
             "gpu_launches": args.steps * (7 if headline.startswith("warmstart") else 1),
             "clocks": clocks,
             "headline_form": headline, "forms": form_summary,
+            "source_digest": {k: source_digest(k) for k in KERNEL_SOURCES},
         }
         if world == 1 and not args.no_cpu_baseline and args.workload == "config2":
-            cb = cpu_baseline(args.seed)
-            cb.pop("seconds", None)
+            cb = cpu_baseline(args.seed, workload=batch)
+            cb.pop("seconds", None); cb.pop("solved", None)
             line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)
     for hx in handles.values():

@@ -304,6 +304,18 @@ traj_status traj_warmstart_features(traj_warmstart *w, int n_scenes, const doubl
 /* proposals: device FP32 [rows][8][2][11] = line + network output */
 traj_status traj_warmstart_forward(traj_warmstart *w, int rows, const void *features,
                                    const float *line, float *proposals);
+/* Features, forward and proposals in one asynchronous pass on device inputs only
+ * (no host copy, no synchronisation): start, goal device FP64 [n][2]; offsets
+ * device int [n + 1] into n_obs obstacles (device FP32 [n_obs][2] each); features
+ * (device BF16 [n][400]) and line (device FP32 [n][22]) are caller scratch that
+ * receive the same values as traj_warmstart_features; proposals device FP32
+ * [n][8][2][11]. n_scenes is a multiple of 8 in [8, max_rows]. Offsets are
+ * checked on the device: a scene whose range leaves [0, n_obs] gets no obstacle
+ * features and makes the next traj_warmstart_sync return TRAJ_EINVAL. */
+traj_status traj_warmstart_propose(traj_warmstart *w, int n_scenes, int n_obs, const double *start,
+                                   const double *goal, const int *offsets, const float *centers,
+                                   const float *semi_axes, const float *velocities, void *features,
+                                   float *line, float *proposals);
 /* targets: device FP32 [rows][8][22] label offsets; n_labels: device int [rows];
  * loss: device FP32 scalar; grads (nullable): FP32 [num_params], host or device */
 traj_status traj_warmstart_gradients(traj_warmstart *w, int rows, const void *features,
@@ -312,7 +324,8 @@ traj_status traj_warmstart_gradients(traj_warmstart *w, int rows, const void *fe
 traj_status traj_warmstart_train_step(traj_warmstart *w, int rows, const void *features,
                                       const float *targets, const int *n_labels, float lr,
                                       float weight_decay, float *loss);
-/* synchronise; TRAJ_ECUDA if a GEMM pipeline wait expired since creation */
+/* synchronise; TRAJ_EINVAL if traj_warmstart_propose met bad offsets, TRAJ_ECUDA if
+ * a GEMM pipeline wait expired, since the previous sync (the flags are then cleared) */
 traj_status traj_warmstart_sync(traj_warmstart *w);
 
 /* Human-readable name of a status code (static string). */

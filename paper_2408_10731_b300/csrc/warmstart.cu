@@ -35,13 +35,20 @@ constexpr int P_W1 = 0, P_B1 = P_W1 + HID * IN_PAD, P_W2 = P_B1 + HID, P_B2 = P_
 constexpr int U_W1 = 0, U_B1 = U_W1 + HID * IN, U_W2 = U_B1 + HID, U_TOTAL = U_W2 + (P_TOTAL - P_W2);
 
 // ---- features -----------------------------------------------------------------
+// n_obs bounds the obstacle arrays: a scene whose offsets leave [0, n_obs] (or
+// decrease) is treated as obstacle-free and raises bit 1 of *err.
 __global__ void k_features(const double *start, const double *goal, const int *offsets,
-                           const float *cen, const float *ax, const float *vel,
-                           __nv_bfloat16 *X, float *line) {
+                           int n_obs, const float *cen, const float *ax, const float *vel,
+                           __nv_bfloat16 *X, float *line, int *err) {
   __shared__ float key[MAX_OBS_PER_SCENE];
   __shared__ int idx[MAX_OBS_PER_SCENE];
   const int s = blockIdx.x;
-  const int o0 = offsets[s], n = min(offsets[s + 1] - o0, MAX_OBS_PER_SCENE);
+  int o0 = offsets[s], o1 = offsets[s + 1];
+  if (o0 < 0 || o1 < o0 || o1 > n_obs) {
+    if (threadIdx.x == 0) atomicOr(err, 2);
+    o0 = o1 = 0;
+  }
+  const int n = min(o1 - o0, MAX_OBS_PER_SCENE);
   int np2 = 64;
   while (np2 < n) np2 <<= 1;
   const float sx = (float)start[2 * s], sy = (float)start[2 * s + 1];
@@ -422,10 +429,30 @@ traj_status traj_warmstart_features(traj_warmstart *w, int n_scenes, const doubl
   WS_CK(cudaMemcpyAsync(w->d_start, start, sizeof(double) * 2 * n_scenes, cudaMemcpyDefault, w->stream));
   WS_CK(cudaMemcpyAsync(w->d_goal, goal, sizeof(double) * 2 * n_scenes, cudaMemcpyDefault, w->stream));
   WS_CK(cudaMemcpyAsync(w->d_offsets, offsets, sizeof(int) * (n_scenes + 1), cudaMemcpyDefault, w->stream));
-  k_features<<<n_scenes, 256, 0, w->stream>>>(w->d_start, w->d_goal, w->d_offsets, centers, semi_axes,
-                                               velocities, reinterpret_cast<__nv_bfloat16 *>(features), line);
+  k_features<<<n_scenes, 256, 0, w->stream>>>(w->d_start, w->d_goal, w->d_offsets, offsets[n_scenes],
+                                               centers, semi_axes, velocities,
+                                               reinterpret_cast<__nv_bfloat16 *>(features), line, w->err);
   WS_CK(cudaGetLastError());
   WS_CK(cudaStreamSynchronize(w->stream)); // host sources of start/goal/offsets
+  return TRAJ_OK;
+}
+
+traj_status traj_warmstart_propose(traj_warmstart *w, int n_scenes, int n_obs, const double *start,
+                                   const double *goal, const int *offsets, const float *centers,
+                                   const float *semi_axes, const float *velocities, void *features,
+                                   float *line, float *proposals) {
+  if (!w || !start || !goal || !offsets || !features || !line || !proposals || n_obs < 0)
+    return ws_fail(TRAJ_EINVAL, "NULL argument or negative obstacle count");
+  if (n_obs > 0 && (!centers || !semi_axes || !velocities)) return ws_fail(TRAJ_EINVAL, "NULL obstacles");
+  traj_status rc = check_rows(w, n_scenes);
+  if (rc != TRAJ_OK) return rc;
+  k_features<<<n_scenes, 256, 0, w->stream>>>(start, goal, offsets, n_obs, centers, semi_axes,
+                                               velocities, reinterpret_cast<__nv_bfloat16 *>(features),
+                                               line, w->err);
+  WS_CK(cudaGetLastError());
+  WS_CK(forward(w, n_scenes, features));
+  k_proposals<<<(n_scenes * OUT + 255) / 256, 256, 0, w->stream>>>(w->Y, line, n_scenes, proposals);
+  WS_CK(cudaGetLastError());
   return TRAJ_OK;
 }
 
@@ -473,6 +500,9 @@ traj_status traj_warmstart_sync(traj_warmstart *w) {
   WS_CK(cudaStreamSynchronize(w->stream));
   int err = 0;
   WS_CK(cudaMemcpy(&err, w->err, sizeof(int), cudaMemcpyDeviceToHost));
+  WS_CK(cudaMemsetAsync(w->err, 0, sizeof(int), w->stream));
+  WS_CK(cudaStreamSynchronize(w->stream));
+  if (err & 2) return ws_fail(TRAJ_EINVAL, "obstacle offsets outside [0, n_obs] in traj_warmstart_propose");
   if (err) return ws_fail(TRAJ_ECUDA, "a tensor-core GEMM pipeline wait expired");
   return TRAJ_OK;
 }

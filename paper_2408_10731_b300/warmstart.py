@@ -38,12 +38,14 @@ def _lib():
         lib.traj_warmstart_get_params.argtypes = [_vp, _vp]
         lib.traj_warmstart_features.argtypes = [_vp, _ci, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         lib.traj_warmstart_forward.argtypes = [_vp, _ci, _vp, _vp, _vp]
+        lib.traj_warmstart_propose.argtypes = [_vp, _ci, _ci] + [_vp] * 9
         lib.traj_warmstart_gradients.argtypes = [_vp, _ci, _vp, _vp, _vp, _vp, _vp]
         lib.traj_warmstart_train_step.argtypes = [_vp, _ci, _vp, _vp, _vp, _cf, _cf, _vp]
         lib.traj_warmstart_sync.argtypes = [_vp]
         lib.traj_get_accel_cost.argtypes = [_vp, _vp]
         for n in ("traj_warmstart_create", "traj_warmstart_destroy", "traj_warmstart_set_params",
                   "traj_warmstart_get_params", "traj_warmstart_features", "traj_warmstart_forward",
+                  "traj_warmstart_propose",
                   "traj_warmstart_gradients", "traj_warmstart_train_step", "traj_warmstart_sync",
                   "traj_get_accel_cost"):
             getattr(lib, n).restype = _ci
@@ -142,6 +144,33 @@ class WarmStart:
                                                  line[r0:r1].contiguous().data_ptr(),
                                                  out[r0:r1].data_ptr()), "forward")
         return out[:rows]
+
+    def stage(self, batch):
+        """The scene arrays of a batch as device tensors plus feature/line/proposal
+        buffers, for propose() (one host-to-device copy, done here)."""
+        torch = self.torch
+        dev = torch.device("cuda")
+        P = batch.n_problems
+        if P % 8 != 0 or P > self.max_rows:
+            raise ValueError("propose() needs a multiple of 8 scenes, at most max_rows")
+        f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev)
+        return dict(P=P, n_obs=int(batch.offsets[-1]),
+                    start=torch.as_tensor(np.ascontiguousarray(batch.start, np.float64), device=dev),
+                    goal=torch.as_tensor(np.ascontiguousarray(batch.goal, np.float64), device=dev),
+                    offsets=torch.as_tensor(np.ascontiguousarray(batch.offsets, np.int32), device=dev),
+                    centers=f32(batch.centers), axes=f32(batch.semi_axes), vel=f32(batch.velocities),
+                    X=torch.zeros(P, IN_PAD, dtype=torch.bfloat16, device=dev),
+                    line=torch.zeros(P, D22, dtype=torch.float32, device=dev),
+                    out=torch.empty(P, HEADS, 2, 11, dtype=torch.float32, device=dev))
+
+    def propose(self, st):
+        """Proposals [P, 8, 2, 11] for a staged scene set (asynchronous, device only)."""
+        _check(_lib().traj_warmstart_propose(
+            self._h, st["P"], st["n_obs"], st["start"].data_ptr(), st["goal"].data_ptr(),
+            st["offsets"].data_ptr(), st["centers"].data_ptr(), st["axes"].data_ptr(),
+            st["vel"].data_ptr(), st["X"].data_ptr(), st["line"].data_ptr(), st["out"].data_ptr()),
+            "propose")
+        return st["out"]
 
     def gradients(self, X, targets, n_labels):
         g = np.zeros(num_params(), np.float32)

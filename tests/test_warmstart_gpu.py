@@ -89,3 +89,26 @@ def test_gradients_and_adamw_match_oracle():
                           np.zeros_like(params), 1, 1e-3, 1e-2)
     np.testing.assert_allclose(new, ref, rtol=1e-5, atol=1e-7)
     ws.close()
+
+
+def test_device_propose_matches_host_path_and_flags_bad_offsets():
+    """traj_warmstart_propose (device inputs, no synchronisation) gives bitwise the
+    features and proposals of traj_warmstart_features + traj_warmstart_forward;
+    offsets outside the obstacle range are reported by the next sync."""
+    torch, warmstart, b, ws, params, X, line = _setup()
+    prop = ws.forward(X, line).cpu().numpy()
+    st = ws.stage(b)
+    out = ws.propose(st)
+    ws.sync()
+    np.testing.assert_array_equal(st["X"].float().cpu().numpy(), X.float().cpu().numpy())
+    np.testing.assert_array_equal(st["line"].cpu().numpy(), line.cpu().numpy())
+    np.testing.assert_array_equal(out.cpu().numpy(), prop)
+    bad = dict(st)
+    bad["offsets"] = st["offsets"].clone()
+    bad["offsets"][-1] = st["n_obs"] + 5
+    ws.propose(bad)
+    from paper_2408_10731_b300.trajbatch import TrajBatchError
+    with pytest.raises(TrajBatchError):
+        ws.sync()
+    ws.sync()  # the flag is cleared once reported
+    ws.close()
