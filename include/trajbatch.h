@@ -150,6 +150,12 @@ typedef struct traj_solve_stats {
 traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
                        traj_solve_stats *stats);
 
+/* Statistics of the last solve, as traj_solve fills them (synchronises the stream;
+ * the same return codes as a traj_solve with stats): lets a caller launch
+ * asynchronously (stats = NULL) and read the statistics later. No paper
+ * counterpart. */
+traj_status traj_get_solve_stats(traj_batch *b, traj_solve_stats *stats);
+
 /* Results of the last solve into caller buffers (host or device, each
  * nullable): coeffs[n_traj][dim][11] FP32, residual[n_traj][3] FP32
  * (obstacle, velocity, acceleration), iters[n_traj] int32 (iterations run),

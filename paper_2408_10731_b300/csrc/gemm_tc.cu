@@ -4,15 +4,17 @@
 //   C[M x N] = A[M x K] * B[N x K]^T,   A, B row-major BF16 (K contiguous),
 //   FP32 accumulation in tensor memory, fused epilogues (bias, GELU, GELU').
 //
-// One CTA computes one 128 x 128 tile with 4 warps: warp 0 lane 0 streams
-// 128 x 64 A and B tiles into shared memory with TMA (128-byte swizzle, a
-// 4-stage ring of mbarriers), warp 1 lane 0 issues tcgen05.mma (kind::f16,
-// M = 128, N = 128, K = 16 per instruction) into a 128-column FP32
-// accumulator in TMEM and commits each stage back to the producer, and all
-// four warps read the accumulator with tcgen05.ld (warp w owns rows
-// 32w..32w+31) for the epilogue. Every mbarrier wait is bounded: on
-// expiry the CTA sets the error flag, skips the remaining work, still frees
-// its TMEM and returns.
+// One CTA computes one 128 x 64 tile with 4 warps: warp 0 lane 0 streams
+// 128 x 64 A and 64 x 64 B tiles into shared memory with TMA (128-byte
+// swizzle, a 4-stage ring of mbarriers), warp 1 lane 0 issues tcgen05.mma
+// (kind::f16, M = 128, N = 64, K = 16 per instruction) into a 64-column FP32
+// accumulator in TMEM and commits each stage back to the producer. The
+// epilogue: all four warps read the accumulator with tcgen05.ld (warp w owns
+// rows 32w..32w+31) into a padded shared-memory tile (the operand ring, free
+// once the MMAs are done), then write the outputs row by row with consecutive
+// threads on consecutive columns (coalesced), applying bias / GELU / GELU'
+// there. Every mbarrier wait is bounded: on expiry the CTA sets the error
+// flag, skips the remaining work, still frees its TMEM and returns.
 #include "internal.cuh"
 #include "tcgen05.cuh"
 #include <cuda.h>
@@ -23,7 +25,8 @@
 
 namespace tb {
 
-constexpr int GM_BM = 128, GM_BN = 128, GM_BK = 64, GM_STAGES = 4;
+constexpr int GM_BM = 128, GM_BN = 64, GM_BK = 64, GM_STAGES = 4;
+constexpr int GM_LDS = GM_BN + 1; // padded row of the epilogue staging tile (floats)
 constexpr int GM_TILE_A = GM_BM * GM_BK * 2;
 constexpr int GM_TILE_B = GM_BN * GM_BK * 2;
 constexpr int GM_SMEM = GM_STAGES * (GM_TILE_A + GM_TILE_B) + 1024 /*align*/ + 256 /*barriers*/;
@@ -127,39 +130,49 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   __syncwarp();
   const bool ok = mbar_wait(smem_u32(done), 0);
   asm volatile("tcgen05.fence::after_thread_sync;");
+  float *stage = reinterpret_cast<float *>(smem); // [GM_BM][GM_LDS], over the idle operand ring
   if (!ok) {
     if (lane == 0) atomicOr(g.err, 1);
   } else {
-    const int row = m0 + warp * 32 + lane;
-#pragma unroll 1
+    const int r = warp * 32 + lane;
+#pragma unroll
     for (int c = 0; c < GM_BN; c += 16) {
-      uint32_t r[16];
+      uint32_t v[16];
       const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,"
                    "%11,%12,%13,%14,%15}, [%16];"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                     "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                     "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                     "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                     "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                    : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < g.M) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c + j;
-          if (col >= g.N) continue;
-          const float v = __uint_as_float(r[j]);
-          const size_t o = (size_t)row * g.ldo + col;
-          if constexpr (EPI == 0) {
-            g.out_f32[o] = v;
-          } else if constexpr (EPI == 1) {
-            const float z = v + g.bias[col];
-            if (g.out_f32) g.out_f32[o] = z;
-            g.out_bf16[o] = __float2bfloat16_rn(gelu_tanh(z));
-          } else if constexpr (EPI == 2) {
-            g.out_f32[o] = v + g.bias[col];
-          } else {
-            g.out_bf16[o] = __float2bfloat16_rn(v * gelu_tanh_grad(g.aux[o]));
-          }
+      for (int j = 0; j < 16; ++j) stage[r * GM_LDS + c + j] = __uint_as_float(v[j]);
+    }
+  }
+  const bool all_ok = __syncthreads_and(ok);
+  if (all_ok) {
+    // consecutive threads on consecutive columns: 64 columns x 2 rows per pass
+    const int cl = threadIdx.x & (GM_BN - 1), r0 = threadIdx.x / GM_BN;
+    const int col = n0 + cl;
+    if (col < g.N) {
+      const float bias = (EPI == 1 || EPI == 2) ? g.bias[col] : 0.f;
+#pragma unroll 4
+      for (int rr = r0; rr < GM_BM; rr += 128 / GM_BN) {
+        const int row = m0 + rr;
+        if (row >= g.M) break;
+        const float v = stage[rr * GM_LDS + cl];
+        const size_t o = (size_t)row * g.ldo + col;
+        if constexpr (EPI == 0) {
+          g.out_f32[o] = v;
+        } else if constexpr (EPI == 1) {
+          const float z = v + bias;
+          if (g.out_f32) g.out_f32[o] = z;
+          g.out_bf16[o] = __float2bfloat16_rn(gelu_tanh(z));
+        } else if constexpr (EPI == 2) {
+          g.out_f32[o] = v + bias;
+        } else {
+          g.out_bf16[o] = __float2bfloat16_rn(v * gelu_tanh_grad(g.aux[o]));
         }
       }
     }
@@ -186,15 +199,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Row-major BF16 matrix [rows][cols] (cols contiguous, cols % 8 == 0, 16-byte aligned base)
-// as a 2D tensor map with 64 x 128 boxes and the 128-byte swizzle; out-of-range
+// as a 2D tensor map with 64-column x box_rows boxes and the 128-byte swizzle; out-of-range
 // elements of a box read as zero.
-static cudaError_t make_map(CUtensorMap *m, const void *ptr, int rows, int cols) {
+static cudaError_t make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   if ((cols % 8) != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return cudaErrorInvalidValue;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {(cuuint32_t)GM_BK, (cuuint32_t)GM_BM};
+  cuuint32_t box[2] = {(cuuint32_t)GM_BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -207,9 +220,9 @@ cudaError_t launch_gemm_bf16(int epi, const void *A, const void *B, int M, int N
                              const float *aux, int *err, cudaStream_t s) {
   if (M < 1 || N < 1 || K < 1) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
-  cudaError_t e = make_map(&ma, A, M, K);
+  cudaError_t e = make_map(&ma, A, M, K, GM_BM);
   if (e != cudaSuccess) return e;
-  if ((e = make_map(&mb, B, N, K)) != cudaSuccess) return e;
+  if ((e = make_map(&mb, B, N, K, GM_BN)) != cudaSuccess) return e;
   GemmArgs g{M, N, K, out_f32, reinterpret_cast<__nv_bfloat16 *>(out_bf16), ldo, bias, aux, err};
   dim3 grid((M + GM_BM - 1) / GM_BM, (N + GM_BN - 1) / GM_BN);
   switch (epi) {

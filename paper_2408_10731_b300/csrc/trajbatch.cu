@@ -361,6 +361,43 @@ traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
   return TRAJ_OK;
 }
 
+// Statistics of the last solve (synchronises the stream) and its status: the
+// error flags first, then TRAJ_NOT_CONVERGED unless every trajectory converged.
+static traj_status solve_stats(traj_batch *b, traj_solve_stats *stats) {
+  CK(b, cudaStreamSynchronize(b->stream));
+  const int B = b->n_traj;
+  std::vector<int> it(B);
+  std::vector<float> res((size_t)B * 3);
+  std::vector<signed char> st(B);
+  int flags = 0;
+  CK(b, cudaMemcpy(it.data(), b->d_iters, sizeof(int) * B, cudaMemcpyDeviceToHost));
+  CK(b, cudaMemcpy(res.data(), b->d_res, sizeof(float) * B * 3, cudaMemcpyDeviceToHost));
+  CK(b, cudaMemcpy(st.data(), b->d_status, B, cudaMemcpyDeviceToHost));
+  CK(b, cudaMemcpy(&flags, b->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+  float ms = 0.f;
+  CK(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  traj_solve_stats s{};
+  s.n_traj = B;
+  std::vector<int> sorted = it;
+  std::sort(sorted.begin(), sorted.end());
+  s.iters_min = sorted.front();
+  s.iters_max = sorted.back();
+  s.iters_median = sorted[B / 2];
+  for (int k = 0; k < B; ++k) {
+    if (st[k] == TRAJ_TRAJ_CONVERGED) ++s.n_solved;
+    if (st[k] == TRAJ_TRAJ_NAN) continue;
+    s.max_res_obs = std::max(s.max_res_obs, res[k * 3 + 0]);
+    s.max_res_v = std::max(s.max_res_v, res[k * 3 + 1]);
+    s.max_res_a = std::max(s.max_res_a, res[k * 3 + 2]);
+  }
+  s.gpu_ms = ms;
+  *stats = s;
+  if (flags & 8) return fail(b, TRAJ_ECUDA, "a tensor-core pipeline wait expired");
+  if (flags & 1) return fail(b, TRAJ_ETIMEOUT, "deadline reached");
+  if (flags & 2) return fail(b, TRAJ_ENAN, "non-finite input in some trajectories");
+  return s.n_solved == B ? TRAJ_OK : TRAJ_NOT_CONVERGED;
+}
+
 traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
                        traj_solve_stats *stats) {
   if (!b) return TRAJ_EINVAL;
@@ -430,38 +467,13 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   CK(b, cudaEventRecord(b->ev1, b->stream));
   b->have_result = true;
   if (!stats) return TRAJ_OK;
-  CK(b, cudaStreamSynchronize(b->stream));
-  const int B = b->n_traj;
-  std::vector<int> it(B);
-  std::vector<float> res((size_t)B * 3);
-  std::vector<signed char> st(B);
-  int flags = 0;
-  CK(b, cudaMemcpy(it.data(), b->d_iters, sizeof(int) * B, cudaMemcpyDeviceToHost));
-  CK(b, cudaMemcpy(res.data(), b->d_res, sizeof(float) * B * 3, cudaMemcpyDeviceToHost));
-  CK(b, cudaMemcpy(st.data(), b->d_status, B, cudaMemcpyDeviceToHost));
-  CK(b, cudaMemcpy(&flags, b->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
-  float ms = 0.f;
-  CK(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
-  traj_solve_stats s{};
-  s.n_traj = B;
-  std::vector<int> sorted = it;
-  std::sort(sorted.begin(), sorted.end());
-  s.iters_min = sorted.front();
-  s.iters_max = sorted.back();
-  s.iters_median = sorted[B / 2];
-  for (int k = 0; k < B; ++k) {
-    if (st[k] == TRAJ_TRAJ_CONVERGED) ++s.n_solved;
-    if (st[k] == TRAJ_TRAJ_NAN) continue;
-    s.max_res_obs = std::max(s.max_res_obs, res[k * 3 + 0]);
-    s.max_res_v = std::max(s.max_res_v, res[k * 3 + 1]);
-    s.max_res_a = std::max(s.max_res_a, res[k * 3 + 2]);
-  }
-  s.gpu_ms = ms;
-  *stats = s;
-  if (flags & 8) return fail(b, TRAJ_ECUDA, "a tensor-core pipeline wait expired");
-  if (flags & 1) return fail(b, TRAJ_ETIMEOUT, "deadline reached");
-  if (flags & 2) return fail(b, TRAJ_ENAN, "non-finite input in some trajectories");
-  return s.n_solved == B ? TRAJ_OK : TRAJ_NOT_CONVERGED;
+  return solve_stats(b, stats);
+}
+
+traj_status traj_get_solve_stats(traj_batch *b, traj_solve_stats *stats) {
+  if (!b || !stats) return TRAJ_EINVAL;
+  if (!b->have_result) return fail(b, TRAJ_ESTATE, "no solve has run");
+  return solve_stats(b, stats);
 }
 
 traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual, int *iters,

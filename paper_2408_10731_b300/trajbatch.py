@@ -90,6 +90,7 @@ def load_library():
     lib.traj_set_obstacles.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.traj_set_initial.argtypes = [_vp, _c_int, _vp, _vp]
     lib.traj_solve.argtypes = [_vp, _c_int, _c_float, _c_double, ctypes.POINTER(SolveStats)]
+    lib.traj_get_solve_stats.argtypes = [_vp, ctypes.POINTER(SolveStats)]
     lib.traj_get_trajectories.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.traj_get_state.argtypes = [_vp, _vp, _vp]
     lib.traj_status_string.argtypes = [_c_int]
@@ -107,7 +108,7 @@ def load_library():
                                        _vp, _vp, _vp, _vp, _c_int, _vp, _vp, _c_int, _c_float,
                                        _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
-                 "traj_set_obstacles", "traj_set_initial", "traj_solve",
+                 "traj_set_obstacles", "traj_set_initial", "traj_solve", "traj_get_solve_stats",
                  "traj_get_trajectories", "traj_get_state", "traj_measure_fp32_peak",
                  "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune",
                  "traj_sampler_step", "traj_gemm_bf16"):
@@ -221,6 +222,12 @@ class TrajBatch:
                                   ctypes.byref(st) if stats else None)
         self._check(rc, ok=(0, 1) if stats else (0,))
         return st.as_dict() if stats else None
+
+    def last_stats(self):
+        """Statistics of the last solve (synchronises)."""
+        st = SolveStats()
+        self._check(self._lib.traj_get_solve_stats(self._h, ctypes.byref(st)), ok=(0, 1))
+        return st.as_dict()
 
     def get_trajectories(self, coeffs=None, residual=None, iters=None, status=None):
         """Into the given buffers (host or device); allocates numpy arrays if all are None."""

@@ -68,3 +68,20 @@ def test_mixed_3d_projection_mode_and_launch_errors():
         assert e.value.code == -4
     finally:
         h.close()
+
+
+def test_mixed_full_size_sampled_error(capsys):
+    """The bench workload at full size in the tensor-core form (1024 trajectories,
+    the default launch): 24 sampled trajectories against the oracle after 20
+    iterations, error reported and bounded as above."""
+    b = scenes.config2(0)
+    g = gpu_solve(b, 20, precision="mixed")
+    pick = np.random.default_rng(5).choice(b.n_traj, 24, replace=False)
+    sub = b.subset(pick)
+    o = am.solve(sub, 20, tol=-1.0)
+    err = position_error(sub, g["xi"][pick], o["xi"])
+    with capsys.disabled():
+        print(f"\nmixed vs FP64, full-size launch, 24 sampled: max {err.max():.2e} m, "
+              f"median {np.median(err):.2e} m")
+    assert err.max() <= 5e-2 and np.median(err) <= 5e-3
+    assert np.all(np.isfinite(g["xi"])) and np.all(g["iters"] == 20)

@@ -99,6 +99,29 @@ def test_full_size_config2_sampled_parity():
     np.testing.assert_allclose(g["xi"] @ P[-1], b.goal[b.traj_problem], atol=1e-4)
 
 
+def test_full_size_uneven_sampled_parity():
+    """The uneven workload at full size (2048 problems x 8 = 16384 trajectories, one
+    launch) in the launch shapes the bench uses; 32 sampled trajectories, spread over
+    every horizon, recomputed by the oracle one by one."""
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.config4(0)
+    rng = np.random.default_rng(11)
+    pick = np.concatenate([rng.choice(np.nonzero(b.n_steps[b.traj_problem] == n_p)[0], 8, replace=False)
+                           for n_p in (50, 75, 100, 150)])
+    o_full = am.solve(b.subset(pick), 20, tol=-1.0)
+    h = tb.from_batch(b)
+    try:
+        for w, bps, team in ((8, 0, 2), (4, 0, 1)):
+            h.set_launch_shape(w, bps, team)
+            h.solve(20, tol=-1.0)
+            g = h.get_trajectories()
+            assert np.all(np.isfinite(g["xi"])) and np.all(g["iters"] == 20)
+            err = position_error(b.subset(pick), g["xi"][pick], o_full["xi"])
+            assert err.max() <= POS_TOL, (team, err.max())
+    finally:
+        h.close()
+
+
 def test_determinism_and_shard_equivalence():
     """Trajectories are independent: a batch split into two shards (as replicas on
     two GPUs would run it) gives bitwise the same results as one launch."""
