@@ -237,6 +237,16 @@ def run_priest(args, torch):
         for it in range(c3["n_outer"]):
             h.sampler_step(cfg, it, mu, sigma, best)
 
+    # launch shape of the projection solve: tuned on the sampler's own first samples
+    h.sampler_step(cfg, 0, mu, sigma, best)
+    if args.shape:
+        w, bps, team = (int(x) for x in args.shape.split(","))
+        h.set_launch_shape(w, bps, team)
+        shape = {"warps_per_block": w, "blocks_per_sm": bps, "warps_per_trajectory": team,
+                 "fixed": True}
+    else:
+        from paper_2408_10731_b300 import autotune
+        shape = autotune.tuned(h, b, "fp32-project", iters=c3["n_inner"])
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize()
@@ -248,14 +258,25 @@ def run_priest(args, torch):
     # residual of the returned trajectory (one more projection-free evaluation on the host
     # is not needed: the sampler's best is a projected sample; report its c_aug)
     bc = float(best[D].item())
+    # ALU roofline of the run: every outer iteration projects all samples for n_inner
+    # fixed iterations (the refit, sampling and sorts are < 1 % of the run)
+    fp32_peak = trajbatch.measure_fp32_peak(5)
+    ops = c3["n_outer"] * algorithmic_ops(b, np.full(b.n_traj, c3["n_inner"]))
+    achieved = ops / (float(np.mean(ms)) * 1e-3)
     line = {"metric": "ms per projection-guided sampler run (3D, 4096 samples, 10 outer x 20 "
                       "inner)", "value": float(np.mean(ms)), "unit": "ms", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)),
             "higher_is_better": False, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "3D: 256 spheres r~U(0.1,0.3) on 12 box surfaces in 20x20x5 m, "
                                    "n_p=100 over 20 s, B=4096, N_proj=2991, N_elite=410, gamma 1, "
-                                   "sigma_lr 0.5"},
-            "best_cost_aug": bc, "gpu_launches_per_step": c3["n_outer"] * 6}
+                                   "sigma_lr 0.5", "launch_shape": shape},
+            "best_cost_aug": bc, "gpu_launches_per_step": c3["n_outer"] * 6,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 2e12,
+                         "unit": "Top/s", "frac": achieved / (fp32_peak / 2.0), "traffic": None,
+                         "kernel": kernel_name("fp32", shape) + " (3D, projection mode; whole run timed)",
+                         "peak_source": "measured FFMA microbenchmark (traj_measure_fp32_peak), "
+                                        "FP32 lane-ops/s",
+                         "algorithmic_ops_per_run": ops}}
     print(json.dumps(line), flush=True)
     h.close()
 

@@ -239,10 +239,13 @@ __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const 
     for (int a = 0; a < DIM; ++a) p2[m][a] = make_float2(pos[m][a], pos[m][a]);
   }
   mo = 0.f;
+  // the test reads the first PT float4 of a record; the semi-axes (the rest) are
+  // loaded only when a point is inside
+  constexpr int PT = DIM == 2 ? 3 : 5;
   for (int q = 0; q < n_pairs; ++q) {
     float4 o[PV];
 #pragma unroll
-    for (int k = 0; k < PV; ++k) o[k] = __ldg(&obs[PV * q + k]);
+    for (int k = 0; k < PT; ++k) o[k] = __ldg(&obs[PV * q + k]);
     float2 sm[MAXNT];
     unsigned sign = 0u;
 #pragma unroll
@@ -251,6 +254,8 @@ __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const 
       sign |= __float_as_uint(sm[m].x) | __float_as_uint(sm[m].y);
     }
     if ((int)sign < 0) { // some timestep is inside one of the two obstacles
+#pragma unroll
+      for (int k = PT; k < PV; ++k) o[k] = __ldg(&obs[PV * q + k]);
 #pragma unroll
       for (int m = 0; m < MAXNT; ++m) {
         if (sm[m].x < 0.f) pair_project<DIM, 0>(o, pos[m], tm[m], acc[m], mo);
