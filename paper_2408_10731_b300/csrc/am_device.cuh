@@ -157,11 +157,6 @@ __device__ __forceinline__ void qp_step(const float *C, int lane, float rho, flo
 }
 
 // ---- obstacles (Algorithm 2 lines 4-5 for the obstacle groups) ---------------------
-// Component k (0..3, a compile-time constant after unrolling) of a float4.
-__device__ __forceinline__ float f4c(const float4 &v, int k) {
-  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
-}
-
 // ||u||^2 - 1 of both obstacles of a record at one timestep (packed), with
 // u = p * ia + (nc + nv t): negative inside the ellipse / ellipsoid.
 template <int DIM>
@@ -182,54 +177,84 @@ __device__ __forceinline__ float2 pair_sm1(const float4 (&o)[pair_vec(DIM)], con
   return s;
 }
 
-// Projection of one timestep onto obstacle H of a record (only called when the
-// point is inside): the alpha and d steps give g - o = Delta * max(1, 1/||u||), so
-// acc += g - p = Delta (1/||u|| - 1) with Delta = u * a; at the centre atan2(0, 0) = 0
-// pushes along +x (3D: beta = 0, along +z). mo takes the max of ||g - p||^2.
-template <int DIM, int H>
-__device__ __forceinline__ void pair_project(const float4 (&o)[pair_vec(DIM)], const float (&p)[DIM],
-                                             float t, float (&acc)[DIM], float &mo) {
-  float u[DIM], ax[DIM];
+// Projection of one timestep onto both obstacles of a record, packed: each half
+// with sm < 0 (the point is inside) contributes g - p = (u * a) (1/||u|| - 1),
+// the alpha and d steps giving g - o = Delta * max(1, 1/||u||) with Delta = u * a;
+// at the centre atan2(0, 0) = 0 pushes along +x by the x semi-axis (3D: beta = 0,
+// +z). A half with sm >= 0 contributes exactly zero. acc accumulates the halves in
+// order; mo takes the max of ||g - p||^2.
+template <int DIM>
+__device__ __forceinline__ void pair_project(const float4 (&o)[pair_vec(DIM)], const float2 (&p2)[DIM],
+                                             float2 t2, float2 sm, float (&acc)[DIM], float &mo) {
+  constexpr int IA = DIM;
+  float2 ux = __ffma2_rn(make_float2(o[0].z, o[0].w), t2, make_float2(o[0].x, o[0].y));
+  ux = __ffma2_rn(make_float2(o[IA].x, o[IA].y), p2[0], ux);
+  float2 uy = __ffma2_rn(make_float2(o[1].z, o[1].w), t2, make_float2(o[1].x, o[1].y));
+  uy = __ffma2_rn(make_float2(o[IA].z, o[IA].w), p2[1], uy);
+  float2 s = __ffma2_rn(uy, uy, __fmul2_rn(ux, ux));
+  float2 uz = make_float2(0.f, 0.f), ax, ay, az = make_float2(0.f, 0.f);
+  if constexpr (DIM == 3) {
+    uz = __ffma2_rn(make_float2(o[2].z, o[2].w), t2, make_float2(o[2].x, o[2].y));
+    uz = __ffma2_rn(make_float2(o[4].x, o[4].y), p2[2], uz);
+    s = __ffma2_rn(uz, uz, s);
+    ax = make_float2(o[4].z, o[4].w); ay = make_float2(o[5].x, o[5].y); az = make_float2(o[5].z, o[5].w);
+  } else {
+    ax = make_float2(o[3].x, o[3].y); ay = make_float2(o[3].z, o[3].w);
+  }
+  const bool in0 = sm.x < 0.f, in1 = sm.y < 0.f;
+  const float w0 = (in0 && s.x > 0.f) ? fmaxf(rsqrtf(s.x) - 1.f, 0.f) : 0.f;
+  const float w1 = (in1 && s.y > 0.f) ? fmaxf(rsqrtf(s.y) - 1.f, 0.f) : 0.f;
+  const float2 w = make_float2(w0, w1);
+  float2 ex = __fmul2_rn(__fmul2_rn(ux, ax), w);
+  float2 ey = __fmul2_rn(__fmul2_rn(uy, ay), w);
+  float2 ez = make_float2(0.f, 0.f);
+  if constexpr (DIM == 3) ez = __fmul2_rn(__fmul2_rn(uz, az), w);
+  const bool c0 = in0 && !(s.x > 0.f), c1 = in1 && !(s.y > 0.f); // at the centre
   if constexpr (DIM == 2) {
-    u[0] = fmaf(f4c(o[2], H), p[0], fmaf(f4c(o[0], 2 + H), t, f4c(o[0], H)));
-    u[1] = fmaf(f4c(o[2], 2 + H), p[1], fmaf(f4c(o[1], 2 + H), t, f4c(o[1], H)));
-    ax[0] = f4c(o[3], H); ax[1] = f4c(o[3], 2 + H);
+    if (c0) ex.x = ax.x;
+    if (c1) ex.y = ax.y;
   } else {
-    u[0] = fmaf(f4c(o[3], H), p[0], fmaf(f4c(o[0], 2 + H), t, f4c(o[0], H)));
-    u[1] = fmaf(f4c(o[3], 2 + H), p[1], fmaf(f4c(o[1], 2 + H), t, f4c(o[1], H)));
-    u[2] = fmaf(f4c(o[4], H), p[2], fmaf(f4c(o[2], 2 + H), t, f4c(o[2], H)));
-    ax[0] = f4c(o[4], 2 + H); ax[1] = f4c(o[5], H); ax[2] = f4c(o[5], 2 + H);
+    if (c0) ez.x = az.x;
+    if (c1) ez.y = az.y;
   }
-  float s = u[0] * u[0];
-#pragma unroll
-  for (int a = 1; a < DIM; ++a) s = fmaf(u[a], u[a], s);
-  float e[DIM];
-  if (s > 0.f) {
-    const float w = fmaxf(rsqrtf(s) - 1.f, 0.f);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) e[a] = (u[a] * ax[a]) * w;
-  } else {
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) e[a] = 0.f;
-    e[DIM == 2 ? 0 : 2] = ax[DIM == 2 ? 0 : 2];
+  acc[0] = (acc[0] + ex.x) + ex.y;
+  acc[1] = (acc[1] + ey.x) + ey.y;
+  float2 n2 = __ffma2_rn(ey, ey, __fmul2_rn(ex, ex));
+  if constexpr (DIM == 3) {
+    acc[2] = (acc[2] + ez.x) + ez.y;
+    n2 = __ffma2_rn(ez, ez, n2);
   }
-  float n2 = 0.f;
+  mo = fmaxf(mo, fmaxf(n2.x, n2.y));
+}
+
+// The projections of one record whose test found a point inside: the semi-axes
+// (the record's last float4) are loaded here, and only the timestep slots with a
+// point inside are projected.
+template <int DIM, int MAXNT>
+__device__ __forceinline__ void project_record(float4 (&o)[pair_vec(DIM)], const float4 *rec,
+                                               const float2 (&p2)[MAXNT][DIM],
+                                               const float2 (&t2)[MAXNT], const float2 (&sm)[MAXNT],
+                                               float (&acc)[MAXNT][DIM], float &mo) {
+  constexpr int PV = pair_vec(DIM), PT = pair_test_vec(DIM);
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) { acc[a] += e[a]; n2 = fmaf(e[a], e[a], n2); }
-  mo = fmaxf(mo, n2);
+  for (int k = PT; k < PV; ++k) o[k] = __ldg(&rec[k]);
+#pragma unroll
+  for (int m = 0; m < MAXNT; ++m)
+    if ((int)(__float_as_uint(sm[m].x) | __float_as_uint(sm[m].y)) < 0)
+      pair_project<DIM>(o, p2[m], t2[m], sm[m], acc[m], mo);
 }
 
 // Pair loop: all of the lane's timesteps against the problem's obstacle-pair
-// records, one record (two obstacles) per step. The tests are branch-free and
-// packed; the sign bits of all ||u||^2 - 1 are OR-ed, and only when one is negative
-// (a point inside, a few percent of the steps) does the warp take the projection
-// branch.
+// records, two records (four obstacles) per step, each with its own test. The
+// tests are branch-free and packed; the sign bits of all ||u||^2 - 1 of a record
+// are OR-ed, and only when one is negative (a point inside, a few percent of the
+// tests) does the warp take that record's projection branch.
 // acc accumulates sum_j (g_j - p) (= -sum_j r_j); mo is the lane's max ||r_j||^2.
 template <int DIM, int MAXNT>
 __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const float (&tm)[MAXNT],
                                           const float4 *obs, int n_o, float (&acc)[MAXNT][DIM],
                                           float &mo) {
-  constexpr int PV = pair_vec(DIM);
+  constexpr int PV = pair_vec(DIM), PT = pair_test_vec(DIM);
   const int n_pairs = pair_count(n_o);
   float2 p2[MAXNT][DIM], t2[MAXNT];
 #pragma unroll
@@ -239,29 +264,38 @@ __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const 
     for (int a = 0; a < DIM; ++a) p2[m][a] = make_float2(pos[m][a], pos[m][a]);
   }
   mo = 0.f;
-  // the test reads the first PT float4 of a record; the semi-axes (the rest) are
-  // loaded only when a point is inside
-  constexpr int PT = DIM == 2 ? 3 : 5;
-  for (int q = 0; q < n_pairs; ++q) {
+  int q = 0;
+  for (; q + 1 < n_pairs; q += 2) {
+    float4 oa[PV], ob[PV];
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+      oa[k] = __ldg(&obs[PV * q + k]);
+      ob[k] = __ldg(&obs[PV * (q + 1) + k]);
+    }
+    float2 sa[MAXNT], sb[MAXNT];
+    unsigned ga = 0u, gb = 0u;
+#pragma unroll
+    for (int m = 0; m < MAXNT; ++m) {
+      sa[m] = pair_sm1<DIM>(oa, p2[m], t2[m]);
+      sb[m] = pair_sm1<DIM>(ob, p2[m], t2[m]);
+      ga |= __float_as_uint(sa[m].x) | __float_as_uint(sa[m].y);
+      gb |= __float_as_uint(sb[m].x) | __float_as_uint(sb[m].y);
+    }
+    if ((int)ga < 0) project_record<DIM, MAXNT>(oa, obs + PV * q, p2, t2, sa, acc, mo);
+    if ((int)gb < 0) project_record<DIM, MAXNT>(ob, obs + PV * (q + 1), p2, t2, sb, acc, mo);
+  }
+  if (q < n_pairs) {
     float4 o[PV];
 #pragma unroll
     for (int k = 0; k < PT; ++k) o[k] = __ldg(&obs[PV * q + k]);
     float2 sm[MAXNT];
-    unsigned sign = 0u;
+    unsigned g = 0u;
 #pragma unroll
     for (int m = 0; m < MAXNT; ++m) {
       sm[m] = pair_sm1<DIM>(o, p2[m], t2[m]);
-      sign |= __float_as_uint(sm[m].x) | __float_as_uint(sm[m].y);
+      g |= __float_as_uint(sm[m].x) | __float_as_uint(sm[m].y);
     }
-    if ((int)sign < 0) { // some timestep is inside one of the two obstacles
-#pragma unroll
-      for (int k = PT; k < PV; ++k) o[k] = __ldg(&obs[PV * q + k]);
-#pragma unroll
-      for (int m = 0; m < MAXNT; ++m) {
-        if (sm[m].x < 0.f) pair_project<DIM, 0>(o, pos[m], tm[m], acc[m], mo);
-        if (sm[m].y < 0.f) pair_project<DIM, 1>(o, pos[m], tm[m], acc[m], mo);
-      }
-    }
+    if ((int)g < 0) project_record<DIM, MAXNT>(o, obs + PV * q, p2, t2, sm, acc, mo);
   }
 }
 

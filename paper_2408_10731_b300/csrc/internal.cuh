@@ -58,6 +58,8 @@ __host__ __device__ inline int table_floats(int n_p) { return 3 * ROW * n_p; }
 //      {iax0, iax1, iay0, iay1}, {iaz0, iaz1, ax0, ax1}, {ay0, ay1, az0, az1}
 // Sentinel half: nc = 1e18, nv = 0, ia = a = 1.
 __host__ __device__ constexpr int pair_vec(int dim) { return dim == 2 ? 4 : 6; }
+// The containment test reads only the first pair_test_vec float4 of a record.
+__host__ __device__ constexpr int pair_test_vec(int dim) { return dim == 2 ? 3 : 5; }
 __host__ __device__ constexpr int pair_count(int n_o) { return (n_o + 1) / 2; }
 constexpr float PAIR_SENTINEL = 1.0e18f;
 
