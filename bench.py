@@ -47,9 +47,8 @@ KERNEL_SOURCES = {
     "k_am_mixed": ("am_mixed.cu", "am_device.cuh", "internal.cuh", "tcgen05.cuh"),
 }
 MEASURED_TRAFFIC = {
-    "k_am_fp32": (736768, "af53a3a82dbe8c9b"),
-    "k_am_team": (710400, "af53a3a82dbe8c9b"),
-    "k_am_mixed": (717824, "b1c35f74ceb4999e"),
+    "k_am_fp32": (859392, "fa231ac34a91b6d6"),
+    "k_am_mixed": (728320, "fbcc66079630c1a8"),
 }
 
 
