@@ -67,6 +67,20 @@ def measured_traffic(kernel):
     return entry[0] if entry and entry[1] == source_digest(kernel) else None
 
 
+def combine_ranks(dist, world, total_ms, n_solved, e2e_rate, device="cpu"):
+    """Whole-job figures over the ranks (weak scaling, one independent batch per rank):
+    the slowest rank's timed total, the solved trajectories of all ranks, and the sum
+    of the ranks' end-to-end rates. One all_gather; no collective touches the data path."""
+    if world <= 1 or dist is None:
+        return float(total_ms), float(n_solved), float(e2e_rate)
+    import torch
+    t = torch.tensor([total_ms, n_solved, e2e_rate], device=device, dtype=torch.float64)
+    gathered = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(gathered, t)
+    g = torch.stack(gathered).cpu().numpy()
+    return float(g[:, 0].max()), float(g[:, 1].sum()), float(g[:, 2].sum())
+
+
 def kernel_name(precision, shape):
     """The solve kernel a handle of this precision and launch shape runs."""
     if precision == "mixed":
@@ -429,16 +443,8 @@ def main():
     total_ms = float(np.sum(h_step_ms))
     n_solved = float(np.sum(h_solved))
     e2e_val = float(np.mean(e2e_solved)) / float(np.mean(e2e_s))
-    if world > 1:
-        t = torch.tensor([total_ms, n_solved, e2e_val, float(np.mean(e2e_s))], device="cuda",
-                         dtype=torch.float64)
-        gathered = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(gathered, t)
-        g = torch.stack(gathered).cpu().numpy()
-        total_ms_max = float(g[:, 0].max()); n_solved_all = float(g[:, 1].sum())
-        e2e_all = float(g[:, 2].mean() * world)
-    else:
-        total_ms_max, n_solved_all, e2e_all = total_ms, n_solved, e2e_val
+    total_ms_max, n_solved_all, e2e_all = combine_ranks(
+        dist if world > 1 else None, world, total_ms, n_solved, e2e_val, device="cuda")
     value = n_solved_all / (total_ms_max * 1e-3)
     form_summary = {}
     for name, (sm, km, sv, o) in results.items():
