@@ -170,8 +170,21 @@ traj_status traj_get_accel_cost(traj_batch *b, float *cost);
 
 /* Solver state for checkpoint/resume and warm starts (nullable outputs):
  * multipliers lambda[n_traj][dim][11] and the last residual contraction
- * u = F^T (F xi - g) [n_traj][dim][11], FP32, host or device. */
+ * u = F^T (F xi - g) [n_traj][dim][11], FP32, host or device. Together with the
+ * coefficients of traj_get_trajectories this is the whole iteration state. */
 traj_status traj_get_state(traj_batch *b, float *lambda, float *u);
+
+/* Resume from an exported state (checkpoint/resume; the multipliers carried from
+ * one receding-horizon call to the next, Paper II's MPC use): coefficients,
+ * lambda and u as traj_get_trajectories / traj_get_state return them, FP32
+ * [n_traj][dim][11] each, host or device, for the current trajectories. The
+ * following traj_solve calls start with a QP step from this state instead of the
+ * initial projection, and run up to max_iters more iterations (iters counts these);
+ * solving N iterations, exporting, and resuming for M gives the iterate of N + M
+ * iterations (bitwise, same launch shape). traj_set_initial returns to fresh
+ * starts. Smoothness/tracking cost only (TRAJ_EINVAL in projection mode). No
+ * paper counterpart as an interface. */
+traj_status traj_set_state(traj_batch *b, const float *coeffs, const float *lambda, const float *u);
 
 /* Solve without allocating any memory, for callers that cannot allocate
  * device memory: code running under an allocator or memory pool owned by

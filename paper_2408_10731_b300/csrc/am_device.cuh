@@ -126,6 +126,20 @@ __device__ __forceinline__ void scatter_pairs(const float2 (&up)[DIM][6], int la
   }
 }
 
+// Resume: the owner lanes' multipliers and last contraction of trajectory b from the
+// imported state (lane 16 a + i: axis a, coefficient i; axis 2 at lanes i, 16 + i).
+template <int DIM>
+__device__ __forceinline__ void resume_state(const SolveArgs &A, int b, int oa, int ri, float &lam,
+                                             float &lam2, float &uo, float &uo2) {
+  const size_t base = (size_t)b * DIM * NC;
+  lam = A.lam0[base + oa * NC + ri];
+  uo = A.u0[base + oa * NC + ri];
+  if constexpr (DIM == 3) {
+    lam2 = A.lam0[base + 2 * NC + ri];
+    uo2 = A.u0[base + 2 * NC + ri];
+  }
+}
+
 // Algorithm 2 line 2 at the owner lanes, compensated FP32:
 // xi^k = hq + G xi^{k-1} + K11 (lambda^{k-1} - rho u^{k-1}).
 template <int DIM>

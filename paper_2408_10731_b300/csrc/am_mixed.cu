@@ -165,6 +165,10 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
     float mo = 0.f, mv = 0.f, ma = 0.f;
     signed char st = -1;
     int k = 0;
+    if (A.lam0) {
+      resume_state<DIM>(A, b, oa, ri, lam, lam2, uo, uo2);
+      k = 1;
+    }
     for (;; ++k) {
       if (k > 0) qp_step<DIM>(C, lane, rho, hq_hi, hq_lo, hq2_hi, hq2_lo, lam, lam2, uo, uo2, xo, xo2);
       float2 xp[DIM][6];

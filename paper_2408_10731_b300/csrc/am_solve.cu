@@ -96,6 +96,10 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
   float lam = 0.f, lam2 = 0.f, uo = 0.f, uo2 = 0.f;
   float mo, mv, ma;
   int k = 0;
+  if (A.lam0) { // resume from (xi, lambda, u) of an earlier solve: the next step is a QP step
+    resume_state<DIM>(A, b, oa, ri, lam, lam2, uo, uo2);
+    k = 1;
+  }
   signed char st = 1;
   for (;; ++k) {
     if (k > 0) qp_step<DIM>(C, lane, rho, hq_hi, hq_lo, hq2_hi, hq2_lo, lam, lam2, uo, uo2, xo, xo2);
@@ -210,6 +214,10 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
   float lam = 0.f, lam2 = 0.f, uo = 0.f, uo2 = 0.f;
   float mo, mv, ma;
   int k = 0, par = 0;
+  if (A.lam0) {
+    resume_state<DIM>(A, b, oa, ri, lam, lam2, uo, uo2);
+    k = 1;
+  }
   signed char st = 1;
   for (;; ++k) {
     if (k > 0) qp_step<DIM>(C, lane, rho, hq_hi, hq_lo, hq2_hi, hq2_lo, lam, lam2, uo, uo2, xo, xo2);

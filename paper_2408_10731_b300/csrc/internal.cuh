@@ -73,6 +73,8 @@ struct SolveArgs {
   const int *traj_problem;
   const int *order;
   const float *xi0;
+  const float *lam0;          // resume: multipliers and last contraction of the iterate in
+  const float *u0;            //   xi0 ([n_traj][dim][11]); both NULL for a fresh start
   float *xi;
   float *lam;
   float *u;

@@ -37,6 +37,8 @@ struct traj_batch {
   int *d_obs_index = nullptr; // CSR obstacle offsets [P + 1], then first pair record [P + 1]
   int *d_traj_problem = nullptr, *d_order = nullptr;
   float *d_xi0 = nullptr, *d_xi = nullptr, *d_lam = nullptr, *d_u = nullptr, *d_res = nullptr;
+  float *d_lam0 = nullptr, *d_u0 = nullptr; // imported state (traj_set_state)
+  bool resume = false;                       // the next solves continue the imported state
   int *d_iters = nullptr;
   signed char *d_status = nullptr;
   int *d_queue = nullptr, *d_flags = nullptr;
@@ -48,7 +50,7 @@ struct traj_batch {
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_valid = false;
-  int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1, g_team = -1;
+  int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1, g_team = -1, g_resume = -1;
   float g_tol = 0.f;
   unsigned long long g_timeout = 0;
   std::vector<int> tbl_off; // per problem, float offset of its basis tables
@@ -94,7 +96,7 @@ template <class T> static cudaError_t dalloc(T **p, size_t n) {
 static void free_all(traj_batch *b) {
   void *ptrs[] = {b->d_problems, b->d_T, b->d_start, b->d_goal, b->d_constants, b->d_tables,
                   b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_index,
-                  b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res,
+                  b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res, b->d_lam0, b->d_u0,
                   b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0, b->d_L, b->d_r,
                   b->d_caug, b->d_proj, b->d_elite, b->d_sflag};
   for (void *p : ptrs)
@@ -185,6 +187,7 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
       (e = dalloc(&b->d_order, B)) || (e = dalloc(&b->d_xi0, B * D * NC)) ||
       (e = dalloc(&b->d_xi, B * D * NC)) || (e = dalloc(&b->d_lam, B * D * NC)) ||
       (e = dalloc(&b->d_u, B * D * NC)) || (e = dalloc(&b->d_res, B * 3)) ||
+      (e = dalloc(&b->d_lam0, B * D * NC)) || (e = dalloc(&b->d_u0, B * D * NC)) ||
       (e = dalloc(&b->d_iters, B)) || (e = dalloc(&b->d_status, B)) || (e = dalloc(&b->d_queue, 1)) ||
       (e = dalloc(&b->d_flags, 1)) || (e = dalloc(&b->d_t0, 1)) || (e = dalloc(&b->d_L, 48 * 48)) ||
       (e = dalloc(&b->d_r, B)) || (e = dalloc(&b->d_caug, B)) || (e = dalloc(&b->d_proj, B)) ||
@@ -326,6 +329,10 @@ traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
                              const float *coeffs0) {
   if (!b) return TRAJ_EINVAL;
   if (!b->have_obstacles) return fail(b, TRAJ_ESTATE, "traj_set_obstacles must come first");
+  if (b->resume) { // a fresh start from here on
+    b->resume = false;
+    invalidate_graph(b);
+  }
   if (!traj_problem && coeffs0 && b->have_initial && n_traj == b->n_traj) {
     // coefficients only: keep the trajectory -> problem map and the work order
     CK(b, cudaMemcpyAsync(b->d_xi0, coeffs0, sizeof(float) * n_traj * b->cfg.dim * NC,
@@ -417,6 +424,8 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   a.traj_problem = b->d_traj_problem;
   a.order = b->d_order;
   a.xi0 = b->d_xi0;
+  a.lam0 = b->resume ? b->d_lam0 : nullptr;
+  a.u0 = b->resume ? b->d_u0 : nullptr;
   a.xi = b->d_xi;
   a.lam = b->d_lam;
   a.u = b->d_u;
@@ -437,7 +446,7 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   const bool same = b->graph_valid && b->g_max_iters == max_iters && b->g_tol == tol &&
                     b->g_timeout == a.timeout_ns && b->g_n_traj == b->n_traj &&
                     b->g_warps == b->shape.warps_per_block && b->g_bps == b->shape.blocks_per_sm &&
-                    b->g_team == b->shape.team;
+                    b->g_team == b->shape.team && b->g_resume == (int)b->resume;
   if (!same) {
     // capture {clear counters; persistent solve} on the handle's capture stream
     invalidate_graph(b);
@@ -461,6 +470,7 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
     b->g_max_iters = max_iters; b->g_tol = tol; b->g_timeout = a.timeout_ns;
     b->g_n_traj = b->n_traj; b->g_warps = b->shape.warps_per_block; b->g_bps = b->shape.blocks_per_sm;
     b->g_team = b->shape.team;
+    b->g_resume = (int)b->resume;
   }
   CK(b, cudaEventRecord(b->ev0, b->stream));
   CK(b, cudaGraphLaunch(b->graph_exec, b->stream));
@@ -508,6 +518,26 @@ traj_status traj_get_state(traj_batch *b, float *lambda, float *u) {
   if (lambda) { CK(b, cudaMemcpyAsync(lambda, b->d_lam, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(lambda); }
   if (u) { CK(b, cudaMemcpyAsync(u, b->d_u, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(u); }
   if (host) CK(b, cudaStreamSynchronize(b->stream));
+  return TRAJ_OK;
+}
+
+traj_status traj_set_state(traj_batch *b, const float *coeffs, const float *lambda, const float *u) {
+  if (!b) return TRAJ_EINVAL;
+  if (!coeffs || !lambda || !u) return fail(b, TRAJ_EINVAL, "NULL state array");
+  if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
+  if (b->cfg.cost_mode != TRAJ_COST_SMOOTH_TRACK)
+    return fail(b, TRAJ_EINVAL, "resume needs the smoothness/tracking cost (projection mode reads "
+                                "its sample from the initial coefficients)");
+  const size_t n = (size_t)b->n_traj * b->cfg.dim * NC;
+  CK(b, cudaMemcpyAsync(b->d_xi0, coeffs, sizeof(float) * n, cudaMemcpyDefault, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_lam0, lambda, sizeof(float) * n, cudaMemcpyDefault, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_u0, u, sizeof(float) * n, cudaMemcpyDefault, b->stream));
+  if (is_host_ptr(coeffs) || is_host_ptr(lambda) || is_host_ptr(u)) CK(b, cudaStreamSynchronize(b->stream));
+  if (!b->resume) {
+    b->resume = true;
+    invalidate_graph(b);
+  }
+  b->have_result = false;
   return TRAJ_OK;
 }
 

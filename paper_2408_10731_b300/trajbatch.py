@@ -93,6 +93,7 @@ def load_library():
     lib.traj_get_solve_stats.argtypes = [_vp, ctypes.POINTER(SolveStats)]
     lib.traj_get_trajectories.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.traj_get_state.argtypes = [_vp, _vp, _vp]
+    lib.traj_set_state.argtypes = [_vp, _vp, _vp, _vp]
     lib.traj_status_string.argtypes = [_c_int]
     lib.traj_status_string.restype = ctypes.c_char_p
     lib.traj_last_error.argtypes = [_vp]
@@ -109,7 +110,7 @@ def load_library():
                                        _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
                  "traj_set_obstacles", "traj_set_initial", "traj_solve", "traj_get_solve_stats",
-                 "traj_get_trajectories", "traj_get_state", "traj_measure_fp32_peak",
+                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_measure_fp32_peak",
                  "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune",
                  "traj_sampler_step", "traj_gemm_bf16"):
         getattr(lib, name).restype = _c_int
@@ -278,6 +279,13 @@ class TrajBatch:
         self._check(self._lib.traj_get_state(self._h, _ptr(lam, np.float32)[0],
                                              _ptr(u, np.float32)[0]))
         return dict(lam=lam, u=u)
+
+    def set_state(self, xi, lam, u):
+        """Resume the next solves from an exported (xi, lambda, u) state."""
+        xp, kx = _ptr(xi, np.float32)
+        lp, kl = _ptr(lam, np.float32)
+        up, ku = _ptr(u, np.float32)
+        self._check(self._lib.traj_set_state(self._h, xp, lp, up))
 
 
 def gemm_bf16(A, B, C, err, stream=None):

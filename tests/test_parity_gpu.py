@@ -242,3 +242,48 @@ def test_launch_shape_graph_replay_and_autotune_do_not_change_results():
                                       refs[choice["warps_per_trajectory"]]["xi"])
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("precision,shape", [("fp32", (4, 0, 1)), ("fp32", (8, 0, 2)),
+                                             ("mixed", (0, 0, 1))])
+def test_checkpoint_resume_continues_bitwise(precision, shape):
+    """Solving N iterations, exporting (xi, lambda, u) and resuming for M more gives
+    bitwise the iterate of N + M iterations in one solve; traj_set_initial returns
+    to fresh starts."""
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.config2(2, n_scenes=8, inits=8)
+    h = tb.from_batch(b, precision=precision)
+    try:
+        h.set_launch_shape(*shape)
+        h.solve(40, tol=-1.0)
+        direct = h.get_trajectories()
+        direct.update(h.get_state())
+        h.set_initial(b.traj_problem, b.xi0)
+        h.solve(25, tol=-1.0)
+        mid = h.get_trajectories()
+        mid.update(h.get_state())
+        h.set_state(mid["xi"], mid["lam"], mid["u"])
+        h.solve(15, tol=-1.0)
+        res = h.get_trajectories()
+        res.update(h.get_state())
+        assert np.all(res["iters"] == 15)
+        for key in ("xi", "lam", "u", "residual"):
+            np.testing.assert_array_equal(res[key], direct[key], err_msg=key)
+        h.set_initial(b.traj_problem, b.xi0)  # fresh start again
+        h.solve(40, tol=-1.0)
+        np.testing.assert_array_equal(h.get_trajectories()["xi"], direct["xi"])
+    finally:
+        h.close()
+
+
+def test_resume_is_refused_in_projection_mode():
+    from paper_2408_10731_b300 import trajbatch as tb
+    c3 = scenes.config3(0, n_traj=16)
+    h = tb.from_batch(c3["batch"], cost_mode="project")
+    try:
+        z = np.zeros((16, 3, 11), np.float32)
+        with pytest.raises(tb.TrajBatchError) as e:
+            h.set_state(z, z, z)
+        assert e.value.code == -1
+    finally:
+        h.close()
