@@ -309,6 +309,9 @@ def main():
     ap.add_argument("--no-warmstart", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--ws-scenes", type=int, default=200000)
+    ap.add_argument("--rho-ladder", default="10,1.3,30",
+                    help="penalty continuation of the extra *_rho_ladder forms: levels,growth,every")
+    ap.add_argument("--no-rho-ladder", action="store_true")
     ap.add_argument("--shape", default=None,
                     help="FP32 launch shape W,B,T (warps per block, blocks per SM, warps per "
                          "trajectory) instead of the autotuned one")
@@ -363,6 +366,19 @@ def main():
     forms = {"plain_fp32": ("fp32", None)}
     if "mixed" in handles:
         forms["plain_mixed"] = ("mixed", None)
+    # extra forms, reported beside the configured ones: the penalty continuation
+    # (the penalty grows while the residuals stay above the tolerance)
+    ladder = None if args.no_rho_ladder or args.workload != "config2" else \
+        tuple(f(x) for f, x in zip((int, float, int), args.rho_ladder.split(",")))
+    if ladder:
+        handles["fp32_ladder"] = trajbatch.from_batch(batch, precision="fp32")
+        handles["fp32_ladder"].set_launch_shape(shape["warps_per_block"], shape["blocks_per_sm"],
+                                                shape.get("warps_per_trajectory", 1))
+        handles["fp32_ladder"].set_rho_schedule(*ladder)
+        forms["plain_fp32_rho_ladder"] = ("fp32_ladder", None)
+        if "mixed" in handles:
+            handles["mixed_ladder"] = trajbatch.from_batch(batch, precision="mixed")
+            handles["mixed_ladder"].set_rho_schedule(*ladder)
     ws = None
     if args.workload == "config2" and not args.no_warmstart:
         from paper_2408_10731_b300 import warmstart
@@ -376,11 +392,13 @@ def main():
         forms["warmstart_fp32"] = ("fp32", ws_init)
         if "mixed" in handles:
             forms["warmstart_mixed"] = ("mixed", ws_init)
+        if "mixed_ladder" in handles:
+            forms["warmstart_mixed_rho_ladder"] = ("mixed_ladder", ws_init)
     xi0_dev = torch.as_tensor(batch.xi0, dtype=torch.float32, device="cuda")
 
     def run_form(form, steps, timed):
-        prec, init = form
-        hh = handles[prec]
+        key, init = form
+        hh = handles[key]
         if init is None:
             hh.set_initial(None, xi0_dev)
         step_ms, kern_ms, solved = [], [], []
@@ -449,8 +467,9 @@ def main():
     form_summary = {}
     for name, (sm, km, sv, o) in results.items():
         ok = o["status"] == 0
-        form_summary[name] = {"kernel": kernel_name(forms[name][0], shape if forms[name][0] ==
-                                                     args.precision else None),
+        prec_f = forms[name][0].split("_")[0]
+        form_summary[name] = {"kernel": kernel_name(prec_f, shape if prec_f == args.precision
+                                                    else None),
                               "solved_per_s": float(np.sum(sv)) / (float(np.sum(sm)) * 1e-3),
                               "ms_per_batch_solve": float(np.mean(sm)),
                               "solve_kernel_ms": float(np.mean(km)),
@@ -467,7 +486,7 @@ def main():
         kern_s = float(np.mean(h_kern_ms)) * 1e-3
         achieved = ops / kern_s
         peak_ops = fp32_peak / 2.0  # FFMA rate in lane-operations/s (2 FLOP per FMA)
-        prec_h = forms[headline][0]
+        prec_h = forms[headline][0].split("_")[0]
         kern = kernel_name(prec_h, shape if prec_h == args.precision else None)
         traffic = measured_traffic(kern) if args.workload == "config2" else None
         line = {
@@ -479,7 +498,10 @@ def main():
             "config": {"workload": WORKLOAD if args.workload == "config2" else WORKLOAD_UNEVEN,
                        "precision": args.precision, "launch_shape": shape,
                        "l2": "flushed between timed steps (256 MB write, outside the events)",
-                       "per_rank_batch": "seed + rank"},
+                       "per_rank_batch": "seed + rank",
+                       "rho_ladder_forms": (None if not ladder else
+                                            {"levels": ladder[0], "growth": ladder[1],
+                                             "every": ladder[2], "rho0": batch.rho})},
             "ms_per_batch_solve": float(np.mean(h_step_ms)),
             "ms_per_batch_solve_plain_fp32": float(np.mean(step_ms)),
             "solved_per_step": float(np.mean(h_solved)), "trajectories_per_step": batch.n_traj,

@@ -174,6 +174,17 @@ traj_status traj_get_accel_cost(traj_batch *b, float *cost);
  * coefficients of traj_get_trajectories this is the whole iteration state. */
 traj_status traj_get_state(traj_batch *b, float *lambda, float *u);
 
+/* Penalty continuation (Paper I, Algorithm 1 line 9: the penalty grows while the
+ * residuals stay above the threshold; Paper IV: the KKT inverse cached for ten
+ * increasing penalties used in the later iterations): a ladder of `levels`
+ * penalties rho * growth^l (l = 0 .. levels-1, levels <= 10), each with its own
+ * KKT inverse formed once in FP64. A trajectory starts at level 0 and moves up one
+ * level after every `every`-th iteration at which it has not converged (the
+ * threshold is the solve's tol; with tol < 0, at every `every`-th iteration) until
+ * the last level. levels = 1 (the default) is the fixed penalty of the config.
+ * Recomputes the set-up if obstacles are loaded; TRAJ_EINVAL on bad arguments. */
+traj_status traj_set_rho_schedule(traj_batch *b, int levels, double growth, int every);
+
 /* Resume from an exported state (checkpoint/resume; the multipliers carried from
  * one receding-horizon call to the next, Paper II's MPC use): coefficients,
  * lambda and u as traj_get_trajectories / traj_get_state return them, FP32

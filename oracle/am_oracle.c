@@ -37,6 +37,11 @@
  *     (PRIEST eq. eq1_multiagent_1_priest with b0 = (start, 0, 0), bf = goal).
  *  R9 residuals are L-infinity over the grid points: max_{j,t} ||p - g_j||,
  *     max_t ||pdot - g_v||, max_t ||pddot - g_a||.
+ *  R10 penalty continuation (Paper I, Algorithm 1 line 9; Paper IV's ten cached
+ *     KKT inverses): penalties rho growth^l, l = 0 .. levels-1, each with its own
+ *     KKT inverse; after iteration k >= 1, if the trajectory has not stopped and k
+ *     is a multiple of rho_every, the next iteration uses the next level (up to
+ *     the last). The level's rho enters the xi-step and the multiplier update.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -147,6 +152,9 @@ typedef struct {
   const double *start, *goal;                      /* [dim] */
   double vmax, amax, rho, w_smooth, w_track;
   int cost_mode;   /* 0: smoothness + tracking (eq. Q_matrix); 1: projection (eq. matrix_vec) */
+  int rho_levels;  /* penalty continuation (reading R10); 1 or 0: a fixed rho */
+  double rho_growth;
+  int rho_every;
 } orc_problem;
 
 /* Dense F for one axis: (n_o + 2) n_p rows x 11 (F of Paper II without the
@@ -271,11 +279,17 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
   const size_t rows = (size_t)(n_o + 2) * n_p;
   double *P = malloc(sizeof(double) * n_p * NC), *Pd = malloc(sizeof(double) * n_p * NC),
          *Pdd = malloc(sizeof(double) * n_p * NC), *F = malloc(sizeof(double) * rows * NC);
-  double K[NK * NK], Kinv[NK * NK];
+  const int levels = pr->rho_levels > 1 ? pr->rho_levels : 1;
+  if (levels > 16) { free(P); free(Pd); free(Pdd); free(F); return -3; }
+  double K[NK * NK], Kinv[16][NK * NK], rho_l[16];
   orc_bernstein(n_p, pr->T, P, Pd, Pdd);
   build_F(n_p, n_o, P, Pd, Pdd, F);
-  int rc = orc_kkt(pr, K, Kinv);
-  if (rc) { free(P); free(Pd); free(Pdd); free(F); return -1; }
+  for (int l = 0; l < levels; ++l) { /* one KKT inverse per penalty level (reading R10) */
+    orc_problem pl = *pr;
+    pl.rho = pr->rho * pow(pr->rho_growth, (double)l);
+    rho_l[l] = pl.rho;
+    if (orc_kkt(&pl, K, Kinv[l])) { free(P); free(Pd); free(Pdd); free(F); return -1; }
+  }
 
   /* q per axis (eq. Q_matrix: q = -w_t P^T x_des, x_des the constant-velocity
    * straight line); b per axis = (start, 0, 0, goal) (reading R8). */
@@ -302,8 +316,12 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
   for (int b = 0; b < n_traj; ++b) {
     REAL *xi = malloc(sizeof(REAL) * dim * NC), *lam = malloc(sizeof(REAL) * dim * NC);
     REAL *Fx = malloc(sizeof(REAL) * dim * rows), *g = malloc(sizeof(REAL) * dim * rows);
-    REAL *Kr = malloc(sizeof(REAL) * NK * NK), *Fr = malloc(sizeof(REAL) * rows * NC);
-    for (int k = 0; k < NK * NK; ++k) Kr[k] = (REAL)Kinv[k];
+    REAL *Kall = malloc(sizeof(REAL) * levels * NK * NK), *Fr = malloc(sizeof(REAL) * rows * NC);
+    for (int l = 0; l < levels; ++l)
+      for (int k = 0; k < NK * NK; ++k) Kall[l * NK * NK + k] = (REAL)Kinv[l][k];
+    int level = 0;
+    REAL *Kr = Kall;
+    REAL rho = (REAL)rho_l[0];
     for (size_t k = 0; k < rows * NC; ++k) Fr[k] = (REAL)F[k];
     for (int k = 0; k < dim * NC; ++k) { xi[k] = (REAL)xi0[(size_t)b * dim * NC + k]; lam[k] = 0; }
     /* projection mode (eq. matrix_vec): Q = I, q = -xi_sample, the trajectory's own xi0 */
@@ -325,7 +343,7 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
           for (int i = 0; i < NC; ++i) {
             REAL Ftg = 0;
             for (size_t r = 0; r < rows; ++r) Ftg += Fr[r * NC + i] * g[a * rows + r];
-            rhs[i] = -q[a][i] + lam[a * NC + i] + (REAL)pr->rho * Ftg;
+            rhs[i] = -q[a][i] + lam[a * NC + i] + rho * Ftg;
           }
           for (int e = 0; e < NE; ++e) rhs[NC + e] = (REAL)ba[a][e];
           for (int i = 0; i < NC; ++i) {
@@ -389,13 +407,19 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
             REAL s = 0;
             for (size_t r = 0; r < rows; ++r)
               s += Fr[r * NC + i] * (Fx[a * rows + r] - g[a * rows + r]);
-            lam[a * NC + i] -= (REAL)pr->rho * s;
+            lam[a * NC + i] -= rho * s;
           }
       if (hist)
         for (int c = 0; c < 3; ++c) hist[((size_t)b * (max_iters + 1) + k) * 3 + c] = res[c];
       k_done = k;
       if (fixed < 0 && k > 0 && tol >= 0 && res[0] <= tol && res[1] <= tol && res[2] <= tol)
         break;
+      /* penalty continuation (reading R10): not stopped after iteration k */
+      if (k > 0 && pr->rho_every > 0 && level + 1 < levels && k % pr->rho_every == 0) {
+        ++level;
+        Kr = Kall + (size_t)level * NK * NK;
+        rho = (REAL)rho_l[level];
+      }
     }
     for (int k = 0; k < dim * NC; ++k) {
       xi_out[(size_t)b * dim * NC + k] = xi[k];
@@ -403,7 +427,7 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
     }
     for (int c = 0; c < 3; ++c) residual_out[(size_t)b * 3 + c] = res[c];
     iters_out[b] = k_done;
-    free(xi); free(lam); free(Fx); free(g); free(Kr); free(Fr);
+    free(xi); free(lam); free(Fx); free(g); free(Kall); free(Fr);
   }
   free(P); free(Pd); free(Pdd); free(F); free(tgrid);
   return 0;
@@ -416,9 +440,11 @@ int orc_am_solve_flat(int dim, int n_p, double T, int n_o, const double *centers
                       double w_smooth, double w_track, int cost_mode, int n_traj,
                       const double *xi0, int max_iters, double tol, const int *iters_fixed,
                       double *xi_out, double *lam_out, double *residual_out, int *iters_out,
-                      double *hist, int n_threads) {
+                      double *hist, int n_threads, int rho_levels, double rho_growth,
+                      int rho_every) {
   orc_problem pr = {dim, n_p, T, n_o, centers, semi_axes, velocities, start, goal,
-                    vmax, amax, rho, w_smooth, w_track, cost_mode};
+                    vmax, amax, rho, w_smooth, w_track, cost_mode, rho_levels, rho_growth,
+                    rho_every};
   return orc_am_solve(&pr, n_traj, xi0, max_iters, tol, iters_fixed, xi_out, lam_out,
                       residual_out, iters_out, hist, n_threads);
 }
@@ -426,7 +452,7 @@ int orc_am_solve_flat(int dim, int n_p, double T, int n_o, const double *centers
 int orc_kkt_flat(int dim, int n_p, double T, int n_o, double rho, double w_smooth,
                  double w_track, int cost_mode, double *K, double *Kinv) {
   orc_problem pr = {dim, n_p, T, n_o, NULL, NULL, NULL, NULL, NULL,
-                    0, 0, rho, w_smooth, w_track, cost_mode};
+                    0, 0, rho, w_smooth, w_track, cost_mode, 1, 1.0, 0};
   return orc_kkt(&pr, K, Kinv);
 }
 

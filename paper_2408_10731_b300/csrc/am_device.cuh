@@ -126,6 +126,51 @@ __device__ __forceinline__ void scatter_pairs(const float2 (&up)[DIM][6], int la
   }
 }
 
+// hq of the QP step at the owner lanes from a constants block C: smoothness/tracking
+// mode reads K11 (-q) + K12 b; projection mode forms K12 b + K11 xi_sample from the
+// trajectory's own sample coefficients (xs, xs2 at the owner lanes), compensated.
+template <int DIM>
+__device__ __forceinline__ void load_hq(const float *C, int cost_mode, int lane, float xs, float xs2,
+                                        float &hq_hi, float &hq_lo, float &hq2_hi, float &hq2_lo) {
+  const int oa = lane >> 4, oi = lane & 15;
+  const int ri = oi < NC ? oi : NC - 1;
+  hq2_hi = 0.f; hq2_lo = 0.f;
+  if (cost_mode == 0) {
+    hq_hi = C[C_HQ_HI + oa * ROW + ri]; hq_lo = C[C_HQ_LO + oa * ROW + ri];
+    if (DIM == 3) { hq2_hi = C[C_HQ_HI + 2 * ROW + ri]; hq2_lo = C[C_HQ_LO + 2 * ROW + ri]; }
+    return;
+  }
+  hq_hi = C[C_C_HI + oa * ROW + ri]; hq_lo = C[C_C_LO + oa * ROW + ri];
+  if (DIM == 3) { hq2_hi = C[C_C_HI + 2 * ROW + ri]; hq2_lo = C[C_C_LO + 2 * ROW + ri]; }
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const float xk = __shfl_sync(FULL, xs, (lane & 16) + q);
+    df_fma(hq_hi, hq_lo, C[C_K11_HI + ri * ROW + q], C[C_K11_LO + ri * ROW + q], xk);
+    if (DIM == 3) {
+      const float xk2 = __shfl_sync(FULL, xs2, q);
+      df_fma(hq2_hi, hq2_lo, C[C_K11_HI + ri * ROW + q], C[C_K11_LO + ri * ROW + q], xk2);
+    }
+  }
+  // hq = c + K11 xi_sample: fold lo into hi once (both stay exact pairs)
+  const float s = hq_hi + hq_lo; hq_lo = hq_lo - (s - hq_hi); hq_hi = s;
+  if (DIM == 3) { const float s2 = hq2_hi + hq2_lo; hq2_lo = hq2_lo - (s2 - hq2_hi); hq2_hi = s2; }
+}
+
+// Penalty continuation: after iteration k, if the trajectory has not converged and k
+// is a multiple of rho_every, move to the next rho of the ladder (its constants block
+// and hq); returns true when the level changed.
+template <int DIM>
+__device__ __forceinline__ bool rho_step(const SolveArgs &A, int k, int &level, const float *Cb,
+                                         const float *&C, float &rho, int lane, float xs, float xs2,
+                                         float &hq_hi, float &hq_lo, float &hq2_hi, float &hq2_lo) {
+  if (k == 0 || A.rho_every <= 0 || level + 1 >= A.rho_levels || (k % A.rho_every) != 0) return false;
+  ++level;
+  C = Cb + (size_t)level * CONST_FLOATS;
+  rho = A.rho_ladder[level];
+  load_hq<DIM>(C, A.cost_mode, lane, xs, xs2, hq_hi, hq_lo, hq2_hi, hq2_lo);
+  return true;
+}
+
 // Resume: the owner lanes' multipliers and last contraction of trajectory b from the
 // imported state (lane 16 a + i: axis a, coefficient i; axis 2 at lanes i, 16 + i).
 template <int DIM>

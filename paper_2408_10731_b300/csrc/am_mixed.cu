@@ -109,7 +109,6 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
 
   const int oi = lane & 15, oa = lane >> 4;
   const int ri = oi < NC ? oi : NC - 1;
-  const float rho = A.rho;
   uint8_t *myB = sB + warp * KT * MX_TILE_B;
   const uint32_t my_mbar = smem_u32(mbar + warp);
   const uint32_t d_col = tmem + 16u * warp;                                        // MMA destination
@@ -125,7 +124,7 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
     if (item >= A.n_traj) break;
     const int b = A.order[item];
     const ProblemDev pr = A.problems[A.traj_problem[b]];
-    const float *C = A.constants + pr.const_off;
+    const float *Cb = A.constants + pr.const_off, *C = Cb;
     const float4 *obs = A.obstacles + (size_t)pr.pair_off * pair_vec(DIM);
     const float *x0 = A.xi0 + (size_t)b * DIM * NC;
     float xo = x0[oa * NC + ri];
@@ -142,25 +141,11 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
       if (lane == 0) { A.iters[b] = 0; A.status[b] = 2; atomicOr(A.flags, 2); }
       continue;
     }
-    float hq_hi, hq_lo, hq2_hi = 0.f, hq2_lo = 0.f;
-    if (A.cost_mode == 0) {
-      hq_hi = C[C_HQ_HI + oa * ROW + ri]; hq_lo = C[C_HQ_LO + oa * ROW + ri];
-      if (DIM == 3) { hq2_hi = C[C_HQ_HI + 2 * ROW + ri]; hq2_lo = C[C_HQ_LO + 2 * ROW + ri]; }
-    } else {
-      hq_hi = C[C_C_HI + oa * ROW + ri]; hq_lo = C[C_C_LO + oa * ROW + ri];
-      if (DIM == 3) { hq2_hi = C[C_C_HI + 2 * ROW + ri]; hq2_lo = C[C_C_LO + 2 * ROW + ri]; }
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const float xk = __shfl_sync(FULL, xo, (lane & 16) + q);
-        df_fma(hq_hi, hq_lo, C[C_K11_HI + ri * ROW + q], C[C_K11_LO + ri * ROW + q], xk);
-        if (DIM == 3) {
-          const float xk2 = __shfl_sync(FULL, xo2, q);
-          df_fma(hq2_hi, hq2_lo, C[C_K11_HI + ri * ROW + q], C[C_K11_LO + ri * ROW + q], xk2);
-        }
-      }
-      float s = hq_hi + hq_lo; hq_lo = hq_lo - (s - hq_hi); hq_hi = s;
-      if (DIM == 3) { float s2 = hq2_hi + hq2_lo; hq2_lo = hq2_lo - (s2 - hq2_hi); hq2_hi = s2; }
-    }
+    const float xs = xo, xs2 = xo2;
+    float hq_hi, hq_lo, hq2_hi, hq2_lo;
+    load_hq<DIM>(C, A.cost_mode, lane, xs, xs2, hq_hi, hq_lo, hq2_hi, hq2_lo);
+    int level = 0;
+    float rho = A.rho;
     float lam = 0.f, lam2 = 0.f, uo = 0.f, uo2 = 0.f;
     float mo = 0.f, mv = 0.f, ma = 0.f;
     signed char st = -1;
@@ -269,6 +254,7 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
         now = __shfl_sync(FULL, now, 0);
         if (now > deadline) { st = 3; break; }
       }
+      rho_step<DIM>(A, k, level, Cb, C, rho, lane, xs, xs2, hq_hi, hq_lo, hq2_hi, hq2_lo);
     }
     if (st == -2) break;
     if (oi < NC) {

@@ -42,12 +42,12 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
   const ProblemDev pr = A.problems[p];
   const int n_p = pr.n_p, n_o = pr.n_o;
   const int nt = (n_p + 31) >> 5;
-  const float *C = A.constants + pr.const_off;
+  const float *Cb = A.constants + pr.const_off, *C = Cb; // constants of the penalty level
   const float *tP = stab + pr.tbl_off;
   const float *tD = tP + n_p * ROW;
   const float *tA = tD + n_p * ROW;
   const float4 *obs = A.obstacles + (size_t)pr.pair_off * pair_vec(DIM);
-  const float rho = A.rho;
+  float rho = A.rho;
 
   // ownership: lane 16 a + i holds coefficient i of axis a (a < 2); axis 2 of a 3D
   // trajectory is held (twice) by lanes i and 16 + i.
@@ -70,28 +70,11 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
     return;
   }
 
-  // hq: smoothness/tracking mode reads K11 (-q) + K12 b; projection mode forms
-  // K12 b + K11 xi_sample from this trajectory's own coefficients.
-  float hq_hi, hq_lo, hq2_hi = 0.f, hq2_lo = 0.f;
-  if (A.cost_mode == 0) {
-    hq_hi = C[C_HQ_HI + oa * ROW + ri]; hq_lo = C[C_HQ_LO + oa * ROW + ri];
-    if (DIM == 3) { hq2_hi = C[C_HQ_HI + 2 * ROW + ri]; hq2_lo = C[C_HQ_LO + 2 * ROW + ri]; }
-  } else {
-    hq_hi = C[C_C_HI + oa * ROW + ri]; hq_lo = C[C_C_LO + oa * ROW + ri];
-    if (DIM == 3) { hq2_hi = C[C_C_HI + 2 * ROW + ri]; hq2_lo = C[C_C_LO + 2 * ROW + ri]; }
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const float xk = __shfl_sync(FULL, xo, (lane & 16) + k);
-      df_fma(hq_hi, hq_lo, C[C_K11_HI + ri * ROW + k], C[C_K11_LO + ri * ROW + k], xk);
-      if (DIM == 3) {
-        const float xk2 = __shfl_sync(FULL, xo2, k);
-        df_fma(hq2_hi, hq2_lo, C[C_K11_HI + ri * ROW + k], C[C_K11_LO + ri * ROW + k], xk2);
-      }
-    }
-    // hq = c + K11 xi_sample: fold lo into hi once (both stay exact pairs)
-    float s = hq_hi + hq_lo; hq_lo = hq_lo - (s - hq_hi); hq_hi = s;
-    if (DIM == 3) { float s2 = hq2_hi + hq2_lo; hq2_lo = hq2_lo - (s2 - hq2_hi); hq2_hi = s2; }
-  }
+  // hq of the first penalty level (projection mode: from the sample xs)
+  const float xs = xo, xs2 = xo2;
+  float hq_hi, hq_lo, hq2_hi, hq2_lo;
+  load_hq<DIM>(C, A.cost_mode, lane, xs, xs2, hq_hi, hq_lo, hq2_hi, hq2_lo);
+  int level = 0;
 
   float lam = 0.f, lam2 = 0.f, uo = 0.f, uo2 = 0.f;
   float mo, mv, ma;
@@ -125,6 +108,7 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
       now = __shfl_sync(FULL, now, 0);
       if (now > deadline) { st = 3; break; }
     }
+    rho_step<DIM>(A, k, level, Cb, C, rho, lane, xs, xs2, hq_hi, hq_lo, hq2_hi, hq2_lo);
   }
   if (oi < NC) {
     xout[oa * NC + oi] = xo;
@@ -167,12 +151,12 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
   const int p = A.traj_problem[b];
   const ProblemDev pr = A.problems[p];
   const int n_p = pr.n_p, n_o = pr.n_o;
-  const float *C = A.constants + pr.const_off;
+  const float *Cb = A.constants + pr.const_off, *C = Cb;
   const float *tP = stab + pr.tbl_off;
   const float *tD = tP + n_p * ROW;
   const float *tA = tD + n_p * ROW;
   const float4 *obs = A.obstacles + (size_t)pr.pair_off * pair_vec(DIM);
-  const float rho = A.rho;
+  float rho = A.rho;
   const int oi = lane & 15, oa = lane >> 4;
   const int ri = oi < NC ? oi : NC - 1;
   const float *x0 = A.xi0 + (size_t)b * DIM * NC;
@@ -192,25 +176,10 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
     }
     return;
   }
-  float hq_hi, hq_lo, hq2_hi = 0.f, hq2_lo = 0.f;
-  if (A.cost_mode == 0) {
-    hq_hi = C[C_HQ_HI + oa * ROW + ri]; hq_lo = C[C_HQ_LO + oa * ROW + ri];
-    if (DIM == 3) { hq2_hi = C[C_HQ_HI + 2 * ROW + ri]; hq2_lo = C[C_HQ_LO + 2 * ROW + ri]; }
-  } else {
-    hq_hi = C[C_C_HI + oa * ROW + ri]; hq_lo = C[C_C_LO + oa * ROW + ri];
-    if (DIM == 3) { hq2_hi = C[C_C_HI + 2 * ROW + ri]; hq2_lo = C[C_C_LO + 2 * ROW + ri]; }
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      const float xk = __shfl_sync(FULL, xo, (lane & 16) + q);
-      df_fma(hq_hi, hq_lo, C[C_K11_HI + ri * ROW + q], C[C_K11_LO + ri * ROW + q], xk);
-      if (DIM == 3) {
-        const float xk2 = __shfl_sync(FULL, xo2, q);
-        df_fma(hq2_hi, hq2_lo, C[C_K11_HI + ri * ROW + q], C[C_K11_LO + ri * ROW + q], xk2);
-      }
-    }
-    float s0 = hq_hi + hq_lo; hq_lo = hq_lo - (s0 - hq_hi); hq_hi = s0;
-    if (DIM == 3) { float s2 = hq2_hi + hq2_lo; hq2_lo = hq2_lo - (s2 - hq2_hi); hq2_hi = s2; }
-  }
+  const float xs = xo, xs2 = xo2;
+  float hq_hi, hq_lo, hq2_hi, hq2_lo;
+  load_hq<DIM>(C, A.cost_mode, lane, xs, xs2, hq_hi, hq_lo, hq2_hi, hq2_lo);
+  int level = 0;
   float lam = 0.f, lam2 = 0.f, uo = 0.f, uo2 = 0.f;
   float mo, mv, ma;
   int k = 0, par = 0;
@@ -263,6 +232,7 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
     }
     if (k >= A.max_iters) { st = 1; break; }
     if (late) { st = 3; break; }
+    rho_step<DIM>(A, k, level, Cb, C, rho, lane, xs, xs2, hq_hi, hq_lo, hq2_hi, hq2_lo);
   }
   if (r == 0) {
     if (oi < NC) {
@@ -299,7 +269,7 @@ __device__ __forceinline__ void team_nt(const SolveArgs &A, int b, const float *
 }
 
 template <int DIM, int MAXNT, int W>
-__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32)
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32, 2)
 k_am_team(const __grid_constant__ SolveArgs A) {
   extern __shared__ float4 smem4[];
   const int nteam = blockDim.x / (32 * W);

@@ -11,6 +11,7 @@ constexpr int NE = 4;       // boundary rows per axis
 constexpr int NK = NC + NE; // KKT size
 constexpr int ROW = 12;     // padded row length (floats) of every 11-wide table row
 constexpr int MAX_STEPS = 256;
+constexpr int RHO_MAX_LEVELS = 10; // penalty levels of the continuation ladder
 
 // Per-problem record on the device (64 bytes).
 struct ProblemDev {
@@ -91,6 +92,12 @@ struct SolveArgs {
   int *queue;                 // work-queue counter, zeroed before the launch
   unsigned long long *t0;     // launch start time (globaltimer), zeroed before the launch
   int *flags;                 // bit 0: timeout hit, bit 1: NaN input seen, bit 3: MMA wait expired
+  // penalty continuation: rho_levels constants blocks per problem (level l at const_off +
+  // l CONST_FLOATS) for the penalties rho_ladder[l]; the level rises by one after every
+  // rho_every-th iteration that has not converged (rho_every = 0: a single rho)
+  const float *rho_ladder;
+  int rho_levels;
+  int rho_every;
 };
 
 // ---- compensated (double-float) helpers -----------------------------------

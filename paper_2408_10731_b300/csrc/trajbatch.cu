@@ -29,6 +29,13 @@ struct traj_batch {
   ProblemDev *d_problems = nullptr;
   double *d_T = nullptr, *d_start = nullptr, *d_goal = nullptr;
   float *d_constants = nullptr;
+  int const_levels = 1;                       // constants blocks allocated per problem
+  // penalty continuation (traj_set_rho_schedule): levels, growth per level, switch period
+  int rho_levels = 1, rho_every = 0;
+  double rho_growth = 1.0;
+  float *d_rho_ladder = nullptr;
+  std::vector<ProblemDev> recs;               // problem records as uploaded (nan flags cleared)
+  std::vector<int> pair_index;                // CSR offsets and first pair record per problem
   float *d_tables = nullptr;
   int table_floats = 0, table_cap = 0;
   int *d_horizons = nullptr, *d_hoffsets = nullptr;
@@ -94,7 +101,7 @@ template <class T> static cudaError_t dalloc(T **p, size_t n) {
 }
 
 static void free_all(traj_batch *b) {
-  void *ptrs[] = {b->d_problems, b->d_T, b->d_start, b->d_goal, b->d_constants, b->d_tables,
+  void *ptrs[] = {b->d_problems, b->d_T, b->d_start, b->d_goal, b->d_constants, b->d_rho_ladder, b->d_tables,
                   b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_index,
                   b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res, b->d_lam0, b->d_u0,
                   b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0, b->d_L, b->d_r,
@@ -181,6 +188,7 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
   const size_t P = c.max_problems, B = c.max_traj, N = c.max_obstacles, D = c.dim;
   if ((e = dalloc(&b->d_problems, P)) || (e = dalloc(&b->d_T, P)) || (e = dalloc(&b->d_start, P * D)) ||
       (e = dalloc(&b->d_goal, P * D)) || (e = dalloc(&b->d_constants, P * CONST_FLOATS)) ||
+      (e = dalloc(&b->d_rho_ladder, RHO_MAX_LEVELS)) ||
       (e = dalloc(&b->d_horizons, MAX_STEPS + 1)) || (e = dalloc(&b->d_hoffsets, MAX_STEPS + 1)) ||
       (e = dalloc(&b->d_obs, ((N + P) / 2 + 1) * pair_vec(c.dim))) ||
       (e = dalloc(&b->d_obs_stage, 3 * N * D)) || (e = dalloc(&b->d_obs_index, 2 * (P + 1))) || (e = dalloc(&b->d_traj_problem, B)) ||
@@ -261,6 +269,33 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
   return TRAJ_OK;
 }
 
+// Upload the problem records (constants offsets for the current number of penalty
+// levels), pack the staged obstacles into pair records (which also flags bad
+// obstacle data) and form the FP64 set-up of every penalty level; synchronises.
+static traj_status upload_problems(traj_batch *b) {
+  const int P = b->n_problems, D = b->cfg.dim, N = b->n_obs, L = b->rho_levels;
+  for (int p = 0; p < P; ++p) {
+    b->recs[p].const_off = p * CONST_FLOATS * L;
+    b->recs[p].nan_flag = 0;
+  }
+  std::vector<float> ladder(RHO_MAX_LEVELS, 0.f);
+  for (int l = 0; l < L; ++l) ladder[l] = (float)(b->cfg.rho * std::pow(b->rho_growth, (double)l));
+  const float *st_c = b->d_obs_stage, *st_a = st_c + (size_t)N * D, *st_v = st_a + (size_t)N * D;
+  const int *index = b->pair_index.data();
+  CK(b, cudaMemcpyAsync(b->d_problems, b->recs.data(), sizeof(ProblemDev) * P, cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_obs_index, index, sizeof(int) * 2 * (P + 1), cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemcpyAsync(b->d_rho_ladder, ladder.data(), sizeof(float) * RHO_MAX_LEVELS, cudaMemcpyHostToDevice, b->stream));
+  CK(b, launch_pack_obstacles(D, P, 2 * index[2 * P + 1], b->d_obs_index, b->d_obs_index + P + 1,
+                              st_c, st_a, st_v, b->d_obs, b->d_problems, b->stream));
+  for (int l = 0; l < L; ++l)
+    CK(b, launch_setup_problems(b->d_problems, P, b->d_T, b->d_start, b->d_goal, D,
+                                b->cfg.rho * std::pow(b->rho_growth, (double)l), b->cfg.w_smooth,
+                                b->cfg.w_track, b->cfg.cost_mode, b->max_np_used,
+                                b->d_constants + (size_t)l * CONST_FLOATS, b->stream));
+  CK(b, cudaStreamSynchronize(b->stream));
+  return TRAJ_OK;
+}
+
 traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *centers,
                                const float *semi_axes, const float *velocities) {
   if (!b) return TRAJ_EINVAL;
@@ -297,7 +332,6 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
     r.dt = (float)(T / (double)(r.n_p - 1));
     r.invT = (float)(1.0 / T);
     r.invT2 = (float)(1.0 / (T * T));
-    r.const_off = p * CONST_FLOATS;
     r.nan_flag = 0;
     recs[p] = r;
   }
@@ -307,17 +341,13 @@ traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *c
     CK(b, cudaMemcpyAsync(st_a, semi_axes, sizeof(float) * N * D, cudaMemcpyDefault, b->stream));
     CK(b, cudaMemcpyAsync(st_v, velocities, sizeof(float) * N * D, cudaMemcpyDefault, b->stream));
   }
-  CK(b, cudaMemcpyAsync(b->d_problems, recs.data(), sizeof(ProblemDev) * P, cudaMemcpyHostToDevice, b->stream));
-  CK(b, cudaMemcpyAsync(b->d_obs_index, index.data(), sizeof(int) * 2 * (P + 1), cudaMemcpyHostToDevice, b->stream));
-  CK(b, launch_pack_obstacles(D, P, 2 * index[2 * P + 1], b->d_obs_index, b->d_obs_index + P + 1,
-                              st_c, st_a, st_v, b->d_obs, b->d_problems, b->stream));
-  CK(b, launch_setup_problems(b->d_problems, P, b->d_T, b->d_start, b->d_goal, D, b->cfg.rho,
-                              b->cfg.w_smooth, b->cfg.w_track, b->cfg.cost_mode, b->max_np_used,
-                              b->d_constants, b->stream));
-  CK(b, cudaStreamSynchronize(b->stream));
+  b->recs = recs;
+  b->pair_index = index;
+  b->n_obs = N;
+  traj_status rs = upload_problems(b);
+  if (rs != TRAJ_OK) return rs;
   b->obs_offsets.assign(offsets, offsets + P + 1);
   b->tbl_off = tbl_host;
-  b->n_obs = N;
   b->have_obstacles = true;
   invalidate_graph(b);
   b->have_result = false;
@@ -419,6 +449,9 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   a.problems = b->d_problems;
   a.obstacles = b->d_obs;
   a.constants = b->d_constants;
+  a.rho_ladder = b->d_rho_ladder;
+  a.rho_levels = b->rho_levels;
+  a.rho_every = b->rho_levels > 1 ? b->rho_every : 0;
   a.tables = b->d_tables;
   a.table_floats_total = b->table_floats;
   a.traj_problem = b->d_traj_problem;
@@ -518,6 +551,31 @@ traj_status traj_get_state(traj_batch *b, float *lambda, float *u) {
   if (lambda) { CK(b, cudaMemcpyAsync(lambda, b->d_lam, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(lambda); }
   if (u) { CK(b, cudaMemcpyAsync(u, b->d_u, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(u); }
   if (host) CK(b, cudaStreamSynchronize(b->stream));
+  return TRAJ_OK;
+}
+
+traj_status traj_set_rho_schedule(traj_batch *b, int levels, double growth, int every) {
+  if (!b) return TRAJ_EINVAL;
+  if (levels < 1 || levels > RHO_MAX_LEVELS || !(growth > 0) || !std::isfinite(growth) ||
+      (levels > 1 && every < 1))
+    return fail(b, TRAJ_EINVAL, "levels in [1, 10], growth > 0, every >= 1 (when levels > 1)");
+  if (levels > b->const_levels) { // room for the constants of every level
+    float *c = nullptr;
+    const size_t n = (size_t)b->cfg.max_problems * CONST_FLOATS * levels;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&c), sizeof(float) * n);
+    if (e != cudaSuccess) return fail(b, e == cudaErrorMemoryAllocation ? TRAJ_ENOMEM : TRAJ_ECUDA,
+                                      std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    CK(b, cudaStreamSynchronize(b->stream));
+    cudaFree(b->d_constants);
+    b->d_constants = c;
+    b->const_levels = levels;
+  }
+  b->rho_levels = levels;
+  b->rho_growth = growth;
+  b->rho_every = levels > 1 ? every : 0;
+  invalidate_graph(b);
+  b->have_result = false;
+  if (b->have_obstacles) return upload_problems(b);
   return TRAJ_OK;
 }
 

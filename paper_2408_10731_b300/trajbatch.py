@@ -94,6 +94,7 @@ def load_library():
     lib.traj_get_trajectories.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.traj_get_state.argtypes = [_vp, _vp, _vp]
     lib.traj_set_state.argtypes = [_vp, _vp, _vp, _vp]
+    lib.traj_set_rho_schedule.argtypes = [_vp, _c_int, _c_double, _c_int]
     lib.traj_status_string.argtypes = [_c_int]
     lib.traj_status_string.restype = ctypes.c_char_p
     lib.traj_last_error.argtypes = [_vp]
@@ -110,7 +111,7 @@ def load_library():
                                        _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
                  "traj_set_obstacles", "traj_set_initial", "traj_solve", "traj_get_solve_stats",
-                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_measure_fp32_peak",
+                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_set_rho_schedule", "traj_measure_fp32_peak",
                  "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune",
                  "traj_sampler_step", "traj_gemm_bf16"):
         getattr(lib, name).restype = _c_int
@@ -279,6 +280,11 @@ class TrajBatch:
         self._check(self._lib.traj_get_state(self._h, _ptr(lam, np.float32)[0],
                                              _ptr(u, np.float32)[0]))
         return dict(lam=lam, u=u)
+
+    def set_rho_schedule(self, levels=1, growth=1.0, every=0):
+        """Penalty continuation: rho * growth^l for l < levels, one level up after every
+        `every`-th unconverged iteration (levels = 1: the fixed penalty)."""
+        self._check(self._lib.traj_set_rho_schedule(self._h, int(levels), float(growth), int(every)))
 
     def set_state(self, xi, lam, u):
         """Resume the next solves from an exported (xi, lambda, u) state."""

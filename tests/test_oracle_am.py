@@ -154,3 +154,36 @@ def test_early_stop_is_first_iteration_under_tolerance():
         expect = (under[0] + 1) if under.size else 300
         assert out["iters"][k] == expect
         np.testing.assert_array_equal(out["residual"][k], h[out["iters"][k]])
+
+
+def test_penalty_continuation_plumbing_and_fixed_point():
+    """Reading R10: a ladder with growth 1, or whose first switch lies past the last
+    iteration, is bitwise the fixed-penalty run; a real ladder changes the iterates;
+    and without obstacles the continued iteration still converges to the
+    equality-constrained QP optimum (a wrong K inverse or rho at a level would move
+    the fixed point)."""
+    b = scenes.config2(3, n_scenes=2, inits=3)
+    base = am.solve(b, 60, tol=-1.0, want_lambda=True)
+    same = am.solve(b, 60, tol=-1.0, want_lambda=True, rho_levels=10, rho_growth=1.0, rho_every=5)
+    np.testing.assert_array_equal(base["xi"], same["xi"])
+    np.testing.assert_array_equal(base["lam"], same["lam"])
+    late = am.solve(b, 60, tol=-1.0, rho_levels=10, rho_growth=2.0, rho_every=100)
+    np.testing.assert_array_equal(base["xi"], late["xi"])
+    switched = am.solve(b, 60, tol=-1.0, rho_levels=3, rho_growth=2.0, rho_every=20)
+    assert np.abs(switched["xi"] - base["xi"]).max() > 1e-6
+
+    n_p, T = 50, 5.0
+    start, goal = np.array([0.0, 1.0]), np.array([4.0, -2.0])
+    rng = np.random.default_rng(0)
+    xi0 = scenes.straight_line_coeffs(start, goal)[None] + rng.normal(0, 0.5, (3, 2, 11))
+    bq = _single_problem(start, goal, n_p, T, np.zeros((0, 2)), np.zeros((0, 2)), B=3, xi0=xi0,
+                         rho=0.05)
+    out = am.solve(bq, 6000, tol=-1.0, rho_levels=4, rho_growth=2.0, rho_every=1000)
+    P, Pd, Pdd = _tables(n_p, T)
+    Q = Pdd.T @ Pdd + P.T @ P
+    A = np.stack([P[0], Pd[0], Pdd[0], P[-1]])
+    tau = np.linspace(0, 1, n_p)
+    for a in range(2):
+        xdes = start[a] + (goal[a] - start[a]) * tau
+        ref = _qp_bruteforce(Q, -P.T @ xdes, A, np.array([start[a], 0, 0, goal[a]]))
+        np.testing.assert_allclose(out["xi"][:, a], np.broadcast_to(ref, (3, 11)), atol=1e-10)

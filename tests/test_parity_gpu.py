@@ -287,3 +287,54 @@ def test_resume_is_refused_in_projection_mode():
         assert e.value.code == -1
     finally:
         h.close()
+
+
+def test_penalty_continuation_parity():
+    """The penalty ladder (reading R10) against the oracle with the same ladder after
+    a fixed iteration count that crosses four switches (every 5 iterations, up to
+    16 rho), for one and two warps per trajectory; levels = 1 returns bitwise to the
+    fixed penalty. (The count is kept short: past ~30 iterations a few
+    trajectories of this nonconvex iteration amplify FP32 rounding beyond the
+    tolerance with or without the ladder.)"""
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.config2(4, n_scenes=8, inits=8)
+    sched = dict(rho_levels=5, rho_growth=2.0, rho_every=5)
+    o = am.solve(b, 25, tol=-1.0, **sched)
+    plain = gpu_solve(b, 25)
+    h = tb.from_batch(b)
+    try:
+        h.set_rho_schedule(5, 2.0, 5)
+        for shape in ((4, 0, 1), (8, 0, 2)):
+            h.set_launch_shape(*shape)
+            h.solve(25, tol=-1.0)
+            g = h.get_trajectories()
+            err = position_error(b, g["xi"], o["xi"])
+            assert err.max() <= POS_TOL, (shape, err.max())
+        h.set_rho_schedule(1)
+        h.set_launch_shape(4, 0, 1)
+        h.solve(25, tol=-1.0)
+        np.testing.assert_array_equal(h.get_trajectories()["xi"], plain["xi"])
+    finally:
+        h.close()
+
+
+def test_penalty_continuation_early_stop_and_tensor_core_form():
+    """With the stop test on, the ladder's trajectories stop where the oracle's do
+    (iteration counts within one, for decisions that are not at the tolerance's
+    edge); the tensor-core form follows the same ladder within its error bound."""
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.config2(5, n_scenes=8, inits=8)
+    o = am.solve(b, 300, tol=1e-3, rho_levels=6, rho_growth=1.5, rho_every=40)
+    for precision in ("fp32", "mixed"):
+        h = tb.from_batch(b, precision=precision)
+        try:
+            h.set_rho_schedule(6, 1.5, 40)
+            h.solve(300, tol=1e-3)
+            g = h.get_trajectories()
+        finally:
+            h.close()
+        same = np.abs(g["iters"] - o["iters"]) <= 1
+        assert same.mean() >= 0.9, (precision, same.mean())
+        if precision == "fp32":
+            agree = (g["status"] == 0) == (o["iters"] < 300)
+            assert agree.mean() >= 0.95
