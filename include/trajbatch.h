@@ -174,6 +174,15 @@ traj_status traj_get_accel_cost(traj_batch *b, float *cost);
  * coefficients of traj_get_trajectories this is the whole iteration state. */
 traj_status traj_get_state(traj_batch *b, float *lambda, float *u);
 
+/* Workspace bounds (Paper III, PRIEST: G xi <= tau with G = [-P; P] per axis and a
+ * slack s = max(0, tau - G xi)): lower <= p(t) <= upper at every grid point, per
+ * problem, host FP64 [n_problems][dim] each, finite with lower < upper; both NULL
+ * removes them. The rows join the obstacle group: their residual
+ * p - clamp(p, lower, upper) enters F^T r with the basis P and the obstacle
+ * residual column takes the maximum of both. Recomputes the set-up if obstacles
+ * are loaded; traj_set_problems clears the bounds. */
+traj_status traj_set_workspace(traj_batch *b, const double *lower, const double *upper);
+
 /* Penalty continuation (Paper I, Algorithm 1 line 9: the penalty grows while the
  * residuals stay above the threshold; Paper IV: the KKT inverse cached for ten
  * increasing penalties used in the later iterations): a ladder of `levels`

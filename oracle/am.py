@@ -35,7 +35,7 @@ def _lib(real: str = "f64"):
             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp, _dp,
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
             ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, _ip, _dp, _dp, _dp,
-            _ip, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+            _ip, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
         lib.orc_kkt_flat.restype = ctypes.c_int
         lib.orc_kkt_flat.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -108,13 +108,15 @@ def project_bound(w, bound, real="f64"):
 def solve(batch, max_iters: int, tol: float = -1.0, cost_mode: int = 0, w_smooth: float = 1.0,
           w_track: float = 1.0, iters_fixed=None, want_lambda: bool = False,
           want_hist: bool = False, n_threads: int = 0, real: str = "f64", xi0=None,
-          rho_levels: int = 1, rho_growth: float = 1.0, rho_every: int = 0):
+          rho_levels: int = 1, rho_growth: float = 1.0, rho_every: int = 0,
+          box_lo=None, box_hi=None):
     """Run Algorithm 2 on every trajectory of a scenes.Batch.
 
     Returns dict(xi [B,dim,11], residual [B,3], iters [B], lam?, hist?).
     tol < 0 disables the early stop; iters_fixed[B] runs exactly that many
     iterations per trajectory (no stop test). rho_levels / rho_growth / rho_every:
     the penalty continuation of reading R10 (rho_levels = 1: a fixed rho).
+    box_lo / box_hi [n_problems][dim]: workspace bounds of reading R11 (None: none).
     """
     lib = _lib(real)
     dim = batch.dim
@@ -141,7 +143,9 @@ def solve(batch, max_iters: int, tol: float = -1.0, cost_mode: int = 0, w_smooth
             _p(v), _p(st), _p(gl), float(batch.vmax), float(batch.amax), float(batch.rho),
             float(w_smooth), float(w_track), int(cost_mode), idx.size, _p(x0), int(max_iters),
             float(tol), _p(fx, _ip), _p(xo), _p(lo), _p(ro), _p(io, _ip), _p(ho),
-            int(n_threads), int(rho_levels), float(rho_growth), int(rho_every))
+            int(n_threads), int(rho_levels), float(rho_growth), int(rho_every),
+            _p(None if box_lo is None else np.ascontiguousarray(box_lo[p], np.float64)),
+            _p(None if box_hi is None else np.ascontiguousarray(box_hi[p], np.float64)))
         if rc:
             raise RuntimeError(f"oracle solve failed for problem {p}: {rc}")
         xi[idx] = xo; res[idx] = ro; its[idx] = io

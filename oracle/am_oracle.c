@@ -37,6 +37,10 @@
  *     (PRIEST eq. eq1_multiagent_1_priest with b0 = (start, 0, 0), bf = goal).
  *  R9 residuals are L-infinity over the grid points: max_{j,t} ||p - g_j||,
  *     max_t ||pdot - g_v||, max_t ||pddot - g_a||.
+ *  R11 workspace bounds (PRIEST eqs. bound_con, lagrange): G = [-P; P] per axis,
+ *     tau = [-lo; hi], slack s = max(0, tau - G xi) from the current iterate, and
+ *     the rows' target e = tau - s; their residual norms join the obstacle group's
+ *     maximum (column 0).
  *  R10 penalty continuation (Paper I, Algorithm 1 line 9; Paper IV's ten cached
  *     KKT inverses): penalties rho growth^l, l = 0 .. levels-1, each with its own
  *     KKT inverse; after iteration k >= 1, if the trajectory has not stopped and k
@@ -152,6 +156,7 @@ typedef struct {
   const double *start, *goal;                      /* [dim] */
   double vmax, amax, rho, w_smooth, w_track;
   int cost_mode;   /* 0: smoothness + tracking (eq. Q_matrix); 1: projection (eq. matrix_vec) */
+  const double *box_lo, *box_hi; /* [dim] workspace bounds (reading R11) or NULL */
   int rho_levels;  /* penalty continuation (reading R10); 1 or 0: a fixed rho */
   double rho_growth;
   int rho_every;
@@ -160,13 +165,19 @@ typedef struct {
 /* Dense F for one axis: (n_o + 2) n_p rows x 11 (F of Paper II without the
  * heading rows; F~ of eq. f_e per axis). Row j*n_p + t is P[t] (obstacle j),
  * row n_o*n_p + t is Pdot[t], row (n_o+1)*n_p + t is Pddot[t]. */
-static void build_F(int n_p, int n_o, const double *P, const double *Pd, const double *Pdd,
-                    double *F) {
+static void build_F(int n_p, int n_o, int box, const double *P, const double *Pd,
+                    const double *Pdd, double *F) {
   for (int j = 0; j < n_o; ++j)
     for (int t = 0; t < n_p; ++t)
       memcpy(&F[((size_t)j * n_p + t) * NC], &P[t * NC], sizeof(double) * NC);
   memcpy(&F[(size_t)n_o * n_p * NC], Pd, sizeof(double) * n_p * NC);
   memcpy(&F[(size_t)(n_o + 1) * n_p * NC], Pdd, sizeof(double) * n_p * NC);
+  if (box) /* workspace rows: -P (lower bounds), then P (upper bounds) (reading R11) */
+    for (int t = 0; t < n_p; ++t)
+      for (int i = 0; i < NC; ++i) {
+        F[((size_t)(n_o + 2) * n_p + t) * NC + i] = -P[t * NC + i];
+        F[((size_t)(n_o + 3) * n_p + t) * NC + i] = P[t * NC + i];
+      }
 }
 
 /* KKT matrix K = [[Q + rho F^T F, A^T], [A, 0]] (eq. over_2 with eq.
@@ -174,12 +185,12 @@ static void build_F(int n_p, int n_o, const double *P, const double *Pd, const d
  * same for every axis (block-diagonal D-bar, eq. simple), so one 15x15 K
  * serves all axes. Writes K (15x15) and its inverse; returns orc_invert's code. */
 int orc_kkt(const orc_problem *pr, double *K, double *Kinv) {
-  const int n_p = pr->n_p, n_o = pr->n_o;
-  const size_t rows = (size_t)(n_o + 2) * n_p;
+  const int n_p = pr->n_p, n_o = pr->n_o, box = pr->box_lo != NULL;
+  const size_t rows = (size_t)(n_o + 2 + 2 * box) * n_p;
   double *P = malloc(sizeof(double) * n_p * NC), *Pd = malloc(sizeof(double) * n_p * NC),
          *Pdd = malloc(sizeof(double) * n_p * NC), *F = malloc(sizeof(double) * rows * NC);
   orc_bernstein(n_p, pr->T, P, Pd, Pdd);
-  build_F(n_p, n_o, P, Pd, Pdd, F);
+  build_F(n_p, n_o, box, P, Pd, Pdd, F);
   memset(K, 0, sizeof(double) * NK * NK);
   for (int a = 0; a < NC; ++a)
     for (int b = 0; b < NC; ++b) {
@@ -274,16 +285,16 @@ void orc_project_bound(int dim, const REAL *w, REAL bound, REAL *g) {
 int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_iters,
                  double tol, const int *iters_fixed, double *xi_out, double *lam_out,
                  double *residual_out, int *iters_out, double *hist, int n_threads) {
-  const int dim = pr->dim, n_p = pr->n_p, n_o = pr->n_o;
+  const int dim = pr->dim, n_p = pr->n_p, n_o = pr->n_o, box = pr->box_lo != NULL;
   if (dim < 2 || dim > 3 || n_p < 2 || n_o < 0 || max_iters < 0) return -3;
-  const size_t rows = (size_t)(n_o + 2) * n_p;
+  const size_t rows = (size_t)(n_o + 2 + 2 * box) * n_p;
   double *P = malloc(sizeof(double) * n_p * NC), *Pd = malloc(sizeof(double) * n_p * NC),
          *Pdd = malloc(sizeof(double) * n_p * NC), *F = malloc(sizeof(double) * rows * NC);
   const int levels = pr->rho_levels > 1 ? pr->rho_levels : 1;
   if (levels > 16) { free(P); free(Pd); free(Pdd); free(F); return -3; }
   double K[NK * NK], Kinv[16][NK * NK], rho_l[16];
   orc_bernstein(n_p, pr->T, P, Pd, Pdd);
-  build_F(n_p, n_o, P, Pd, Pdd, F);
+  build_F(n_p, n_o, box, P, Pd, Pdd, F);
   for (int l = 0; l < levels; ++l) { /* one KKT inverse per penalty level (reading R10) */
     orc_problem pl = *pr;
     pl.rho = pr->rho * pow(pr->rho_growth, (double)l);
@@ -399,6 +410,23 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
           if (nrm > res[1 + grp]) res[1 + grp] = nrm;
         }
       }
+      /* workspace rows (reading R11): slack s = max(0, tau - G xi), target tau - s */
+      if (box)
+        for (int t = 0; t < n_p; ++t) {
+          REAL nrm = 0;
+          for (int side = 0; side < 2; ++side)
+            for (int a = 0; a < dim; ++a) {
+              size_t r = (size_t)(n_o + 2 + side) * n_p + t;
+              REAL tau = side == 0 ? -(REAL)pr->box_lo[a] : (REAL)pr->box_hi[a];
+              REAL sl = tau - Fx[a * rows + r];
+              if (sl < 0) sl = 0;
+              g[a * rows + r] = tau - sl;
+              REAL e = Fx[a * rows + r] - g[a * rows + r];
+              nrm += e * e;
+            }
+          nrm = R_SQRT(nrm);
+          if (nrm > res[0]) res[0] = nrm;
+        }
       /* Line 6 -- multiplier update lambda <- lambda - rho F^T (F xi - g) (reading R2).
        * At k = 0 (initialisation) lambda0 = 0 and only g0 is formed (reading R3). */
       if (k > 0)
@@ -441,10 +469,10 @@ int orc_am_solve_flat(int dim, int n_p, double T, int n_o, const double *centers
                       const double *xi0, int max_iters, double tol, const int *iters_fixed,
                       double *xi_out, double *lam_out, double *residual_out, int *iters_out,
                       double *hist, int n_threads, int rho_levels, double rho_growth,
-                      int rho_every) {
+                      int rho_every, const double *box_lo, const double *box_hi) {
   orc_problem pr = {dim, n_p, T, n_o, centers, semi_axes, velocities, start, goal,
-                    vmax, amax, rho, w_smooth, w_track, cost_mode, rho_levels, rho_growth,
-                    rho_every};
+                    vmax, amax, rho, w_smooth, w_track, cost_mode, box_lo, box_hi, rho_levels,
+                    rho_growth, rho_every};
   return orc_am_solve(&pr, n_traj, xi0, max_iters, tol, iters_fixed, xi_out, lam_out,
                       residual_out, iters_out, hist, n_threads);
 }
@@ -452,7 +480,7 @@ int orc_am_solve_flat(int dim, int n_p, double T, int n_o, const double *centers
 int orc_kkt_flat(int dim, int n_p, double T, int n_o, double rho, double w_smooth,
                  double w_track, int cost_mode, double *K, double *Kinv) {
   orc_problem pr = {dim, n_p, T, n_o, NULL, NULL, NULL, NULL, NULL,
-                    0, 0, rho, w_smooth, w_track, cost_mode, 1, 1.0, 0};
+                    0, 0, rho, w_smooth, w_track, cost_mode, NULL, NULL, 1, 1.0, 0};
   return orc_kkt(&pr, K, Kinv);
 }
 

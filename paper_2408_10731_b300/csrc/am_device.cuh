@@ -358,6 +358,32 @@ __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const 
   }
 }
 
+// Workspace bounds (PRIEST's G xi <= tau, G = [-P; P] per axis, slack s = max(0, tau -
+// G xi)): the residual rows are max(lo - p, 0) and max(p - hi, 0), i.e. the point's
+// offset from the box, p - clamp(p, lo, hi), which joins the obstacle group's sum
+// (P^T G^T r has the basis P) and its maximum norm.
+template <int DIM, int MAXNT>
+__device__ __forceinline__ void box_residuals(const ProblemDev *pr, const float (&pos)[MAXNT][DIM],
+                                              int t0, int ts, int n_p, int nt,
+                                              float (&acc)[MAXNT][DIM], float &mo) {
+  float lo[DIM], hi[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { lo[a] = pr->lo[a]; hi[a] = pr->hi[a]; }
+#pragma unroll
+  for (int m = 0; m < MAXNT; ++m) {
+    if (m < nt && t0 + ts * m < n_p) {
+      float n2 = 0.f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const float r = pos[m][a] - fminf(fmaxf(pos[m][a], lo[a]), hi[a]);
+        acc[m][a] -= r;
+        n2 = fmaf(r, r, n2);
+      }
+      mo = fmaxf(mo, n2);
+    }
+  }
+}
+
 // ---- evaluate / project / contract ---------------------------------------------------
 // Positions p(t) = P xi at the lane's timesteps t = t0 + ts m (padding slots get a far
 // sentinel, which is outside every obstacle).
@@ -413,15 +439,17 @@ __device__ __forceinline__ void bound_residuals(const float2 (&xp)[DIM][6], cons
 template <int DIM, int MAXNT>
 __device__ __forceinline__ void project_contract(
     const float2 (&xp)[DIM][6], const float *tP, const float *tD, const float *tA,
-    const float4 *obs, int n_o, int n_p, int nt, float dt, float invT, float invT2, float vmax,
-    float amax, int t0, float2 (&up)[DIM][6], float &mo, float &mv, float &ma, int ts = 32) {
+    const float4 *obs, const ProblemDev *pr, int n_p, int nt, float dt, float invT, float invT2,
+    float vmax, float amax, int t0, float2 (&up)[DIM][6], float &mo, float &mv, float &ma,
+    int ts = 32) {
   float pos[MAXNT][DIM], acc[MAXNT][DIM], tm[MAXNT];
   eval_positions<DIM, MAXNT>(xp, tP, n_p, nt, dt, t0, ts, pos, tm);
 #pragma unroll
   for (int m = 0; m < MAXNT; ++m)
 #pragma unroll
     for (int a = 0; a < DIM; ++a) acc[m][a] = 0.f;
-  pair_loop<DIM, MAXNT>(pos, tm, obs, n_o, acc, mo);
+  pair_loop<DIM, MAXNT>(pos, tm, obs, pr->n_o, acc, mo);
+  if (pr->box) box_residuals<DIM, MAXNT>(pr, pos, t0, ts, n_p, nt, acc, mo);
 #pragma unroll
   for (int a = 0; a < DIM; ++a)
 #pragma unroll
@@ -450,16 +478,17 @@ __device__ __forceinline__ void project_contract(
 template <int DIM, int NT>
 __device__ __forceinline__ void project_only(
     const float2 (&xp)[DIM][6], const float *tP, const float *tD, const float *tA,
-    const float4 *obs, int n_o, int n_p, float dt, float invT, float invT2, float vmax, float amax,
-    int t0, float (&Ro)[NT][DIM], float (&Rv)[NT][DIM], float (&Ra)[NT][DIM], float &mo,
-    float &mv, float &ma, int ts = 32) {
+    const float4 *obs, const ProblemDev *pr, int n_p, float dt, float invT, float invT2,
+    float vmax, float amax, int t0, float (&Ro)[NT][DIM], float (&Rv)[NT][DIM],
+    float (&Ra)[NT][DIM], float &mo, float &mv, float &ma, int ts = 32) {
   float pos[NT][DIM], acc[NT][DIM], tm[NT];
   eval_positions<DIM, NT>(xp, tP, n_p, NT, dt, t0, ts, pos, tm);
 #pragma unroll
   for (int m = 0; m < NT; ++m)
 #pragma unroll
     for (int a = 0; a < DIM; ++a) acc[m][a] = 0.f;
-  pair_loop<DIM, NT>(pos, tm, obs, n_o, acc, mo);
+  pair_loop<DIM, NT>(pos, tm, obs, pr->n_o, acc, mo);
+  if (pr->box) box_residuals<DIM, NT>(pr, pos, t0, ts, n_p, NT, acc, mo);
   mv = 0.f; ma = 0.f;
 #pragma unroll
   for (int m = 0; m < NT; ++m) {

@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
     item = __shfl_sync(FULL, item, 0);
     if (item >= A.n_traj) break;
     const int b = A.order[item];
-    const ProblemDev pr = A.problems[A.traj_problem[b]];
+    const ProblemDev *prp = A.problems + A.traj_problem[b];
+    const ProblemDev pr = *prp;
     const float *Cb = A.constants + pr.const_off, *C = Cb;
     const float4 *obs = A.obstacles + (size_t)pr.pair_off * pair_vec(DIM);
     const float *x0 = A.xi0 + (size_t)b * DIM * NC;
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
       float2 xp[DIM][6];
       broadcast_pairs<DIM>(xo, xo2, xp);
       float Ro[NT][DIM], Rv[NT][DIM], Ra[NT][DIM];
-      project_only<DIM, NT>(xp, tP, tD, tA, obs, pr.n_o, n_p, pr.dt, pr.invT, pr.invT2, A.vmax,
+      project_only<DIM, NT>(xp, tP, tD, tA, obs, prp, n_p, pr.dt, pr.invT, pr.invT2, A.vmax,
                             A.amax, lane, Ro, Rv, Ra, mo, mv, ma);
       // this warp's B rows: axis a, k = g n_p + t
 #pragma unroll
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
           qp_step<DIM>(C, lane, rho, hq_hi, hq_lo, hq2_hi, hq2_lo, lam, lam2, uo, uo2, xo, xo2);
           ++k;
           broadcast_pairs<DIM>(xo, xo2, xp);
-          project_contract<DIM, NT>(xp, tP, tD, tA, obs, pr.n_o, n_p, NT, pr.dt, pr.invT,
+          project_contract<DIM, NT>(xp, tP, tD, tA, obs, prp, n_p, NT, pr.dt, pr.invT,
                                     pr.invT2, A.vmax, A.amax, lane, up, mo, mv, ma);
           scatter_pairs<DIM>(up, lane, uo, uo2);
           mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);

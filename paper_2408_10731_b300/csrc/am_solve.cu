@@ -40,7 +40,7 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
                                        unsigned long long deadline) {
   const int p = A.traj_problem[b];
   const ProblemDev pr = A.problems[p];
-  const int n_p = pr.n_p, n_o = pr.n_o;
+  const int n_p = pr.n_p;
   const int nt = (n_p + 31) >> 5;
   const float *Cb = A.constants + pr.const_off, *C = Cb; // constants of the penalty level
   const float *tP = stab + pr.tbl_off;
@@ -89,8 +89,8 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
     float2 xp[DIM][6];
     broadcast_pairs<DIM>(xo, xo2, xp);
     float2 up[DIM][6];
-    project_contract<DIM, MAXNT>(xp, tP, tD, tA, obs, n_o, n_p, nt, pr.dt, pr.invT, pr.invT2,
-                                 A.vmax, A.amax, lane, up, mo, mv, ma);
+    project_contract<DIM, MAXNT>(xp, tP, tD, tA, obs, A.problems + p, n_p, nt, pr.dt, pr.invT,
+                                 pr.invT2, A.vmax, A.amax, lane, up, mo, mv, ma);
     scatter_pairs<DIM>(up, lane, uo, uo2);
     mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
     if (k > 0) { // Line 6: multiplier update (lambda0 = 0 at the initial projection)
@@ -150,7 +150,7 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
                                         unsigned long long deadline) {
   const int p = A.traj_problem[b];
   const ProblemDev pr = A.problems[p];
-  const int n_p = pr.n_p, n_o = pr.n_o;
+  const int n_p = pr.n_p;
   const float *Cb = A.constants + pr.const_off, *C = Cb;
   const float *tP = stab + pr.tbl_off;
   const float *tD = tP + n_p * ROW;
@@ -193,8 +193,8 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
     float2 xp[DIM][6];
     broadcast_pairs<DIM>(xo, xo2, xp);
     float2 up[DIM][6];
-    project_contract<DIM, NT>(xp, tP, tD, tA, obs, n_o, n_p, NT, pr.dt, pr.invT, pr.invT2,
-                              A.vmax, A.amax, W * lane + r, up, mo, mv, ma, 32 * W);
+    project_contract<DIM, NT>(xp, tP, tD, tA, obs, A.problems + p, n_p, NT, pr.dt, pr.invT,
+                              pr.invT2, A.vmax, A.amax, W * lane + r, up, mo, mv, ma, 32 * W);
     float part = 0.f, part2 = 0.f;
     scatter_pairs<DIM>(up, lane, part, part2);
     mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);

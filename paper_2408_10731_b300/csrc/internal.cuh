@@ -24,7 +24,8 @@ struct ProblemDev {
   float invT2;    // 1 / T^2 (Pddot = d2B/dtau2 * invT2)
   int const_off;  // float offset of the problem's constants block
   int nan_flag;   // nonzero if the problem's obstacle data is not finite / not positive
-  int pad[7];
+  int box;        // 1: workspace bounds lo <= p(t) <= hi (PRIEST's G xi <= tau with slack)
+  float lo[3], hi[3];
 };
 
 // Constants block per problem (floats), every row padded to ROW:

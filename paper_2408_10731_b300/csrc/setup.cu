@@ -96,7 +96,7 @@ __global__ void k_setup_problems(ProblemDev *problems, const double *Tarr, const
         aa += Pdd[t * NC + a] * Pdd[t * NC + b];
       }
       Q[e] = cost_mode == 0 ? (w_s * aa + w_t * pp) : (a == b ? 1.0 : 0.0);
-      M[e] = (double)n_o * pp + dd + aa;
+      M[e] = (double)(n_o + 2 * pr.box) * pp + dd + aa; // G = [-P; P] per axis adds 2 P^T P
     } else {
       int k = e - NC * NC, ax = k / NC, i = k % NC;
       double s = 0;

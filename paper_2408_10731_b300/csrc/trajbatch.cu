@@ -35,6 +35,7 @@ struct traj_batch {
   double rho_growth = 1.0;
   float *d_rho_ladder = nullptr;
   std::vector<ProblemDev> recs;               // problem records as uploaded (nan flags cleared)
+  std::vector<double> box_lo, box_hi;         // workspace bounds [P][dim] (empty: none)
   std::vector<int> pair_index;                // CSR offsets and first pair record per problem
   float *d_tables = nullptr;
   int table_floats = 0, table_cap = 0;
@@ -264,6 +265,8 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
   b->have_problems = true;
   invalidate_graph(b);
   b->have_obstacles = false;
+  b->box_lo.clear();
+  b->box_hi.clear();
   b->have_result = false;
   b->err.clear();
   return TRAJ_OK;
@@ -274,9 +277,15 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
 // obstacle data) and form the FP64 set-up of every penalty level; synchronises.
 static traj_status upload_problems(traj_batch *b) {
   const int P = b->n_problems, D = b->cfg.dim, N = b->n_obs, L = b->rho_levels;
+  const bool box = !b->box_lo.empty();
   for (int p = 0; p < P; ++p) {
     b->recs[p].const_off = p * CONST_FLOATS * L;
     b->recs[p].nan_flag = 0;
+    b->recs[p].box = box ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+      b->recs[p].lo[a] = box && a < D ? (float)b->box_lo[(size_t)p * D + a] : 0.f;
+      b->recs[p].hi[a] = box && a < D ? (float)b->box_hi[(size_t)p * D + a] : 0.f;
+    }
   }
   std::vector<float> ladder(RHO_MAX_LEVELS, 0.f);
   for (int l = 0; l < L; ++l) ladder[l] = (float)(b->cfg.rho * std::pow(b->rho_growth, (double)l));
@@ -551,6 +560,27 @@ traj_status traj_get_state(traj_batch *b, float *lambda, float *u) {
   if (lambda) { CK(b, cudaMemcpyAsync(lambda, b->d_lam, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(lambda); }
   if (u) { CK(b, cudaMemcpyAsync(u, b->d_u, sizeof(float) * n, cudaMemcpyDefault, b->stream)); host |= is_host_ptr(u); }
   if (host) CK(b, cudaStreamSynchronize(b->stream));
+  return TRAJ_OK;
+}
+
+traj_status traj_set_workspace(traj_batch *b, const double *lower, const double *upper) {
+  if (!b) return TRAJ_EINVAL;
+  if (!b->have_problems) return fail(b, TRAJ_ESTATE, "traj_set_problems must come first");
+  if ((lower == nullptr) != (upper == nullptr)) return fail(b, TRAJ_EINVAL, "give both bounds or neither");
+  const int P = b->n_problems, D = b->cfg.dim;
+  if (lower) {
+    for (int k = 0; k < P * D; ++k)
+      if (!std::isfinite(lower[k]) || !std::isfinite(upper[k]) || !(lower[k] < upper[k]))
+        return fail(b, TRAJ_EINVAL, "workspace bounds must be finite with lower < upper");
+    b->box_lo.assign(lower, lower + (size_t)P * D);
+    b->box_hi.assign(upper, upper + (size_t)P * D);
+  } else {
+    b->box_lo.clear();
+    b->box_hi.clear();
+  }
+  invalidate_graph(b);
+  b->have_result = false;
+  if (b->have_obstacles) return upload_problems(b);
   return TRAJ_OK;
 }
 

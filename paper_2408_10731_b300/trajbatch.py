@@ -95,6 +95,7 @@ def load_library():
     lib.traj_get_state.argtypes = [_vp, _vp, _vp]
     lib.traj_set_state.argtypes = [_vp, _vp, _vp, _vp]
     lib.traj_set_rho_schedule.argtypes = [_vp, _c_int, _c_double, _c_int]
+    lib.traj_set_workspace.argtypes = [_vp, _vp, _vp]
     lib.traj_status_string.argtypes = [_c_int]
     lib.traj_status_string.restype = ctypes.c_char_p
     lib.traj_last_error.argtypes = [_vp]
@@ -111,7 +112,7 @@ def load_library():
                                        _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
                  "traj_set_obstacles", "traj_set_initial", "traj_solve", "traj_get_solve_stats",
-                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_set_rho_schedule", "traj_measure_fp32_peak",
+                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_set_rho_schedule", "traj_set_workspace", "traj_measure_fp32_peak",
                  "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune",
                  "traj_sampler_step", "traj_gemm_bf16"):
         getattr(lib, name).restype = _c_int
@@ -280,6 +281,16 @@ class TrajBatch:
         self._check(self._lib.traj_get_state(self._h, _ptr(lam, np.float32)[0],
                                              _ptr(u, np.float32)[0]))
         return dict(lam=lam, u=u)
+
+    def set_workspace(self, lower=None, upper=None):
+        """Workspace bounds lower <= p(t) <= upper per problem ([n_problems][dim]); None
+        removes them."""
+        if lower is None and upper is None:
+            self._check(self._lib.traj_set_workspace(self._h, None, None))
+            return
+        lp, kl = _ptr(np.asarray(lower, np.float64), np.float64)
+        hp, kh = _ptr(np.asarray(upper, np.float64), np.float64)
+        self._check(self._lib.traj_set_workspace(self._h, lp, hp))
 
     def set_rho_schedule(self, levels=1, growth=1.0, every=0):
         """Penalty continuation: rho * growth^l for l < levels, one level up after every

@@ -187,3 +187,47 @@ def test_penalty_continuation_plumbing_and_fixed_point():
         xdes = start[a] + (goal[a] - start[a]) * tau
         ref = _qp_bruteforce(Q, -P.T @ xdes, A, np.array([start[a], 0, 0, goal[a]]))
         np.testing.assert_allclose(out["xi"][:, a], np.broadcast_to(ref, (3, 11)), atol=1e-10)
+
+
+def test_workspace_bounds_inactive_fixed_point_and_active_feasibility():
+    """Reading R11 (PRIEST's G xi <= tau with slack, G = [-P; P] per axis).
+    Inactive box: the obstacle-free fixed point is still the equality-constrained QP
+    optimum; this fails if G^T G = 2 P^T P were missing from the KKT matrix while the
+    rows enter the multiplier update (or the reverse). Active box (projection mode,
+    samples leaving it): the iteration converges to a point whose grid positions
+    satisfy the bounds, with some of them on a bound, and the rows' residual folds
+    into the obstacle column."""
+    n_p, T = 50, 5.0
+    start, goal = np.array([0.0, 1.0]), np.array([4.0, -2.0])
+    rng = np.random.default_rng(0)
+    xi0 = scenes.straight_line_coeffs(start, goal)[None] + rng.normal(0, 0.5, (3, 2, 11))
+    b = _single_problem(start, goal, n_p, T, np.zeros((0, 2)), np.zeros((0, 2)), B=3, xi0=xi0,
+                        rho=0.05)
+    big_lo, big_hi = np.array([[-50.0, -50.0]]), np.array([[50.0, 50.0]])
+    out = am.solve(b, 6000, tol=-1.0, box_lo=big_lo, box_hi=big_hi)
+    P, Pd, Pdd = _tables(n_p, T)
+    Q = Pdd.T @ Pdd + P.T @ P
+    A = np.stack([P[0], Pd[0], Pdd[0], P[-1]])
+    tau = np.linspace(0, 1, n_p)
+    for a in range(2):
+        xdes = start[a] + (goal[a] - start[a]) * tau
+        ref = _qp_bruteforce(Q, -P.T @ xdes, A, np.array([start[a], 0, 0, goal[a]]))
+        np.testing.assert_allclose(out["xi"][:, a], np.broadcast_to(ref, (3, 11)), atol=1e-10)
+
+    n_p, T = 40, 4.0
+    start, goal = np.array([0.0, 0.0]), np.array([3.0, 1.0])
+    lo, hi = np.array([-0.5, -0.3]), np.array([3.2, 1.2])
+    xi0 = scenes.straight_line_coeffs(start, goal)[None] + np.random.default_rng(7).normal(0, 1.0, (2, 2, 11))
+    b = _single_problem(start, goal, n_p, T, np.zeros((0, 2)), np.zeros((0, 2)), B=2, xi0=xi0,
+                        rho=0.05)
+    h = am.solve(b, 3000, tol=-1.0, cost_mode=1, box_lo=lo[None], box_hi=hi[None], want_hist=True)
+    free = am.solve(b, 3000, tol=-1.0, cost_mode=1)
+    P, _, _ = _tables(n_p, T)
+    pos = np.einsum("ti,kai->kta", P, h["xi"])
+    assert np.all(pos >= lo - 1e-9) and np.all(pos <= hi + 1e-9)
+    on_bound = np.minimum(np.abs(pos - lo), np.abs(pos - hi)).min()
+    assert on_bound < 1e-9
+    assert np.all(h["residual"] < 1e-12)
+    pos_free = np.einsum("ti,kai->kta", P, free["xi"])
+    assert np.any(pos_free > hi + 1e-3) or np.any(pos_free < lo - 1e-3)  # the box mattered
+    assert h["hist"][:, 0, 0].max() > 1e-3  # the initial projection saw the violation

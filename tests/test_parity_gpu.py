@@ -338,3 +338,44 @@ def test_penalty_continuation_early_stop_and_tensor_core_form():
         if precision == "fp32":
             agree = (g["status"] == 0) == (o["iters"] < 300)
             assert agree.mean() >= 0.95
+
+
+def test_workspace_bounds_parity():
+    """Workspace bounds (reading R11) against the oracle: 2D smoothness/tracking with a
+    box that cuts through the initialisations (one and two warps per trajectory), and
+    3D projection mode with the sampler scene's 20 x 20 x 5 m workspace; removing the
+    bounds returns bitwise to the unbounded solve."""
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.config2(6, n_scenes=8, inits=8)
+    lo = np.tile([-0.2, -0.2], (b.n_problems, 1)); hi = np.tile([7.5, 7.0], (b.n_problems, 1))
+    o = am.solve(b, 20, tol=-1.0, box_lo=lo, box_hi=hi)
+    free = gpu_solve(b, 20)
+    h = tb.from_batch(b)
+    try:
+        h.set_workspace(lo, hi)
+        for shape in ((4, 0, 1), (8, 0, 2)):
+            h.set_launch_shape(*shape)
+            h.solve(20, tol=-1.0)
+            g = h.get_trajectories()
+            assert position_error(b, g["xi"], o["xi"]).max() <= POS_TOL, shape
+            np.testing.assert_allclose(g["residual"][:, 0], o["residual"][:, 0], atol=1e-4)
+        assert np.abs(g["xi"] - free["xi"]).max() > 1e-3  # the bounds changed the solve
+        h.set_workspace(None, None)
+        h.set_launch_shape(4, 0, 1)
+        h.solve(20, tol=-1.0)
+        np.testing.assert_array_equal(h.get_trajectories()["xi"], free["xi"])
+    finally:
+        h.close()
+
+    c3 = scenes.config3(1, n_traj=24)
+    b3 = c3["batch"]
+    lo3 = np.array([[0.0, 0.0, 0.0]]); hi3 = np.array([[20.0, 20.0, 5.0]])
+    o3 = am.solve(b3, 20, tol=-1.0, cost_mode=1, box_lo=lo3, box_hi=hi3)
+    h = tb.from_batch(b3, cost_mode="project")
+    try:
+        h.set_workspace(lo3, hi3)
+        h.solve(20, tol=-1.0)
+        g3 = h.get_trajectories()
+    finally:
+        h.close()
+    assert position_error(b3, g3["xi"], o3["xi"]).max() <= POS_TOL
