@@ -47,8 +47,8 @@ KERNEL_SOURCES = {
     "k_am_mixed": ("am_mixed.cu", "am_device.cuh", "internal.cuh", "tcgen05.cuh"),
 }
 MEASURED_TRAFFIC = {
-    "k_am_fp32": (859392, "fa231ac34a91b6d6"),
-    "k_am_mixed": (728320, "fbcc66079630c1a8"),
+    "k_am_fp32": (745216, "d0995091f548b9da"),
+    "k_am_mixed": (731136, "edded2ea9273cf76"),
 }
 
 

@@ -272,7 +272,12 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
  * n_inner projection iterations (Algorithm 2 order with Q = I, q = -sample,
  * eq. matrix_vec); r = the worst of the three L-infinity residuals; the
  * n_proj lowest r form the ConstraintEliteSet, the n_elite lowest
- * c_aug = sum_t ||p''(t)||^2 + w_res * r among them the EliteSet; weights
+ * c_aug = c_1 + w_res * r among them the EliteSet, where
+ * c_1 = sum_t (||p''(t)||^2 + w_curv c_kappa(t) + w_path c_p(t)) on the grid:
+ * c_kappa = ||p' x p''||^2 / ||p'||^6 is the squared curvature (the planar
+ * form of the BARN cost, Section 5; taken as 0 where ||p'|| < 1e-3, which covers the rest start) and c_p the
+ * distance of p(t) from the segment between problem 0's start and goal (a cost
+ * with no closed form: it needs the projection onto the path); weights
  * exp(-(c_aug - min c_aug) / gamma); mean and covariance move by sigma_lr
  * toward the weighted elite mean/covariance (eqs. update_mean,
  * update_covariance; the covariance about the new mean). */
@@ -280,7 +285,11 @@ typedef struct traj_sampler_config {
   int n_inner, n_proj, n_elite;
   float gamma, sigma_lr, eps, w_res;
   unsigned long long seed; /* Philox4x32-10 key (counter = sample, iteration, pair, 0) */
+  float w_curv, w_path;    /* >= 0; 0 and 0 give the acceleration-only cost */
 } traj_sampler_config;
+
+/* Largest number of sampling distributions of traj_sampler_step_multi. */
+#define TRAJ_SAMPLER_MAX_DIST 64
 
 /* Optional device copies of one step's intermediates (each nullable):
  * samples and projected [n_traj][dim*11], residual and cost_aug [n_traj],
@@ -300,6 +309,21 @@ typedef struct traj_sampler_trace {
 traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *cfg, int iteration,
                               float *mu, float *sigma, const float *z, float *best,
                               const traj_sampler_trace *trace);
+
+/* Decentralised sampler (D-PRIEST, Section 5): n_dist distributions refined in
+ * parallel. The n_traj samples split into n_dist contiguous groups of
+ * Bg = n_traj / n_dist (n_dist must divide n_traj, 1 <= n_dist <=
+ * TRAJ_SAMPLER_MAX_DIST, Bg <= 8192); group g draws from N(mu_g, Sigma_g), and
+ * its ConstraintEliteSet, EliteSet and refit use its own samples only, with
+ * cfg->n_proj and cfg->n_elite counted per group (<= Bg). One projection solve
+ * covers all groups. mu [n_dist][dim*11], sigma [n_dist][dim*11][dim*11] and
+ * best [n_dist][dim*11 + 1] are device arrays; Philox draws use the sample's
+ * index in the whole batch, so n_dist = 1 is traj_sampler_step. Trace arrays:
+ * samples ... cost_aug as above over all n_traj; proj_idx [n_dist][n_proj] and
+ * elite_idx [n_dist][n_elite] hold indices local to the group. */
+traj_status traj_sampler_step_multi(traj_batch *b, const traj_sampler_config *cfg, int iteration,
+                                    int n_dist, float *mu, float *sigma, const float *z,
+                                    float *best, const traj_sampler_trace *trace);
 
 /* BF16 tensor-core GEMM, the building block of the warm-start network:
  * C[M][N] = A[M][K] * B[N][K]^T with FP32 accumulation (tcgen05, TMA-staged

@@ -155,15 +155,24 @@ cudaError_t launch_am_mixed(int dim, int n_p, const SolveArgs &a, const LaunchSh
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s,
                             LaunchShape *used);
-cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int B, float eps,
-                                 const float *z, unsigned long long seed, int iteration,
+// The sampler's stages for n_dist distributions of B / n_dist samples each
+// (mu [n_dist][D], sigma and L_scratch [n_dist][D][D]).
+cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int B, int n_dist,
+                                 float eps, const float *z, unsigned long long seed, int iteration,
                                  float *L_scratch, int *flag, float *xi0, float *samples_out,
                                  cudaStream_t s);
+// cost terms: c_aug = sum_t (||p''||^2 + w_curv c_kappa + w_path c_p) + w_res r, with the
+// path from start to goal (device FP64 [dim])
+struct SamplerCost {
+  float w_res, w_curv, w_path;
+  const double *start, *goal;
+};
 cudaError_t launch_sampler_back(const float *xi, const float *res, const float *tables,
-                                int tbl_off, int n_p, float invT2, int dim, int B, float w_r,
-                                int n_proj, int n_elite, float gamma, float sig, float *r_out,
-                                float *caug_out, int *proj_idx, int *elite_idx, float *mu,
-                                float *sigma, float *best, cudaStream_t s);
+                                int tbl_off, int n_p, float invT, float invT2, int dim, int B,
+                                int n_dist, const SamplerCost &cost, int n_proj, int n_elite,
+                                float gamma, float sig, float *r_out, float *caug_out,
+                                int *proj_idx, int *elite_idx, float *mu, float *sigma,
+                                float *best, cudaStream_t s);
 // tcgen05 BF16 GEMM C = A B^T (gemm_tc.cu); epi: 0 FP32 store, 1 bias+GELU (Z f32 and
 // GELU(Z) bf16), 2 bias FP32, 3 C * GELU'(aux) -> bf16.
 cudaError_t launch_gemm_bf16(int epi, const void *A, const void *B, int M, int N, int K,

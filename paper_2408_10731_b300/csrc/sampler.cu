@@ -8,13 +8,18 @@
 //   2. the AM solve kernel in projection mode (Q = I, q = -xi_i, eq.
 //      matrix_vec) for n_inner iterations;
 //   3. residual r_i (worst of the three L-infinity residuals) and augmented
-//      cost c_aug = c_1 + w_r r with c_1 = sum_t ||p''(t)||^2 (Algorithm 3);
+//      cost c_aug = c_1 + w_r r with c_1 = sum_t ||p''(t)||^2 (Algorithm 3), plus
+//      optional curvature and path-distance terms (the BARN cost of Section 5);
 //   4. ConstraintEliteSet: the N_proj lowest r; EliteSet: the N_elite lowest
 //      c_aug among them (deterministic bitonic sorts on (key, index));
 //   5. weights c_m = exp(-(c_aug,m - delta)/gamma), delta = min c_aug, and the
 //      updates of eqs. update_mean and update_covariance (the covariance uses
 //      the new mean). The sign of the exponent follows the reading that good
 //      samples weigh more.
+// Decentralised form (D-PRIEST): the batch splits into n_dist contiguous groups
+// of B / n_dist samples, each with its own mean and covariance. The Cholesky,
+// selection and refit kernels take one CTA per group, so every stage is one
+// launch for all distributions; the projection solve is one launch as before.
 #include "internal.cuh"
 #include <math.h>
 
@@ -37,9 +42,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 __device__ __forceinline__ float u01(uint32_t x) { return ((float)x + 0.5f) * 2.3283064365386963e-10f; }
 
 // ---- kernels ----------------------------------------------------------------
-// Cholesky of Sigma + eps I (D x D, D <= 48) into L (lower, row-major). One CTA.
+// Cholesky of Sigma_g + eps I (D x D, D <= 48) into L_g (lower, row-major). One
+// CTA per distribution g = blockIdx.x.
 __global__ void k_cholesky(const float *sigma, int D, float eps, float *L, int *flag) {
   __shared__ float A[48 * 48];
+  sigma += (size_t)blockIdx.x * D * D;
+  L += (size_t)blockIdx.x * D * D;
   for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
     const int i = e / D, j = e % D;
     A[e] = 0.5f * (sigma[i * D + j] + sigma[j * D + i]) + (i == j ? eps : 0.f);
@@ -66,12 +74,16 @@ __global__ void k_cholesky(const float *sigma, int D, float eps, float *L, int *
   }
 }
 
-// xi_i = mu + L z_i. z from `z` ([B][D]) or, when z == nullptr, Philox with
-// counter (i, iteration, pair, 0) and key (seed lo, seed hi); Box-Muller pairs.
-__global__ void k_sample(const float *mu, const float *L, int D, int B, const float *z,
+// xi_i = mu_g + L_g z_i for sample i of group g = i / Bg. z from `z` ([B][D]) or,
+// when z == nullptr, Philox with counter (i, iteration, pair, 0) and key (seed lo,
+// seed hi); Box-Muller pairs.
+__global__ void k_sample(const float *mu, const float *L, int D, int B, int Bg, const float *z,
                          unsigned long long seed, int iteration, float *xi0, float *samples_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
+  const int g = i / Bg;
+  mu += (size_t)g * D;
+  L += (size_t)g * D * D;
   float zz[48];
   if (z) {
     for (int d = 0; d < D; ++d) zz[d] = z[(size_t)i * D + d];
@@ -98,23 +110,61 @@ __global__ void k_sample(const float *mu, const float *L, int D, int B, const fl
   }
 }
 
-// r_i = max of the three residuals; c_1 = sum_t ||p''(t)||^2 on the grid; c_aug = c_1 + w_r r.
+// r_i = max of the three residuals; c_aug = c_1 + w_r r with
+// c_1 = sum_t ||p''||^2 + w_curv c_kappa + w_path c_p on the grid (PRIEST's BARN cost):
+// c_kappa = ||p' x p''||^2 / ||p'||^6, the squared curvature (0 below a speed of 1e-3 m/s),
+// c_p = distance of p(t) from its projection onto the segment start -> goal of the
+// problem (start, goal: FP64 [dim]).
 __global__ void k_cost(const float *xi, const float *res, const float *tables, int tbl_off,
-                       int n_p, float invT2, int dim, int B, float w_r, float *r_out,
+                       int n_p, float invT, float invT2, int dim, int B, float w_r, float w_curv,
+                       float w_path, const double *start, const double *goal, float *r_out,
                        float *caug_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
-  const float *tA = tables + tbl_off + 2 * n_p * ROW;
+  const float *tP = tables + tbl_off, *tD = tP + n_p * ROW, *tA = tD + n_p * ROW;
+  float sv[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f};
+  for (int a = 0; a < dim; ++a) {
+    sv[a] = (float)start[a];
+    gv[a] = (float)(goal[a] - start[a]);
+  }
+  float L2 = 0.f;
+  for (int a = 0; a < dim; ++a) L2 = fmaf(gv[a], gv[a], L2);
   float c1 = 0.f;
   for (int t = 0; t < n_p; ++t) {
-    float a2 = 0.f;
+    float pos[3] = {0.f, 0.f, 0.f}, vel[3] = {0.f, 0.f, 0.f}, acc[3] = {0.f, 0.f, 0.f};
     for (int a = 0; a < dim; ++a) {
-      float s = 0.f;
-      for (int k = 0; k < NC; ++k) s = fmaf(tA[t * ROW + k], xi[((size_t)i * dim + a) * NC + k], s);
-      s *= invT2;
-      a2 = fmaf(s, s, a2);
+      const float *x = xi + ((size_t)i * dim + a) * NC;
+      float sp = 0.f, sd = 0.f, sa = 0.f;
+      for (int k = 0; k < NC; ++k) {
+        sp = fmaf(tP[t * ROW + k], x[k], sp);
+        sd = fmaf(tD[t * ROW + k], x[k], sd);
+        sa = fmaf(tA[t * ROW + k], x[k], sa);
+      }
+      pos[a] = sp; vel[a] = sd * invT; acc[a] = sa * invT2;
     }
-    c1 += a2;
+    float a2 = 0.f;
+    for (int a = 0; a < dim; ++a) a2 = fmaf(acc[a], acc[a], a2);
+    float c = a2;
+    if (w_curv != 0.f) {
+      const float cx = vel[1] * acc[2] - vel[2] * acc[1], cy = vel[2] * acc[0] - vel[0] * acc[2],
+                  cz = vel[0] * acc[1] - vel[1] * acc[0];
+      const float v2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
+      if (v2 > 1e-6f) c += w_curv * (cx * cx + cy * cy + cz * cz) / (v2 * v2 * v2);
+    }
+    if (w_path != 0.f) {
+      float u = 0.f;
+      if (L2 > 0.f) {
+        for (int a = 0; a < dim; ++a) u = fmaf(pos[a] - sv[a], gv[a], u);
+        u = fminf(fmaxf(u / L2, 0.f), 1.f);
+      }
+      float d2 = 0.f;
+      for (int a = 0; a < dim; ++a) {
+        const float d = pos[a] - (sv[a] + u * gv[a]);
+        d2 = fmaf(d, d, d2);
+      }
+      c += w_path * sqrtf(d2);
+    }
+    c1 += c;
   }
   float r = fmaxf(res[i * 3 + 0], fmaxf(res[i * 3 + 1], res[i * 3 + 2]));
   if (!(r == r)) r = __int_as_float(0x7f800000); // NaN ranks last
@@ -141,10 +191,15 @@ __device__ void bitonic(float *key, int *idx, int n) {
 }
 
 // Two-stage top-k: the n_proj lowest r, then the n_elite lowest c_aug among them.
-// One CTA; B <= 8192 (padded to a power of two with +inf keys).
+// One CTA per group g = blockIdx.x over its B samples (B <= 8192, padded to a power
+// of two with +inf keys); indices are local to the group.
 __global__ void k_select(const float *r, const float *caug, int B, int n_proj, int n_elite,
                          int *proj_idx, int *elite_idx) {
   extern __shared__ unsigned char sm_raw[];
+  r += (size_t)blockIdx.x * B;
+  caug += (size_t)blockIdx.x * B;
+  proj_idx += (size_t)blockIdx.x * n_proj;
+  elite_idx += (size_t)blockIdx.x * n_elite;
   int n = 1;
   while (n < B) n <<= 1;
   float *key = reinterpret_cast<float *>(sm_raw);
@@ -167,10 +222,18 @@ __global__ void k_select(const float *r, const float *caug, int B, int n_proj, i
   for (int t = threadIdx.x; t < n_elite; t += blockDim.x) elite_idx[t] = idx[t];
 }
 
-// Weighted refit (eqs. update_mean, update_covariance) and the best elite.
-__global__ void k_refit(const float *xi, const float *caug, const int *elite, int n_elite, int D,
-                        float gamma, float sig, float *mu, float *sigma, float *best) {
+// Weighted refit (eqs. update_mean, update_covariance) and the best elite. One CTA
+// per group g = blockIdx.x of Bg samples.
+__global__ void k_refit(const float *xi, const float *caug, const int *elite, int Bg, int n_elite,
+                        int D, float gamma, float sig, float *mu, float *sigma, float *best) {
   __shared__ float w_s[8192];
+  const size_t g = blockIdx.x;
+  xi += g * Bg * D;
+  caug += g * Bg;
+  elite += g * n_elite;
+  mu += g * D;
+  sigma += g * D * D;
+  best += g * (D + 1);
   __shared__ float mu_new[48];
   __shared__ float red[32];
   const float delta = caug[elite[0]];
@@ -235,33 +298,39 @@ cudaError_t launch_accel_cost(const float *xi, const int *traj_problem, const Pr
   return cudaGetLastError();
 }
 
-cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int B, float eps,
-                                 const float *z, unsigned long long seed, int iteration,
+cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int B, int n_dist,
+                                 float eps, const float *z, unsigned long long seed, int iteration,
                                  float *L_scratch, int *flag, float *xi0, float *samples_out,
                                  cudaStream_t s) {
-  k_cholesky<<<1, 64, 0, s>>>(sigma, D, eps, L_scratch, flag);
+  k_cholesky<<<n_dist, 64, 0, s>>>(sigma, D, eps, L_scratch, flag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sample<<<(B + 127) / 128, 128, 0, s>>>(mu, L_scratch, D, B, z, seed, iteration, xi0, samples_out);
+  k_sample<<<(B + 127) / 128, 128, 0, s>>>(mu, L_scratch, D, B, B / n_dist, z, seed, iteration, xi0,
+                                           samples_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sampler_back(const float *xi, const float *res, const float *tables,
-                                int tbl_off, int n_p, float invT2, int dim, int B, float w_r,
-                                int n_proj, int n_elite, float gamma, float sig, float *r_out,
-                                float *caug_out, int *proj_idx, int *elite_idx, float *mu,
-                                float *sigma, float *best, cudaStream_t s) {
-  k_cost<<<(B + 127) / 128, 128, 0, s>>>(xi, res, tables, tbl_off, n_p, invT2, dim, B, w_r, r_out, caug_out);
+                                int tbl_off, int n_p, float invT, float invT2, int dim, int B,
+                                int n_dist, const SamplerCost &cost, int n_proj, int n_elite,
+                                float gamma, float sig, float *r_out, float *caug_out,
+                                int *proj_idx, int *elite_idx, float *mu, float *sigma,
+                                float *best, cudaStream_t s) {
+  k_cost<<<(B + 127) / 128, 128, 0, s>>>(xi, res, tables, tbl_off, n_p, invT, invT2, dim, B,
+                                         cost.w_res, cost.w_curv, cost.w_path, cost.start,
+                                         cost.goal, r_out, caug_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const int Bg = B / n_dist;
   int n = 1;
-  while (n < B) n <<= 1;
+  while (n < Bg) n <<= 1;
   const size_t smem = (size_t)n * (sizeof(float) + sizeof(int));
   e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_select<<<1, 1024, smem, s>>>(r_out, caug_out, B, n_proj, n_elite, proj_idx, elite_idx);
+  k_select<<<n_dist, 1024, smem, s>>>(r_out, caug_out, Bg, n_proj, n_elite, proj_idx, elite_idx);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_refit<<<1, 1024, 0, s>>>(xi, caug_out, elite_idx, n_elite, dim * NC, gamma, sig, mu, sigma, best);
+  k_refit<<<n_dist, 1024, 0, s>>>(xi, caug_out, elite_idx, Bg, n_elite, dim * NC, gamma, sig, mu,
+                                  sigma, best);
   return cudaGetLastError();
 }
 

@@ -198,7 +198,7 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
       (e = dalloc(&b->d_u, B * D * NC)) || (e = dalloc(&b->d_res, B * 3)) ||
       (e = dalloc(&b->d_lam0, B * D * NC)) || (e = dalloc(&b->d_u0, B * D * NC)) ||
       (e = dalloc(&b->d_iters, B)) || (e = dalloc(&b->d_status, B)) || (e = dalloc(&b->d_queue, 1)) ||
-      (e = dalloc(&b->d_flags, 1)) || (e = dalloc(&b->d_t0, 1)) || (e = dalloc(&b->d_L, 48 * 48)) ||
+      (e = dalloc(&b->d_flags, 1)) || (e = dalloc(&b->d_t0, 1)) || (e = dalloc(&b->d_L, TRAJ_SAMPLER_MAX_DIST * (D * NC) * (D * NC))) ||
       (e = dalloc(&b->d_r, B)) || (e = dalloc(&b->d_caug, B)) || (e = dalloc(&b->d_proj, B)) ||
       (e = dalloc(&b->d_elite, B)) || (e = dalloc(&b->d_sflag, 1)))
     return bail("cudaMalloc", e);
@@ -680,9 +680,9 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
   return best_t < 1e30f ? TRAJ_OK : fail(b, TRAJ_ECUDA, "no launch shape ran");
 }
 
-traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *sc, int iteration,
-                              float *mu, float *sigma, const float *z, float *best,
-                              const traj_sampler_trace *trace) {
+traj_status traj_sampler_step_multi(traj_batch *b, const traj_sampler_config *sc, int iteration,
+                                    int n_dist, float *mu, float *sigma, const float *z,
+                                    float *best, const traj_sampler_trace *trace) {
   if (!b) return TRAJ_EINVAL;
   if (!sc || !mu || !sigma || !best) return fail(b, TRAJ_EINVAL, "NULL sampler argument");
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
@@ -691,29 +691,40 @@ traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *sc, int 
   const int B = b->n_traj, D = b->cfg.dim * NC;
   for (int k = 0; k < B; ++k)
     if (b->traj_problem[k] != 0) return fail(b, TRAJ_EINVAL, "sampler trajectories must all belong to problem 0");
-  if (B > 8192) return fail(b, TRAJ_ESHAPE, "sampler batch must be <= 8192");
-  if (sc->n_inner < 0 || sc->n_proj < 1 || sc->n_proj > B || sc->n_elite < 1 ||
+  if (n_dist < 1 || n_dist > TRAJ_SAMPLER_MAX_DIST || B % n_dist != 0)
+    return fail(b, TRAJ_EINVAL, "n_dist must be in [1, TRAJ_SAMPLER_MAX_DIST] and divide n_traj");
+  const int Bg = B / n_dist;
+  if (Bg > 8192) return fail(b, TRAJ_ESHAPE, "samples per distribution must be <= 8192");
+  if (sc->n_inner < 0 || sc->n_proj < 1 || sc->n_proj > Bg || sc->n_elite < 1 ||
       sc->n_elite > sc->n_proj || !(sc->gamma > 0) || !(sc->sigma_lr > 0) || sc->sigma_lr > 1 ||
-      !(sc->eps >= 0) || !(sc->w_res >= 0))
+      !(sc->eps >= 0) || !(sc->w_res >= 0) || !(sc->w_curv >= 0) || !(sc->w_path >= 0))
     return fail(b, TRAJ_EINVAL, "sampler config out of range");
-  CK(b, launch_sampler_front(mu, sigma, D, B, sc->eps, z, sc->seed, iteration, b->d_L, b->d_sflag,
-                             b->d_xi0, trace ? trace->samples : nullptr, b->stream));
+  CK(b, launch_sampler_front(mu, sigma, D, B, n_dist, sc->eps, z, sc->seed, iteration, b->d_L,
+                             b->d_sflag, b->d_xi0, trace ? trace->samples : nullptr, b->stream));
   traj_status rc = traj_solve(b, sc->n_inner, -1.0f, 0.0, nullptr);
   if (rc != TRAJ_OK) return rc;
   const int n_p = b->n_steps[0];
   const double T = b->duration[0];
-  CK(b, launch_sampler_back(b->d_xi, b->d_res, b->d_tables, b->tbl_off[0], n_p, (float)(1.0 / (T * T)),
-                            b->cfg.dim, B, sc->w_res, sc->n_proj, sc->n_elite, sc->gamma,
-                            sc->sigma_lr, b->d_r, b->d_caug, b->d_proj, b->d_elite, mu, sigma, best,
-                            b->stream));
+  const SamplerCost cost{sc->w_res, sc->w_curv, sc->w_path, b->d_start, b->d_goal};
+  CK(b, launch_sampler_back(b->d_xi, b->d_res, b->d_tables, b->tbl_off[0], n_p, (float)(1.0 / T),
+                            (float)(1.0 / (T * T)), b->cfg.dim, B, n_dist, cost, sc->n_proj,
+                            sc->n_elite, sc->gamma, sc->sigma_lr, b->d_r, b->d_caug, b->d_proj,
+                            b->d_elite, mu, sigma, best, b->stream));
   if (trace) {
+    const size_t np = (size_t)n_dist * sc->n_proj, ne = (size_t)n_dist * sc->n_elite;
     if (trace->projected) CK(b, cudaMemcpyAsync(trace->projected, b->d_xi, sizeof(float) * B * D, cudaMemcpyDeviceToDevice, b->stream));
     if (trace->residual) CK(b, cudaMemcpyAsync(trace->residual, b->d_r, sizeof(float) * B, cudaMemcpyDeviceToDevice, b->stream));
     if (trace->cost_aug) CK(b, cudaMemcpyAsync(trace->cost_aug, b->d_caug, sizeof(float) * B, cudaMemcpyDeviceToDevice, b->stream));
-    if (trace->proj_idx) CK(b, cudaMemcpyAsync(trace->proj_idx, b->d_proj, sizeof(int) * sc->n_proj, cudaMemcpyDeviceToDevice, b->stream));
-    if (trace->elite_idx) CK(b, cudaMemcpyAsync(trace->elite_idx, b->d_elite, sizeof(int) * sc->n_elite, cudaMemcpyDeviceToDevice, b->stream));
+    if (trace->proj_idx) CK(b, cudaMemcpyAsync(trace->proj_idx, b->d_proj, sizeof(int) * np, cudaMemcpyDeviceToDevice, b->stream));
+    if (trace->elite_idx) CK(b, cudaMemcpyAsync(trace->elite_idx, b->d_elite, sizeof(int) * ne, cudaMemcpyDeviceToDevice, b->stream));
   }
   return TRAJ_OK;
+}
+
+traj_status traj_sampler_step(traj_batch *b, const traj_sampler_config *sc, int iteration,
+                              float *mu, float *sigma, const float *z, float *best,
+                              const traj_sampler_trace *trace) {
+  return traj_sampler_step_multi(b, sc, iteration, 1, mu, sigma, z, best, trace);
 }
 
 traj_status traj_gemm_bf16(int M, int N, int K, const void *A, const void *B, float *C, int *err,

@@ -52,7 +52,7 @@ class LaunchShape(ctypes.Structure):
 class SamplerConfig(ctypes.Structure):
     _fields_ = [("n_inner", _c_int), ("n_proj", _c_int), ("n_elite", _c_int), ("gamma", _c_float),
                 ("sigma_lr", _c_float), ("eps", _c_float), ("w_res", _c_float),
-                ("seed", ctypes.c_ulonglong)]
+                ("seed", ctypes.c_ulonglong), ("w_curv", _c_float), ("w_path", _c_float)]
 
 
 class SamplerTrace(ctypes.Structure):
@@ -106,6 +106,8 @@ def load_library():
                                   ctypes.POINTER(_c_float)]
     lib.traj_sampler_step.argtypes = [_vp, ctypes.POINTER(SamplerConfig), _c_int, _vp, _vp, _vp,
                                       _vp, ctypes.POINTER(SamplerTrace)]
+    lib.traj_sampler_step_multi.argtypes = [_vp, ctypes.POINTER(SamplerConfig), _c_int, _c_int,
+                                            _vp, _vp, _vp, _vp, ctypes.POINTER(SamplerTrace)]
     lib.traj_gemm_bf16.argtypes = [_c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _vp]
     lib.traj_solve_noalloc.argtypes = [ctypes.POINTER(TrajConfig), _c_int, _vp, _vp, _vp, _vp,
                                        _vp, _vp, _vp, _vp, _c_int, _vp, _vp, _c_int, _c_float,
@@ -114,7 +116,7 @@ def load_library():
                  "traj_set_obstacles", "traj_set_initial", "traj_solve", "traj_get_solve_stats",
                  "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_set_rho_schedule", "traj_set_workspace", "traj_measure_fp32_peak",
                  "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune",
-                 "traj_sampler_step", "traj_gemm_bf16"):
+                 "traj_sampler_step", "traj_sampler_step_multi", "traj_gemm_bf16"):
         getattr(lib, name).restype = _c_int
     _LIB = lib
     return lib
@@ -260,20 +262,28 @@ class TrajBatch:
         return dict(warps_per_block=shape.warps_per_block, blocks_per_sm=shape.blocks_per_sm,
                     warps_per_trajectory=shape.warps_per_trajectory, ms=ms.value)
 
-    def sampler_step(self, cfg: dict, iteration, mu, sigma, best, z=None, trace=None):
-        """One outer iteration of the projection-guided sampler (device tensors)."""
+    def sampler_step(self, cfg: dict, iteration, mu, sigma, best, z=None, trace=None,
+                     n_dist=None):
+        """One outer iteration of the projection-guided sampler (device tensors). With
+        n_dist, the decentralised form: mu [n_dist][D], sigma [n_dist][D][D] and best
+        [n_dist][D + 1], each distribution refined from its own n_traj / n_dist samples."""
         sc = SamplerConfig(int(cfg["n_inner"]), int(cfg["n_proj"]), int(cfg["n_elite"]),
                            float(cfg["gamma"]), float(cfg["sigma_lr"]), float(cfg["eps"]),
-                           float(cfg.get("w_res", 1.0)), int(cfg.get("seed", 0)))
+                           float(cfg.get("w_res", 1.0)), int(cfg.get("seed", 0)),
+                           float(cfg.get("w_curv", 0.0)), float(cfg.get("w_path", 0.0)))
         tr = None
         if trace is not None:
             tr = SamplerTrace(*[_ptr(trace.get(k), dt)[0] for k, dt in (
                 ("samples", np.float32), ("projected", np.float32), ("residual", np.float32),
                 ("cost_aug", np.float32), ("proj_idx", np.int32), ("elite_idx", np.int32))])
-        self._check(self._lib.traj_sampler_step(
-            self._h, ctypes.byref(sc), int(iteration), _ptr(mu, np.float32)[0],
-            _ptr(sigma, np.float32)[0], _ptr(z, np.float32)[0], _ptr(best, np.float32)[0],
-            ctypes.byref(tr) if tr is not None else None))
+        args = (_ptr(mu, np.float32)[0], _ptr(sigma, np.float32)[0], _ptr(z, np.float32)[0],
+                _ptr(best, np.float32)[0], ctypes.byref(tr) if tr is not None else None)
+        if n_dist is None:
+            self._check(self._lib.traj_sampler_step(self._h, ctypes.byref(sc), int(iteration),
+                                                    *args))
+        else:
+            self._check(self._lib.traj_sampler_step_multi(self._h, ctypes.byref(sc),
+                                                          int(iteration), int(n_dist), *args))
 
     def get_state(self):
         lam = np.zeros((self.n_traj, self.dim, 11), np.float32)

@@ -69,3 +69,94 @@ def test_refit_uniform_weights_is_the_elite_sample_mean_and_covariance():
     np.testing.assert_allclose(sig2, 1.5 * np.eye(7) + 0.25 * (np.cov(X[elite].T, bias=True) + shift),
                                atol=1e-12)
     np.testing.assert_array_equal(best, X[elite[0]])
+
+
+def _fit(n_p, T, pos):
+    """Degree-10 Bernstein coefficients [dim][11] of a polynomial sampled at the grid."""
+    from oracle import am
+    P, _, _ = am.bernstein(n_p, T)
+    return np.linalg.lstsq(P, pos, rcond=None)[0].T
+
+
+def _batch(dim, n_p, T, start, goal):
+    import types
+    return types.SimpleNamespace(dim=dim, n_steps=np.array([n_p]), duration=np.array([T]),
+                                 start=np.array([start], float), goal=np.array([goal], float))
+
+
+def test_curvature_of_a_parabola_is_its_closed_form():
+    """p(t) = (t, t^2): kappa = 2 / (1 + 4 t^2)^1.5, and ||p''||^2 = 4, so
+    c_1 = sum_t (4 + w 4 / (1 + 4 t^2)^3); the same curve in a tilted 3D plane
+    gives the same sum."""
+    n_p, T = 60, 3.0
+    t = np.linspace(0.0, T, n_p)
+    closed = (4.0 + 0.7 * 4.0 / (1.0 + 4.0 * t ** 2) ** 3).sum()
+    b2 = _batch(2, n_p, T, [0, 0], [1, 1])
+    X = _fit(n_p, T, np.stack([t, t ** 2], 1))
+    _, c = priest.costs(b2, X.reshape(1, -1), np.zeros((1, 3)), w_r=0.0, w_curv=0.7)
+    np.testing.assert_allclose(c[0], closed, rtol=1e-9)
+    e1 = np.array([2.0, 1.0, 2.0]) / 3.0
+    e2 = np.array([1.0, -2.0, 0.0]) / np.sqrt(5.0)
+    X3 = _fit(n_p, T, t[:, None] * e1 + (t ** 2)[:, None] * e2)
+    b3 = _batch(3, n_p, T, [0, 0, 0], [1, 1, 1])
+    _, c3 = priest.costs(b3, X3.reshape(1, -1), np.zeros((1, 3)), w_r=0.0, w_curv=0.7)
+    np.testing.assert_allclose(c3[0], closed, rtol=1e-9)
+
+
+def test_curvature_vanishes_on_a_straight_line_with_varying_speed():
+    """p(t) = (t^2, 2 t^2): p' and p'' are parallel, so c_kappa = 0 and only
+    ||p''||^2 = 4 + 16 remains; at t = 0 the speed is 0 and the term is 0."""
+    n_p, T = 40, 2.0
+    t = np.linspace(0.0, T, n_p)
+    X = _fit(n_p, T, np.stack([t ** 2, 2 * t ** 2], 1))
+    _, c = priest.costs(_batch(2, n_p, T, [0, 0], [1, 1]), X.reshape(1, -1), np.zeros((1, 3)),
+                        w_r=0.0, w_curv=5.0)
+    np.testing.assert_allclose(c[0], 20.0 * n_p, rtol=1e-9)
+
+
+def test_path_distance_of_offset_and_overshooting_lines():
+    """Path start (0, 0) -> goal (10, 0); p(t) = (-2 + 14 t / T, h): distance h over
+    the segment, and the distance to the nearer end point beyond it."""
+    n_p, T, h = 50, 5.0, 1.5
+    t = np.linspace(0.0, T, n_p)
+    x = -2.0 + 14.0 * t / T
+    d = np.where(x < 0, np.hypot(x, h), np.where(x > 10, np.hypot(x - 10, h), h))
+    X = _fit(n_p, T, np.stack([x, np.full(n_p, h)], 1))
+    b = _batch(2, n_p, T, [0, 0], [10, 0])
+    _, c0 = priest.costs(b, X.reshape(1, -1), np.zeros((1, 3)), w_r=0.0)
+    _, c = priest.costs(b, X.reshape(1, -1), np.zeros((1, 3)), w_r=0.0, w_path=2.0)
+    np.testing.assert_allclose(c0[0], 0.0, atol=1e-9)       # straight line, constant speed
+    np.testing.assert_allclose(c[0] - c0[0], 2.0 * d.sum(), rtol=1e-9)
+    # 3D: the same line lifted by a perpendicular offset in z adds in quadrature
+    X3 = _fit(n_p, T, np.stack([x, np.full(n_p, h), np.full(n_p, 2.0)], 1))
+    b3 = _batch(3, n_p, T, [0, 0, 0], [10, 0, 0])
+    _, c3 = priest.costs(b3, X3.reshape(1, -1), np.zeros((1, 3)), w_r=0.0, w_path=1.0)
+    d3 = np.where(x < 0, np.sqrt(x ** 2 + h ** 2 + 4), np.where(
+        x > 10, np.sqrt((x - 10) ** 2 + h ** 2 + 4), np.hypot(h, 2.0)))
+    np.testing.assert_allclose(c3[0], d3.sum(), rtol=1e-9)
+
+
+def test_decentralised_step_is_independent_steps_per_group():
+    """D-PRIEST with two distributions = two single-distribution steps, each on its
+    own group of samples (draws given); n_dist = 1 reproduces step()."""
+    from paper_2408_10731_b300 import scenes
+    Bg, D = 6, 33
+    c_full = scenes.config3(0, n_traj=2 * Bg)
+    c_half = scenes.config3(0, n_traj=Bg)
+    cfg = priest.SamplerConfig(n_inner=3, n_proj=4, n_elite=2, w_curv=0.5, w_path=0.2)
+    z = scenes.normal_draws(5, (2 * Bg, D)).astype(np.float64)
+    rng = np.random.default_rng(1)
+    mus = np.stack([c_full["mu0"], c_full["mu0"] + rng.normal(size=D)]).astype(np.float64)
+    sigmas = np.stack([np.eye(D) * 2.0, np.eye(D) * 0.5])
+    m = priest.step_multi(c_full["batch"], cfg, 0, mus, sigmas, z=z)
+    for g in range(2):
+        s = priest.step(c_half["batch"], cfg, 0, mus[g], sigmas[g], z=z[g * Bg:(g + 1) * Bg])
+        np.testing.assert_array_equal(m["elite_idx"][g], s["elite_idx"])
+        np.testing.assert_array_equal(m["proj_idx"][g], s["proj_idx"])
+        np.testing.assert_allclose(m["mu"][g], s["mu"], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(m["sigma"][g], s["sigma"], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(m["cost_aug"][g * Bg:(g + 1) * Bg], s["cost_aug"], rtol=1e-12)
+    one = priest.step_multi(c_half["batch"], cfg, 0, mus[:1], sigmas[:1], z=z[:Bg])
+    s0 = priest.step(c_half["batch"], cfg, 0, mus[0], sigmas[0], z=z[:Bg])
+    np.testing.assert_array_equal(one["elite_idx"][0], s0["elite_idx"])
+    np.testing.assert_allclose(one["best"][0], s0["best"], rtol=1e-12)

@@ -120,3 +120,92 @@ def test_full_size_sampler_run_invariants():
         np.testing.assert_allclose(xb @ P[-1], b.goal[0], atol=1e-3)
     finally:
         h.close()
+
+
+def test_decentralised_sampler_with_barn_cost_matches_oracle_stagewise():
+    """D-PRIEST: four distributions over groups of 64 samples, on-device Philox
+    draws, the cost with curvature and path-distance terms. Every stage is checked
+    against the oracle on the GPU's own inputs to it; the selections exactly.
+    c_aug tolerance: c_kappa ~ ||p'||^-4 near the rest start, where p' is an
+    11-term FP32 sum of O(10) products (absolute error ~1e-5 m/s at speeds
+    ~0.2 m/s), so its relative error is ~4 x 5e-5; 1e-3 leaves a margin of 5."""
+    import torch
+    B, n_dist, D = 256, 4, 33
+    Bg = B // n_dist
+    c3, b, h = _handle(B)
+    cfg = dict(n_inner=20, n_proj=math.ceil(0.73 * Bg), n_elite=math.ceil(0.10 * Bg), gamma=1.0,
+               sigma_lr=0.5, eps=1e-6, w_res=1.0, seed=11, w_curv=0.05, w_path=0.5)
+    rng = np.random.default_rng(3)
+    mus = np.stack([c3["mu0"] + (g > 0) * rng.normal(0.0, 1.0, D) for g in range(n_dist)])
+    sigmas = np.stack([c3["sigma0"] * (0.5 + 0.5 * g) for g in range(n_dist)])
+    mu, sigma = _cuda(mus), _cuda(sigmas)
+    best = _cuda(np.zeros((n_dist, D + 1)))
+    try:
+        for it in range(2):
+            mu_in = mu.cpu().numpy().astype(np.float64)
+            sig_in = sigma.cpu().numpy().astype(np.float64)
+            tr = dict(samples=torch.zeros(B, D, device="cuda"),
+                      projected=torch.zeros(B, D, device="cuda"),
+                      residual=torch.zeros(B, device="cuda"), cost_aug=torch.zeros(B, device="cuda"),
+                      proj_idx=torch.zeros(n_dist, cfg["n_proj"], dtype=torch.int32, device="cuda"),
+                      elite_idx=torch.zeros(n_dist, cfg["n_elite"], dtype=torch.int32,
+                                            device="cuda"))
+            h.sampler_step(cfg, it, mu, sigma, best, trace=tr, n_dist=n_dist)
+            g_ = {k: v.cpu().numpy() for k, v in tr.items()}
+            z = priest.philox_normals(B, D, cfg["seed"], it)
+            for g in range(n_dist):
+                sl = slice(g * Bg, (g + 1) * Bg)
+                ref = priest.sample(mu_in[g], sig_in[g], z[sl], cfg["eps"])
+                np.testing.assert_allclose(g_["samples"][sl], ref, atol=2e-4, rtol=2e-5)
+            xs = g_["samples"].astype(np.float64).reshape(B, 3, 11)
+            o = am.solve(b, cfg["n_inner"], tol=-1.0, cost_mode=1, xi0=xs)
+            err = position_error(b, g_["projected"].reshape(B, 3, 11), o["xi"])
+            assert err.max() <= POS_TOL, err.max()
+            r_o, c_o = priest.costs(b, g_["projected"].astype(np.float64), o["residual"],
+                                    cfg["w_res"], w_curv=cfg["w_curv"], w_path=cfg["w_path"])
+            _, c_plain = priest.costs(b, g_["projected"].astype(np.float64), o["residual"])
+            assert np.all(c_o > c_plain)                    # the extra terms are live
+            np.testing.assert_allclose(g_["residual"], r_o, atol=2e-5, rtol=1e-4)
+            np.testing.assert_allclose(g_["cost_aug"], c_o, rtol=1e-3)
+            B_ = best.cpu().numpy()
+            for g in range(n_dist):
+                sl = slice(g * Bg, (g + 1) * Bg)
+                p_o, e_o = priest.select(g_["residual"][sl], g_["cost_aug"][sl], cfg["n_proj"],
+                                         cfg["n_elite"])
+                np.testing.assert_array_equal(g_["proj_idx"][g], p_o)
+                np.testing.assert_array_equal(g_["elite_idx"][g], e_o)
+                m_o, s_o, best_o, bc_o = priest.refit(g_["projected"][sl].astype(np.float64),
+                                                      g_["cost_aug"][sl].astype(np.float64), e_o,
+                                                      mu_in[g], sig_in[g], cfg["gamma"],
+                                                      cfg["sigma_lr"])
+                np.testing.assert_allclose(mu.cpu().numpy()[g], m_o, rtol=1e-4, atol=1e-4)
+                np.testing.assert_allclose(sigma.cpu().numpy()[g], s_o, rtol=1e-3, atol=1e-4)
+                np.testing.assert_array_equal(B_[g, :D], g_["projected"][sl][e_o[0]])
+                assert B_[g, D] == g_["cost_aug"][sl][e_o[0]]
+    finally:
+        h.close()
+
+
+def test_decentralised_sampler_with_one_distribution_is_the_plain_step():
+    """n_dist = 1 through traj_sampler_step_multi gives bitwise the result of
+    traj_sampler_step (same Philox draws, same kernels)."""
+    import torch
+    B, D = 128, 33
+    outs = []
+    for multi in (False, True):
+        c3, b, h = _handle(B)
+        cfg = dict(n_inner=10, n_proj=90, n_elite=13, gamma=1.0, sigma_lr=0.5, eps=1e-6,
+                   seed=4, w_path=0.3)
+        mu, sigma, best = _cuda(c3["mu0"]), _cuda(c3["sigma0"]), _cuda(np.zeros(D + 1))
+        try:
+            for it in range(2):
+                if multi:
+                    h.sampler_step(cfg, it, mu, sigma, best, n_dist=1)
+                else:
+                    h.sampler_step(cfg, it, mu, sigma, best)
+            torch.cuda.synchronize()
+            outs.append((mu.cpu().numpy(), sigma.cpu().numpy(), best.cpu().numpy()))
+        finally:
+            h.close()
+    for a, c in zip(*outs):
+        np.testing.assert_array_equal(a, c)
