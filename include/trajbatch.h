@@ -403,6 +403,76 @@ const char *traj_last_error(traj_batch *b);
  * FMA), best of `reps` timed launches each. No paper counterpart (measurement). */
 traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_per_s);
 
+/* ---- Joint multi-agent optimizer (Paper IV, Algorithm 5) ---------------------
+ * A batch of independent scenes, each with n_agents agents solved jointly: every
+ * agent is a degree-10 Bernstein polynomial per axis on an n_steps-point grid
+ * over [0, T_s]; cost 1/2 sum_i sum_t ||p_i''(t)||^2 (the QP form of eq.
+ * eq_step_x); position fixed at both ends with zero velocity and acceleration
+ * (eqs. eq_multiagent_start, eq_multiagent_final); agents are spheroids of
+ * horizontal radius r_s and half-height h_s (circles of radius r_s in 2D), kept
+ * apart pairwise through x_i - x_j = d_ij e(alpha_ij, beta_ij), d_ij >= 1, on the
+ * spheroid (2r, 2r, 2h) (eq. sphere_proposed); static obstacles are spheres of
+ * radius r_o kept out through the spheroid (r + r_o, r + r_o, h + r_o).
+ * Each iteration: the x-step through KKT inverses cached once per scene and
+ * penalty (eq. kkt_step_x), alpha/beta in closed form (eqs. com_alpha_i,
+ * com_beta_i), d (eq. com_d_i, then d >= 1) and the multiplier updates (eqs.
+ * update_lamda_xi .. update_lamda_zi). The initial iterate is each agent's
+ * obstacle-free optimum; the residual is the largest ||x_i - x_j - d e|| over
+ * pairs, obstacles and grid points, and a scene stops at the first iteration
+ * whose residual is <= tol. Penalty ladder: rho growth^l, l < rho_levels, one
+ * level up after every rho_every-th unconverged iteration (the paper caches ten
+ * increasing penalties for the later iterations). One CTA solves one scene. */
+typedef struct traj_ma_batch traj_ma_batch;
+
+typedef struct traj_ma_config {
+  int dim;           /* 2 or 3 */
+  int max_scenes;    /* >= 1 */
+  int max_agents;    /* 1 .. 64 */
+  int max_obstacles; /* static spheres over all scenes, >= 0 */
+  int n_steps;       /* grid points per agent trajectory, 2 .. 256 */
+  float rho;         /* rho_o of level 0, > 0 */
+  int rho_levels;    /* 0 or 1: a fixed rho; up to 10 */
+  float rho_growth;  /* > 0 when rho_levels > 1 */
+  int rho_every;     /* >= 0; 0 keeps level 0 */
+} traj_ma_config;
+
+typedef struct traj_ma_stats {
+  float gpu_ms;         /* CUDA-event time of the solve launch */
+  int n_converged;      /* scenes with residual <= tol */
+  int max_iters_run;    /* largest iteration count over the scenes */
+  int lambda_in_shared; /* 1 if the pair multipliers stayed in shared memory */
+} traj_ma_stats;
+
+/* Allocates the device workspace for the capacities (multipliers for every agent
+ * pair and obstacle-agent pair of every grid point) on the given stream. */
+traj_status traj_ma_create(const traj_ma_config *cfg, void *cuda_stream, traj_ma_batch **out);
+traj_status traj_ma_destroy(traj_ma_batch *b);
+
+/* Host arrays: duration [n_scenes] (s, FP64), start and goal [n_scenes][n_agents][dim]
+ * (FP64), radius [n_scenes] and height [n_scenes] (FP32; height may be NULL in 2D),
+ * obs_offsets [n_scenes + 1] (CSR over the obstacles, obs_offsets[0] = 0),
+ * obs_centers [n_obs][dim] and obs_radii [n_obs] (FP32; NULL when there are none).
+ * Forms and inverts the scenes' KKT matrices in FP64 on the GPU and synchronises.
+ * TRAJ_ESHAPE if the sizes exceed the capacities or n_agents x n_steps does not fit
+ * one CTA's shared memory; TRAJ_EINVAL for a singular KKT matrix or bad values. */
+traj_status traj_ma_set_problems(traj_ma_batch *b, int n_scenes, int n_agents,
+                                 const double *duration, const double *start, const double *goal,
+                                 const float *radius, const float *height, const int *obs_offsets,
+                                 const float *obs_centers, const float *obs_radii);
+
+/* Runs up to max_iters iterations (0: the initial iterate only) from the initial
+ * iterate; tol < 0 runs all of them. Asynchronous unless stats is non-NULL, which
+ * synchronises and fills it. */
+traj_status traj_ma_solve(traj_ma_batch *b, int max_iters, float tol, traj_ma_stats *stats);
+
+/* coeffs [n_scenes][n_agents][dim][11], residual [n_scenes], iters [n_scenes]
+ * (each nullable; host or device); synchronises. */
+traj_status traj_ma_get_trajectories(traj_ma_batch *b, float *coeffs, float *residual, int *iters);
+
+/* Detail of the last failure on this multi-agent handle, or of the last failed
+ * traj_ma_create on this thread when b is NULL. */
+const char *traj_ma_last_error(traj_ma_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,10 @@ Readings (where the print is silent or inconsistent):
       would allow overlap and is read as a slip;
   M2  dx / (a cos alpha) is read as sqrt(dx^2 + dy^2) / a, its value wherever
       cos alpha != 0 (cos alpha has the sign of dx), so that the 0/0 at dx = 0 is
-      defined; at dx = dy = dz = 0, atan2(0, 0) = 0 gives alpha = beta = 0;
+      defined; at dx = dy = dz = 0, atan2(0, 0) = 0 gives alpha = beta = 0, i.e.
+      e = (0, 0, b) (2D: (a, 0)) for the pair (i, j) with i < j and the opposite
+      direction for (j, i), so that the two agents are pushed apart rather than
+      both the same way (every other e is already odd in delta);
   M3  initialisation: xi^0 is the obstacle-free optimum of each agent's QP;
       alpha^0, beta^0, d^0 follow from xi^0 with lambda^0 = 0;
   M4  the residual of iteration k is max over pairs, obstacles and grid points
@@ -137,16 +140,23 @@ def kkt_inverse(Q0, A_fo, Aeq, rho, N):
     return np.linalg.inv(K)
 
 
-def direction(delta, a, b, dim):
+def direction(delta, a, b, dim, sign=1.0):
     """e(alpha, beta) of eq. sphere_proposed from eqs. com_alpha_i and com_beta_i
-    (readings M2, M6): delta [..., dim] -> e [..., dim]."""
+    (readings M2, M6): delta [..., dim] -> e [..., dim]; `sign` (broadcast to
+    delta[..., 0]) orients e where delta = 0."""
     alpha = np.arctan2(delta[..., 1], delta[..., 0])
     if dim == 2:
-        return np.stack([a * np.cos(alpha), a * np.sin(alpha)], -1)
-    rxy = np.hypot(delta[..., 0], delta[..., 1])
-    beta = np.arctan2(rxy / a, delta[..., 2] / b)
-    return np.stack([a * np.cos(alpha) * np.sin(beta), a * np.sin(alpha) * np.sin(beta),
-                     b * np.cos(beta)], -1)
+        e = np.stack([a * np.cos(alpha), a * np.sin(alpha)], -1)
+    else:
+        rxy = np.hypot(delta[..., 0], delta[..., 1])
+        beta = np.arctan2(rxy / a, delta[..., 2] / b)
+        e = np.stack([a * np.cos(alpha) * np.sin(beta), a * np.sin(alpha) * np.sin(beta),
+                      b * np.cos(beta) * np.ones_like(alpha)], -1)
+    zero = np.all(delta == 0.0, axis=-1)
+    if np.any(zero):
+        e = np.where(zero[..., None], e * np.broadcast_to(np.asarray(sign, float),
+                                                           zero.shape)[..., None], e)
+    return e
 
 
 def d_step(e, delta, lam, rho):
@@ -204,6 +214,8 @@ def solve(prob: MAProblem, iters: int, tol: float = -1.0, xi0=None, want_hist=Fa
     Kinv = [kkt_inverse(Q0, A_fo, Aeq, r, N) for r in rhos]
     e_bd = boundary_values(prob.start, prob.goal)          # [N, dim, 6]
     a_ag, b_ag = 2.0 * prob.radius, 2.0 * prob.height
+    ag_pairs, _ = pair_lists(N, n_o)
+    sgn = np.array([1.0 if i < j else -1.0 for (i, j) in ag_pairs])[:, None]
     if n_o:
         a_ob = prob.radius + np.asarray(prob.obs_radii, float)
         b_ob = prob.height + np.asarray(prob.obs_radii, float)
@@ -219,7 +231,7 @@ def solve(prob: MAProblem, iters: int, tol: float = -1.0, xi0=None, want_hist=Fa
     lam_ob = np.zeros_like(dob)
     level = 0
     rho = rhos[level]
-    e_ag = direction(dag, a_ag, b_ag, dim)
+    e_ag = direction(dag, a_ag, b_ag, dim, sgn)
     d_ag = d_step(e_ag, dag, lam_ag, rho)
     if n_o:
         e_ob = direction(dob, a_ob_rows, b_ob_rows, dim)
@@ -239,7 +251,7 @@ def solve(prob: MAProblem, iters: int, tol: float = -1.0, xi0=None, want_hist=Fa
         pos = np.einsum("tk,iak->ita", P, xi)
         dag, dob = _deltas(prob, pos)
         # alpha, beta (eqs. com_alpha_i, com_beta_i), d (eq. com_d_i) with lambda^k
-        e_ag = direction(dag, a_ag, b_ag, dim)
+        e_ag = direction(dag, a_ag, b_ag, dim, sgn)
         d_ag = d_step(e_ag, dag, lam_ag, rho)
         r_ag = dag - d_ag[..., None] * e_ag
         lam_ag = lam_ag + rho * r_ag                      # eqs. update_lamda_*

@@ -11,31 +11,10 @@
 //  * Obstacle packing: moving ellipses/ellipsoids into the float4 records the
 //    solve kernel reads, with a per-problem flag for non-finite data.
 #include "internal.cuh"
+#include "basis.cuh"
 #include <math.h>
 
 namespace tb {
-
-__device__ double bern_d(int n, int i, double tau) {
-  if (i < 0 || i > n) return 0.0;
-  double c = 1.0;
-  for (int k = 1; k <= i; ++k) c = c * (double)(n - i + k) / (double)k;
-  double p = 1.0;
-  for (int k = 0; k < i; ++k) p *= tau;
-  for (int k = 0; k < n - i; ++k) p *= (1.0 - tau);
-  return c * p;
-}
-
-// Unscaled basis values at grid point t of an n_p-point horizon (FP64).
-__device__ void basis_row(int n_p, int t, double *P, double *dB, double *ddB) {
-  const int n = NC - 1;
-  double tau = (double)t / (double)(n_p - 1);
-  for (int i = 0; i < NC; ++i) {
-    P[i] = bern_d(n, i, tau);
-    dB[i] = n * (bern_d(n - 1, i - 1, tau) - bern_d(n - 1, i, tau));
-    ddB[i] = n * (n - 1) *
-             (bern_d(n - 2, i - 2, tau) - 2.0 * bern_d(n - 2, i - 1, tau) + bern_d(n - 2, i, tau));
-  }
-}
 
 __global__ void k_tables(const int *horizons, const int *offsets, float *tables) {
   const int h = blockIdx.x;

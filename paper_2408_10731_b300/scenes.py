@@ -302,3 +302,113 @@ def normal_draws(seed: int, shape) -> np.ndarray:
     """Host-side standard normal draws (float32-exact) for sampler parity runs."""
     rng = np.random.default_rng(seed)
     return f32(rng.standard_normal(shape))
+
+
+# ---- multi-agent scenes (Paper IV benchmarks) ---------------------------------------
+@dataclasses.dataclass
+class MAScenes:
+    """A batch of multi-agent scenes with a common agent count and grid."""
+    dim: int
+    n_steps: int
+    duration: np.ndarray      # [S]
+    start: np.ndarray         # [S, N, dim]
+    goal: np.ndarray          # [S, N, dim]
+    radius: np.ndarray        # [S] agent radius r
+    height: np.ndarray        # [S] agent half-height h (3D)
+    obs_offsets: np.ndarray   # [S + 1]
+    obs_centers: np.ndarray   # [n_obs, dim]
+    obs_radii: np.ndarray     # [n_obs]
+    name: str = ""
+
+    @property
+    def n_scenes(self):
+        return self.start.shape[0]
+
+    @property
+    def n_agents(self):
+        return self.start.shape[1]
+
+
+def _ma_pack(dim, n_steps, T, start, goal, radius, obs, name):
+    S = start.shape[0]
+    offs = np.zeros(S + 1, np.int32)
+    cen, rad = [], []
+    for s in range(S):
+        c, r = obs[s] if obs else (np.zeros((0, dim)), np.zeros(0))
+        offs[s + 1] = offs[s] + len(r)
+        cen.append(c)
+        rad.append(r)
+    return MAScenes(dim=dim, n_steps=n_steps, duration=np.full(S, float(T)),
+                    start=f32(start), goal=f32(goal), radius=np.full(S, radius, np.float32),
+                    height=np.full(S, radius, np.float32), obs_offsets=offs,
+                    obs_centers=f32(np.concatenate(cen)) if cen else np.zeros((0, dim), np.float32),
+                    obs_radii=f32(np.concatenate(rad)) if rad else np.zeros(0, np.float32),
+                    name=name)
+
+
+def ma_square(seed: int, n_scenes: int, n_agents: int, dim: int = 3, side: float = 8.0,
+              radius: float = 0.25, jitter: float = 0.05, T: float = 10.0,
+              n_steps: int = 100) -> MAScenes:
+    """Square benchmark of Paper IV: agents evenly spaced on the perimeter of a
+    side x side square (a random phase per scene), each going to the antipodal
+    point through the centre; every coordinate jittered by U(-jitter, jitter);
+    3D agents fly at z = 1 m. Agents are spheres (h = r)."""
+    rng = np.random.default_rng(seed)
+    start = np.zeros((n_scenes, n_agents, dim))
+    goal = np.zeros_like(start)
+    ctr = np.array([side / 2, side / 2])
+    for s in range(n_scenes):
+        phase = rng.uniform(0, 4 * side / n_agents)
+        for k in range(n_agents):
+            u = (phase + k * 4 * side / n_agents) % (4 * side)
+            e, f = int(u // side), u % side
+            p = [np.array([f, 0.0]), np.array([side, f]), np.array([side - f, side]),
+                 np.array([0.0, side - f])][e]
+            start[s, k, :2] = p
+            goal[s, k, :2] = 2 * ctr - p
+        if dim == 3:
+            start[s, :, 2] = 1.0
+            goal[s, :, 2] = 1.0
+        start[s] += rng.uniform(-jitter, jitter, (n_agents, dim))
+        goal[s] += rng.uniform(-jitter, jitter, (n_agents, dim))
+    return _ma_pack(dim, n_steps, T, start, goal, radius, None,
+                    f"ma_square_{n_agents}_seed{seed}")
+
+
+def _separated(rng, n, lo, hi, min_sep, avoid=None):
+    pts = []
+    while len(pts) < n:
+        p = rng.uniform(lo, hi)
+        if all(np.linalg.norm(p - q) >= min_sep for q in pts):
+            pts.append(p)
+    return np.array(pts)
+
+
+def ma_random(seed: int, n_scenes: int, n_agents: int, dim: int = 3, room: float = 8.0,
+              radius: float = 0.25, n_obstacles: int = 0, obs_radius=(0.2, 0.4),
+              T: float = 10.0, n_steps: int = 100) -> MAScenes:
+    """Random benchmark of Paper IV: starts and goals uniform in a room x room
+    square (3D: z in [0.5, 1.5] m) with pairwise separation >= 2r + 0.2 m among the
+    starts and among the goals (rejection sampling); optionally n_obstacles static
+    spheres of radius U(obs_radius), centres uniform in the room, redrawn while one
+    covers a start or goal with margin r + 0.1 m."""
+    rng = np.random.default_rng(seed)
+    lo = np.array([0.0, 0.0, 0.5])[:dim]
+    hi = np.array([room, room, 1.5])[:dim]
+    start = np.zeros((n_scenes, n_agents, dim))
+    goal = np.zeros_like(start)
+    obs = []
+    for s in range(n_scenes):
+        start[s] = _separated(rng, n_agents, lo, hi, 2 * radius + 0.2)
+        goal[s] = _separated(rng, n_agents, lo, hi, 2 * radius + 0.2)
+        cen, rad = [], []
+        while len(cen) < n_obstacles:
+            c = rng.uniform(lo, hi)
+            r = rng.uniform(*obs_radius)
+            ends = np.concatenate([start[s], goal[s]])
+            if np.all(np.linalg.norm(ends - c, axis=1) >= r + radius + 0.1):
+                cen.append(c)
+                rad.append(r)
+        obs.append((np.array(cen).reshape(-1, dim), np.array(rad)))
+    return _ma_pack(dim, n_steps, T, start, goal, radius, obs if n_obstacles else None,
+                    f"ma_random_{n_agents}_seed{seed}")

@@ -165,3 +165,20 @@ def test_penalty_ladder_of_growth_one_is_the_fixed_penalty():
     p3 = _prob(start, goal, n_p=40, rho=1.5, rho_levels=4, rho_growth=2.0, rho_every=10)
     c = ma.solve(p3, 30)
     assert np.abs(c["xi"] - a["xi"]).max() > 1e-6
+
+
+def test_coincident_agents_are_pushed_apart():
+    """Reading M2 at delta = 0: the pair (i, j), i < j, gets e = (0, 0, b) and (j, i)
+    the opposite, so that every multiplier stays odd in the pair and two agents
+    that start on top of each other separate (3D: vertically)."""
+    e = ma.direction(np.zeros((2, 3)), 0.6, 0.8, 3, np.array([1.0, -1.0]))
+    np.testing.assert_allclose(e, [[0, 0, 0.8], [0, 0, -0.8]])
+    start = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]])
+    goal = np.array([[5.0, 0.0, 1.0], [5.0, 0.0, 1.0]])
+    prob = _prob(start, goal, r=0.3, h=0.3, n_p=40, T=5.0, rho=2.0)
+    out = ma.solve(prob, 60)
+    pos = ma.positions(prob, out["xi"])
+    mid = pos[:, 20]
+    assert mid[0, 2] - mid[1, 2] > 0.1          # agent 0 above agent 1 mid-way
+    np.testing.assert_allclose(pos[0, :, 2] + pos[1, :, 2], 2.0, atol=1e-9)
+    np.testing.assert_allclose(out["lam_ag"][0], -out["lam_ag"][1], atol=1e-12)
