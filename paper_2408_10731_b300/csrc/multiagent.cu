@@ -47,7 +47,7 @@ namespace {
 constexpr int MA_NE = 6;             // boundary rows: p, p', p'' at both ends
 constexpr int MA_NK = NC + MA_NE;    // 17
 constexpr int MA_MAX_AGENTS = 64;
-constexpr int MA_THREADS = 512;
+constexpr int MA_THREADS = 1024;
 // constants of one scene and penalty level (floats): six (hi, lo) matrices
 constexpr int MA_G_M = 0, MA_H_M = 242, MA_E_M = 484, MA_G_D = 616, MA_H_D = 858, MA_E_D = 1100;
 constexpr int MA_LEVEL_FLOATS = 1232;
@@ -74,7 +74,7 @@ struct MaArgs {
 
 // shared-memory carve-up in floats (identical on host and device)
 struct MaSmem {
-  int P, PT, xbar, xbar_n, dlt0, dlt1, u, ubar, pos, w, Lold, lam, pairs, se, red, total;
+  int P, xbar, xbar_n, dlt0, dlt1, u, ubar, pos, w, Lold, lam, pairs, se, red, total;
 };
 
 __host__ __device__ inline MaSmem ma_smem(int dim, int N, int n_p, int npairs, bool lam_in_smem) {
@@ -82,7 +82,6 @@ __host__ __device__ inline MaSmem ma_smem(int dim, int N, int n_p, int npairs, b
   int o = 0;
   auto take = [&](int n) { int r = o; o += (n + 3) & ~3; return r; };
   m.P = take(n_p * ROW);
-  m.PT = take(NC * n_p);
   m.xbar = take(2 * dim * NC); // (hi, lo) halves
   m.xbar_n = take(2 * dim * NC);
   m.dlt0 = take(2 * N * dim * NC);
@@ -224,48 +223,50 @@ __global__ void k_ma_setup(int N, int n_p, const double *Tarr, const int *obs_of
 }
 
 // ---- solve --------------------------------------------------------------------
-// e of eqs. com_alpha_i / com_beta_i in closed form: delta / R, R the spheroid
-// norm of delta; at delta = 0 the angles are 0: e = (0, 0, b) in 3D, (a, 0) in 2D.
-template <int DIM>
-__device__ __forceinline__ void ma_direction(const float (&dl)[DIM], float a, float b,
-                                             float (&e)[DIM]) {
-  float R2;
-  if constexpr (DIM == 3) R2 = (dl[0] * dl[0] + dl[1] * dl[1]) / (a * a) + dl[2] * dl[2] / (b * b);
-  else R2 = (dl[0] * dl[0] + dl[1] * dl[1]) / (a * a);
-  if (R2 > 0.f) {
-    const float R = sqrtf(R2);
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) e[k] = dl[k] / R;
-  } else {
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) e[k] = 0.f;
-    if constexpr (DIM == 3) e[2] = b;
-    else e[0] = a;
-  }
-}
-
-// d-step (eq. com_d_i, d >= 1), residual r = delta - d e, and the multiplier
-// update lambda += rho r (skipped in the initial pass, which stores r instead).
+// One pair at one grid point: e of eqs. com_alpha_i / com_beta_i in closed form,
+// e = delta / R with R the spheroid norm of delta (R^2 = (dx^2 + dy^2) / a^2 +
+// dz^2 / b^2); the d-step of eq. com_d_i, d = max(1, e.(delta + lambda / rho) / e.e)
+// = max(1, R delta.(delta + lambda / rho) / |delta|^2); the residual
+// r = delta - d e = delta (1 - d / R); and the multiplier update lambda += rho r in
+// place (the initial pass, lambda = 0, leaves r instead). At delta = 0 the angles
+// are 0: e = (0, 0, b) in 3D, (a, 0) in 2D. ia2 = 1 / a^2, ib2 = 1 / b^2.
 // Returns ||r||.
 template <int DIM>
-__device__ __forceinline__ float ma_pair(const float (&dl)[DIM], float a, float b, float *lam,
-                                         int stride, float rho, float irho, bool init) {
-  float e[DIM], lm[DIM];
-  ma_direction<DIM>(dl, a, b, e);
-  float num = 0.f, den = 0.f;
+__device__ __forceinline__ float ma_pair(const float (&dl)[DIM], float a, float b, float ia2,
+                                         float ib2, float (&lm)[DIM], float rho, float irho,
+                                         bool init) {
+  if (init) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) lm[k] = 0.f;
+  }
+  float n2 = 0.f, num = 0.f;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    lm[k] = init ? 0.f : lam[k * stride];
-    num = fmaf(e[k], fmaf(lm[k], irho, dl[k]), num);
-    den = fmaf(e[k], e[k], den);
+    n2 = fmaf(dl[k], dl[k], n2);
+    num = fmaf(dl[k], fmaf(lm[k], irho, dl[k]), num);
   }
-  const float d = fmaxf(num / den, 1.f);
+  float r[DIM];
+  if (n2 > 0.f) {
+    float R2;
+    if constexpr (DIM == 3) R2 = fmaf(dl[2] * dl[2], ib2, (dl[0] * dl[0] + dl[1] * dl[1]) * ia2);
+    else R2 = n2 * ia2;
+    const float R = sqrtf(R2);
+    const float d = fmaxf(R * num / n2, 1.f);
+    const float f = 1.f - d / R;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) r[k] = dl[k] * f;
+  } else {
+    const int ax = DIM == 3 ? 2 : 0;
+    const float ee = DIM == 3 ? b : a;
+    const float d = fmaxf(lm[ax] * irho / ee, 1.f);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) r[k] = k == ax ? -d * ee : 0.f;
+  }
   float rr = 0.f;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    const float r = fmaf(-d, e[k], dl[k]);
-    rr = fmaf(r, r, rr);
-    lam[k * stride] = init ? r : fmaf(rho, r, lm[k]);
+    rr = fmaf(r[k], r[k], rr);
+    lm[k] = init ? r[k] : fmaf(rho, r[k], lm[k]);
   }
   return sqrtf(rr);
 }
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
   float *sm = reinterpret_cast<float *>(sm4);
   const int s = blockIdx.x, N = A.N, n_p = A.n_p, npairs = A.npairs;
   const MaSmem L = ma_smem(DIM, N, n_p, npairs, A.lam_in_smem != 0);
-  float *Ps = sm + L.P, *PT = sm + L.PT, *xbar = sm + L.xbar, *xbar_n = sm + L.xbar_n;
+  float *Ps = sm + L.P, *xbar = sm + L.xbar, *xbar_n = sm + L.xbar_n;
   float *u = sm + L.u, *ubar = sm + L.ubar;
   float *pos = sm + L.pos, *w = sm + L.w, *Lold = sm + L.Lold, *red = sm + L.red;
   // bv[(i DIM + a) 4 + {0,1,2,3}]: (start hi, lo, goal hi, lo) of agent i's deviation from
@@ -307,15 +308,18 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
   const int xsz = DIM * NC, dsz = N * DIM * NC; // offsets of the lo halves
   const int tid = threadIdx.x, nth = blockDim.x;
   const int plane = DIM * n_p;
+  // grid-point-major work split: thread -> (grid point t_me, slot); nslot slots per point
+  const int nslot = nth / n_p, t_me = tid % n_p, slot = tid / n_p;
+  const bool on = slot < nslot;
   float *lam = A.lam_in_smem ? sm + L.lam : A.lam_ag + (size_t)s * npairs * plane;
   const int ob0 = A.obs_off[s], n_o = A.obs_off[s + 1] - ob0;
   float *lamo = A.lam_ob + (size_t)ob0 * N * plane;
   const float2 shp = A.shape[s];
   const float a_ag = 2.f * shp.x, b_ag = 2.f * shp.y;
+  const float ia2_ag = 1.f / (a_ag * a_ag), ib2_ag = 1.f / (b_ag * b_ag);
 
   // tables, boundary values, pair list
   for (int e = tid; e < n_p * ROW; e += nth) Ps[e] = A.P[e];
-  for (int e = tid; e < NC * n_p; e += nth) PT[e] = A.P[(e % n_p) * ROW + e / n_p];
   for (int e = tid; e < N * DIM; e += nth) {
     st[e] = A.start[(size_t)s * N * DIM + e];
     gl[e] = A.goal[(size_t)s * N * DIM + e];
@@ -327,6 +331,9 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
     pairs[p] = i | ((i + 1 + rem) << 16);
   }
   __syncthreads();
+  float Prow[NC]; // position basis at this thread's grid point
+#pragma unroll
+  for (int q = 0; q < NC; ++q) Prow[q] = Ps[t_me * ROW + q];
   for (int e = tid; e < 2 * DIM; e += nth) { // compensated agent means
     const int a = e % DIM;
     const float *src = e < DIM ? st : gl;
@@ -428,43 +435,71 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
       float *tmp = dlt; dlt = dlt_n; dlt_n = tmp;
       __syncthreads();
     }
-    // positions on the grid
-    for (int e = tid; e < N * plane; e += nth) {
-      const int ia = e / n_p, t = e % n_p, a = ia % DIM;
-      const float *xd = dlt + ia * NC, *xb = xbar + a * NC;
-      float acc = 0.f, acl = 0.f;
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        float ch, cl;
-        two_sum(xb[q], xd[q], ch, cl);
-        cl += xb[xsz + q] + xd[dsz + q];
-        acc = fmaf(PT[q * n_p + t], ch, acc);
-        acl = fmaf(PT[q * n_p + t], cl, acl);
-      }
-      pos[e] = acc + acl;
+    // positions on the grid from xi = xi_bar + dlt as an exact float pair (cc, in the
+    // free second iterate buffer)
+    float *cc = dlt_n;
+    for (int e = tid; e < dsz; e += nth) {
+      const int a = (e / NC) % DIM, q = e % NC;
+      float ch, cl;
+      two_sum(xbar[a * NC + q], dlt[e], ch, cl);
+      cc[e] = ch;
+      cc[dsz + e] = cl + (xbar[xsz + a * NC + q] + dlt[dsz + e]);
     }
+    __syncthreads();
+    if (on)
+      for (int ia = slot; ia < N * DIM; ia += nslot) {
+        const float *ch = cc + ia * NC, *cl = cc + dsz + ia * NC;
+        float acc = 0.f, acl = 0.f;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          acc = fmaf(Prow[q], ch[q], acc);
+          acl = fmaf(Prow[q], cl[q], acl);
+        }
+        pos[ia * n_p + t_me] = acc + acl;
+      }
     __syncthreads();
     // pair pass (eqs. com_alpha_i, com_beta_i, com_d_i, update_lamda_*)
     const float irho = 1.f / rho;
     float rmax = 0.f;
-    for (int q = tid; q < npairs * n_p; q += nth) {
-      const int p = q / n_p, t = q % n_p, pr = pairs[p], i = pr & 0xffff, j = pr >> 16;
-      float dl[DIM];
+    if (on) {
+      // the next pair's multipliers are loaded while the current pair is computed
+      float nxt[DIM] = {};
+      if (!init && slot < npairs)
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) dl[a] = pos[(i * DIM + a) * n_p + t] - pos[(j * DIM + a) * n_p + t];
-      const float r = ma_pair<DIM>(dl, a_ag, b_ag, lam + (size_t)p * plane + t, n_p, rho, irho, init);
-      rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
-    }
-    for (int q = tid; q < N * n_o * n_p; q += nth) {
-      const int io = q / n_p, t = q % n_p, i = io / n_o, o = io % n_o;
-      const float4 ob = A.obs[ob0 + o];
-      const float ctr[3] = {ob.x, ob.y, ob.z};
-      float dl[DIM];
+        for (int a = 0; a < DIM; ++a) nxt[a] = lam[(size_t)slot * plane + a * n_p + t_me];
+      for (int p = slot; p < npairs; p += nslot) {
+        float lm[DIM];
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) dl[a] = pos[(i * DIM + a) * n_p + t] - ctr[a];
-      const float r = ma_pair<DIM>(dl, shp.x + ob.w, shp.y + ob.w,
-                                   lamo + ((size_t)o * N + i) * plane + t, n_p, rho, irho, init);
-      rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
+        for (int a = 0; a < DIM; ++a) lm[a] = nxt[a];
+        if (!init && p + nslot < npairs)
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) nxt[a] = lam[(size_t)(p + nslot) * plane + a * n_p + t_me];
+        const int pr = pairs[p], i = pr & 0xffff, j = pr >> 16;
+        float dl[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) dl[a] = pos[(i * DIM + a) * n_p + t_me] - pos[(j * DIM + a) * n_p + t_me];
+        const float r = ma_pair<DIM>(dl, a_ag, b_ag, ia2_ag, ib2_ag, lm, rho, irho, init);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) lam[(size_t)p * plane + a * n_p + t_me] = lm[a];
+        rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
+      }
+      for (int io = slot; io < N * n_o; io += nslot) {
+        const int i = io / n_o, o = io % n_o;
+        const float4 ob = A.obs[ob0 + o];
+        const float ctr[3] = {ob.x, ob.y, ob.z};
+        float dl[DIM], lm[DIM];
+        float *lp = lamo + ((size_t)o * N + i) * plane + t_me;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          dl[a] = pos[(i * DIM + a) * n_p + t_me] - ctr[a];
+          lm[a] = init ? 0.f : lp[a * n_p];
+        }
+        const float ao = shp.x + ob.w, bo = shp.y + ob.w;
+        const float r = ma_pair<DIM>(dl, ao, bo, 1.f / (ao * ao), 1.f / (bo * bo), lm, rho, irho, init);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) lp[a * n_p] = lm[a];
+        rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
+      }
     }
     block_max(rmax, red, red + 32);
     res = red[32];
@@ -473,22 +508,35 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
     if (k == A.max_iters) break;
     // w_i from the new and old multiplier sums
     const float c1 = 1.f / rho + 1.f / rho_n, c0 = 1.f / rho;
-    for (int e = tid; e < N * plane; e += nth) {
-      const int ia = e / n_p, t = e % n_p, i = ia / DIM, a = ia % DIM;
-      // pairs (j, i), j < i, enter with the opposite sign; pair (i, j), j > i, is
-      // record i (2N - i - 1) / 2 + (j - i - 1), consecutive in j
-      const float *lt = lam + a * n_p + t;
-      float up = 0.f, dn = 0.f;
-#pragma unroll 4
-      for (int j = 0; j < i; ++j) dn += lt[(size_t)(j * (2 * N - j - 1) / 2 + (i - j - 1)) * plane];
-      const int base = i * (2 * N - i - 1) / 2 - i - 1;
-#pragma unroll 4
-      for (int j = i + 1; j < N; ++j) up += lt[(size_t)(base + j) * plane];
-      float acc = 2.f * (up - dn);
-      for (int o = 0; o < n_o; ++o) acc += lamo[((size_t)o * N + i) * plane + a * n_p + t];
-      w[e] = init ? acc : c1 * acc - c0 * Lold[e]; // Lold is not yet written at init
-      Lold[e] = init ? 0.f : acc;
-    }
+    if (on)
+      for (int i = slot; i < N; i += nslot) {
+        // pairs (j, i), j < i, enter with the opposite sign; record of (j, i) is
+        // j (2N - j - 1) / 2 + (i - j - 1), of (i, j), j > i, i (2N - i - 1) / 2 + (j - i - 1)
+        const float *lt = lam + t_me;
+        float up[DIM], dn[DIM], ob[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) { up[a] = 0.f; dn[a] = 0.f; ob[a] = 0.f; }
+        int p = i - 1;
+        for (int j = 0; j < i; ++j) {
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) dn[a] += lt[(size_t)p * plane + a * n_p];
+          p += N - j - 2;
+        }
+        p = i * (2 * N - i - 1) / 2;
+        for (int j = i + 1; j < N; ++j, ++p)
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) up[a] += lt[(size_t)p * plane + a * n_p];
+        for (int o = 0; o < n_o; ++o)
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) ob[a] += lamo[((size_t)o * N + i) * plane + a * n_p + t_me];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const int e = (i * DIM + a) * n_p + t_me;
+          const float acc = 2.f * (up[a] - dn[a]) + ob[a];
+          w[e] = init ? acc : c1 * acc - c0 * Lold[e]; // Lold is not yet written at init
+          Lold[e] = init ? 0.f : acc;
+        }
+      }
     __syncthreads();
     if (init) { // the initial pass stored r in the multiplier slots: lambda^0 = 0
       for (int e = tid; e < npairs * plane; e += nth) lam[e] = 0.f;
