@@ -74,7 +74,7 @@ struct MaArgs {
 
 // shared-memory carve-up in floats (identical on host and device)
 struct MaSmem {
-  int P, xbar, xbar_n, dlt0, dlt1, u, ubar, pos, w, Lold, lam, pairs, se, red, total;
+  int P, xbar, xbar_n, dlt0, dlt1, u, ubar, pos, w, Lold, lam, se, red, total;
 };
 
 __host__ __device__ inline MaSmem ma_smem(int dim, int N, int n_p, int npairs, bool lam_in_smem) {
@@ -92,7 +92,6 @@ __host__ __device__ inline MaSmem ma_smem(int dim, int N, int n_p, int npairs, b
   m.w = take(N * dim * n_p);
   m.Lold = take(N * dim * n_p);
   m.lam = lam_in_smem ? take(npairs * dim * n_p) : 0;
-  m.pairs = take(npairs);
   m.se = take(2 * N * dim + 4 * (N + 1) * dim); // start, goal; deviations and means (hi, lo)
   m.red = take(64);
   m.total = o;
@@ -230,7 +229,7 @@ __global__ void k_ma_setup(int N, int n_p, const double *Tarr, const int *obs_of
 // r = delta - d e = delta (1 - d / R); and the multiplier update lambda += rho r in
 // place (the initial pass, lambda = 0, leaves r instead). At delta = 0 the angles
 // are 0: e = (0, 0, b) in 3D, (a, 0) in 2D. ia2 = 1 / a^2, ib2 = 1 / b^2.
-// Returns ||r||.
+// Returns ||r||^2.
 template <int DIM>
 __device__ __forceinline__ float ma_pair(const float (&dl)[DIM], float a, float b, float ia2,
                                          float ib2, float (&lm)[DIM], float rho, float irho,
@@ -268,7 +267,7 @@ __device__ __forceinline__ float ma_pair(const float (&dl)[DIM], float a, float 
     rr = fmaf(r[k], r[k], rr);
     lm[k] = init ? r[k] : fmaf(rho, r[k], lm[k]);
   }
-  return sqrtf(rr);
+  return rr;
 }
 
 // (s, e) with s + e = a + b exactly (Knuth's TwoSum)
@@ -303,7 +302,6 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
   // bv[(i DIM + a) 4 + {0,1,2,3}]: (start hi, lo, goal hi, lo) of agent i's deviation from
   // the agent mean (i < N) and of the mean itself (i = N), as exact float pairs
   float *st = sm + L.se, *gl = st + N * DIM, *bv = gl + N * DIM;
-  int *pairs = reinterpret_cast<int *>(sm + L.pairs);
   float *dlt = sm + L.dlt0, *dlt_n = sm + L.dlt1;
   const int xsz = DIM * NC, dsz = N * DIM * NC; // offsets of the lo halves
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -323,12 +321,6 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
   for (int e = tid; e < N * DIM; e += nth) {
     st[e] = A.start[(size_t)s * N * DIM + e];
     gl[e] = A.goal[(size_t)s * N * DIM + e];
-  }
-  for (int p = tid; p < npairs; p += nth) {
-    // p -> (i, j), i < j, row-major over the strict upper triangle
-    int i = 0, rem = p;
-    while (rem >= N - 1 - i) { rem -= N - 1 - i; ++i; }
-    pairs[p] = i | ((i + 1 + rem) << 16);
   }
   __syncthreads();
   float Prow[NC]; // position basis at this thread's grid point
@@ -391,9 +383,16 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
       for (int e = tid; e < N * DIM * NC; e += nth) {
         const int ia = e / NC, kk = e % NC;
         const float *wr = w + ia * n_p;
-        float acc = 0.f;
-        for (int t = 0; t < n_p; ++t) acc = fmaf(Ps[t * ROW + kk], wr[t], acc);
-        u[e] = acc;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f; // four chains for latency
+        int t = 0;
+        for (; t + 3 < n_p; t += 4) {
+          a0 = fmaf(Ps[t * ROW + kk], wr[t], a0);
+          a1 = fmaf(Ps[(t + 1) * ROW + kk], wr[t + 1], a1);
+          a2 = fmaf(Ps[(t + 2) * ROW + kk], wr[t + 2], a2);
+          a3 = fmaf(Ps[(t + 3) * ROW + kk], wr[t + 3], a3);
+        }
+        for (; t < n_p; ++t) a0 = fmaf(Ps[t * ROW + kk], wr[t], a0);
+        u[e] = (a0 + a1) + (a2 + a3);
       }
       __syncthreads();
       for (int e = tid; e < DIM * NC; e += nth) {
@@ -412,13 +411,19 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
         const float *xl = x + (mean ? xsz : dsz);
         const float *uu = mean ? ubar + a * NC : u + (i * DIM + a) * NC;
         const float *ub = ubar + a * NC;
-        float hi = 0.f, lo = 0.f;
+        float hi = 0.f, lo = 0.f, h2 = 0.f, l2 = 0.f; // two chains: G x and H u
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
           df_fma(hi, lo, C[oG + kk * NC + q], C[oG + 121 + kk * NC + q], x[q]);
           lo = fmaf(C[oG + kk * NC + q], xl[q], lo);
           const float uq = mean ? -uu[q] : ub[q] - uu[q];
-          df_fma(hi, lo, C[oH + kk * NC + q], C[oH + 121 + kk * NC + q], uq);
+          df_fma(h2, l2, C[oH + kk * NC + q], C[oH + 121 + kk * NC + q], uq);
+        }
+        {
+          float sh, sl;
+          two_sum(hi, h2, sh, sl);
+          hi = sh;
+          lo = lo + (l2 + sl);
         }
         const float *b4 = bv + (i * DIM + a) * 4; // i = N: the mean
         df_fma(hi, lo, C[oE + kk * MA_NE + 0], C[oE + 66 + kk * MA_NE + 0], b4[0]);
@@ -461,78 +466,89 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
     // pair pass (eqs. com_alpha_i, com_beta_i, com_d_i, update_lamda_*)
     const float irho = 1.f / rho;
     float rmax = 0.f;
-    if (on) {
-      // the next pair's multipliers are loaded while the current pair is computed
-      float nxt[DIM] = {};
-      if (!init && slot < npairs)
+    if (on)
+      // rows of the pair triangle (agent i with every j > i) in snake order over the
+      // slots, so that each slot gets about npairs / nslot pairs; the row owner also
+      // takes agent i's obstacles and leaves 2 sum_{j>i} lambda_ij + sum_o lambda_io
+      // (the part of agent i's multiplier sum it can form alone) in w
+      for (int kb = 0; kb * nslot < N; ++kb) {
+        const int i = kb * nslot + ((kb & 1) ? nslot - 1 - slot : slot);
+        if (i >= N) continue;
+        float pi[DIM], part[DIM];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) nxt[a] = lam[(size_t)slot * plane + a * n_p + t_me];
-      for (int p = slot; p < npairs; p += nslot) {
-        float lm[DIM];
+        for (int a = 0; a < DIM; ++a) { pi[a] = pos[(i * DIM + a) * n_p + t_me]; part[a] = 0.f; }
+        const int p0 = i * (2 * N - i - 1) / 2, np_row = N - 1 - i;
+        float nxt[DIM] = {};
+        if (!init && np_row > 0)
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) lm[a] = nxt[a];
-        if (!init && p + nslot < npairs)
+          for (int a = 0; a < DIM; ++a) nxt[a] = lam[(size_t)p0 * plane + a * n_p + t_me];
+        for (int jj = 0; jj < np_row; ++jj) {
+          const int p = p0 + jj, j = i + 1 + jj;
+          float lm[DIM];
 #pragma unroll
-          for (int a = 0; a < DIM; ++a) nxt[a] = lam[(size_t)(p + nslot) * plane + a * n_p + t_me];
-        const int pr = pairs[p], i = pr & 0xffff, j = pr >> 16;
-        float dl[DIM];
+          for (int a = 0; a < DIM; ++a) lm[a] = nxt[a];
+          if (!init && jj + 1 < np_row) // the next pair's multipliers, loaded early
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) dl[a] = pos[(i * DIM + a) * n_p + t_me] - pos[(j * DIM + a) * n_p + t_me];
-        const float r = ma_pair<DIM>(dl, a_ag, b_ag, ia2_ag, ib2_ag, lm, rho, irho, init);
+            for (int a = 0; a < DIM; ++a) nxt[a] = lam[(size_t)(p + 1) * plane + a * n_p + t_me];
+          float dl[DIM];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) lam[(size_t)p * plane + a * n_p + t_me] = lm[a];
-        rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
-      }
-      for (int io = slot; io < N * n_o; io += nslot) {
-        const int i = io / n_o, o = io % n_o;
-        const float4 ob = A.obs[ob0 + o];
-        const float ctr[3] = {ob.x, ob.y, ob.z};
-        float dl[DIM], lm[DIM];
-        float *lp = lamo + ((size_t)o * N + i) * plane + t_me;
+          for (int a = 0; a < DIM; ++a) dl[a] = pi[a] - pos[(j * DIM + a) * n_p + t_me];
+          const float r = ma_pair<DIM>(dl, a_ag, b_ag, ia2_ag, ib2_ag, lm, rho, irho, init);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          dl[a] = pos[(i * DIM + a) * n_p + t_me] - ctr[a];
-          lm[a] = init ? 0.f : lp[a * n_p];
+          for (int a = 0; a < DIM; ++a) {
+            lam[(size_t)p * plane + a * n_p + t_me] = lm[a];
+            part[a] += lm[a];
+          }
+          rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
         }
-        const float ao = shp.x + ob.w, bo = shp.y + ob.w;
-        const float r = ma_pair<DIM>(dl, ao, bo, 1.f / (ao * ao), 1.f / (bo * bo), lm, rho, irho, init);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) lp[a * n_p] = lm[a];
-        rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
+        for (int a = 0; a < DIM; ++a) part[a] *= 2.f;
+        for (int o = 0; o < n_o; ++o) {
+          const float4 ob = A.obs[ob0 + o];
+          const float ctr[3] = {ob.x, ob.y, ob.z};
+          float dl[DIM], lm[DIM];
+          float *lp = lamo + ((size_t)o * N + i) * plane + t_me;
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            dl[a] = pi[a] - ctr[a];
+            lm[a] = init ? 0.f : lp[a * n_p];
+          }
+          const float ao = shp.x + ob.w, bo = shp.y + ob.w;
+          const float r = ma_pair<DIM>(dl, ao, bo, 1.f / (ao * ao), 1.f / (bo * bo), lm, rho, irho, init);
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            lp[a * n_p] = lm[a];
+            part[a] += lm[a];
+          }
+          rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) w[(i * DIM + a) * n_p + t_me] = part[a];
       }
-    }
     block_max(rmax, red, red + 32);
-    res = red[32];
+    res = sqrtf(red[32]);
     k_done = k;
     if (!init && res <= A.tol) break;
     if (k == A.max_iters) break;
-    // w_i from the new and old multiplier sums
+    // w_i from the new and old multiplier sums: the row part left in w minus twice the
+    // column sum sum_{j<i} lambda_ji (record j (2N - j - 1) / 2 + (i - j - 1))
     const float c1 = 1.f / rho + 1.f / rho_n, c0 = 1.f / rho;
     if (on)
       for (int i = slot; i < N; i += nslot) {
-        // pairs (j, i), j < i, enter with the opposite sign; record of (j, i) is
-        // j (2N - j - 1) / 2 + (i - j - 1), of (i, j), j > i, i (2N - i - 1) / 2 + (j - i - 1)
         const float *lt = lam + t_me;
-        float up[DIM], dn[DIM], ob[DIM];
+        float dn[DIM];
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) { up[a] = 0.f; dn[a] = 0.f; ob[a] = 0.f; }
+        for (int a = 0; a < DIM; ++a) dn[a] = 0.f;
         int p = i - 1;
         for (int j = 0; j < i; ++j) {
 #pragma unroll
           for (int a = 0; a < DIM; ++a) dn[a] += lt[(size_t)p * plane + a * n_p];
           p += N - j - 2;
         }
-        p = i * (2 * N - i - 1) / 2;
-        for (int j = i + 1; j < N; ++j, ++p)
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) up[a] += lt[(size_t)p * plane + a * n_p];
-        for (int o = 0; o < n_o; ++o)
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) ob[a] += lamo[((size_t)o * N + i) * plane + a * n_p + t_me];
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
           const int e = (i * DIM + a) * n_p + t_me;
-          const float acc = 2.f * (up[a] - dn[a]) + ob[a];
+          const float acc = w[e] - 2.f * dn[a];
           w[e] = init ? acc : c1 * acc - c0 * Lold[e]; // Lold is not yet written at init
           Lold[e] = init ? 0.f : acc;
         }
