@@ -230,11 +230,10 @@ __global__ void k_ma_setup(int N, int n_p, const double *Tarr, const int *obs_of
 // place (the initial pass, lambda = 0, leaves r instead). At delta = 0 the angles
 // are 0: e = (0, 0, b) in 3D, (a, 0) in 2D. ia2 = 1 / a^2, ib2 = 1 / b^2.
 // Returns ||r||^2.
-template <int DIM>
+template <int DIM, bool INIT>
 __device__ __forceinline__ float ma_pair(const float (&dl)[DIM], float a, float b, float ia2,
-                                         float ib2, float (&lm)[DIM], float rho, float irho,
-                                         bool init) {
-  if (init) {
+                                         float ib2, float (&lm)[DIM], float rho, float irho) {
+  if (INIT) {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) lm[k] = 0.f;
   }
@@ -265,9 +264,81 @@ __device__ __forceinline__ float ma_pair(const float (&dl)[DIM], float a, float 
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
     rr = fmaf(r[k], r[k], rr);
-    lm[k] = init ? r[k] : fmaf(rho, r[k], lm[k]);
+    lm[k] = INIT ? r[k] : fmaf(rho, r[k], lm[k]);
   }
   return rr;
+}
+
+// The pair pass of one thread: rows of the pair triangle (agent i with every j > i)
+// in snake order over the slots, so that each slot gets about npairs / nslot pairs,
+// at grid point t_me; the row owner also takes agent i's obstacles and leaves
+// 2 sum_{j>i} lambda_ij + sum_o lambda_io (the part of agent i's multiplier sum it
+// can form alone) in w. Returns the largest ||r||^2 (NaN as +inf).
+template <int DIM, bool INIT>
+__device__ __forceinline__ float pair_rows(int N, int n_p, int nslot, int slot, int t_me,
+                                           const float *pos, float *lam, float *lamo,
+                                           const float4 *obs, int n_o, float2 shp, float rho,
+                                           float irho, float *w) {
+  const int plane = DIM * n_p;
+  const float a_ag = 2.f * shp.x, b_ag = 2.f * shp.y;
+  const float ia2 = 1.f / (a_ag * a_ag), ib2 = 1.f / (b_ag * b_ag);
+  float rmax = 0.f;
+  for (int kb = 0; kb * nslot < N; ++kb) {
+    const int i = kb * nslot + ((kb & 1) ? nslot - 1 - slot : slot);
+    if (i >= N) continue;
+    const float *pin = pos + i * plane + t_me;
+    float pi[DIM], part[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { pi[a] = pin[a * n_p]; part[a] = 0.f; }
+    const int np_row = N - 1 - i;
+    float *lp = lam + (size_t)(i * (2 * N - i - 1) / 2) * plane + t_me;
+    const float *pj = pin + plane;
+    float nxt[DIM] = {};
+    if (!INIT && np_row > 0)
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) nxt[a] = lp[a * n_p];
+    for (int jj = 0; jj < np_row; ++jj, lp += plane, pj += plane) {
+      float lm[DIM], dl[DIM];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) lm[a] = nxt[a];
+      if (!INIT && jj + 1 < np_row) // the next pair's multipliers, loaded early
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) nxt[a] = lp[plane + a * n_p];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) dl[a] = pi[a] - pj[a * n_p];
+      const float rr = ma_pair<DIM, INIT>(dl, a_ag, b_ag, ia2, ib2, lm, rho, irho);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        lp[a * n_p] = lm[a];
+        part[a] += lm[a];
+      }
+      rmax = fmaxf(rmax, rr != rr ? __int_as_float(0x7f800000) : rr);
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) part[a] *= 2.f;
+    float *lo = lamo + (size_t)i * plane + t_me;
+    for (int o = 0; o < n_o; ++o, lo += (size_t)N * plane) {
+      const float4 ob = obs[o];
+      const float ctr[3] = {ob.x, ob.y, ob.z};
+      float dl[DIM], lm[DIM];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        dl[a] = pi[a] - ctr[a];
+        lm[a] = INIT ? 0.f : lo[a * n_p];
+      }
+      const float ao = shp.x + ob.w, bo = shp.y + ob.w;
+      const float rr = ma_pair<DIM, INIT>(dl, ao, bo, 1.f / (ao * ao), 1.f / (bo * bo), lm, rho, irho);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        lo[a * n_p] = lm[a];
+        part[a] += lm[a];
+      }
+      rmax = fmaxf(rmax, rr != rr ? __int_as_float(0x7f800000) : rr);
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) w[i * plane + a * n_p + t_me] = part[a];
+  }
+  return rmax;
 }
 
 // (s, e) with s + e = a + b exactly (Knuth's TwoSum)
@@ -313,8 +384,6 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
   const int ob0 = A.obs_off[s], n_o = A.obs_off[s + 1] - ob0;
   float *lamo = A.lam_ob + (size_t)ob0 * N * plane;
   const float2 shp = A.shape[s];
-  const float a_ag = 2.f * shp.x, b_ag = 2.f * shp.y;
-  const float ia2_ag = 1.f / (a_ag * a_ag), ib2_ag = 1.f / (b_ag * b_ag);
 
   // tables, boundary values, pair list
   for (int e = tid; e < n_p * ROW; e += nth) Ps[e] = A.P[e];
@@ -467,64 +536,10 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
     const float irho = 1.f / rho;
     float rmax = 0.f;
     if (on)
-      // rows of the pair triangle (agent i with every j > i) in snake order over the
-      // slots, so that each slot gets about npairs / nslot pairs; the row owner also
-      // takes agent i's obstacles and leaves 2 sum_{j>i} lambda_ij + sum_o lambda_io
-      // (the part of agent i's multiplier sum it can form alone) in w
-      for (int kb = 0; kb * nslot < N; ++kb) {
-        const int i = kb * nslot + ((kb & 1) ? nslot - 1 - slot : slot);
-        if (i >= N) continue;
-        float pi[DIM], part[DIM];
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) { pi[a] = pos[(i * DIM + a) * n_p + t_me]; part[a] = 0.f; }
-        const int p0 = i * (2 * N - i - 1) / 2, np_row = N - 1 - i;
-        float nxt[DIM] = {};
-        if (!init && np_row > 0)
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) nxt[a] = lam[(size_t)p0 * plane + a * n_p + t_me];
-        for (int jj = 0; jj < np_row; ++jj) {
-          const int p = p0 + jj, j = i + 1 + jj;
-          float lm[DIM];
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) lm[a] = nxt[a];
-          if (!init && jj + 1 < np_row) // the next pair's multipliers, loaded early
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) nxt[a] = lam[(size_t)(p + 1) * plane + a * n_p + t_me];
-          float dl[DIM];
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) dl[a] = pi[a] - pos[(j * DIM + a) * n_p + t_me];
-          const float r = ma_pair<DIM>(dl, a_ag, b_ag, ia2_ag, ib2_ag, lm, rho, irho, init);
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) {
-            lam[(size_t)p * plane + a * n_p + t_me] = lm[a];
-            part[a] += lm[a];
-          }
-          rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
-        }
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) part[a] *= 2.f;
-        for (int o = 0; o < n_o; ++o) {
-          const float4 ob = A.obs[ob0 + o];
-          const float ctr[3] = {ob.x, ob.y, ob.z};
-          float dl[DIM], lm[DIM];
-          float *lp = lamo + ((size_t)o * N + i) * plane + t_me;
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) {
-            dl[a] = pi[a] - ctr[a];
-            lm[a] = init ? 0.f : lp[a * n_p];
-          }
-          const float ao = shp.x + ob.w, bo = shp.y + ob.w;
-          const float r = ma_pair<DIM>(dl, ao, bo, 1.f / (ao * ao), 1.f / (bo * bo), lm, rho, irho, init);
-#pragma unroll
-          for (int a = 0; a < DIM; ++a) {
-            lp[a * n_p] = lm[a];
-            part[a] += lm[a];
-          }
-          rmax = fmaxf(rmax, r != r ? __int_as_float(0x7f800000) : r);
-        }
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) w[(i * DIM + a) * n_p + t_me] = part[a];
-      }
+      rmax = init ? pair_rows<DIM, true>(N, n_p, nslot, slot, t_me, pos, lam, lamo, A.obs + ob0, n_o,
+                                         shp, rho, irho, w)
+                  : pair_rows<DIM, false>(N, n_p, nslot, slot, t_me, pos, lam, lamo, A.obs + ob0,
+                                          n_o, shp, rho, irho, w);
     block_max(rmax, red, red + 32);
     res = sqrtf(red[32]);
     k_done = k;
@@ -535,15 +550,14 @@ __global__ void __launch_bounds__(MA_THREADS, 1) k_ma_solve(MaArgs A) {
     const float c1 = 1.f / rho + 1.f / rho_n, c0 = 1.f / rho;
     if (on)
       for (int i = slot; i < N; i += nslot) {
-        const float *lt = lam + t_me;
         float dn[DIM];
 #pragma unroll
         for (int a = 0; a < DIM; ++a) dn[a] = 0.f;
-        int p = i - 1;
+        const float *lc = lam + (size_t)(i - 1) * plane + t_me; // pair (0, i)
         for (int j = 0; j < i; ++j) {
 #pragma unroll
-          for (int a = 0; a < DIM; ++a) dn[a] += lt[(size_t)p * plane + a * n_p];
-          p += N - j - 2;
+          for (int a = 0; a < DIM; ++a) dn[a] += lc[a * n_p];
+          lc += (size_t)(N - j - 2) * plane; // to pair (j + 1, i)
         }
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
