@@ -473,6 +473,72 @@ traj_status traj_ma_get_trajectories(traj_ma_batch *b, float *coeffs, float *res
  * traj_ma_create on this thread when b is NULL. */
 const char *traj_ma_last_error(traj_ma_batch *b);
 
+/* ---- Multi-circle footprint with heading (Paper II, Algorithm 2) -------------
+ * A batch of 2D trajectories of a robot whose footprint is n_circles circles of
+ * radius r_circle at offsets r_m along its heading psi(t) (a rectangle as
+ * overlapping circles, eq. coll_multiagent). Per trajectory x, y and psi are
+ * degree-10 Bernstein polynomials, with slack copies c, s of cos psi, sin psi
+ * (eqs. cos_ref, sin_ref); cost sum_t (x''^2 + y''^2 + psi''^2 + (x - x_des)^2 +
+ * (y - y_des)^2), x_des the constant-velocity line (eq. acc_cost); start
+ * position with zero velocity and acceleration and goal position fixed, the
+ * heading fixed at both ends (eqs. eq_multiagent_1, eq1_multiagent_1); speed <=
+ * vmax, acceleration <= amax; every circle kept outside every moving ellipse
+ * inflated by r_circle. One iteration: the xi-step per half (x, c) and (y, s)
+ * through a KKT inverse cached per problem (eq. zeta_1_sepration_1), the heading
+ * step through the convex surrogate on the unwrapped atan2(s, c) (eq.
+ * compute_convex_surrogate), the alpha/d steps in closed form (eqs. zeta_2,
+ * alpha_v, alpha_a, compute_d_mij, compute_dv, compute_da) and the multiplier
+ * updates (eqs. update_lambda2_1, update_lambda2_2). One warp per trajectory. */
+typedef struct traj_fp_batch traj_fp_batch;
+
+typedef struct traj_fp_config {
+  int max_problems, max_traj, max_obstacles; /* capacities, >= 1 (obstacles >= 0) */
+  int max_steps;                             /* grid points per problem, 2 .. 256 */
+  int n_circles;                             /* 1 .. 8 */
+  float circle_offsets[8];                   /* r_m along the heading (m), first n_circles used */
+  float r_circle;                            /* circle radius (m), >= 0 */
+  float vmax, amax;                          /* > 0 */
+  float rho, rho_psi;                        /* penalties of the xi- and heading steps, > 0 */
+} traj_fp_config;
+
+typedef struct traj_fp_stats {
+  float gpu_ms;      /* CUDA-event time of the solve launch */
+  int n_solved;      /* trajectories with all four residuals <= tol */
+  int max_iters_run; /* largest iteration count */
+} traj_fp_stats;
+
+traj_status traj_fp_create(const traj_fp_config *cfg, void *cuda_stream, traj_fp_batch **out);
+traj_status traj_fp_destroy(traj_fp_batch *b);
+
+/* Host arrays: n_steps [P], duration [P] (s), start and goal [P][2] (FP64),
+ * heading_start and heading_goal [P] (rad, FP64), obs_offsets [P + 1] (CSR,
+ * obs_offsets[0] = 0), centers, semi_axes, velocities [n_obs][2] (FP32; an
+ * obstacle sits at centre + velocity t). Forms the per-problem tables and the
+ * FP64 KKT inverses on the GPU and synchronises. */
+traj_status traj_fp_set_problems(traj_fp_batch *b, int n_problems, const int *n_steps,
+                                 const double *duration, const double *start, const double *goal,
+                                 const double *heading_start, const double *heading_goal,
+                                 const int *obs_offsets, const float *centers,
+                                 const float *semi_axes, const float *velocities);
+
+/* Host arrays: traj_problem [n_traj], xi0 [n_traj][3][11] (x, y, psi). The copies
+ * c, s start as cos psi, sin psi of xi0 on the grid; multipliers start at 0. */
+traj_status traj_fp_set_initial(traj_fp_batch *b, int n_traj, const int *traj_problem,
+                                const float *xi0);
+
+/* Up to max_iters iterations per trajectory; a trajectory stops at the first
+ * iteration whose four residuals (obstacle, speed, acceleration: L-infinity
+ * distance to the feasible target over the grid; heading copy: max_t
+ * ||(c, s) - (cos psi, sin psi)||) are <= tol (tol < 0: never). Asynchronous
+ * unless stats is non-NULL (then synchronises). */
+traj_status traj_fp_solve(traj_fp_batch *b, int max_iters, float tol, traj_fp_stats *stats);
+
+/* coeffs [n_traj][5][11] in the order x, c, y, s, psi; residual [n_traj][4];
+ * iters [n_traj] (each nullable; host or device); synchronises. */
+traj_status traj_fp_get_trajectories(traj_fp_batch *b, float *coeffs, float *residual, int *iters);
+
+const char *traj_fp_last_error(traj_fp_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

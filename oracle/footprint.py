@@ -33,8 +33,10 @@ of R8 for x and y, L-infinity residuals over the grid):
   H3  A_psi fixes the heading at both ends (first and last row of P);
   H4  lambda_psi <- lambda_psi - rho_psi P^T (P xi_psi - psi^) (the printed
       update reuses F's residual, which has the wrong dimension);
-  H5  initialisation: xi_x, xi_y and xi_psi are given; c, s start as
-      cos psi, sin psi on the grid; alpha, d from them, lambda = 0;
+  H5  initialisation: xi_x, xi_y and xi_psi are given; the targets of the first
+      xi-step use c, s = cos psi, sin psi on the grid, lambda = 0; the copy
+      coefficients start as cos / sin of the heading coefficients (they are
+      returned after zero iterations and do not enter the first xi-step);
   H6  a fourth residual, max_t ||(c, s) - (cos psi, sin psi)||, joins the stop
       test.
 
@@ -187,8 +189,8 @@ def solve(prob: FPProblem, xi0, iters, tol=-1.0, want_hist=False):
     bpsi = np.array([prob.psi0, prob.psif])
     ob = obstacle_positions(prob, t)                                      # [n_o, n_p, 2]
     ax = prob.semi_axes[:, None, :] + prob.r_circle                       # reading H1
-    xh = [np.concatenate([xi0[:, 0], np.zeros((B, NC))], 1),
-          np.concatenate([xi0[:, 1], np.zeros((B, NC))], 1)]             # (xi_x, xi_c), (xi_y, xi_s)
+    xh = [np.concatenate([xi0[:, 0], np.cos(xi0[:, 2])], 1),
+          np.concatenate([xi0[:, 1], np.sin(xi0[:, 2])], 1)]             # (xi_x, xi_c), (xi_y, xi_s)
     xpsi = xi0[:, 2].copy()
     lam = [np.zeros((B, 2 * NC)), np.zeros((B, 2 * NC))]
     lpsi = np.zeros((B, NC))
