@@ -395,6 +395,98 @@ def run_multiagent(args, torch):
     h.close()
 
 
+def footprint_ops(n_p, n_o, n_c, iters):
+    """FP32 lane operations per trajectory for `iters` iterations of the footprint
+    method (+ the initial pass). Per grid point: the containment test of each
+    circle against each ellipse [footprint offset 2 FMA + the 9 of the point test],
+    the evaluations of x, y (value, speed, acceleration), c, s and psi [9 x 11 FMA]
+    and of c, s, psi for the heading step [3 x 11], the speed and acceleration
+    tests [8], the contractions F^T r [88] and P^T (psi^ - psi) [11]. Per
+    trajectory: the xi-step [44 x 44 FMA] and the heading step [11 x 11]."""
+    per_t = n_c * n_o * 11 + 99 + 33 + 8 + 88 + 11
+    return (n_p * per_t + 44 * 44 + 11 * 11) * (np.asarray(iters, np.float64) + 1.0)
+
+
+def run_footprint(args, torch):
+    """Paper II's batch optimizer for a rectangular robot (3 circles, heading):
+    1000 trajectories (125 scenes x 8 initialisations, 20 moving ellipses each),
+    a fixed number of iterations; one step = one batch solve."""
+    from paper_2408_10731_b300 import scenes, footprint as gfp, trajbatch
+    b = scenes.config2(args.seed, n_scenes=125, inits=8, n_obstacles=20)
+    d = b.goal - b.start
+    head = np.arctan2(d[:, 1], d[:, 0])
+    xpsi0 = np.repeat(head[b.traj_problem][:, None], 11, 1)
+    offs, rc, iters = (-0.35, 0.0, 0.35), 0.15, 100
+    h = gfp.from_batch(b, head, head, xpsi0, offs, rc)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        h.solve(iters, -1.0, stats=False)
+    torch.cuda.synchronize()
+    clk = ClockSampler(_pci_id(torch, 0))
+    clk.mark()
+    ms = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream); h.solve(iters, -1.0, stats=False); e1.record(stream); e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk.mark()
+    clocks = clk.stop()
+    step_ms = float(np.mean(ms))
+    out = h.get_trajectories()
+    e2e = []
+    xi0 = np.concatenate([b.xi0[:, :2], xpsi0[:, None, :]], 1)
+    for _ in range(max(1, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.set_initial(b.traj_problem, xi0)
+        h.solve(iters, -1.0, stats=False)
+        r = h.get_trajectories()
+        e2e.append(time.perf_counter() - t0)
+    ops = float(b.n_traj * footprint_ops(100, 20, len(offs), iters))
+    fp32_peak = trajbatch.measure_fp32_peak(5)
+    achieved = ops / (step_ms * 1e-3)
+    line = {"metric": "ms per iteration, batch of 1000 trajectories (3-circle footprint with "
+                      "heading, 20 moving ellipses)", "value": step_ms / iters, "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "125 scenes x 8 initialisations N(straight line, 0.5 m), 2D, "
+                                   "n_p=100 over 10 s, 20 constant-velocity ellipses (semi-axes "
+                                   "U(0.2,0.8) m), footprint circles at -0.35/0/0.35 m of radius "
+                                   f"0.15 m, heading fixed at both ends, {iters} fixed iterations",
+                       "l2": "inputs and state stay on chip; one launch per step"},
+            "residual_median": [float(np.median(out["residual"][:, k])) for k in range(4)],
+            "e2e": {"value": float(np.mean(e2e)) * 1e3 / iters, "unit": "ms",
+                    "h2d_bytes_per_step": int(xi0.astype(np.float32).nbytes + b.traj_problem.nbytes),
+                    "d2h_bytes_per_step": int(r["xi"].nbytes + r["residual"].nbytes + r["iterations"].nbytes)},
+            "gpu_launches": 1, "clocks": clocks,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 2e12,
+                         "unit": "Top/s", "frac": achieved / (fp32_peak / 2.0), "traffic": None,
+                         "kernel": "k_fp_solve<4>",
+                         "peak_source": "measured FFMA microbenchmark (traj_measure_fp32_peak), "
+                                        "FP32 lane-ops/s",
+                         "algorithmic_ops_per_launch": ops},
+            "context": "Paper II reports 4.5 ms per iteration at a batch of 1000 on its (unnamed) GPU"}
+    if not args.no_cpu_baseline:
+        from oracle import footprint as fp
+        c, a, v = b.obstacles(0)
+        prob = fp.FPProblem(n_p=100, T=float(b.duration[0]), start=b.start[0], goal=b.goal[0],
+                            psi0=float(head[0]), psif=float(head[0]), centers=np.asarray(c, float),
+                            semi_axes=np.asarray(a, float), velocities=np.asarray(v, float),
+                            offsets=np.asarray(offs), r_circle=rc, vmax=b.vmax, amax=b.amax,
+                            rho=b.rho)
+        idx = np.nonzero(b.traj_problem == 0)[0]
+        t0 = time.perf_counter()
+        fp.solve(prob, xi0[idx], 20)
+        t_it = (time.perf_counter() - t0) / 20
+        line["cpu_baseline"] = {"value": t_it * 1e3 * b.n_traj / len(idx), "unit": "ms",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"scene 0 ({len(idx)} trajectories), 20 iterations, "
+                                          "scaled to 1000 trajectories per iteration"}
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,7 +498,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workload", default="config2",
-                    choices=["config2", "uneven", "priest", "multiagent"])
+                    choices=["config2", "uneven", "priest", "multiagent", "footprint"])
     ap.add_argument("--ma-agents", type=int, default=32)
     ap.add_argument("--ma-scenes", type=int, default=148)
     ap.add_argument("--ma-radius", type=float, default=0.4)
@@ -437,6 +529,8 @@ def main():
         return run_priest(args, torch)
     if args.workload == "multiagent":
         return run_multiagent(args, torch)
+    if args.workload == "footprint":
+        return run_footprint(args, torch)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))

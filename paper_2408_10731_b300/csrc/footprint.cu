@@ -53,7 +53,7 @@ struct FpArgs {
   const float *tables;   // per problem [3][n_p][ROW]: P, Pdot, Pddot (time-scaled)
   const float *consts;   // per problem FC_FLOATS
   const float4 *obs;     // per obstacle (cx, cy, vx, vy)
-  const float2 *obs_ax;  // per obstacle (a + r_circle, b + r_circle)
+  const float2 *obs_ax;  // per obstacle 1 / (a + r_circle), 1 / (b + r_circle)
   const float *xi0;      // [n_traj][3][11]: x, y, psi
   float *xi_out;         // [n_traj][5][11]: x, c, y, s, psi
   float *res_out;        // [n_traj][4]: obstacle, speed, acceleration, heading copy
@@ -283,8 +283,8 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
       if (t >= n_p) break;
       const float *rp_ = tP + t * ROW, *rd = tD + t * ROW, *ra = tA + t * ROW;
       const float x = dot11p(rp_, X, XLO), y = dot11p(rp_, X + FP_H, XLO);
-      const float vx = dot11p(rd, X, XLO), vy = dot11p(rd, X + FP_H, XLO);
-      const float axx = dot11p(ra, X, XLO), ayy = dot11p(ra, X + FP_H, XLO);
+      const float vx = dot11(rd, X), vy = dot11(rd, X + FP_H); // bound tests: hi part
+      const float axx = dot11(ra, X), ayy = dot11(ra, X + FP_H);
       const float psi = dot11p(rp_, XP, PLO);
       float sp, cp;
       sincosf(psi, &sp, &cp);
@@ -305,21 +305,21 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
         float sx = 0.f, sy = 0.f; // sum over obstacles of the circle's residuals
         for (int j = 0; j < n_o; ++j) {
           const float4 o = ob[j];
-          const float2 ab = oax[j];
+          const float2 ia = oax[j]; // reciprocal inflated semi-axes
           const float dx = fx - fmaf(o.z, tt, o.x), dy = fy - fmaf(o.w, tt, o.y);
-          const float ux = dx / ab.x, uy = dy / ab.y;
-          const float u2 = ux * ux + uy * uy;
-          float ex = 0.f, ey = 0.f;
+          const float ux = dx * ia.x, uy = dy * ia.y;
+          const float u2 = fmaf(ux, ux, uy * uy);
           if (u2 < 1.f) { // inside: pushed out along the ray (d = 1)
+            float ex, ey;
             if (u2 > 0.f) {
               const float f = 1.f - 1.f / sqrtf(u2);
               ex = dx * f;
               ey = dy * f;
-            } else { ex = -ab.x; ey = 0.f; } // atan2(0, 0) = 0
+            } else { ex = -1.f / ia.x; ey = 0.f; } // atan2(0, 0) = 0
+            rmax[0] = fmaxf(rmax[0], sqrtf(ex * ex + ey * ey));
+            sx += ex;
+            sy += ey;
           }
-          rmax[0] = fmaxf(rmax[0], sqrtf(ex * ex + ey * ey));
-          sx += ex;
-          sy += ey;
         }
         // F xi - g for the collision rows: (x + r cF) - target = e - r (c - cF)
         const float ox = sx - (float)n_o * r * (c - cF), oy = sy - (float)n_o * r * (s - sF);
@@ -605,7 +605,7 @@ traj_status traj_fp_set_problems(traj_fp_batch *b, int n_problems, const int *n_
       if (!std::isfinite(x)) return fp_fail(b, TRAJ_ENAN, "non-finite obstacle data");
     if (!(v[4] > 0) || !(v[5] > 0)) return fp_fail(b, TRAJ_EINVAL, "semi-axes must be positive");
     obs[j] = make_float4(v[0], v[1], v[2], v[3]);
-    ax[j] = make_float2(v[4] + c.r_circle, v[5] + c.r_circle);
+    ax[j] = make_float2((float)(1.0 / ((double)v[4] + c.r_circle)), (float)(1.0 / ((double)v[5] + c.r_circle)));
   }
   if (tbl > b->tables_cap) {
     if (b->d_tables) cudaFree(b->d_tables);
