@@ -203,9 +203,6 @@ __device__ __forceinline__ void bound_res(float wx, float wy, float bound, float
 // (the iterate as exact float pairs: X / XL, XP / XPL)
 constexpr int WS_X = 0, WS_XL = 44, WS_LAM = 88, WS_V = 132, WS_XP = 176, WS_XPL = 187,
               WS_UP = 198, WS_U = 209, WS_FLOATS = 256;
-// per-point rows of the residual array (n_p each)
-constexpr int RR_VX = 0, RR_AX = 1, RR_OX = 2, RR_OCX = 3, RR_VY = 4, RR_AY = 5, RR_OY = 6,
-              RR_OCY = 7, RR_DPSI = 8, RR_N = 9;
 
 // dot of 11 coefficients (shared, broadcast) with a table row
 __device__ __forceinline__ float dot11(const float *row, const float *c) {
@@ -244,8 +241,7 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int traj = blockIdx.x * FP_WARPS + w;
   if (traj >= A.n_traj) return; // whole warp; no block-wide barrier follows
-  float *ws = smf + w * (WS_FLOATS + RR_N * max_np);
-  float *RR = ws + WS_FLOATS;
+  float *ws = smf + w * WS_FLOATS;
   const FpProblemDev pr = A.problems[A.traj_problem[traj]];
   const int n_p = pr.n_p, n_o = pr.n_o, n_c = A.n_c;
   const float *tP = A.tables + pr.tbl_off, *tD = tP + n_p * ROW, *tA = tD + n_p * ROW;
@@ -275,8 +271,13 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
   // projections at the lane's points; writes the per-point residual rows and returns
   // the residual maxima (obstacle, speed, acceleration, copy). init: the copies are
   // cos / sin psi for the targets while F xi uses the zero copy coefficients.
+  // The contraction u = F^T r is accumulated per lane over its points (44 partial
+  // sums) and reduced across the warp into U.
   auto project = [&](bool init, float (&rmax)[4]) {
     rmax[0] = rmax[1] = rmax[2] = rmax[3] = 0.f;
+    float acc[44];
+#pragma unroll
+    for (int e = 0; e < 44; ++e) acc[e] = 0.f;
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
       const int t = lane + 32 * q;
@@ -329,38 +330,27 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
       // copies: F xi - g = cF - cos psi
       const float rcx = cF - cp, rcy = sF - sp;
       if (!init) rmax[3] = fmaxf(rmax[3], sqrtf((c - cp) * (c - cp) + (s - sp) * (s - sp)));
-      RR[RR_VX * max_np + t] = rvx; RR[RR_VY * max_np + t] = rvy;
-      RR[RR_AX * max_np + t] = rax; RR[RR_AY * max_np + t] = ray;
-      RR[RR_OX * max_np + t] = Rox; RR[RR_OY * max_np + t] = Roy;
-      RR[RR_OCX * max_np + t] = Rcx + rcx; RR[RR_OCY * max_np + t] = Rcy + rcy;
-    }
-  };
-
-  // u = F^T r per half (44 outputs) from the residual rows
-  auto contract = [&]() {
-    __syncwarp();
-    for (int e = lane; e < 44; e += 32) {
-      const int h = e / FP_H, i = e % FP_H;
-      const float *rv = RR + (h ? RR_VY : RR_VX) * max_np, *ra = RR + (h ? RR_AY : RR_AX) * max_np;
-      const float *ro = RR + (h ? RR_OY : RR_OX) * max_np, *rc = RR + (h ? RR_OCY : RR_OCX) * max_np;
-      float s0 = 0.f, s1 = 0.f;
-      if (i < NC) {
-        for (int t = 0; t < n_p; ++t) {
-          s0 = fmaf(tD[t * ROW + i], rv[t], s0);
-          s0 = fmaf(tA[t * ROW + i], ra[t], s0);
-          s1 = fmaf(tP[t * ROW + i], ro[t], s1);
-        }
-      } else {
-        for (int t = 0; t < n_p; ++t) s1 = fmaf(tP[t * ROW + i - NC], rc[t], s1);
+      const float qx = Rcx + rcx, qy = Rcy + rcy;
+#pragma unroll
+      for (int kk = 0; kk < NC; ++kk) {
+        const float p0 = rp_[kk], d0 = rd[kk], a0 = ra[kk];
+        acc[kk] = fmaf(p0, Rox, fmaf(a0, rax, fmaf(d0, rvx, acc[kk])));
+        acc[NC + kk] = fmaf(p0, qx, acc[NC + kk]);
+        acc[FP_H + kk] = fmaf(p0, Roy, fmaf(a0, ray, fmaf(d0, rvy, acc[FP_H + kk])));
+        acc[FP_H + NC + kk] = fmaf(p0, qy, acc[FP_H + NC + kk]);
       }
-      U[e] = s0 + s1;
+    }
+#pragma unroll
+    for (int e = 0; e < 44; ++e) {
+      float v = acc[e];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == (e & 31)) U[e] = v;
     }
     __syncwarp();
   };
 
   float rmax[4];
   project(true, rmax);
-  contract();
   for (int e = lane; e < 44; e += 32) V[e] = -rho * U[e];
   __syncwarp();
   float res[4] = {rmax[0], rmax[1], rmax[2], rmax[3]};
@@ -395,22 +385,29 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
     // the surrogate's solution is an increment: xi_psi^k = xi_psi^{k-1} +
     // rho_psi K_psi P^T (psi^^k - psi^{k-1}) for k >= 2; the first step is
     // hq_psi + G_psi xi_psi^0 + rho_psi K_psi P^T (psi^^1 - psi^0) (lambda_psi^0 = 0).
+    {
+      float up[NC];
 #pragma unroll
-    for (int q = 0; q < PPL; ++q) {
-      const int t = lane + 32 * q;
-      if (t >= n_p) break;
-      const float *rp_ = tP + t * ROW;
-      const float c = dot11p(rp_, X + NC, XLO), s = dot11p(rp_, X + FP_H + NC, XLO);
-      const float psi = dot11p(rp_, XP, PLO);
-      RR[RR_DPSI * max_np + t] = wrap_pi(atan2f(s, c) - psi);
+      for (int kk = 0; kk < NC; ++kk) up[kk] = 0.f;
+#pragma unroll
+      for (int q = 0; q < PPL; ++q) {
+        const int t = lane + 32 * q;
+        if (t >= n_p) break;
+        const float *rp_ = tP + t * ROW;
+        const float c = dot11p(rp_, X + NC, XLO), s = dot11p(rp_, X + FP_H + NC, XLO);
+        const float psi = dot11p(rp_, XP, PLO);
+        const float dpsi = wrap_pi(atan2f(s, c) - psi);
+#pragma unroll
+        for (int kk = 0; kk < NC; ++kk) up[kk] = fmaf(rp_[kk], dpsi, up[kk]);
+      }
+#pragma unroll
+      for (int kk = 0; kk < NC; ++kk) {
+        float v = up[kk];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == kk) UP[kk] = rp * v;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    if (lane < NC) {
-      float a = 0.f;
-      for (int t = 0; t < n_p; ++t) a = fmaf(tP[t * ROW + lane], RR[RR_DPSI * max_np + t], a);
-      UP[lane] = rp * a;
-    }
-    __syncwarp();
     float xph = 0.f, xpl = 0.f;
     if (lane < NC) {
       float hi, lo;
@@ -434,7 +431,6 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
     __syncwarp();
     // alpha / d steps and the residual rows at the new iterate
     project(false, rmax);
-    contract();
     // multipliers (eq. update_lambda2_1; reading H4) and v = lambda - rho u
     for (int e = lane; e < 44; e += 32) {
       const float l = LAM[e] - rho * U[e];
@@ -687,7 +683,7 @@ traj_status traj_fp_solve(traj_fp_batch *b, int max_iters, float tol, traj_fp_st
   A.res_out = b->d_res;
   A.iters_out = b->d_iters;
   const int max_np = b->max_np;
-  const size_t smem = sizeof(float) * FP_WARPS * (WS_FLOATS + RR_N * max_np);
+  const size_t smem = sizeof(float) * FP_WARPS * WS_FLOATS;
   const int grid = (b->n_traj + FP_WARPS - 1) / FP_WARPS;
   cudaStream_t s = b->stream;
   auto kern = max_np <= 64 ? k_fp_solve<2> : max_np <= 128 ? k_fp_solve<4> : k_fp_solve<8>;
