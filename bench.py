@@ -268,6 +268,34 @@ def run_priest(args, torch):
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream); run(); e1.record(stream); e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+    # D-PRIEST: 4 distributions of 1024 samples each refined in parallel, with the BARN
+    # cost terms (curvature, distance to the straight path); same solve and launch shape
+    nd = 4
+    cfg_d = dict(cfg, n_proj=int(np.ceil(0.73 * 1024)), n_elite=int(np.ceil(0.10 * 1024)),
+                 w_curv=0.05, w_path=0.5)
+    mus0 = mu0.repeat(nd, 1)
+    mus0[1:] += torch.randn(nd - 1, D, generator=torch.Generator(device=dev).manual_seed(args.seed),
+                            device=dev)
+    sig0 = s0.repeat(nd, 1, 1)
+    mus, sigs, bests = mus0.clone(), sig0.clone(), torch.zeros(nd, D + 1, device=dev)
+
+    def run_d():
+        mus.copy_(mus0); sigs.copy_(sig0)
+        for it in range(c3["n_outer"]):
+            h.sampler_step(cfg_d, it, mus, sigs, bests, n_dist=nd)
+
+    for _ in range(args.warmup):
+        run_d()
+    torch.cuda.synchronize()
+    msd = []
+    for _ in range(max(3, args.steps // 2)):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream); run_d(); e1.record(stream); e1.synchronize()
+        msd.append(e0.elapsed_time(e1))
+    dpriest = {"ms_per_run": float(np.mean(msd)), "distributions": nd, "samples_per_distribution": 1024,
+               "best_cost_aug": [float(x) for x in bests[:, D].cpu()],
+               "cost": "sum_t ||p''||^2 + 0.05 curvature^2 + 0.5 path distance + residual",
+               "launches_per_run": c3["n_outer"] * 6}
     # residual of the returned trajectory (one more projection-free evaluation on the host
     # is not needed: the sampler's best is a projected sample; report its c_aug)
     bc = float(best[D].item())
@@ -284,6 +312,7 @@ def run_priest(args, torch):
                                    "n_p=100 over 20 s, B=4096, N_proj=2991, N_elite=410, gamma 1, "
                                    "sigma_lr 0.5", "launch_shape": shape},
             "best_cost_aug": bc, "gpu_launches_per_step": c3["n_outer"] * 6,
+            "forms": {"d_priest_barn": dpriest},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 2e12,
                          "unit": "Top/s", "frac": achieved / (fp32_peak / 2.0), "traffic": None,
                          "kernel": kernel_name("fp32", shape) + " (3D, projection mode; whole run timed)",
