@@ -120,3 +120,48 @@ def test_early_stop_matches_oracle_iterations():
     e_pos, e_psi = _errors(b, out, 400, psi0, psif, xpsi0, tol=tol)
     assert e_pos <= POS_TOL and e_psi <= PSI_TOL, (e_pos, e_psi)
     assert st["n_solved"] == int(np.sum(np.all(out["residual"] <= tol, axis=1)))
+
+
+def test_eight_circles_on_the_longest_horizon_and_errors():
+    """Eight footprint circles and n_p = 256 (the longest grid, eight points per
+    lane); non-finite inputs, bad problem indices and calls out of order are
+    refused."""
+    from paper_2408_10731_b300 import footprint as gfp
+    from paper_2408_10731_b300.trajbatch import TrajBatchError
+    offs = tuple(np.linspace(-0.7, 0.7, 8))
+    b = scenes.config2(21, n_scenes=1, inits=2, n_obstacles=6)
+    b.n_steps = np.array([256], np.int32)
+    b.duration = np.array([20.0])
+    psi0, psif = _headings(b)
+    xpsi0 = np.repeat(psi0[b.traj_problem][:, None], 11, 1)
+    h = gfp.from_batch(b, psi0, psif, xpsi0, offs, RC)
+    try:
+        h.solve(10)
+        out = h.get_trajectories()
+    finally:
+        h.close()
+    c, a, v = b.obstacles(0)
+    prob = fp.FPProblem(n_p=256, T=20.0, start=b.start[0], goal=b.goal[0], psi0=float(psi0[0]),
+                        psif=float(psif[0]), centers=np.asarray(c, float),
+                        semi_axes=np.asarray(a, float), velocities=np.asarray(v, float),
+                        offsets=np.asarray(offs), r_circle=RC, vmax=b.vmax, amax=b.amax, rho=b.rho)
+    ref = fp.solve(prob, np.concatenate([b.xi0[:, :2], xpsi0[:, None]], 1), 10)
+    P, _, _ = am.bernstein(256, 20.0)
+    for r in (0.0,) + offs:
+        g, x = out["xi"].astype(np.float64), ref["xi"]
+        pg = np.stack([g[:, 0] @ P.T + r * (g[:, 1] @ P.T), g[:, 2] @ P.T + r * (g[:, 3] @ P.T)], -1)
+        po = np.stack([x[:, 0] @ P.T + r * (x[:, 1] @ P.T), x[:, 2] @ P.T + r * (x[:, 3] @ P.T)], -1)
+        assert np.linalg.norm(pg - po, axis=-1).max() <= POS_TOL
+    h = gfp.FootprintBatch(2, 4, 4, 100, (0.0,), 0.1, 1.0, 1.0)
+    try:
+        with pytest.raises(TrajBatchError):
+            h.solve(5)                       # before set_problems / set_initial
+        h.set_problems([50], [5.0], [[0, 0]], [[4, 4]], [0.0], [0.0], [0, 0],
+                       np.zeros((0, 2)), np.zeros((0, 2)), np.zeros((0, 2)))
+        with pytest.raises(TrajBatchError):
+            h.set_initial([1], np.zeros((1, 3, 11)))        # problem index out of range
+        bad = np.zeros((1, 3, 11)); bad[0, 0, 3] = np.inf
+        with pytest.raises(TrajBatchError):
+            h.set_initial([0], bad)
+    finally:
+        h.close()

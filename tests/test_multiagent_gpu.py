@@ -151,3 +151,27 @@ def test_capacity_errors():
             h.set_problems(sc)
     finally:
         h.close()
+
+
+def test_maximum_agents_and_errors():
+    """64 agents (the largest team, multipliers in device memory) against the
+    oracle; non-finite inputs and calls out of order are refused."""
+    from paper_2408_10731_b300 import multiagent as gma
+    from paper_2408_10731_b300.trajbatch import TrajBatchError
+    sc = scenes.ma_random(9, n_scenes=1, n_agents=64, dim=2, room=16.0, radius=0.3, n_steps=40,
+                          T=8.0)
+    out, st = _run(sc, 12, rho=2.0)
+    assert st["lambda_in_shared"] == 0
+    ref = ma.solve(_problem(sc, 0, rho=2.0), 12)
+    assert _pos_err(sc, 0, out["xi"][0], ref["xi"]) <= POS_TOL
+    h = gma.MultiAgentBatch(2, 1, 4, 0, 40)
+    try:
+        with pytest.raises(TrajBatchError):
+            h.solve(5)                       # before set_problems
+        bad = scenes.ma_random(1, n_scenes=1, n_agents=4, dim=2, n_steps=40)
+        bad.start = bad.start.copy()
+        bad.start[0, 1, 0] = np.nan
+        with pytest.raises(TrajBatchError):
+            h.set_problems(bad)
+    finally:
+        h.close()
