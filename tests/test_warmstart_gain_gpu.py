@@ -1,4 +1,4 @@
-"""What the trained warm-start network gains: held-out scenes solved from the
+"""What the trained warm-start network gains: 4096 held-out scenes solved from the
 network's K = 8 proposals versus the initialisations the optimizer uses without
 it -- the straight line (zero offsets, the fallback) and 8 random draws
 N(straight line, 0.5 m). The network is trained on the GPU by the library's own
@@ -18,22 +18,22 @@ def _solve(batch, xi0, tp, cap=500, tol=1e-3):
     b = dataclasses.replace(batch, xi0=scenes.f32(xi0), traj_problem=tp)
     h = tb.from_batch(b)
     try:
-        h.solve(cap, tol)
+        st = h.solve(cap, tol)
         out = h.get_trajectories()
     finally:
         h.close()
     ok = (out["status"] == 0).reshape(batch.n_problems, 8)
-    return ok, out["iters"].reshape(batch.n_problems, 8)
+    return ok, out["iters"].reshape(batch.n_problems, 8), st["gpu_ms"]
 
 
 def test_trained_network_gains_over_the_fallback_initialisation(capsys):
     import torch
     from paper_2408_10731_b300 import warmstart
-    ws, info = warmstart.trained(seed=1000, n_scenes=50000, epochs=20)
+    ws, info = warmstart.trained(seed=1000, n_scenes=200000, epochs=20)
     try:
         if info is not None:  # trained in this process: the loss must fall well below the start
             assert info["losses"][-1] < 0.5 * info["losses"][0], info["losses"]
-        held = scenes.ellipse_scenes(99, 512)
+        held = scenes.ellipse_scenes(99, 4096)
         P = held.n_problems
         xi_l, tp = warmstart.proposals(ws, held)
         ws.sync()
@@ -42,15 +42,20 @@ def test_trained_network_gains_over_the_fallback_initialisation(capsys):
         res = {}
         for name, x in (("learned", xi_l.cpu().numpy()), ("straight", np.repeat(line, 8, 0)),
                         ("random", np.repeat(line, 8, 0) + rng.normal(0, 0.5, (P * 8, 2, 11)))):
-            ok, it = _solve(held, x, tp)
+            ok, it, ms = _solve(held, x, tp)
             res[name] = dict(scenes=float(ok.any(1).mean()), traj=int(ok.sum()),
-                             it_med=float(np.median(it[ok])) if ok.any() else np.inf)
+                             it_med=float(np.median(it[ok])) if ok.any() else np.inf,
+                             it_p90=float(np.percentile(it[ok], 90)) if ok.any() else np.inf,
+                             solved_per_s=float(ok.sum() / (ms * 1e-3)))
         with capsys.disabled():
-            print("\nwarm-start gain on 512 held-out scenes:", res)
-        # against the zero-offset fallback: more scenes solved and fewer iterations
+            print("\nwarm-start gain on 4096 held-out scenes:", res)
+        # against the zero-offset fallback: more scenes and more trajectories solved
+        # (the median iteration count of the solved ones is not compared: the fallback
+        # solves only the easy scenes)
         assert res["learned"]["scenes"] >= 1.3 * res["straight"]["scenes"], res
-        assert res["learned"]["it_med"] <= res["straight"]["it_med"], res
-        # against random draws the gain is within noise on this scene family (recorded above)
-        assert res["learned"]["traj"] >= 0.8 * res["random"]["traj"], res
+        assert res["learned"]["traj"] >= res["straight"]["traj"], res
+        # against random draws: at least as many trajectories solved (fewer scenes with
+        # a solution: the proposals cover fewer homotopies; recorded above)
+        assert res["learned"]["traj"] >= 0.95 * res["random"]["traj"], res
     finally:
         ws.close()
