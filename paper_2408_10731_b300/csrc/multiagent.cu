@@ -207,8 +207,8 @@ __device__ __forceinline__ float ma_pair(const float (&dl)[DIM], float a, float 
     if constexpr (DIM == 3) R2 = fmaf(dl[2] * dl[2], ib2, (dl[0] * dl[0] + dl[1] * dl[1]) * ia2);
     else R2 = n2 * ia2;
     const float R = sqrtf(R2);
-    const float d = fmaxf(R * num / n2, 1.f);
-    const float f = 1.f - d / R;
+    const float d = fmaxf(__fdividef(R * num, n2), 1.f); // 2-ulp quotients (MUFU reciprocal)
+    const float f = 1.f - __fdividef(d, R);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) r[k] = dl[k] * f;
   } else {
