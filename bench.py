@@ -516,6 +516,54 @@ def run_footprint(args, torch):
     h.close()
 
 
+def run_gemm(args, torch):
+    """The warm-start network's tcgen05 BF16 GEMM (C = A B^T, FP32 accumulate): the
+    training shapes of the network (4096 rows: 400 -> 256, 256 -> 256, 256 -> 176)
+    and a square 8192^3 problem for the tensor roofline."""
+    from paper_2408_10731_b300 import trajbatch
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev).manual_seed(args.seed)
+    stream = torch.cuda.current_stream()
+    peak = None
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks):
+        with open(peaks) as fh:
+            peak = json.load(fh).get("bf16_tflops")
+    shapes = [(4096, 256, 400), (4096, 256, 256), (4096, 176, 256), (8192, 8192, 8192)]
+    out = {}
+    for M, N, K in shapes:
+        A = torch.randn(M, K, generator=g, device=dev).to(torch.bfloat16)
+        B = torch.randn(N, K, generator=g, device=dev).to(torch.bfloat16)
+        C = torch.empty(M, N, device=dev)
+        err = torch.zeros(1, dtype=torch.int32, device=dev)
+        for _ in range(args.warmup):
+            trajbatch.gemm_bf16(A, B, C, err)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(5, args.steps)):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream); trajbatch.gemm_bf16(A, B, C, err); e1.record(stream); e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = float(np.median(ms))
+        ref = (A[:64].float() @ B.float().T)
+        rel = float((C[:64] - ref).abs().max() / ref.abs().max())
+        assert int(err.item()) == 0 and rel < 1e-2, (M, N, K, rel)
+        out[f"{M}x{N}x{K}"] = {"ms": t, "tflops": 2.0 * M * N * K / (t * 1e-3) / 1e12}
+    big = out["8192x8192x8192"]
+    line = {"metric": "BF16 GEMM TFLOP/s (tcgen05, 128x64 tiles, FP32 accumulate), 8192^3",
+            "value": big["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": big["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "C = A B^T with A [M, K], B [N, K] normal draws in BF16, C in FP32",
+                       "l2": "the 8192^3 operands (256 MB) exceed L2"},
+            "shapes": out, "gpu_launches": 1,
+            "roofline": {"bound": "tensor", "achieved": big["tflops"], "peak": peak,
+                         "unit": "TFLOP/s", "frac": big["tflops"] / peak if peak else None,
+                         "traffic": None, "kernel": "k_gemm_bf16<0>",
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -527,7 +575,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workload", default="config2",
-                    choices=["config2", "uneven", "priest", "multiagent", "footprint"])
+                    choices=["config2", "uneven", "priest", "multiagent", "footprint", "gemm"])
     ap.add_argument("--ma-agents", type=int, default=32)
     ap.add_argument("--ma-scenes", type=int, default=148)
     ap.add_argument("--ma-radius", type=float, default=0.4)
@@ -560,6 +608,8 @@ def main():
         return run_multiagent(args, torch)
     if args.workload == "footprint":
         return run_footprint(args, torch)
+    if args.workload == "gemm":
+        return run_gemm(args, torch)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
