@@ -4,11 +4,13 @@
 //   C[M x N] = A[M x K] * B[N x K]^T,   A, B row-major BF16 (K contiguous),
 //   FP32 accumulation in tensor memory, fused epilogues (bias, GELU, GELU').
 //
-// One CTA computes one 128 x 64 tile with 4 warps: warp 0 lane 0 streams
-// 128 x 64 A and 64 x 64 B tiles into shared memory with TMA (128-byte
-// swizzle, a 4-stage ring of mbarriers), warp 1 lane 0 issues tcgen05.mma
-// (kind::f16, M = 128, N = 64, K = 16 per instruction) into a 64-column FP32
-// accumulator in TMEM and commits each stage back to the producer. The
+// One CTA computes one 128 x BN tile (BN = 64, or 128 when N > 64) with 4 warps:
+// warp 0 lane 0 streams 128 x 64 A and BN x 64 B tiles into shared memory with
+// TMA (128-byte swizzle, a ring of 4 stages for BN = 64 and 3 for BN = 128, so
+// that two CTAs share an SM), warp 1 lane 0 issues tcgen05.mma (kind::f16,
+// M = 128, N = BN, K = 16 per instruction) into a BN-column FP32 accumulator in
+// TMEM and commits each stage back to the producer. The wider tile halves the
+// re-reads of A from L2. The
 // epilogue: all four warps read the accumulator with tcgen05.ld (warp w owns
 // rows 32w..32w+31) into a padded shared-memory tile (the operand ring, free
 // once the MMAs are done), then write the outputs row by row with consecutive
@@ -25,11 +27,15 @@
 
 namespace tb {
 
-constexpr int GM_BM = 128, GM_BN = 64, GM_BK = 64, GM_STAGES = 4;
-constexpr int GM_LDS = GM_BN + 1; // padded row of the epilogue staging tile (floats)
+constexpr int GM_BM = 128, GM_BK = 64;
 constexpr int GM_TILE_A = GM_BM * GM_BK * 2;
-constexpr int GM_TILE_B = GM_BN * GM_BK * 2;
-constexpr int GM_SMEM = GM_STAGES * (GM_TILE_A + GM_TILE_B) + 1024 /*align*/ + 256 /*barriers*/;
+template <int BN> struct GemmTile {
+  static constexpr int STAGES = BN == 64 ? 4 : 3;
+  static constexpr int LDS = BN + 1; // padded row of the epilogue staging tile (floats)
+  static constexpr int TILE_B = BN * GM_BK * 2;
+  static constexpr int SMEM = STAGES * (GM_TILE_A + TILE_B) + 1024 /*align*/ + 256 /*barriers*/;
+  static_assert(GM_BM * LDS * 4 <= STAGES * (GM_TILE_A + TILE_B), "staging tile over the ring");
+};
 
 struct GemmArgs {
   int M, N, K;
@@ -52,10 +58,12 @@ __device__ __forceinline__ float gelu_tanh_grad(float z) {
   return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * k0 * (1.f + 3.f * k1 * z * z);
 }
 
-template <int EPI>
+template <int EPI, int GM_BN>
 __global__ void __launch_bounds__(128, 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const __grid_constant__ GemmArgs g) {
+  constexpr int GM_STAGES = GemmTile<GM_BN>::STAGES, GM_LDS = GemmTile<GM_BN>::LDS;
+  constexpr int GM_TILE_B = GemmTile<GM_BN>::TILE_B;
   extern __shared__ uint8_t gm_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gm_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sA = smem;
@@ -152,7 +160,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   }
   const bool all_ok = __syncthreads_and(ok);
   if (all_ok) {
-    // consecutive threads on consecutive columns: 64 columns x 2 rows per pass
+    // consecutive threads on consecutive columns: BN columns x 128 / BN rows per pass
     const int cl = threadIdx.x & (GM_BN - 1), r0 = threadIdx.x / GM_BN;
     const int col = n0 + cl;
     if (col < g.N) {
@@ -222,29 +230,24 @@ cudaError_t launch_gemm_bf16(int epi, const void *A, const void *B, int M, int N
   CUtensorMap ma, mb;
   cudaError_t e = make_map(&ma, A, M, K, GM_BM);
   if (e != cudaSuccess) return e;
-  if ((e = make_map(&mb, B, N, K, GM_BN)) != cudaSuccess) return e;
   GemmArgs g{M, N, K, out_f32, reinterpret_cast<__nv_bfloat16 *>(out_bf16), ldo, bias, aux, err};
-  dim3 grid((M + GM_BM - 1) / GM_BM, (N + GM_BN - 1) / GM_BN);
-  switch (epi) {
-  case 0:
-    cudaFuncSetAttribute(k_gemm_bf16<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM);
-    k_gemm_bf16<0><<<grid, 128, GM_SMEM, s>>>(ma, mb, g);
-    break;
-  case 1:
-    cudaFuncSetAttribute(k_gemm_bf16<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM);
-    k_gemm_bf16<1><<<grid, 128, GM_SMEM, s>>>(ma, mb, g);
-    break;
-  case 2:
-    cudaFuncSetAttribute(k_gemm_bf16<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM);
-    k_gemm_bf16<2><<<grid, 128, GM_SMEM, s>>>(ma, mb, g);
-    break;
-  case 3:
-    cudaFuncSetAttribute(k_gemm_bf16<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM);
-    k_gemm_bf16<3><<<grid, 128, GM_SMEM, s>>>(ma, mb, g);
-    break;
-  default:
-    return cudaErrorInvalidValue;
+  if (epi < 0 || epi > 3) return cudaErrorInvalidValue;
+  const int bn = N > 64 ? 128 : 64;
+  if ((e = make_map(&mb, B, N, K, bn)) != cudaSuccess) return e;
+  dim3 grid((M + GM_BM - 1) / GM_BM, (N + bn - 1) / bn);
+  void (*kern)(CUtensorMap, CUtensorMap, GemmArgs) = nullptr;
+  int smem = 0;
+  if (bn == 64) {
+    smem = GemmTile<64>::SMEM;
+    kern = epi == 0 ? k_gemm_bf16<0, 64> : epi == 1 ? k_gemm_bf16<1, 64>
+         : epi == 2 ? k_gemm_bf16<2, 64> : k_gemm_bf16<3, 64>;
+  } else {
+    smem = GemmTile<128>::SMEM;
+    kern = epi == 0 ? k_gemm_bf16<0, 128> : epi == 1 ? k_gemm_bf16<1, 128>
+         : epi == 2 ? k_gemm_bf16<2, 128> : k_gemm_bf16<3, 128>;
   }
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  kern<<<grid, 128, smem, s>>>(ma, mb, g);
   return cudaGetLastError();
 }
 
