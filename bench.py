@@ -296,6 +296,19 @@ def run_priest(args, torch):
                "best_cost_aug": [float(x) for x in bests[:, D].cpu()],
                "cost": "sum_t ||p''||^2 + 0.05 curvature^2 + 0.5 path distance + residual",
                "launches_per_run": c3["n_outer"] * 6}
+    # PRIEST's workspace bounds (the 20 x 20 x 5 m box of the scene) as extra rows of F
+    h.set_workspace([[0.0, 0.0, 0.0]], [[20.0, 20.0, 5.0]])
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    msw = []
+    for _ in range(max(3, args.steps // 2)):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream); run(); e1.record(stream); e1.synchronize()
+        msw.append(e0.elapsed_time(e1))
+    wsb = {"ms_per_run": float(np.mean(msw)), "box_lo": [0.0, 0.0, 0.0], "box_hi": [20.0, 20.0, 5.0],
+           "best_cost_aug": float(best[D].item())}
+    h.set_workspace(None, None)
     # residual of the returned trajectory (one more projection-free evaluation on the host
     # is not needed: the sampler's best is a projected sample; report its c_aug)
     bc = float(best[D].item())
@@ -312,7 +325,7 @@ def run_priest(args, torch):
                                    "n_p=100 over 20 s, B=4096, N_proj=2991, N_elite=410, gamma 1, "
                                    "sigma_lr 0.5", "launch_shape": shape},
             "best_cost_aug": bc, "gpu_launches_per_step": c3["n_outer"] * 6,
-            "forms": {"d_priest_barn": dpriest},
+            "forms": {"d_priest_barn": dpriest, "workspace_bounds": wsb},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 2e12,
                          "unit": "Top/s", "frac": achieved / (fp32_peak / 2.0), "traffic": None,
                          "kernel": kernel_name("fp32", shape) + " (3D, projection mode; whole run timed)",
