@@ -268,11 +268,11 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
   if (lane < NC) { XP[lane] = A.xi0[((size_t)traj * 3 + 2) * NC + lane]; XP[PLO + lane] = 0.f; }
   __syncwarp();
 
-  // projections at the lane's points; writes the per-point residual rows and returns
-  // the residual maxima (obstacle, speed, acceleration, copy). init: the copies are
-  // cos / sin psi for the targets while F xi uses the zero copy coefficients.
-  // The contraction u = F^T r is accumulated per lane over its points (44 partial
-  // sums) and reduced across the warp into U.
+  // Projections at the lane's points with this lane's residual maxima (obstacle,
+  // speed, acceleration, copy). init: the footprint targets use cos / sin psi on the
+  // grid while F xi uses the copy coefficients. The contraction u = F^T (F xi - g) is
+  // accumulated per lane over its points (44 partial sums) and reduced across the
+  // warp into U.
   auto project = [&](bool init, float (&rmax)[4]) {
     rmax[0] = rmax[1] = rmax[2] = rmax[3] = 0.f;
     float acc[44];
@@ -429,9 +429,9 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
     __syncwarp();
     if (lane < NC) { XP[lane] = xph; XP[PLO + lane] = xpl; }
     __syncwarp();
-    // alpha / d steps and the residual rows at the new iterate
+    // alpha / d steps, residual maxima and u at the new iterate
     project(false, rmax);
-    // multipliers (eq. update_lambda2_1; reading H4) and v = lambda - rho u
+    // multipliers (eq. update_lambda2_1) and v = lambda - rho u
     for (int e = lane; e < 44; e += 32) {
       const float l = LAM[e] - rho * U[e];
       LAM[e] = l;
