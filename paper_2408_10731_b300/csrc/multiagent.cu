@@ -70,7 +70,6 @@ struct MaArgs {
   float *xi_out;            // [S][N][dim][NC]
   float *res_out;           // [S]
   int *iters_out;           // [S]
-  int *err;                 // bit 0: singular KKT in the set-up
 };
 
 // shared-memory carve-up in floats (identical on host and device)
@@ -781,7 +780,6 @@ traj_status traj_ma_solve(traj_ma_batch *b, int max_iters, float tol, traj_ma_st
   A.xi_out = b->d_xi;
   A.res_out = b->d_res;
   A.iters_out = b->d_iters;
-  A.err = b->d_err;
   cudaStream_t s = b->stream;
   auto kern = c.dim == 3 ? k_ma_solve<3> : k_ma_solve<2>;
   MA_CK(b, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
