@@ -165,3 +165,23 @@ def test_eight_circles_on_the_longest_horizon_and_errors():
             h.set_initial([0], bad)
     finally:
         h.close()
+
+
+def test_full_size_bench_workload_sampled():
+    """The bench's workload (125 scenes x 8 initialisations, 20 moving ellipses, three
+    circles) in one launch; three problems checked against the oracle after 20
+    iterations."""
+    b = scenes.config2(0, n_scenes=125, inits=8, n_obstacles=20)
+    psi0, psif = _headings(b)
+    xpsi0 = np.repeat(psi0[b.traj_problem][:, None], 11, 1)
+    out, _ = _run(b, psi0, psif, xpsi0, 20)
+    P, _, _ = am.bernstein(100, float(b.duration[0]))
+    for p in (0, 62, 124):
+        idx = np.nonzero(b.traj_problem == p)[0]
+        ref = fp.solve(_problem(b, p, psi0, psif), np.concatenate(
+            [b.xi0[idx, :2], xpsi0[idx].reshape(-1, 1, 11)], 1), 20)
+        g, x = out["xi"][idx].astype(np.float64), ref["xi"]
+        for r in (0.0,) + OFFS:
+            pg = np.stack([g[:, 0] @ P.T + r * (g[:, 1] @ P.T), g[:, 2] @ P.T + r * (g[:, 3] @ P.T)], -1)
+            po = np.stack([x[:, 0] @ P.T + r * (x[:, 1] @ P.T), x[:, 2] @ P.T + r * (x[:, 3] @ P.T)], -1)
+            assert np.linalg.norm(pg - po, axis=-1).max() <= POS_TOL, p

@@ -175,3 +175,16 @@ def test_maximum_agents_and_errors():
             h.set_problems(bad)
     finally:
         h.close()
+
+
+def test_full_size_bench_workload_sampled():
+    """The bench's workload (148 scenes x 32 agents, random benchmark, r = 0.4 m,
+    the bench's penalty ladder) in one launch; three scenes checked against the
+    oracle after 20 iterations."""
+    sc = scenes.ma_random(0, n_scenes=148, n_agents=32, dim=3, room=8.0, radius=0.4,
+                          n_steps=100, T=10.0)
+    out, st = _run(sc, 20, rho=2.0, rho_levels=10, rho_growth=1.5, rho_every=20)
+    assert st["lambda_in_shared"] == 0
+    for s in (0, 77, 147):
+        ref = ma.solve(_problem(sc, s, rho=2.0, rho_levels=10, rho_growth=1.5, rho_every=20), 20)
+        assert _pos_err(sc, s, out["xi"][s], ref["xi"]) <= POS_TOL, s
