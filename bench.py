@@ -48,7 +48,7 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     "k_am_fp32": (745216, "d0995091f548b9da"),
-    "k_am_mixed": (731136, "edded2ea9273cf76"),
+    "k_am_mixed": (728576, "304cbed190840c6d"),
 }
 
 

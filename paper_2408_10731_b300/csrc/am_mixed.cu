@@ -6,20 +6,25 @@
 // tensor cores, every warp on its own (no CTA barrier inside the iteration):
 //
 //   D_w[128 x 16] (FP32, TMEM columns 16 w ..) = A[128 x K] * B_w[16 x K]^T,
-//   K = 3 n_p padded to a multiple of 64,
-//   A row 32 q + i (q = 0..3, i < 11) = basis column i, BF16:
-//                  [P(t, i) | dB(t, i) | d2B(t, i)]; the 11 rows are repeated in
-//                  each 32-row quarter because warp w may only read TMEM lanes
-//                  32 (w % 4) .. + 31; the other rows are zero,
-//   B_w row a < dim = warp w's residuals of axis a, BF16:
-//                  [sum_j r_j(t) | r_v(t) / T | r_a(t) / T^2], other rows zero,
-//   so that D_w[32 (w % 4) + i][a] = u_a[i].
+//   K = n_p padded to a multiple of 16 (contraction over the timesteps),
+//   A rows 32 q + r of every quarter q (warp w may only read TMEM lanes
+//                  32 (w % 4) .. + 31, so the 32 rows are repeated per quarter), BF16:
+//                  r = i < 11: P(t, i); r = 11 + i: dB(t, i); r = 22 + i (i < 10): d2B(t, i),
+//   B_w row g dim + a = warp w's residual group g of axis a, BF16:
+//                  g = 0: sum_j r_j(t); 1: r_v(t) / T; 2: r_a(t) / T^2;
+//                  3: r_a(n_p - 1 - t) / T^2 (time-reversed), other rows zero,
+//   so that u_a[i] = D[i][a] + D[11 + i][dim + a] + D[22 + i][2 dim + a] (i < 10) and
+//   u_a[10] = D[0][a] + ... : the last column of d2B is the time-reversed first one
+//   (d2B_10(tau) = d2B_0(1 - tau) on the symmetric grid tau_t = t / (n_p - 1)),
+//   whence its term D[22][3 dim + a]. Packing the three basis groups along M keeps
+//   K at n_p: ceil(n_p / 16) MMAs per iteration (7 at n_p = 100).
 //
 // A is written once per CTA. Per iteration a warp writes its B_w rows, fences
 // them into the async proxy, and its lane 0 issues the K/16 tcgen05.mma
-// (kind::f16, M = 128, N = 16) and commits to the warp's own mbarrier; the warp
-// then reads its dim columns with one tcgen05.ld. Both operands live in shared
-// memory in the K-major 128-byte swizzle layout.
+// (kind::f16, M = 128, N = 16) and commits to the warp's own mbarrier; while the
+// MMAs run the warp reduces its residual maxima, then reads its 4 dim columns with
+// one tcgen05.ld and sums the three groups with shuffles. Both operands live in
+// shared memory in the K-major 128-byte swizzle layout.
 //
 // Refinement: when an iteration's residuals meet the tolerance, the warp
 // recomputes that iteration's contraction in FP32, redoes the multiplier update
@@ -37,7 +42,8 @@ constexpr int MX_MAX_WARPS = 8;
 constexpr int MX_TILE_A = 128 * 128; // bytes of one 128-row x 64-column BF16 tile
 constexpr int MX_TILE_B = 16 * 128;  // bytes of one 16-row x 64-column BF16 tile
 
-__host__ __device__ inline int mixed_kt(int n_p) { return (3 * n_p + 63) / 64; }
+__host__ __device__ inline int mixed_kp(int n_p) { return (n_p + 15) & ~15; }       // K
+__host__ __device__ inline int mixed_kt(int n_p) { return (mixed_kp(n_p) + 63) / 64; } // 64-wide tiles
 __host__ __device__ inline size_t mixed_smem(int n_p, int table_floats, int warps) {
   return 1024 + (size_t)mixed_kt(n_p) * (MX_TILE_A + (size_t)warps * MX_TILE_B) +
          sizeof(float) * table_floats + 8 * MX_MAX_WARPS + 16;
@@ -73,13 +79,14 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
   __syncthreads();
   {
     const int tbl = A.problems[0].tbl_off;
-    for (int e = tid; e < NC * KT * 64; e += blockDim.x) {
-      const int i = e / (KT * 64), k = e % (KT * 64);
-      const float v = k < 3 * n_p ? stab[tbl + k * ROW + i] : 0.f; // k = g n_p + t
+    for (int e = tid; e < 32 * KT * 64; e += blockDim.x) {
+      const int r = e / (KT * 64), k = e % (KT * 64);
+      const int g = r < NC ? 0 : (r < 2 * NC ? 1 : 2), i = r - g * NC; // basis group, column
+      const float v = k < n_p ? stab[tbl + (g * n_p + k) * ROW + i] : 0.f;
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<__nv_bfloat16 *>(sA + (k >> 6) * MX_TILE_A + sw128_offset(32 * q + i, k & 63)) = h;
+        *reinterpret_cast<__nv_bfloat16 *>(sA + (k >> 6) * MX_TILE_A + sw128_offset(32 * q + r, k & 63)) = h;
     }
   }
   if (warp == 0) {
@@ -114,6 +121,7 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
   const uint32_t d_col = tmem + 16u * warp;                                        // MMA destination
   const uint32_t d_read = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 16u * warp; // this warp's quarter
   const uint32_t idesc = idesc_bf16(128, 16);
+  const int n_k16 = mixed_kp(n_p) / 16;
   const float *tP = stab + A.problems[0].tbl_off, *tD = tP + n_p * ROW, *tA = tD + n_p * ROW;
   uint32_t phase = 0;
 
@@ -162,18 +170,18 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
       float Ro[NT][DIM], Rv[NT][DIM], Ra[NT][DIM];
       project_only<DIM, NT>(xp, tP, tD, tA, obs, prp, n_p, pr.dt, pr.invT, pr.invT2, A.vmax,
                             A.amax, lane, Ro, Rv, Ra, mo, mv, ma);
-      // this warp's B rows: axis a, k = g n_p + t
+      // this warp's B rows g dim + a at k = t (group 3: k = n_p - 1 - t)
 #pragma unroll
       for (int m = 0; m < NT; ++m) {
         const int t = lane + 32 * m;
         if (t < n_p) {
 #pragma unroll
           for (int a = 0; a < DIM; ++a) {
-            const float vals[3] = {Ro[m][a], Rv[m][a], Ra[m][a]};
+            const float vals[4] = {Ro[m][a], Rv[m][a], Ra[m][a], Ra[m][a]};
 #pragma unroll
-            for (int g = 0; g < 3; ++g) {
-              const int kk = g * n_p + t;
-              *reinterpret_cast<__nv_bfloat16 *>(myB + (kk >> 6) * MX_TILE_B + sw128_offset(a, kk & 63)) =
+            for (int g = 0; g < 4; ++g) {
+              const int kk = g < 3 ? t : n_p - 1 - t;
+              *reinterpret_cast<__nv_bfloat16 *>(myB + (kk >> 6) * MX_TILE_B + sw128_offset(g * DIM + a, kk & 63)) =
                   __float2bfloat16_rn(vals[g]);
             }
           }
@@ -184,21 +192,20 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
       __syncwarp();
       if (lane == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int j = 0; j < KT; ++j) {
-          const uint64_t da = sdesc_sw128(smem_u32(sA + j * MX_TILE_A));
-          const uint64_t db = sdesc_sw128(smem_u32(myB + j * MX_TILE_B));
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
-            asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                         :: "r"(d_col), "l"(da + 2 * ks), "l"(db + 2 * ks), "r"(idesc), "r"(acc));
-          }
+        for (int s16 = 0; s16 < n_k16; ++s16) {
+          const int j = s16 >> 2, ks = s16 & 3;
+          const uint64_t da = sdesc_sw128(smem_u32(sA + j * MX_TILE_A)) + 2 * ks;
+          const uint64_t db = sdesc_sw128(smem_u32(myB + j * MX_TILE_B)) + 2 * ks;
+          const uint32_t acc = s16 > 0 ? 1u : 0u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                       :: "r"(d_col), "l"(da), "l"(db), "r"(idesc), "r"(acc));
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(my_mbar) : "memory");
       }
       __syncwarp();
+      mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma); // while the MMAs run
       const bool waited = __all_sync(FULL, mbar_wait(my_mbar, phase));
       phase ^= 1u;
       if (!waited) { // the MMA never completed: give up on this warp's work
@@ -207,23 +214,30 @@ __global__ void __launch_bounds__(MX_MAX_WARPS * 32) k_am_mixed(const __grid_con
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t r[4];
-      if constexpr (DIM == 2) {
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
-                     : "=r"(r[0]), "=r"(r[1]) : "r"(d_read));
-        r[2] = r[3] = 0u;
-      } else {
+      uint32_t r[4 * DIM];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                     "=r"(r[6]), "=r"(r[7])
+                   : "r"(d_read));
+      if constexpr (DIM == 3)
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(d_read));
-      }
+                     : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]) : "r"(d_read + 8u));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      // lane l (< 11) holds u_a[l] in r[a]; lane 16 a + i takes u_a[i]
-      const float v0 = __shfl_sync(FULL, __uint_as_float(r[0]), oi);
-      const float v1 = __shfl_sync(FULL, __uint_as_float(r[1]), oi);
-      const float un = oa ? v1 : v0;
-      const float un2 = DIM == 3 ? __shfl_sync(FULL, __uint_as_float(r[2]), oi) : 0.f;
-      mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
+      // lane l holds row l of the quarter: its basis group's column per axis (v), and
+      // lane 22 also the time-reversed term of column 10 (w); lane 16 a + i sums u_a[i]
+      float uax[DIM];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const float v = __uint_as_float(lane < NC ? r[a] : (lane < 2 * NC ? r[DIM + a] : r[2 * DIM + a]));
+        const float s1 = __shfl_sync(FULL, v, ri);
+        const float s2 = __shfl_sync(FULL, v, NC + ri);
+        const float s3 = __shfl_sync(FULL, v, 2 * NC + (ri < NC - 1 ? ri : 0));
+        const float s4 = __shfl_sync(FULL, __uint_as_float(r[3 * DIM + a]), 2 * NC);
+        uax[a] = (s1 + s2) + (ri < NC - 1 ? s3 : s4);
+      }
+      const float un = oa ? uax[1] : uax[0];
+      const float un2 = DIM == 3 ? uax[2] : 0.f;
       if (k == 0) {
         uo = un; uo2 = un2;
       } else {
