@@ -85,3 +85,19 @@ def test_mixed_full_size_sampled_error(capsys):
               f"median {np.median(err):.2e} m")
     assert err.max() <= 5e-2 and np.median(err) <= 5e-3
     assert np.all(np.isfinite(g["xi"])) and np.all(g["iters"] == 20)
+
+
+@pytest.mark.parametrize("n_steps", [17, 37, 75, 150, 256])
+def test_mixed_every_contraction_length(n_steps, capsys):
+    """Horizons whose padded contraction length K = n_p rounded up to 16 spans one
+    to four 64-wide tiles, with a ragged last tile and odd n_p (the time-reversed
+    residual that stands in for the last d2B column pairs t with n_p - 1 - t)."""
+    b = scenes.config2(3, n_scenes=4, inits=4, n_obstacles=20, n_steps=n_steps)
+    g = gpu_solve(b, 20, precision="mixed")
+    o = am.solve(b, 20, tol=-1.0)
+    err = position_error(b, g["xi"], o["xi"])
+    with capsys.disabled():
+        print(f"\nmixed vs FP64 after 20 iterations, n_p = {n_steps}: max {err.max():.2e} m, "
+              f"median {np.median(err):.2e} m")
+    assert err.max() <= 5e-2 and np.median(err) <= 5e-3
+    assert np.all(g["iters"] == 20)
