@@ -35,6 +35,12 @@ WORKLOAD_UNEVEN = ("uneven 2D batch: 2048 problems, obstacle counts log-uniform 
                    "n_p in {50,75,100,150} over T=0.1 n_p s, goal 0.55 vmax T away, 8 "
                    "initialisations each = 16384 trajectories in one persistent launch "
                    "(CUDA graph, autotuned CTA shape), cap 500 iterations, tol 1e-3")
+WORKLOAD_LONG = ("long-horizon 2D batch (Paper I's n_o = 10, n_p = 1000): 128 scenes, n_p=1000 "
+                 "over T=10 s, 10 constant-velocity axis-aligned ellipses (semi-axes U(0.2,0.8) m, "
+                 "speed U(0,1) m/s), start (0,0), goal 0.55 vmax T along the diagonal, 8 "
+                 "initialisations N(straight line, 0.5 m) = 1024 trajectories, grid points "
+                 "streamed in chunks of 128, vmax 1.5 m/s, amax 2 m/s^2, rho 1, cap 500 "
+                 "iterations, tol 1e-3")
 
 
 # DRAM bytes (read + write) per launch of each solve kernel on the 1024-trajectory
@@ -44,6 +50,7 @@ WORKLOAD_UNEVEN = ("uneven 2D batch: 2048 problems, obstacle counts log-uniform 
 KERNEL_SOURCES = {
     "k_am_fp32": ("am_solve.cu", "am_device.cuh", "internal.cuh"),
     "k_am_team": ("am_solve.cu", "am_device.cuh", "internal.cuh"),
+    "k_am_long": ("am_solve.cu", "am_device.cuh", "internal.cuh"),
     "k_am_mixed": ("am_mixed.cu", "am_device.cuh", "internal.cuh", "tcgen05.cuh"),
 }
 MEASURED_TRAFFIC = {
@@ -81,10 +88,12 @@ def combine_ranks(dist, world, total_ms, n_solved, e2e_rate, device="cpu"):
     return float(g[:, 0].max()), float(g[:, 1].sum()), float(g[:, 2].sum())
 
 
-def kernel_name(precision, shape):
+def kernel_name(precision, shape, max_np=100):
     """The solve kernel a handle of this precision and launch shape runs."""
     if precision == "mixed":
         return "k_am_mixed"
+    if max_np > 256:
+        return "k_am_long"
     return "k_am_team" if shape and shape.get("warps_per_trajectory", 1) > 1 else "k_am_fp32"
 
 
@@ -588,7 +597,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workload", default="config2",
-                    choices=["config2", "uneven", "priest", "multiagent", "footprint", "gemm"])
+                    choices=["config2", "uneven", "long", "priest", "multiagent", "footprint",
+                             "gemm"])
     ap.add_argument("--ma-agents", type=int, default=32)
     ap.add_argument("--ma-scenes", type=int, default=148)
     ap.add_argument("--ma-radius", type=float, default=0.4)
@@ -635,6 +645,8 @@ def main():
     from paper_2408_10731_b300 import autotune
     if args.workload == "uneven":
         batch = scenes.config4(args.seed + rank)
+    elif args.workload == "long":
+        batch = scenes.long_horizon(args.seed + rank, n_scenes=128, inits=8, n_steps=1000)
     else:
         batch = scenes.config2(args.seed + rank)
     h = trajbatch.from_batch(batch, precision=args.precision)
@@ -762,7 +774,7 @@ def main():
         ok = o["status"] == 0
         prec_f = forms[name][0].split("_")[0]
         form_summary[name] = {"kernel": kernel_name(prec_f, shape if prec_f == args.precision
-                                                    else None),
+                                                    else None, int(batch.n_steps.max())),
                               "solved_per_s": float(np.sum(sv)) / (float(np.sum(sm)) * 1e-3),
                               "ms_per_batch_solve": float(np.mean(sm)),
                               "solve_kernel_ms": float(np.mean(km)),
@@ -780,7 +792,8 @@ def main():
         achieved = ops / kern_s
         peak_ops = fp32_peak / 2.0  # FFMA rate in lane-operations/s (2 FLOP per FMA)
         prec_h = forms[headline][0].split("_")[0]
-        kern = kernel_name(prec_h, shape if prec_h == args.precision else None)
+        kern = kernel_name(prec_h, shape if prec_h == args.precision else None,
+                           int(batch.n_steps.max()))
         traffic = measured_traffic(kern) if args.workload == "config2" else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -788,7 +801,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+bf16" if prec_h == "mixed" else "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.workload == "config2" else WORKLOAD_UNEVEN,
+            "config": {"workload": {"config2": WORKLOAD, "uneven": WORKLOAD_UNEVEN,
+                                    "long": WORKLOAD_LONG}[args.workload],
                        "precision": args.precision, "launch_shape": shape,
                        "l2": "flushed between timed steps (256 MB write, outside the events)",
                        "per_rank_batch": "seed + rank",
@@ -813,8 +827,9 @@ def main():
             "headline_form": headline, "forms": form_summary,
             "source_digest": {k: source_digest(k) for k in KERNEL_SOURCES},
         }
-        if world == 1 and not args.no_cpu_baseline and args.workload == "config2":
-            cb = cpu_baseline(args.seed, workload=batch)
+        if world == 1 and not args.no_cpu_baseline and args.workload in ("config2", "long"):
+            cb = cpu_baseline(args.seed, scenes_idx=range(16) if args.workload == "config2"
+                              else range(4), workload=batch)
             cb.pop("seconds", None); cb.pop("solved", None)
             line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)

@@ -85,7 +85,8 @@ typedef struct traj_config {
   int max_problems;  /* capacity: problems (scenes) */
   int max_traj;      /* capacity: trajectories */
   int max_obstacles; /* capacity: obstacles summed over problems */
-  int max_steps;     /* capacity: timesteps n_p of any problem (<= 256) */
+  int max_steps;     /* capacity: timesteps n_p of any problem (<= 1024; above 256
+                      * the FP32 form only) */
   double vmax, amax; /* velocity / acceleration bounds (eqs. fv, fa) */
   double rho;        /* penalty weight (one rho for every constraint group) */
   double w_smooth, w_track; /* cost weights of TRAJ_COST_SMOOTH_TRACK */
@@ -97,7 +98,7 @@ typedef struct traj_config {
 typedef struct traj_batch traj_batch; /* opaque; owns the device workspace */
 
 /* Create a handle. Validates the config (dim in {2,3}, degree 10, positive
- * capacities, max_steps <= 256, vmax/amax/rho > 0) and allocates the
+ * capacities, max_steps <= 1024, vmax/amax/rho > 0) and allocates the
  * workspace on the stream. *out is set only on TRAJ_OK. */
 traj_status traj_batch_create(const traj_config *cfg, traj_batch **out);
 
@@ -146,7 +147,13 @@ typedef struct traj_solve_stats {
  * every iteration k >= 1, or until max_iters. tol < 0 never stops early.
  * timeout_ms > 0 sets a device-side deadline (TRAJ_ETIMEOUT if hit).
  * Asynchronous on the stream when stats == NULL; with stats it synchronises
- * and fills them. Calling it again restarts from coeffs0. */
+ * and fills them. Calling it again restarts from coeffs0.
+ * Long horizons (Paper I plans over up to 1000 grid points): a batch whose
+ * longest problem has more than 256 grid points runs one warp per trajectory
+ * that streams its grid points in chunks of 128 every iteration (FP32 form
+ * only; TRAJ_ESHAPE in the tensor-core form or with warps_per_trajectory > 1).
+ * The basis tables of the distinct horizons stay within 160 KB (n_p = 1000
+ * alone takes 144 KB). */
 traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
                        traj_solve_stats *stats);
 

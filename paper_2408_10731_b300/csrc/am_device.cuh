@@ -49,10 +49,12 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
   return v[0];
 }
 
+// Warp maximum of a non-negative float (a squared residual norm). Non-negative
+// IEEE floats order as their bit patterns do as unsigned integers, so one
+// redux.sync unsigned max gives the exact maximum (a NaN, whose pattern is above
+// every finite one, is kept rather than dropped as fmaxf would).
 __device__ __forceinline__ float warp_max(float x) {
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) x = fmaxf(x, __shfl_xor_sync(FULL, x, s));
-  return x;
+  return __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(x)));
 }
 
 __device__ __forceinline__ void load_row(const float *row, float (&r)[12]) {
@@ -467,6 +469,49 @@ __device__ __forceinline__ void project_contract(
       bound_residuals<DIM>(xp, rd, ra, invT, invT2, vmax, amax, Rv, Ra, mv, ma);
 #pragma unroll
       for (int a = 0; a < DIM; ++a) contract_row3(up[a], rp, rd, ra, -acc[m][a], Rv[a], Ra[a]);
+    }
+  }
+}
+
+// Long horizons (more grid points than a lane holds in registers): the lane's
+// timesteps t = c0 + lane + 32 m, m < CNT, one chunk of 32 CNT grid points at a
+// time, each chunk evaluated, projected onto every obstacle and the bounds, and
+// contracted; the contraction and the residual maxima accumulate over the chunks.
+template <int DIM, int CNT>
+__device__ __forceinline__ void project_contract_chunked(
+    const float2 (&xp)[DIM][6], const float *tP, const float *tD, const float *tA,
+    const float4 *obs, const ProblemDev *pr, int n_p, float dt, float invT, float invT2,
+    float vmax, float amax, int lane, float2 (&up)[DIM][6], float &mo, float &mv, float &ma) {
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) up[a][j] = make_float2(0.f, 0.f);
+  mo = 0.f; mv = 0.f; ma = 0.f;
+  for (int c0 = 0; c0 < n_p; c0 += 32 * CNT) {
+    const int nt = min(CNT, (n_p - c0 + 31) >> 5);
+    float pos[CNT][DIM], acc[CNT][DIM], tm[CNT];
+    eval_positions<DIM, CNT>(xp, tP, n_p, nt, dt, c0 + lane, 32, pos, tm);
+#pragma unroll
+    for (int m = 0; m < CNT; ++m)
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) acc[m][a] = 0.f;
+    float moc;
+    pair_loop<DIM, CNT>(pos, tm, obs, pr->n_o, acc, moc);
+    mo = fmaxf(mo, moc);
+    if (pr->box) box_residuals<DIM, CNT>(pr, pos, c0 + lane, 32, n_p, nt, acc, mo);
+#pragma unroll
+    for (int m = 0; m < CNT; ++m) {
+      const int t = c0 + lane + 32 * m;
+      if (m < nt && t < n_p) {
+        float rp[12], rd[12], ra[12];
+        load_row(tP + t * ROW, rp);
+        load_row(tD + t * ROW, rd);
+        load_row(tA + t * ROW, ra);
+        float Rv[DIM], Ra[DIM];
+        bound_residuals<DIM>(xp, rd, ra, invT, invT2, vmax, amax, Rv, Ra, mv, ma);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) contract_row3(up[a], rp, rd, ra, -acc[m][a], Rv[a], Ra[a]);
+      }
     }
   }
 }

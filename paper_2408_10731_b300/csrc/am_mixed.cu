@@ -330,7 +330,7 @@ static cudaError_t launch_mx(const SolveArgs &a, int n_p, const LaunchShape &sha
 cudaError_t launch_am_mixed(int dim, int n_p, const SolveArgs &a, const LaunchShape &shape,
                             int n_sm, cudaStream_t s, LaunchShape *used) {
   const int nt = (n_p + 31) / 32;
-  if (shape.team > 1) return cudaErrorInvalidValue;
+  if (shape.team > 1 || nt > 8) return cudaErrorInvalidValue; // one warp, at most 256 grid points
   if (dim == 2) {
     if (nt <= 2) return launch_mx<2, 2>(a, n_p, shape, n_sm, s, used);
     if (nt <= 4) return launch_mx<2, 4>(a, n_p, shape, n_sm, s, used);

@@ -35,7 +35,7 @@ namespace tb {
 
 constexpr int MAX_WARPS_PER_BLOCK = 8;
 
-template <int DIM, int MAXNT>
+template <int DIM, int MAXNT, bool CHUNKED = false>
 __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *stab, int lane,
                                        unsigned long long deadline) {
   const int p = A.traj_problem[b];
@@ -89,8 +89,12 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
     float2 xp[DIM][6];
     broadcast_pairs<DIM>(xo, xo2, xp);
     float2 up[DIM][6];
-    project_contract<DIM, MAXNT>(xp, tP, tD, tA, obs, A.problems + p, n_p, nt, pr.dt, pr.invT,
-                                 pr.invT2, A.vmax, A.amax, lane, up, mo, mv, ma);
+    if constexpr (CHUNKED)
+      project_contract_chunked<DIM, MAXNT>(xp, tP, tD, tA, obs, A.problems + p, n_p, pr.dt,
+                                           pr.invT, pr.invT2, A.vmax, A.amax, lane, up, mo, mv, ma);
+    else
+      project_contract<DIM, MAXNT>(xp, tP, tD, tA, obs, A.problems + p, n_p, nt, pr.dt, pr.invT,
+                                   pr.invT2, A.vmax, A.amax, lane, up, mo, mv, ma);
     scatter_pairs<DIM>(up, lane, uo, uo2);
     mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
     if (k > 0) { // Line 6: multiplier update (lambda0 = 0 at the initial projection)
@@ -349,6 +353,39 @@ k_am_fp32(const __grid_constant__ SolveArgs A) {
   }
 }
 
+// Horizons beyond 32 * 8 grid points: one warp per trajectory, the timesteps
+// streamed in chunks of LONG_CNT slots (128 grid points) per iteration. Basis
+// tables are staged in shared memory as in k_am_fp32 (at most 160 KB).
+constexpr int LONG_CNT = 4;
+
+template <int DIM>
+__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32, 1)
+k_am_long(const __grid_constant__ SolveArgs A) {
+  extern __shared__ float4 smem4[];
+  const float4 *g4 = reinterpret_cast<const float4 *>(A.tables);
+  for (int i = threadIdx.x; i < A.table_floats_total / 4; i += blockDim.x) smem4[i] = g4[i];
+  __syncthreads();
+  const float *stab = reinterpret_cast<const float *>(smem4);
+  const int lane = threadIdx.x & 31;
+  unsigned long long deadline = 0;
+  if (A.timeout_ns) {
+    unsigned long long t0 = 0;
+    if (lane == 0) {
+      const unsigned long long now = globaltimer_ns();
+      const unsigned long long prev = atomicCAS(A.t0, 0ull, now);
+      t0 = prev ? prev : now;
+    }
+    deadline = __shfl_sync(FULL, t0, 0) + A.timeout_ns;
+  }
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(A.queue, 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= A.n_traj) break;
+    solve_one<DIM, LONG_CNT, true>(A, A.order[item], stab, lane, deadline);
+  }
+}
+
 template <int W> struct TeamKernel {
   template <int DIM, int MAXNT> static constexpr auto get() { return k_am_team<DIM, (MAXNT + W - 1) / W, W>; }
 };
@@ -380,10 +417,37 @@ static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_
   return cudaGetLastError();
 }
 
+// k_am_long: the shape's warps per block and blocks per SM apply; the team is one warp.
+template <int DIM>
+static cudaError_t launch_long(const SolveArgs &a, const LaunchShape &shape, int n_sm,
+                               cudaStream_t s, LaunchShape *used) {
+  const int warps = shape.warps_per_block > 0 ? shape.warps_per_block : 4;
+  if (warps > MAX_WARPS_PER_BLOCK) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float) * (size_t)a.table_floats_total;
+  cudaError_t e = cudaFuncSetAttribute(k_am_long<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_am_long<DIM>, warps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  if (shape.blocks_per_sm > 0 && shape.blocks_per_sm < occ) occ = shape.blocks_per_sm;
+  long long want = ((long long)a.n_traj + warps - 1) / warps;
+  long long grid = (long long)n_sm * occ;
+  if (want < grid) grid = want;
+  if (grid < 1) grid = 1;
+  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = 1; }
+  k_am_long<DIM><<<(unsigned)grid, warps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s, LaunchShape *used) {
   if (precision == 1) return launch_am_mixed(dim, max_np, a, shape, n_sm, s, used);
   const int nt = (max_np + 31) / 32;
+  if (nt > 8) { // long horizons: chunked, one warp per trajectory
+    if (shape.team != 0 && shape.team != 1) return cudaErrorInvalidValue;
+    return dim == 2 ? launch_long<2>(a, shape, n_sm, s, used) : launch_long<3>(a, shape, n_sm, s, used);
+  }
   const int team = shape.team;
   if (team != 0 && team != 1 && team != 2 && team != 4) return cudaErrorInvalidValue;
 #define TB_PICK(D, N)                                                                   \

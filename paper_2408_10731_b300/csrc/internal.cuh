@@ -10,7 +10,8 @@ constexpr int NC = 11;      // Bernstein degree 10 -> 11 coefficients per axis
 constexpr int NE = 4;       // boundary rows per axis
 constexpr int NK = NC + NE; // KKT size
 constexpr int ROW = 12;     // padded row length (floats) of every 11-wide table row
-constexpr int MAX_STEPS = 256;
+constexpr int MAX_STEPS = 256;       // grid points per problem held in registers by a warp
+constexpr int MAX_STEPS_LONG = 1024; // batch handle, FP32 form: longer horizons run chunked
 constexpr int RHO_MAX_LEVELS = 10; // penalty levels of the continuation ladder
 
 // Per-problem record on the device (64 bytes).

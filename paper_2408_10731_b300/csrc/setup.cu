@@ -37,57 +37,79 @@ __device__ __forceinline__ void split_store(float *hi, float *lo, double x) {
   *lo = (float)(x - (double)h);
 }
 
-// One block per problem. Dynamic shared memory: 3 * max_np * NC doubles.
-__global__ void k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
-                                 const double *goal, int dim, double rho, double w_s, double w_t,
-                                 int cost_mode, float *constants) {
+// One block of SETUP_THREADS per problem. The scaled basis rows are staged in
+// shared memory SETUP_CHUNK grid points at a time (3 * min(max_np, SETUP_CHUNK) * NC
+// doubles), so any horizon fits; each thread keeps its Gram / q sums over the
+// chunks in a register, adding the grid points in ascending order.
+constexpr int SETUP_THREADS = 256, SETUP_CHUNK = 256;
+static_assert(NC * NC + 3 * NC <= SETUP_THREADS, "one Gram / q element per thread");
+
+__global__ void __launch_bounds__(SETUP_THREADS)
+k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
+                 const double *goal, int dim, double rho, double w_s, double w_t,
+                 int cost_mode, float *constants) {
   extern __shared__ double sm[];
   __shared__ double Q[NC * NC], M[NC * NC], qv[3 * NC];
   __shared__ double W[NK * 2 * NK];
   __shared__ double K11[NC * NC], K12[NC * NE], Gm[NC * NC];
+  __shared__ double Bnd[NE][NC]; // boundary rows P_0, Pd_0, Pdd_0, P_{n_p - 1}
   __shared__ int piv_s;
   const int p = blockIdx.x;
   const ProblemDev pr = problems[p];
   const int n_p = pr.n_p, n_o = pr.n_o;
   const double T = Tarr[p];
-  double *P = sm, *Pd = sm + n_p * NC, *Pdd = sm + 2 * n_p * NC;
+  const int CH = n_p < SETUP_CHUNK ? n_p : SETUP_CHUNK;
+  double *P = sm, *Pd = sm + CH * NC, *Pdd = sm + 2 * CH * NC;
   const double iT = 1.0 / T, iT2 = 1.0 / (T * T);
 
-  for (int t = threadIdx.x; t < n_p; t += blockDim.x) {
+  if (threadIdx.x < 2) {
     double a[NC], b[NC], c[NC];
-    basis_row(n_p, t, a, b, c);
+    basis_row(n_p, threadIdx.x == 0 ? 0 : n_p - 1, a, b, c);
     for (int i = 0; i < NC; ++i) {
-      P[t * NC + i] = a[i];
-      Pd[t * NC + i] = b[i] * iT;
-      Pdd[t * NC + i] = c[i] * iT2;
+      if (threadIdx.x == 0) { Bnd[0][i] = a[i]; Bnd[1][i] = b[i] * iT; Bnd[2][i] = c[i] * iT2; }
+      else Bnd[3][i] = a[i];
     }
   }
-  __syncthreads();
 
-  // Q, M = F^T F (closed form of the stacked F), q per axis
-  for (int e = threadIdx.x; e < NC * NC + 3 * NC; e += blockDim.x) {
-    if (e < NC * NC) {
-      int a = e / NC, b = e % NC;
-      double pp = 0, dd = 0, aa = 0;
-      for (int t = 0; t < n_p; ++t) {
-        pp += P[t * NC + a] * P[t * NC + b];
-        dd += Pd[t * NC + a] * Pd[t * NC + b];
-        aa += Pdd[t * NC + a] * Pdd[t * NC + b];
+  // Q, M = F^T F (closed form of the stacked F), q per axis: element el of thread el
+  const int el = threadIdx.x;
+  const bool gram = el < NC * NC, qrow = el >= NC * NC && el < NC * NC + 3 * NC;
+  const int ga = gram ? el / NC : 0, gb = gram ? el % NC : 0;
+  const int qk = qrow ? el - NC * NC : 0, qax = qk / NC, qi = qk % NC;
+  const double s0 = qrow && qax < dim ? start[p * dim + qax] : 0.0;
+  const double g0 = qrow && qax < dim ? goal[p * dim + qax] : 0.0;
+  double pp = 0, dd = 0, aa = 0, sq = 0;
+  for (int c0 = 0; c0 < n_p; c0 += CH) {
+    const int nc = n_p - c0 < CH ? n_p - c0 : CH;
+    __syncthreads(); // the previous chunk has been read
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+      double a[NC], b[NC], c[NC];
+      basis_row(n_p, c0 + t, a, b, c);
+      for (int i = 0; i < NC; ++i) {
+        P[t * NC + i] = a[i];
+        Pd[t * NC + i] = b[i] * iT;
+        Pdd[t * NC + i] = c[i] * iT2;
       }
-      Q[e] = cost_mode == 0 ? (w_s * aa + w_t * pp) : (a == b ? 1.0 : 0.0);
-      M[e] = (double)(n_o + 2 * pr.box) * pp + dd + aa; // G = [-P; P] per axis adds 2 P^T P
-    } else {
-      int k = e - NC * NC, ax = k / NC, i = k % NC;
-      double s = 0;
-      if (ax < dim) {
-        double s0 = start[p * dim + ax], g0 = goal[p * dim + ax];
-        for (int t = 0; t < n_p; ++t) {
-          double tau = (double)t / (double)(n_p - 1);
-          s += P[t * NC + i] * (s0 + (g0 - s0) * tau);
-        }
-      }
-      qv[k] = -w_t * s; // q = -w_t P^T x_des
     }
+    __syncthreads();
+    if (gram) {
+      for (int t = 0; t < nc; ++t) {
+        pp += P[t * NC + ga] * P[t * NC + gb];
+        dd += Pd[t * NC + ga] * Pd[t * NC + gb];
+        aa += Pdd[t * NC + ga] * Pdd[t * NC + gb];
+      }
+    } else if (qrow && qax < dim) {
+      for (int t = 0; t < nc; ++t) {
+        double tau = (double)(c0 + t) / (double)(n_p - 1);
+        sq += P[t * NC + qi] * (s0 + (g0 - s0) * tau);
+      }
+    }
+  }
+  if (gram) {
+    Q[el] = cost_mode == 0 ? (w_s * aa + w_t * pp) : (ga == gb ? 1.0 : 0.0);
+    M[el] = (double)(n_o + 2 * pr.box) * pp + dd + aa; // G = [-P; P] per axis adds 2 P^T P
+  } else if (qrow) {
+    qv[qk] = -w_t * sq; // q = -w_t P^T x_des
   }
   __syncthreads();
   // augmented [K | I]
@@ -98,12 +120,10 @@ __global__ void k_setup_problems(ProblemDev *problems, const double *Tarr, const
     else if (r < NC && c < NC) v = Q[r * NC + c] + rho * M[r * NC + c];
     else if (r < NC && c >= NC) { // A^T
       int er = c - NC;
-      const double *row = er == 0 ? &P[0] : er == 1 ? &Pd[0] : er == 2 ? &Pdd[0] : &P[(n_p - 1) * NC];
-      v = row[r];
+      v = Bnd[er][r];
     } else if (r >= NC && c < NC) {
       int er = r - NC;
-      const double *row = er == 0 ? &P[0] : er == 1 ? &Pd[0] : er == 2 ? &Pdd[0] : &P[(n_p - 1) * NC];
-      v = row[c];
+      v = Bnd[er][c];
     } else v = 0.0;
     W[e] = v;
   }
@@ -232,12 +252,14 @@ cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const 
                                   double rho, double w_smooth, double w_track, int cost_mode,
                                   int max_np, float *d_constants, cudaStream_t s) {
   if (n_problems <= 0) return cudaSuccess;
-  size_t smem = sizeof(double) * 3 * (size_t)max_np * NC;
+  const int ch = max_np < SETUP_CHUNK ? max_np : SETUP_CHUNK;
+  size_t smem = sizeof(double) * 3 * (size_t)ch * NC;
   cudaError_t e = cudaFuncSetAttribute(k_setup_problems,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_setup_problems<<<n_problems, 256, smem, s>>>(d_problems, d_T, d_start, d_goal, dim, rho,
-                                                 w_smooth, w_track, cost_mode, d_constants);
+  k_setup_problems<<<n_problems, SETUP_THREADS, smem, s>>>(d_problems, d_T, d_start, d_goal, dim,
+                                                           rho, w_smooth, w_track, cost_mode,
+                                                           d_constants);
   return cudaGetLastError();
 }
 

@@ -149,8 +149,8 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
   if (c.dim != 2 && c.dim != 3) { g_create_error = "dim must be 2 or 3"; return TRAJ_EINVAL; }
   if (c.degree != 10) { g_create_error = "degree must be 10"; return TRAJ_EINVAL; }
   if (c.max_problems < 1 || c.max_traj < 1 || c.max_obstacles < 0 || c.max_steps < 2 ||
-      c.max_steps > MAX_STEPS) {
-    g_create_error = "capacities out of range (max_steps must be in [2, 256])";
+      c.max_steps > MAX_STEPS_LONG) {
+    g_create_error = "capacities out of range (max_steps must be in [2, 1024])";
     return TRAJ_EINVAL;
   }
   if (!(c.vmax > 0) || !(c.amax > 0) || !(c.rho > 0) || !(c.w_smooth >= 0) || !(c.w_track >= 0) ||
@@ -190,7 +190,7 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
   if ((e = dalloc(&b->d_problems, P)) || (e = dalloc(&b->d_T, P)) || (e = dalloc(&b->d_start, P * D)) ||
       (e = dalloc(&b->d_goal, P * D)) || (e = dalloc(&b->d_constants, P * CONST_FLOATS)) ||
       (e = dalloc(&b->d_rho_ladder, RHO_MAX_LEVELS)) ||
-      (e = dalloc(&b->d_horizons, MAX_STEPS + 1)) || (e = dalloc(&b->d_hoffsets, MAX_STEPS + 1)) ||
+      (e = dalloc(&b->d_horizons, MAX_STEPS_LONG + 1)) || (e = dalloc(&b->d_hoffsets, MAX_STEPS_LONG + 1)) ||
       (e = dalloc(&b->d_obs, ((N + P) / 2 + 1) * pair_vec(c.dim))) ||
       (e = dalloc(&b->d_obs_stage, 3 * N * D)) || (e = dalloc(&b->d_obs_index, 2 * (P + 1))) || (e = dalloc(&b->d_traj_problem, B)) ||
       (e = dalloc(&b->d_order, B)) || (e = dalloc(&b->d_xi0, B * D * NC)) ||
@@ -450,10 +450,16 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
   if (max_iters < 0) return fail(b, TRAJ_EINVAL, "max_iters must be >= 0");
   if (std::isnan(tol) || !(timeout_ms >= 0)) return fail(b, TRAJ_EINVAL, "bad tol or timeout");
-  if (b->cfg.precision == TRAJ_PREC_MIXED)
+  if (b->cfg.precision == TRAJ_PREC_MIXED) {
     for (int p = 1; p < b->n_problems; ++p)
       if (b->n_steps[p] != b->n_steps[0])
         return fail(b, TRAJ_ESHAPE, "the tensor-core form needs one horizon (n_steps) per batch");
+    if (b->max_np_used > MAX_STEPS)
+      return fail(b, TRAJ_ESHAPE, "the tensor-core form takes at most 256 grid points per problem");
+  }
+  if (b->max_np_used > MAX_STEPS && b->shape.team != 1)
+    return fail(b, TRAJ_ESHAPE, "horizons above 256 grid points run one warp per trajectory "
+                                "(warps_per_trajectory 1)");
   SolveArgs a{};
   a.problems = b->d_problems;
   a.obstacles = b->d_obs;

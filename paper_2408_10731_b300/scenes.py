@@ -216,6 +216,59 @@ def ellipse_scenes(seed: int, n_scenes: int, n_obstacles: int = 50, inits: int =
                  vmax=1.5, amax=2.0, rho=1.0, name=f"ellipses_seed{seed}")
 
 
+def long_horizon(seed: int = 0, n_scenes: int = 16, inits: int = 8, n_steps=1000,
+                 n_obstacles: int = 10, dim: int = 2, moving: bool = True) -> Batch:
+    """Long horizons in the spirit of Paper I (n_o = 10 obstacles, n_p = 1000 grid
+    points; 2D static, 2D dynamic and 3D problems): grid spacing 0.01 s (T = 0.01 n_p),
+    start at the origin, goal at distance 0.55 vmax T along the diagonal (in 3D with
+    a rise of a quarter of the planar distance), n_obstacles axis-aligned ellipses
+    (ellipsoids in 3D) with semi-axes U(0.2, 0.8) m, centres uniform in the box
+    spanned by start and goal (z in [0, goal z + 1] in 3D), speed U(0, 1) m/s in a
+    uniform random direction (zero when moving is False); obstacles covering the
+    start at t = 0 or the goal at t = T are redrawn. n_steps is one horizon or one
+    per scene. `inits` initialisations N(straight line, 0.5 m) per scene."""
+    rng = np.random.default_rng(seed)
+    vmax, amax = 1.5, 2.0
+    n_np = np.broadcast_to(np.asarray(n_steps, np.int32), (n_scenes,)).copy()
+    cen, ax, vel, xi0, tp, offs = [], [], [], [], [], [0]
+    starts, goals, Ts = [], [], []
+    for s in range(n_scenes):
+        T = 0.01 * float(n_np[s])
+        reach = 0.55 * vmax * T
+        if dim == 2:
+            goal = np.full(2, reach / math.sqrt(2.0))
+        else:
+            planar = reach / math.sqrt(1.0 + 1.0 / 16.0)
+            goal = np.array([planar / math.sqrt(2.0), planar / math.sqrt(2.0), planar / 4.0])
+        start = np.zeros(dim)
+        hi = goal.copy()
+        if dim == 3:
+            hi[2] = goal[2] + 1.0
+        c_l, a_l, v_l = [], [], []
+        while len(c_l) < n_obstacles:
+            a = rng.uniform(0.2, 0.8, dim)
+            c = rng.uniform(np.zeros(dim), hi)
+            speed = rng.uniform(0.0, 1.0) if moving else 0.0
+            d = rng.normal(0.0, 1.0, dim)
+            v = speed * d / max(np.linalg.norm(d), 1e-12)
+            if _inside(start, c, a) or _inside(goal, c + v * T, a):
+                continue
+            c_l.append(c); a_l.append(a); v_l.append(v)
+        cen.append(np.array(c_l)); ax.append(np.array(a_l)); vel.append(np.array(v_l))
+        offs.append(offs[-1] + n_obstacles)
+        xi0.append(straight_line_coeffs(start, goal)[None] +
+                   rng.normal(0.0, 0.5, (inits, dim, N_COEFF)))
+        tp.extend([s] * inits)
+        starts.append(start); goals.append(goal); Ts.append(T)
+    return Batch(dim=dim, n_steps=n_np, duration=np.array(Ts),
+                 start=np.array(starts), goal=np.array(goals),
+                 offsets=np.array(offs, np.int32), centers=f32(np.concatenate(cen)),
+                 semi_axes=f32(np.concatenate(ax)), velocities=f32(np.concatenate(vel)),
+                 traj_problem=np.array(tp, np.int32), xi0=f32(np.concatenate(xi0)),
+                 vmax=vmax, amax=amax, rho=1.0,
+                 name=f"long_horizon_{dim}d_seed{seed}")
+
+
 def config4(seed: int = 0, n_problems: int = 2048, inits: int = 8) -> Batch:
     """Uneven batch: n_o log-uniform in [4,256], n_p in {50,75,100,150}, T = 0.1 n_p."""
     rng = np.random.default_rng(seed)

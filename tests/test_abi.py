@@ -40,7 +40,7 @@ def test_status_strings():
 
 
 @pytest.mark.parametrize("kw,frag", [
-    (dict(dim=4), "dim"), (dict(max_steps=300), "capacities"), (dict(vmax=-1.0), "vmax"),
+    (dict(dim=4), "dim"), (dict(max_steps=1025), "capacities"), (dict(vmax=-1.0), "vmax"),
     (dict(max_traj=0), "capacities"), (dict(precision="fp32", rho=0.0), "rho")])
 def test_config_validation_without_device(kw, frag):
     args = dict(dim=2, max_problems=1, max_traj=4, max_obstacles=4, max_steps=50, vmax=1.5,

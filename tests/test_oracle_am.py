@@ -55,8 +55,10 @@ def _qp_bruteforce(Q, q, A, b):
     return xp + N @ z
 
 
-def test_obstacle_free_fixed_point_is_the_qp_optimum():
-    n_p, T = 50, 5.0
+@pytest.mark.parametrize("n_p,T", [(50, 5.0), (1000, 10.0)])
+def test_obstacle_free_fixed_point_is_the_qp_optimum(n_p, T):
+    """The obstacle-free iteration converges to the QP optimum found by a
+    null-space solve; n_p = 1000 is Paper I's long horizon."""
     start, goal = np.array([0.0, 1.0]), np.array([4.0, -2.0])
     rng = np.random.default_rng(0)
     xi0 = scenes.straight_line_coeffs(start, goal)[None] + rng.normal(0, 0.5, (3, 2, 11))
@@ -231,3 +233,24 @@ def test_workspace_bounds_inactive_fixed_point_and_active_feasibility():
     pos_free = np.einsum("ti,kai->kta", P, free["xi"])
     assert np.any(pos_free > hi + 1e-3) or np.any(pos_free < lo - 1e-3)  # the box mattered
     assert h["hist"][:, 0, 0].max() > 1e-3  # the initial projection saw the violation
+
+
+@pytest.mark.parametrize("dim,moving", [(2, True), (2, False), (3, True)])
+def test_long_horizon_scenes_follow_their_recipe(dim, moving):
+    """Long-horizon inputs: n_p grid points over T = 0.01 n_p, the goal within the
+    rest-to-rest reach vmax (T - vmax / amax), no obstacle covering the start at
+    t = 0 or the goal at t = T, speeds in [0, 1] m/s (zero when static)."""
+    b = scenes.long_horizon(seed=2, n_scenes=6, inits=3, n_steps=[257, 300, 500, 640, 1000, 1000],
+                            dim=dim, moving=moving)
+    assert b.n_traj == 18 and b.xi0.shape == (18, dim, 11)
+    np.testing.assert_allclose(b.duration, 0.01 * b.n_steps)
+    reach = np.linalg.norm(b.goal - b.start, axis=1)
+    assert np.all(reach <= b.vmax * (b.duration - b.vmax / b.amax))
+    for p in range(b.n_problems):
+        sl = slice(b.offsets[p], b.offsets[p + 1])
+        c, a, v = b.centers[sl], b.semi_axes[sl], b.velocities[sl]
+        assert c.shape == (10, dim) and np.all((a >= 0.2) & (a <= 0.8))
+        speed = np.linalg.norm(v, axis=1)
+        assert np.all(speed <= 1.0 + 1e-6) and (moving or np.all(speed == 0))
+        assert np.all((((b.start[p] - c) / a) ** 2).sum(1) > 1.0)
+        assert np.all((((b.goal[p] - (c + v * b.duration[p])) / a) ** 2).sum(1) > 1.0)

@@ -12,7 +12,7 @@ from scipy.interpolate import BPoly
 from oracle import am
 
 
-@pytest.mark.parametrize("n_p,T", [(50, 5.0), (100, 10.0), (75, 7.5), (150, 20.0)])
+@pytest.mark.parametrize("n_p,T", [(50, 5.0), (100, 10.0), (75, 7.5), (150, 20.0), (1000, 10.0)])
 def test_bernstein_against_scipy_bpoly(n_p, T):
     P, Pd, Pdd = am.bernstein(n_p, T)
     t = np.linspace(0.0, T, n_p)
