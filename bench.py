@@ -39,7 +39,7 @@ WORKLOAD_LONG = ("long-horizon 2D batch (Paper I's n_o = 10, n_p = 1000): 128 sc
                  "over T=10 s, 10 constant-velocity axis-aligned ellipses (semi-axes U(0.2,0.8) m, "
                  "speed U(0,1) m/s), start (0,0), goal 0.55 vmax T along the diagonal, 8 "
                  "initialisations N(straight line, 0.5 m) = 1024 trajectories, grid points "
-                 "streamed in chunks of 128, vmax 1.5 m/s, amax 2 m/s^2, rho 1, cap 500 "
+                 "streamed in chunks of 256, vmax 1.5 m/s, amax 2 m/s^2, rho 1, cap 500 "
                  "iterations, tol 1e-3")
 
 

@@ -150,7 +150,8 @@ typedef struct traj_solve_stats {
  * and fills them. Calling it again restarts from coeffs0.
  * Long horizons (Paper I plans over up to 1000 grid points): a batch whose
  * longest problem has more than 256 grid points runs one warp per trajectory
- * that streams its grid points in chunks of 128 every iteration (FP32 form
+ * that streams its grid points in chunks (256 in 2D, 128 in 3D) every
+ * iteration (FP32 form
  * only; TRAJ_ESHAPE in the tensor-core form or with warps_per_trajectory > 1).
  * The basis tables of the distinct horizons stay within 160 KB (n_p = 1000
  * alone takes 144 KB). */
@@ -263,10 +264,11 @@ typedef struct traj_launch_shape {
 } traj_launch_shape;
 
 /* Use this launch shape for later solves (default: FP32 form 4 warps per block,
- * tensor-core form the batch spread over all SMs; occupancy-bound blocks per SM). */
+ * tensor-core form and horizons above 256 grid points the batch spread over all
+ * SMs; occupancy-bound blocks per SM). */
 traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape);
 
-/* Autotuner: times every candidate shape (warps per block in {1,2,4,8} x
+/* Autotuner: times every candidate shape (warps per block in {0,1,2,4,8} x
  * blocks per SM in {occupancy,1,2,4} x warps per trajectory in {1,2,4}, the
  * latter in the FP32 form only) on this handle's own batch with `iters`
  * fixed iterations, keeps the fastest for later solves and reports it in

@@ -354,9 +354,10 @@ k_am_fp32(const __grid_constant__ SolveArgs A) {
 }
 
 // Horizons beyond 32 * 8 grid points: one warp per trajectory, the timesteps
-// streamed in chunks of LONG_CNT slots (128 grid points) per iteration. Basis
-// tables are staged in shared memory as in k_am_fp32 (at most 160 KB).
-constexpr int LONG_CNT = 4;
+// streamed in chunks of long_cnt slots per iteration (256 grid points in 2D, 128
+// in 3D, where eight slots would spill). Basis tables are staged in shared memory
+// as in k_am_fp32 (at most 160 KB).
+template <int DIM> __host__ __device__ constexpr int long_cnt() { return DIM == 2 ? 8 : 4; }
 
 template <int DIM>
 __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32, 1)
@@ -382,7 +383,7 @@ k_am_long(const __grid_constant__ SolveArgs A) {
     if (lane == 0) item = atomicAdd(A.queue, 1);
     item = __shfl_sync(FULL, item, 0);
     if (item >= A.n_traj) break;
-    solve_one<DIM, LONG_CNT, true>(A, A.order[item], stab, lane, deadline);
+    solve_one<DIM, long_cnt<DIM>(), true>(A, A.order[item], stab, lane, deadline);
   }
 }
 
@@ -418,19 +419,32 @@ static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_
 }
 
 // k_am_long: the shape's warps per block and blocks per SM apply; the team is one warp.
+// Default warps per block (0): the fewest that still hold the whole batch in one wave
+// of resident blocks, so that a batch with large tables (one block per SM) is spread
+// over every SM rather than packed into fewer, fuller ones.
 template <int DIM>
 static cudaError_t launch_long(const SolveArgs &a, const LaunchShape &shape, int n_sm,
                                cudaStream_t s, LaunchShape *used) {
-  const int warps = shape.warps_per_block > 0 ? shape.warps_per_block : 4;
+  int warps = shape.warps_per_block > 0 ? shape.warps_per_block : MAX_WARPS_PER_BLOCK;
   if (warps > MAX_WARPS_PER_BLOCK) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * (size_t)a.table_floats_total;
   cudaError_t e = cudaFuncSetAttribute(k_am_long<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  auto resident = [&](int w, int &occ) -> cudaError_t {
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_am_long<DIM>, w * 32, smem);
+    if (r == cudaSuccess && shape.blocks_per_sm > 0 && shape.blocks_per_sm < occ) occ = shape.blocks_per_sm;
+    return r;
+  };
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_am_long<DIM>, warps * 32, smem);
-  if (e != cudaSuccess) return e;
+  if ((e = resident(warps, occ)) != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  if (shape.blocks_per_sm > 0 && shape.blocks_per_sm < occ) occ = shape.blocks_per_sm;
+  while (shape.warps_per_block <= 0 && warps > 1) {
+    int occ_less = 0;
+    if ((e = resident(warps - 1, occ_less)) != cudaSuccess) return e;
+    if ((long long)n_sm * occ_less * (warps - 1) < a.n_traj) break;
+    --warps;
+    occ = occ_less;
+  }
   long long want = ((long long)a.n_traj + warps - 1) / warps;
   long long grid = (long long)n_sm * occ;
   if (want < grid) grid = want;

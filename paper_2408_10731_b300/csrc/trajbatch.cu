@@ -654,7 +654,7 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
   if (!b) return TRAJ_EINVAL;
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
   if (iters < 1) return fail(b, TRAJ_EINVAL, "iters must be >= 1");
-  static const int cand_w[] = {1, 2, 4, 8};
+  static const int cand_w[] = {0, 1, 2, 4, 8}; // 0: the form's default shape
   static const int cand_b[] = {0, 1, 2, 4};
   LaunchShape best{4, 0, 0, 1};
   float best_t = 1e30f;

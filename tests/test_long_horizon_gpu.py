@@ -3,7 +3,7 @@ against the FP64 oracle.
 
 Paper I plans over n_p = 1000 grid points with 10 obstacles. Above 256 grid
 points the FP32 form runs one warp per trajectory that streams its grid points
-in chunks of 128 every iteration, accumulating the contraction F^T r and the
+in chunks (256 in 2D, 128 in 3D) every iteration, accumulating the contraction F^T r and the
 residual maxima over the chunks; the FP64 set-up stages the basis 256 rows at a
 time. The bar is that of every FP32 parity test: max coefficient-evaluated
 position error <= 1e-5 m after a fixed iteration count, residuals to FP32
@@ -100,3 +100,28 @@ def test_long_horizon_refusals():
         h.close()
     with pytest.raises(tb.TrajBatchError):
         tb.TrajBatch(2, 1, 2, 10, 1025, 1.5, 2.0, 1.0, 1.0, 1.0, "fp32", "smooth_track", None)
+
+
+def test_long_horizon_launch_shapes_agree_bitwise():
+    """One warp per trajectory whatever the CTA shape: the spread default, fixed
+    shapes, a replayed graph and the autotuned shape give bitwise the same result."""
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.long_horizon(seed=12, n_scenes=3, inits=3, n_steps=[257, 640, 100])
+    h = tb.from_batch(b)
+    try:
+        ref = None
+        for w, bps in ((0, 0), (8, 0), (2, 0), (8, 1), (1, 1)):
+            h.set_launch_shape(w, bps, 1)
+            for _ in range(2):  # capture, then replay
+                h.solve(15, tol=-1.0)
+                out = h.get_trajectories()
+                ref = out if ref is None else ref
+                np.testing.assert_array_equal(out["xi"], ref["xi"])
+        choice = h.autotune(5)
+        assert choice["warps_per_trajectory"] == 1
+        h.solve(15, tol=-1.0)
+        np.testing.assert_array_equal(h.get_trajectories()["xi"], ref["xi"])
+    finally:
+        h.close()
+    o = am.solve(b, 15, tol=-1.0)
+    assert position_error(b, ref["xi"], o["xi"]).max() <= POS_TOL

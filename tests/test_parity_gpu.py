@@ -236,7 +236,7 @@ def test_launch_shape_graph_replay_and_autotune_do_not_change_results():
         for team, ref in refs.items():
             assert position_error(b, ref["xi"], o["xi"]).max() <= POS_TOL, team
         choice = h.autotune(5)
-        assert 1 <= choice["warps_per_block"] <= 8 and choice["ms"] > 0
+        assert 0 <= choice["warps_per_block"] <= 8 and choice["ms"] > 0  # 0: the default shape
         h.solve(25, tol=-1.0)
         np.testing.assert_array_equal(h.get_trajectories()["xi"],
                                       refs[choice["warps_per_trajectory"]]["xi"])
