@@ -43,10 +43,11 @@ WORKLOAD_LONG = ("long-horizon 2D batch (Paper I's n_o = 10, n_p = 1000): 128 sc
                  "iterations, tol 1e-3")
 
 
-# DRAM bytes (read + write) per launch of each solve kernel on the 1024-trajectory
-# 2D workload, from one ncu capture each (profiles/), valid only for the kernel
-# sources they were taken on: kernel -> (bytes, source digest of KERNEL_SOURCES).
-# A changed source reports null until the kernel is captured again.
+# DRAM bytes (read + write) per launch of each solve kernel on its bench workload
+# (the 1024-trajectory 2D workload; k_am_long on the long-horizon one), from one ncu
+# capture each (profiles/), valid only for the kernel sources they were taken on:
+# (kernel, workload) -> (bytes, source digest of KERNEL_SOURCES). A changed source
+# reports null until the kernel is captured again.
 KERNEL_SOURCES = {
     "k_am_fp32": ("am_solve.cu", "am_device.cuh", "internal.cuh"),
     "k_am_team": ("am_solve.cu", "am_device.cuh", "internal.cuh"),
@@ -54,8 +55,9 @@ KERNEL_SOURCES = {
     "k_am_mixed": ("am_mixed.cu", "am_device.cuh", "internal.cuh", "tcgen05.cuh"),
 }
 MEASURED_TRAFFIC = {
-    "k_am_fp32": (745216, "d0995091f548b9da"),
-    "k_am_mixed": (728576, "304cbed190840c6d"),
+    ("k_am_fp32", "config2"): (743936, "bae4e264e8badb6a"),
+    ("k_am_mixed", "config2"): (742144, "c8bf26aca05bfe5b"),
+    ("k_am_long", "long"): (672768, "bae4e264e8badb6a"),
 }
 
 
@@ -69,8 +71,8 @@ def source_digest(kernel):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    entry = MEASURED_TRAFFIC.get(kernel)
+def measured_traffic(kernel, workload="config2"):
+    entry = MEASURED_TRAFFIC.get((kernel, workload))
     return entry[0] if entry and entry[1] == source_digest(kernel) else None
 
 
@@ -794,7 +796,7 @@ def main():
         prec_h = forms[headline][0].split("_")[0]
         kern = kernel_name(prec_h, shape if prec_h == args.precision else None,
                            int(batch.n_steps.max()))
-        traffic = measured_traffic(kern) if args.workload == "config2" else None
+        traffic = measured_traffic(kern, args.workload)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,

@@ -62,15 +62,6 @@ k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
   double *P = sm, *Pd = sm + CH * NC, *Pdd = sm + 2 * CH * NC;
   const double iT = 1.0 / T, iT2 = 1.0 / (T * T);
 
-  if (threadIdx.x < 2) {
-    double a[NC], b[NC], c[NC];
-    basis_row(n_p, threadIdx.x == 0 ? 0 : n_p - 1, a, b, c);
-    for (int i = 0; i < NC; ++i) {
-      if (threadIdx.x == 0) { Bnd[0][i] = a[i]; Bnd[1][i] = b[i] * iT; Bnd[2][i] = c[i] * iT2; }
-      else Bnd[3][i] = a[i];
-    }
-  }
-
   // Q, M = F^T F (closed form of the stacked F), q per axis: element el of thread el
   const int el = threadIdx.x;
   const bool gram = el < NC * NC, qrow = el >= NC * NC && el < NC * NC + 3 * NC;
@@ -92,6 +83,14 @@ k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
       }
     }
     __syncthreads();
+    // boundary rows from the staged chunks: the first grid point and the last
+    if (c0 == 0 && threadIdx.x < NC) {
+      Bnd[0][threadIdx.x] = P[threadIdx.x];
+      Bnd[1][threadIdx.x] = Pd[threadIdx.x];
+      Bnd[2][threadIdx.x] = Pdd[threadIdx.x];
+    }
+    if (c0 + nc == n_p && threadIdx.x >= 32 && threadIdx.x < 32 + NC)
+      Bnd[3][threadIdx.x - 32] = P[(nc - 1) * NC + threadIdx.x - 32];
     if (gram) {
       for (int t = 0; t < nc; ++t) {
         pp += P[t * NC + ga] * P[t * NC + gb];
