@@ -367,6 +367,18 @@ traj_status traj_warmstart_destroy(traj_warmstart *w);
 /* params: host or device FP32 [num_params]; resets the optimizer state */
 traj_status traj_warmstart_set_params(traj_warmstart *w, const float *params);
 traj_status traj_warmstart_get_params(traj_warmstart *w, float *params);
+/* Training checkpoint and resume (no paper counterpart: the thesis leaves the
+ * learned warm start to future work). params, m, v: FP32 [num_params] each, in
+ * the public flat order, host or device: the FP32 master parameters and AdamW's
+ * first and second moment estimates; step: AdamW's step count (its bias
+ * corrections). get copies them out (synchronises); set restores all four and
+ * the BF16 copies of the weights, so that the next train_step continues as the
+ * uninterrupted run would, bit for bit. TRAJ_EINVAL for NULL buffers or
+ * step < 0; the caller owns every buffer. */
+traj_status traj_warmstart_get_state(traj_warmstart *w, float *params, float *m, float *v,
+                                     int *step);
+traj_status traj_warmstart_set_state(traj_warmstart *w, const float *params, const float *m,
+                                     const float *v, int step);
 /* start, goal [n][2] FP64 and offsets [n + 1] host; obstacles device FP32 [N][2];
  * features: device BF16 [n][400]; line: device FP32 [n][22] straight-line coefficients */
 traj_status traj_warmstart_features(traj_warmstart *w, int n_scenes, const double *start,

@@ -683,7 +683,9 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
     chosen->warps_per_trajectory = best.team;
   }
   if (best_ms) *best_ms = best_t / 2.f;
-  return best_t < 1e30f ? TRAJ_OK : fail(b, TRAJ_ECUDA, "no launch shape ran");
+  if (best_t >= 1e30f) return fail(b, TRAJ_ECUDA, "no launch shape ran");
+  b->err.clear(); // candidates the batch refuses (teams on long horizons) are not errors
+  return TRAJ_OK;
 }
 
 traj_status traj_sampler_step_multi(traj_batch *b, const traj_sampler_config *sc, int iteration,

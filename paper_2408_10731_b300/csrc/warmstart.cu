@@ -408,6 +408,38 @@ traj_status traj_warmstart_get_params(traj_warmstart *w, float *params) {
   return TRAJ_OK;
 }
 
+traj_status traj_warmstart_get_state(traj_warmstart *w, float *params, float *m, float *v,
+                                     int *step) {
+  if (!w || !params || !m || !v || !step) return ws_fail(TRAJ_EINVAL, "NULL training-state argument");
+  const float *src[3] = {w->W, w->m, w->v};
+  float *dst[3] = {params, m, v};
+  for (int i = 0; i < 3; ++i) { // stream order: each copy reads the staging buffer before it is reused
+    k_params_pad<<<(P_TOTAL + 255) / 256, 256, 0, w->stream>>>(src[i], w->stage, 0);
+    WS_CK(cudaGetLastError());
+    WS_CK(cudaMemcpyAsync(dst[i], w->stage, sizeof(float) * U_TOTAL, cudaMemcpyDefault, w->stream));
+  }
+  WS_CK(cudaStreamSynchronize(w->stream));
+  *step = w->step;
+  return TRAJ_OK;
+}
+
+traj_status traj_warmstart_set_state(traj_warmstart *w, const float *params, const float *m,
+                                     const float *v, int step) {
+  if (!w || !params || !m || !v) return ws_fail(TRAJ_EINVAL, "NULL training-state argument");
+  if (step < 0) return ws_fail(TRAJ_EINVAL, "step must be >= 0");
+  const float *src[3] = {params, m, v};
+  float *dst[3] = {w->W, w->m, w->v};
+  for (int i = 0; i < 3; ++i) {
+    WS_CK(cudaMemcpyAsync(w->stage, src[i], sizeof(float) * U_TOTAL, cudaMemcpyDefault, w->stream));
+    k_params_pad<<<(P_TOTAL + 255) / 256, 256, 0, w->stream>>>(w->stage, dst[i], 1);
+    WS_CK(cudaGetLastError());
+  }
+  w->step = step;
+  WS_CK(refresh_bf16(w, 0, 0.f, 0.f)); // BF16 copies of the restored master weights
+  WS_CK(cudaStreamSynchronize(w->stream));
+  return TRAJ_OK;
+}
+
 traj_status traj_warmstart_features(traj_warmstart *w, int n_scenes, const double *start,
                                     const double *goal, const int *offsets, const float *centers,
                                     const float *semi_axes, const float *velocities,

@@ -42,12 +42,14 @@ def _lib():
         lib.traj_warmstart_gradients.argtypes = [_vp, _ci, _vp, _vp, _vp, _vp, _vp]
         lib.traj_warmstart_train_step.argtypes = [_vp, _ci, _vp, _vp, _vp, _cf, _cf, _vp]
         lib.traj_warmstart_sync.argtypes = [_vp]
+        lib.traj_warmstart_get_state.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(_ci)]
+        lib.traj_warmstart_set_state.argtypes = [_vp, _vp, _vp, _vp, _ci]
         lib.traj_get_accel_cost.argtypes = [_vp, _vp]
         for n in ("traj_warmstart_create", "traj_warmstart_destroy", "traj_warmstart_set_params",
                   "traj_warmstart_get_params", "traj_warmstart_features", "traj_warmstart_forward",
                   "traj_warmstart_propose",
                   "traj_warmstart_gradients", "traj_warmstart_train_step", "traj_warmstart_sync",
-                  "traj_get_accel_cost"):
+                  "traj_warmstart_get_state", "traj_warmstart_set_state", "traj_get_accel_cost"):
             getattr(lib, n).restype = _ci
         _READY = True
     return lib
@@ -55,6 +57,51 @@ def _lib():
 
 def num_params() -> int:
     return int(_lib().traj_warmstart_num_params())
+
+
+CHECKPOINT_MAGIC = "trajbatch-warmstart-checkpoint"
+
+
+def write_checkpoint(path, params, m, v, step, **meta):
+    """Flat binary checkpoint: one JSON header line (magic, format version, parameter
+    count, AdamW step, array names in file order, dtype, byte order, caller metadata
+    such as the learning rate or the data cursor), then the arrays params, m and v as
+    raw little-endian FP32 in that order. Written to a temporary name and renamed."""
+    import json
+    import os
+    arrs = [np.ascontiguousarray(a, "<f4") for a in (params, m, v)]
+    n = arrs[0].size
+    if any(a.ndim != 1 or a.size != n for a in arrs):
+        raise ValueError("params, m and v must be 1-D arrays of one length")
+    head = {"magic": CHECKPOINT_MAGIC, "version": 1, "num_params": int(n), "step": int(step),
+            "arrays": ["params", "adam_m", "adam_v"], "dtype": "float32",
+            "byteorder": "little", "meta": meta}
+    tmp = str(path) + ".tmp"
+    with open(tmp, "wb") as f:
+        f.write((json.dumps(head, sort_keys=True) + "\n").encode())
+        for a in arrs:
+            f.write(a.tobytes())
+    os.replace(tmp, path)
+
+
+def read_checkpoint(path):
+    """(params, m, v, step, meta) from a write_checkpoint file; ValueError when the
+    header or the payload size does not match."""
+    import json
+    with open(path, "rb") as f:
+        line = f.readline()
+        try:
+            head = json.loads(line)
+        except ValueError as e:
+            raise ValueError(f"{path}: no checkpoint header") from e
+        if head.get("magic") != CHECKPOINT_MAGIC or head.get("version") != 1:
+            raise ValueError(f"{path}: not a version-1 warm-start checkpoint")
+        n = int(head["num_params"])
+        data = np.frombuffer(f.read(), "<f4")
+    if data.size != 3 * n:
+        raise ValueError(f"{path}: payload holds {data.size} values, expected {3 * n}")
+    p, m, v = (data[i * n:(i + 1) * n].astype(np.float32) for i in range(3))
+    return p, m, v, int(head["step"]), head.get("meta", {})
 
 
 def init_params(seed: int = 0) -> np.ndarray:
@@ -109,6 +156,34 @@ class WarmStart:
         p = np.zeros(num_params(), np.float32)
         _check(_lib().traj_warmstart_get_params(self._h, p.ctypes.data), "get_params")
         return p
+
+    def get_state(self):
+        """Training state: (params, AdamW m, AdamW v, step), FP32 arrays in the public order."""
+        n = num_params()
+        p, m, v = (np.zeros(n, np.float32) for _ in range(3))
+        step = ctypes.c_int(0)
+        _check(_lib().traj_warmstart_get_state(self._h, p.ctypes.data, m.ctypes.data,
+                                               v.ctypes.data, ctypes.byref(step)), "get_state")
+        return p, m, v, int(step.value)
+
+    def set_state(self, params, m, v, step):
+        """Restore a training state; the next train_step continues it bit for bit."""
+        arrs = [np.ascontiguousarray(a, np.float32) for a in (params, m, v)]
+        if any(a.shape != (num_params(),) for a in arrs):
+            raise ValueError(f"each state array must hold {num_params()} FP32 values")
+        _check(_lib().traj_warmstart_set_state(self._h, arrs[0].ctypes.data, arrs[1].ctypes.data,
+                                               arrs[2].ctypes.data, int(step)), "set_state")
+
+    def save_checkpoint(self, path, **meta):
+        """Write the training state to `path` (see write_checkpoint)."""
+        p, m, v, step = self.get_state()
+        write_checkpoint(path, p, m, v, step, **meta)
+
+    def load_checkpoint(self, path):
+        """Restore the training state written by save_checkpoint; returns its metadata."""
+        p, m, v, step, meta = read_checkpoint(path)
+        self.set_state(p, m, v, step)
+        return meta
 
     def features(self, batch):
         """BF16 features [P, 400] and straight-line coefficients [P, 22] (CUDA tensors)."""

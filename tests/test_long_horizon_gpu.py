@@ -119,6 +119,7 @@ def test_long_horizon_launch_shapes_agree_bitwise():
                 np.testing.assert_array_equal(out["xi"], ref["xi"])
         choice = h.autotune(5)
         assert choice["warps_per_trajectory"] == 1
+        assert tb.load_library().traj_last_error(h._h).decode() == ""
         h.solve(15, tol=-1.0)
         np.testing.assert_array_equal(h.get_trajectories()["xi"], ref["xi"])
     finally:

@@ -91,6 +91,55 @@ def test_gradients_and_adamw_match_oracle():
     ws.close()
 
 
+def test_training_checkpoint_resumes_bitwise(tmp_path):
+    """Train 3 AdamW steps, checkpoint (weights, moments, step) to a file, train 4
+    more; a fresh handle that loads the file and trains the same 4 steps ends with
+    bitwise the same weights and moments. The restored moments and step are the
+    saved ones, and one more step from them equals the oracle's AdamW step."""
+    torch, warmstart, b, ws, params, X, line = _setup()
+    rng = np.random.default_rng(4)
+    P = b.n_problems
+    batches = [(torch.as_tensor(rng.normal(0, 0.5, (P, 8, 22)).astype(np.float32), device="cuda"),
+                torch.as_tensor(rng.integers(1, 9, P).astype(np.int32), device="cuda"))
+               for _ in range(7)]
+    for tt, nt in batches[:3]:
+        ws.train_step(X, tt, nt, 1e-3, 1e-2)
+    ws.sync()
+    path = tmp_path / "ws.ckpt"
+    ws.save_checkpoint(path, lr=1e-3, weight_decay=1e-2, next_batch=3)
+    saved = ws.get_state()
+    assert saved[3] == 3 and np.any(saved[1] != 0) and np.all(saved[2] >= 0)
+    for tt, nt in batches[3:]:
+        ws.train_step(X, tt, nt, 1e-3, 1e-2)
+    ws.sync()
+    direct = ws.get_state()
+    ws.close()
+
+    ws2 = warmstart.WarmStart(max_rows=256)
+    ws2.set_params(warmstart.init_params(9))  # unrelated weights, overwritten by the load
+    meta = ws2.load_checkpoint(path)
+    assert meta == {"lr": 1e-3, "weight_decay": 1e-2, "next_batch": 3}
+    back = ws2.get_state()
+    for a, c in zip(back[:3], saved[:3]):
+        np.testing.assert_array_equal(a, c)
+    assert back[3] == 3
+    # the next step from the restored state is the oracle's AdamW step (t = 4)
+    g, _ = ws2.gradients(X, *batches[3])
+    ref, _, _ = mlp.adamw(back[0].astype(np.float64), g.astype(np.float64),
+                          back[1].astype(np.float64), back[2].astype(np.float64), 4, 1e-3, 1e-2)
+    for tt, nt in batches[3:]:
+        ws2.train_step(X, tt, nt, 1e-3, 1e-2)
+        if tt is batches[3][0]:
+            ws2.sync()
+            np.testing.assert_allclose(ws2.get_params().astype(np.float64), ref, rtol=1e-5, atol=1e-7)
+    ws2.sync()
+    resumed = ws2.get_state()
+    for a, c in zip(resumed[:3], direct[:3]):
+        np.testing.assert_array_equal(a, c)
+    assert resumed[3] == direct[3] == 7
+    ws2.close()
+
+
 def test_device_propose_matches_host_path_and_flags_bad_offsets():
     """traj_warmstart_propose (device inputs, no synchronisation) gives bitwise the
     features and proposals of traj_warmstart_features + traj_warmstart_forward;
