@@ -17,6 +17,7 @@ def sources():
 
 def deps():
     return sources() + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + \
+        sorted(glob.glob(os.path.join(HERE, "csrc", "*.h"))) + \
         [os.path.join(ROOT, "include", "trajbatch.h")]
 
 

@@ -19,6 +19,7 @@
 // One warp per trajectory; a lane owns grid points lane, lane + 32, ...
 #include "trajbatch.h"
 #include "internal.cuh"
+#include "nvtx_range.h"
 #include "basis.cuh"
 #include "linalg.cuh"
 
@@ -657,6 +658,7 @@ traj_status traj_fp_set_initial(traj_fp_batch *b, int n_traj, const int *traj_pr
 }
 
 traj_status traj_fp_solve(traj_fp_batch *b, int max_iters, float tol, traj_fp_stats *stats) {
+  tb::NvtxRange nvtx_range("traj_fp_solve");
   if (!b) return TRAJ_EINVAL;
   if (!b->have_initial) return fp_fail(b, TRAJ_ESTATE, "traj_fp_set_initial must come first");
   if (max_iters < 0) return fp_fail(b, TRAJ_EINVAL, "max_iters must be >= 0");

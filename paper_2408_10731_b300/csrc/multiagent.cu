@@ -33,6 +33,7 @@
 // r = (lambda' - lambda) / rho.
 #include "trajbatch.h"
 #include "internal.cuh"
+#include "nvtx_range.h"
 #include "basis.cuh"
 #include "linalg.cuh"
 
@@ -752,6 +753,7 @@ traj_status traj_ma_set_problems(traj_ma_batch *b, int n_scenes, int n_agents,
 }
 
 traj_status traj_ma_solve(traj_ma_batch *b, int max_iters, float tol, traj_ma_stats *stats) {
+  tb::NvtxRange nvtx_range("traj_ma_solve");
   if (!b) return TRAJ_EINVAL;
   if (!b->have_problems) return ma_fail(b, TRAJ_ESTATE, "traj_ma_set_problems must come first");
   if (max_iters < 0) return ma_fail(b, TRAJ_EINVAL, "max_iters must be >= 0");

@@ -5,6 +5,7 @@
 // (FP64 set-up) and am_solve.cu (the iteration); this file only marshals.
 #include "trajbatch.h"
 #include "internal.cuh"
+#include "nvtx_range.h"
 
 #include <algorithm>
 #include <cmath>
@@ -219,6 +220,7 @@ traj_status traj_batch_destroy(traj_batch *b) {
 
 traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
                               const double *duration, const double *start, const double *goal) {
+  tb::NvtxRange nvtx_range("traj_set_problems");
   if (!b) return TRAJ_EINVAL;
   if (!n_steps || !duration || !start || !goal) return fail(b, TRAJ_EINVAL, "NULL problem array");
   if (n_problems < 1 || n_problems > b->cfg.max_problems)
@@ -307,6 +309,7 @@ static traj_status upload_problems(traj_batch *b) {
 
 traj_status traj_set_obstacles(traj_batch *b, const int *offsets, const float *centers,
                                const float *semi_axes, const float *velocities) {
+  tb::NvtxRange nvtx_range("traj_set_obstacles");
   if (!b) return TRAJ_EINVAL;
   if (!b->have_problems) return fail(b, TRAJ_ESTATE, "traj_set_problems must come first");
   if (!offsets) return fail(b, TRAJ_EINVAL, "NULL offsets");
@@ -446,6 +449,7 @@ static traj_status solve_stats(traj_batch *b, traj_solve_stats *stats) {
 
 traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
                        traj_solve_stats *stats) {
+  tb::NvtxRange nvtx_range("traj_solve");
   if (!b) return TRAJ_EINVAL;
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
   if (max_iters < 0) return fail(b, TRAJ_EINVAL, "max_iters must be >= 0");
@@ -536,6 +540,7 @@ traj_status traj_get_solve_stats(traj_batch *b, traj_solve_stats *stats) {
 
 traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual, int *iters,
                                   signed char *status) {
+  tb::NvtxRange nvtx_range("traj_get_trajectories");
   if (!b) return TRAJ_EINVAL;
   if (!b->have_result) return fail(b, TRAJ_ESTATE, "no solve has run");
   const size_t B = b->n_traj, D = b->cfg.dim;
@@ -651,6 +656,7 @@ traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape)
 }
 
 traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, float *best_ms) {
+  tb::NvtxRange nvtx_range("traj_autotune");
   if (!b) return TRAJ_EINVAL;
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
   if (iters < 1) return fail(b, TRAJ_EINVAL, "iters must be >= 1");
@@ -691,6 +697,7 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
 traj_status traj_sampler_step_multi(traj_batch *b, const traj_sampler_config *sc, int iteration,
                                     int n_dist, float *mu, float *sigma, const float *z,
                                     float *best, const traj_sampler_trace *trace) {
+  tb::NvtxRange nvtx_range("traj_sampler_step_multi");
   if (!b) return TRAJ_EINVAL;
   if (!sc || !mu || !sigma || !best) return fail(b, TRAJ_EINVAL, "NULL sampler argument");
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");

@@ -11,6 +11,7 @@
 //   averaged over the labels of the batch.
 #include "trajbatch.h"
 #include "internal.cuh"
+#include "nvtx_range.h"
 
 #include <cuda_bf16.h>
 #include <math.h>
@@ -473,6 +474,7 @@ traj_status traj_warmstart_propose(traj_warmstart *w, int n_scenes, int n_obs, c
                                    const double *goal, const int *offsets, const float *centers,
                                    const float *semi_axes, const float *velocities, void *features,
                                    float *line, float *proposals) {
+  tb::NvtxRange nvtx_range("traj_warmstart_propose");
   if (!w || !start || !goal || !offsets || !features || !line || !proposals || n_obs < 0)
     return ws_fail(TRAJ_EINVAL, "NULL argument or negative obstacle count");
   if (n_obs > 0 && (!centers || !semi_axes || !velocities)) return ws_fail(TRAJ_EINVAL, "NULL obstacles");
@@ -490,6 +492,7 @@ traj_status traj_warmstart_propose(traj_warmstart *w, int n_scenes, int n_obs, c
 
 traj_status traj_warmstart_forward(traj_warmstart *w, int rows, const void *features,
                                    const float *line, float *proposals) {
+  tb::NvtxRange nvtx_range("traj_warmstart_forward");
   if (!w || !features || !line || !proposals) return TRAJ_EINVAL;
   traj_status rc = check_rows(w, rows);
   if (rc != TRAJ_OK) return rc;
@@ -517,6 +520,7 @@ traj_status traj_warmstart_gradients(traj_warmstart *w, int rows, const void *fe
 traj_status traj_warmstart_train_step(traj_warmstart *w, int rows, const void *features,
                                       const float *targets, const int *n_labels, float lr,
                                       float weight_decay, float *loss) {
+  tb::NvtxRange nvtx_range("traj_warmstart_train_step");
   if (!w || !features || !targets || !n_labels || !loss) return TRAJ_EINVAL;
   if (!(lr > 0) || !(weight_decay >= 0)) return ws_fail(TRAJ_EINVAL, "bad learning rate or decay");
   traj_status rc = check_rows(w, rows);
