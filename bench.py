@@ -1,9 +1,14 @@
 #!/usr/bin/env python
-"""Benchmark: solved trajectories/sec at residual <= 1e-3 m on the 2D moving-ellipse
-workload (n_p = 100 over 10 s, 50 constant-velocity ellipses, 128 scenes x 8
-initialisations = 1024 trajectories, iteration cap 500), one batch solve per step.
+"""Benchmark: solved trajectories/sec at residual <= 1e-3 m of the batched optimizer.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|mixed]
+Default workload (config5): the learned warm start on 4096 held-out 2D moving-ellipse
+scenes (n_p = 100 over 10 s, 50 constant-velocity ellipses) x 8 trajectories =
+32 768, iteration cap 500, one batch solve per step (proposals included); beside it
+the plain FP32 form from random and straight-line initialisations on the same scenes.
+Other workloads: config2 (128 scenes x 8), uneven, long, priest, multiagent,
+footprint, mpc, gemm.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|mixed_split]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
 Prints one JSON line (rank 0). Under torchrun each rank solves its own seeded
@@ -31,6 +36,12 @@ WORKLOAD = ("2D moving ellipses: n_p=100 over T=10 s, 50 constant-velocity axis-
             "ellipses (semi-axes U(0.2,0.8) m, speed U(0,1) m/s), start (0,0) goal (8,8), "
             "128 scenes x 8 initialisations N(straight line, 0.5 m) = 1024 trajectories, "
             "vmax 1.5 m/s, amax 2 m/s^2, rho 1, cap 500 iterations, tol 1e-3")
+WORKLOAD_CONFIG5 = ("learned warm start on held-out scenes: {n} config-2-style 2D scenes (seed 99: "
+                    "n_p=100 over T=10 s, 50 constant-velocity axis-aligned ellipses, semi-axes "
+                    "U(0.2,0.8) m, speed U(0,1) m/s, start (0,0) goal (8,8)), K=8 trajectories per "
+                    "scene = {b}: the network's 8 proposals (headline) vs 8 random N(straight line, "
+                    "0.5 m) and 8 straight-line initialisations; vmax 1.5 m/s, amax 2 m/s^2, rho 1, "
+                    "cap 500 iterations, tol 1e-3")
 WORKLOAD_UNEVEN = ("uneven 2D batch: 2048 problems, obstacle counts log-uniform 4-256, horizons "
                    "n_p in {50,75,100,150} over T=0.1 n_p s, goal 0.55 vmax T away, 8 "
                    "initialisations each = 16384 trajectories in one persistent launch "
@@ -63,6 +74,7 @@ MEASURED_TRAFFIC = {
 
 def source_digest(kernel):
     """SHA-256 (first 16 hex digits) over the sources that build a solve kernel."""
+    kernel = kernel.split(" ")[0]
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
         h.update(name.encode())
@@ -72,6 +84,7 @@ def source_digest(kernel):
 
 
 def measured_traffic(kernel, workload="config2"):
+    kernel = kernel.split(" ")[0]
     entry = MEASURED_TRAFFIC.get((kernel, workload))
     return entry[0] if entry and entry[1] == source_digest(kernel) else None
 
@@ -92,33 +105,42 @@ def combine_ranks(dist, world, total_ms, n_solved, e2e_rate, device="cpu"):
 
 def kernel_name(precision, shape, max_np=100):
     """The solve kernel a handle of this precision and launch shape runs."""
-    if precision == "mixed":
-        return "k_am_mixed"
+    if precision in ("mixed", "mixed_split"):
+        return "k_am_mixed" if precision == "mixed" else "k_am_mixed (split operands)"
     if max_np > 256:
         return "k_am_long"
     return "k_am_team" if shape and shape.get("warps_per_trajectory", 1) > 1 else "k_am_fp32"
 
 
 def algorithmic_ops(batch, iters):
-    """FP32 lane operations the method must execute for the given iteration counts.
-
-    Per obstacle-timestep pair (dense containment test, every pair every
-    iteration): Delta = p - (c + v t) [FMA + SUB per axis], u = Delta / a [MUL per
-    axis], s = |u|^2 [MUL + (dim-1) FMA], compare: 2D 9, 3D 13.
-    Per timestep: evaluate p, pdot, pddot [3 * 11 * dim FMA], velocity and
-    acceleration bound tests [2 * (dim + 1)], contraction F^T r [3 * 11 * dim FMA].
-    Per trajectory-iteration: the QP step [2 * 11 * 11 * dim FMA].
-    The initial projection counts as one more evaluate/project/contract pass.
-    """
+    """FP32 lane operations the method must execute for the given iteration counts,
+    counted per trajectory-iteration as the survey's measurement plan does:
+      every obstacle-timestep pair (the dense test, every pair every iteration):
+        13 in 2D, 17 in 3D (Delta = p - (c + v t), u = Delta / a, |u|^2, the
+        compare, and the projection's share: 1 / |u| - 1, the scale and the sum);
+      every velocity and acceleration bound row: 10 (norm, compare, projection);
+      the contractions P xi, Pd xi, Pdd xi (evaluation) and F^T r: 2 x 3 n_p x 11 x dim;
+      the QP step: 2 x 11 x 11 x dim.
+    On the 2D workload (n_o = 50, n_p = 100) that is 5000 x 13 + 200 x 10 + 13 200 +
+    484 = 80 684 per trajectory-iteration. The initial projection counts as one more
+    evaluate / project / contract pass."""
     dim = batch.dim
-    pair = 9 if dim == 2 else 13
-    per_t = 3 * 11 * dim + 2 * (dim + 1) + 3 * 11 * dim
-    qp = 2 * 11 * 11 * dim
+    pair = 13 if dim == 2 else 17
     n_o = np.diff(batch.offsets)[batch.traj_problem]
     n_p = batch.n_steps[batch.traj_problem]
-    proj = n_o * n_p * pair + n_p * per_t
+    proj = n_o * n_p * pair + 2 * n_p * 10 + 2 * 3 * n_p * 11 * dim
+    qp = 2 * 11 * 11 * dim
     it = np.asarray(iters, np.int64)
     return float(np.sum((it + 1) * proj + it * qp))
+
+
+def algorithmic_mufu(batch, iters):
+    """MUFU operations (rsqrtf) per the same count: one per obstacle-timestep pair and
+    one per velocity and acceleration bound row, every pass."""
+    n_o = np.diff(batch.offsets)[batch.traj_problem]
+    n_p = batch.n_steps[batch.traj_problem]
+    it = np.asarray(iters, np.int64)
+    return float(np.sum((it + 1) * (n_o * n_p + 2 * n_p)))
 
 
 class ClockSampler:
@@ -187,35 +209,56 @@ def _pci_id(torch, dev):
         return str(dev)
 
 
-def cpu_baseline(seed=0, scenes_idx=range(16), max_iters=500, tol=1e-3, workload=None):
+def cpu_baseline(seed=0, scenes_idx=range(16), max_iters=500, tol=1e-3, workload=None,
+                 n_threads=None):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload: the
-    listed scenes of the seeded 128-scene batch with all their initialisations."""
+    listed scenes of the seeded batch with all their initialisations; n_threads None
+    uses every host core (OpenMP over trajectories)."""
     from oracle import am
     from paper_2408_10731_b300 import scenes
     full = workload if workload is not None else scenes.config2(seed)
     idx = list(scenes_idx)
     b = full.select_problems(idx)
-    cores = os.cpu_count() or 1
+    cores = n_threads or (os.cpu_count() or 1)
     t0 = time.perf_counter()
     out = am.solve(b, max_iters, tol=tol, n_threads=cores)
     dt = time.perf_counter() - t0
     solved = int(np.sum(np.all(out["residual"] <= tol, axis=1) & (out["iters"] < max_iters + 1)))
     return {"value": solved / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{b.n_traj} trajectories (scenes {idx[0]}..{idx[-1]} of the 128 x 8 "
-                      f"workload, all initialisations), full solve (cap {max_iters}, tol {tol}), "
-                      f"FP64, OpenMP over trajectories; {solved} solved in {dt:.2f} s",
-            "seconds": dt, "solved": solved}
+            "sample": f"{b.n_traj} trajectories (scenes {idx[0]}..{idx[-1]} of the workload, all "
+                      f"initialisations), full solve (cap {max_iters}, tol {tol}), FP64, "
+                      f"{'one thread' if cores == 1 else 'OpenMP over trajectories'}; "
+                      f"{solved} solved in {dt:.2f} s",
+            "seconds": dt, "solved": solved,
+            "trajectory_iterations_per_s": float(np.sum(out["iters"])) / dt}
+
+
+def cpu_baseline_both(batch, wl):
+    """The oracle on the host: all cores on 8 scenes (64 trajectories; 4 scenes of the
+    long horizon), and one thread on one scene (8 trajectories)."""
+    n_all = 4 if wl == "long" else 8
+    allc = cpu_baseline(workload=batch, scenes_idx=range(n_all))
+    one = cpu_baseline(workload=batch, scenes_idx=range(1), n_threads=1)
+    for d in (allc, one):
+        d.pop("seconds", None); d.pop("solved", None)
+    allc["single_thread"] = one
+    return allc
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle timed on the host cores (rank 0 only). Step i
-    solves scenes 2i, 2i + 1 (mod 128) of the seeded workload with all their
-    initialisations, so that successive steps sweep the whole batch; the value is
-    the total solved over the total time of the timed steps."""
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only), on the same
+    workload as the default run. Step i solves scenes 2i, 2i + 1 (mod the scene count)
+    with all their initialisations, so that successive steps sweep the batch; the
+    value is the total solved over the total time of the timed steps."""
     if rank != 0:
         return
     from paper_2408_10731_b300 import scenes
-    full = scenes.config2(args.seed)
+    if args.workload == "config5":
+        full = heldout_scenes(0, args.scenes)
+        workload = WORKLOAD_CONFIG5.format(n=full.n_problems, b=full.n_traj)
+    else:
+        full = scenes.config2(args.seed)
+        workload = WORKLOAD
     P = full.n_problems
 
     def step(i):
@@ -228,12 +271,12 @@ def run_reference(args, rank, world):
         r = step(i)
         solved += r["solved"]; secs.append(r["seconds"])
     value = solved / float(np.sum(secs))
-    sample = (f"16 trajectories per step (scenes 2i, 2i+1 of the 128 x 8 workload, all "
+    sample = (f"16 trajectories per step (scenes 2i, 2i+1 of the workload, all 8 random "
               f"initialisations), full FP64 solve; {solved} solved in {np.sum(secs):.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "data": "synthetic", "config": {"workload": workload, "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -540,6 +583,79 @@ def run_footprint(args, torch):
     h.close()
 
 
+def run_mpc(args, torch):
+    """Paper II's MPC use of the batch optimizer: 125 scenes x 8 plans (B = 1000), each
+    control step shifts the horizon by 0.1 s (the robot follows each scene's best plan,
+    the obstacles move on, the multipliers carry over) and runs 10 warm-started
+    iterations. One bench step = one control step; episodes of 10 control steps start
+    from a converged plan (the episode set-up is outside the timed region)."""
+    from paper_2408_10731_b300 import scenes, trajbatch
+    b = scenes.config2(args.seed, n_scenes=125, inits=8)
+    h = trajbatch.from_batch(b)
+    iters, delta, episode = 10, 0.1, 10
+    stream = torch.cuda.current_stream()
+    res = torch.empty(b.n_traj, 3).pin_memory()
+    coeffs = torch.empty(b.n_traj, 2, 11).pin_memory()
+
+    def start_episode():
+        h.set_problems(b.n_steps, b.duration, b.start, b.goal)
+        h.set_obstacles(b.offsets, b.centers, b.semi_axes, b.velocities)
+        h.set_initial(b.traj_problem, b.xi0)
+        h.solve(500, 1e-3)
+
+    def control_step():
+        h.shift_horizon(delta)
+        h.solve(iters, 1e-3, stats=False)
+
+    start_episode()
+    for _ in range(args.warmup):
+        control_step()
+    ms, solved_frac, e2e = [], [], []
+    clk = ClockSampler(_pci_id(torch, 0))
+    clk.mark()
+    k = 0
+    while len(ms) < args.steps:
+        if k % episode == 0:
+            start_episode()
+        k += 1
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        control_step()
+        e1.record(stream)
+        # end to end: the plans and residuals back to the host every control step
+        h.get_trajectories(coeffs, res, None, None)
+        e2e.append(time.perf_counter() - t0)
+        ms.append(e0.elapsed_time(e1))
+        worst = res.numpy().max(axis=1).reshape(b.n_problems, 8)
+        solved_frac.append(float((worst.min(axis=1) <= 1e-3).mean()))
+    clk.mark()
+    clocks = clk.stop()
+    step_ms = float(np.mean(ms))
+    line = {"metric": "ms per MPC control step (horizon shift + 10 warm-started iterations), "
+                      "B = 1000", "value": step_ms, "unit": "ms", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "125 scenes x 8 plans of the 2D moving-ellipse workload (n_p=100 "
+                                   "over 10 s, 50 ellipses), shift 0.1 s per control step onto "
+                                   "each scene's smallest-residual plan, obstacles moved by their "
+                                   "velocity, multipliers carried, 10 iterations (tol 1e-3); "
+                                   "episodes of 10 control steps from a converged plan",
+                       "l2": "state and inputs stay on the device; one shift (set-up included) "
+                             "and one solve launch per step"},
+            "scenes_with_a_solved_plan": float(np.mean(solved_frac)),
+            "e2e": {"value": 1e3 * float(np.mean(e2e)), "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(coeffs.numel() * 4 + res.numel() * 4)},
+            "gpu_launches": 9,  # 6 shift kernels, obstacle packing, FP64 set-up, solve
+            "clocks": clocks,
+            "context": "Paper II: 10 iterations at a batch of 1000 within its 0.04 s MPC budget "
+                       "(JAX, unnamed GPU)"}
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def run_gemm(args, torch):
     """The warm-start network's tcgen05 BF16 GEMM (C = A B^T, FP32 accumulate): the
     training shapes of the network (4096 rows: 400 -> 256, 256 -> 256, 256 -> 176)
@@ -591,16 +707,19 @@ def run_gemm(args, torch):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_split"],
+                    help="tensor-core form of the headline (and of the plain_<precision> form)")
+    ap.add_argument("--scenes", type=int, default=4096,
+                    help="held-out scenes of the config5 workload (8 trajectories each)")
     ap.add_argument("--max-iters", type=int, default=500)
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--workload", default="config2",
-                    choices=["config2", "uneven", "long", "priest", "multiagent", "footprint",
-                             "gemm"])
+    ap.add_argument("--workload", default="config5",
+                    choices=["config5", "config2", "uneven", "long", "priest", "multiagent",
+                             "footprint", "gemm", "mpc"])
     ap.add_argument("--ma-agents", type=int, default=32)
     ap.add_argument("--ma-scenes", type=int, default=148)
     ap.add_argument("--ma-radius", type=float, default=0.4)
@@ -635,6 +754,24 @@ def main():
         return run_footprint(args, torch)
     if args.workload == "gemm":
         return run_gemm(args, torch)
+    if args.workload == "mpc":
+        return run_mpc(args, torch)
+    return run_solve(args, torch, dist, world, rank, local)
+
+
+def heldout_scenes(rank=0, n_scenes=4096):
+    """The learned warm start's held-out set: config-2-style scenes (seed 99 + rank),
+    8 random initialisations N(straight line, 0.5 m) each."""
+    from paper_2408_10731_b300 import scenes
+    return scenes.ellipse_scenes(99 + rank, n_scenes, inits=8)
+
+
+def run_solve(args, torch, dist, world, rank, local):
+    """The batch solve workloads (config5 = default, config2, uneven, long): one step is
+    one batch solve of the form, initialisation included (the learned warm start's
+    features and network run inside the timed step)."""
+    import dataclasses
+    from paper_2408_10731_b300 import autotune, scenes, trajbatch
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -644,76 +781,84 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    from paper_2408_10731_b300 import autotune
-    if args.workload == "uneven":
+    wl = args.workload
+    if wl == "config5":
+        batch = heldout_scenes(rank, args.scenes)
+    elif wl == "uneven":
         batch = scenes.config4(args.seed + rank)
-    elif args.workload == "long":
+    elif wl == "long":
         batch = scenes.long_horizon(args.seed + rank, n_scenes=128, inits=8, n_steps=1000)
     else:
         batch = scenes.config2(args.seed + rank)
-    h = trajbatch.from_batch(batch, precision=args.precision)
-    if args.shape:
-        w, bps, team = (int(x) for x in args.shape.split(","))
-        h.set_launch_shape(w, bps, team)
-        shape = {"warps_per_block": w, "blocks_per_sm": bps, "warps_per_trajectory": team,
-                 "fixed": True}
-    else:
-        shape = autotune.tuned(h, batch, args.precision, iters=200)
+    tc = args.precision  # the tensor-core form of the headline
+    use_tc = not args.no_mixed and wl != "long"
+    use_ws = not args.no_warmstart and wl in ("config5", "config2")
+    ladder = None if args.no_rho_ladder or wl not in ("config5", "config2") else \
+        tuple(f(x) for f, x in zip((int, float, int), args.rho_ladder.split(",")))
+
+    def tuned_handle(prec, ladder_on=False):
+        hh = trajbatch.from_batch(batch, precision=prec)
+        if ladder_on:
+            hh.set_rho_schedule(*ladder)
+        if args.shape and prec == "fp32":
+            w, bps, team = (int(x) for x in args.shape.split(","))
+            hh.set_launch_shape(w, bps, team)
+            return hh, {"warps_per_block": w, "blocks_per_sm": bps, "warps_per_trajectory": team,
+                        "fixed": True}
+        return hh, autotune.tuned(hh, batch, prec, iters=100)
+
+    handles, shapes = {}, {}
+    handles["fp32"], shapes["fp32"] = tuned_handle("fp32")
+    if use_tc:
+        handles[tc], shapes[tc] = tuned_handle(tc)
+    if ladder:
+        handles["fp32_ladder"], shapes["fp32_ladder"] = tuned_handle("fp32", True)
+        if use_tc:
+            handles[tc + "_ladder"], shapes[tc + "_ladder"] = tuned_handle(tc, True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
     sampler = ClockSampler(_pci_id(torch, local))
     fp32_peak = trajbatch.measure_fp32_peak(5) if rank == 0 else None
+    mufu_peak = trajbatch.measure_mufu_peak(5) if rank == 0 else None
 
-    # forms: the plain FP32 form from N(straight line, 0.5 m) initialisations, and the
-    # learned warm start (network proposals computed inside every timed step)
-    handles = {"fp32": h}
-    if args.workload == "config2" and not args.no_mixed:
-        handles["mixed"] = trajbatch.from_batch(batch, precision="mixed")
-    forms = {"plain_fp32": ("fp32", None)}
-    if "mixed" in handles:
-        forms["plain_mixed"] = ("mixed", None)
-    # extra forms, reported beside the configured ones: the penalty continuation
-    # (the penalty grows while the residuals stay above the tolerance)
-    ladder = None if args.no_rho_ladder or args.workload != "config2" else \
-        tuple(f(x) for f, x in zip((int, float, int), args.rho_ladder.split(",")))
+    xi0_rand = torch.as_tensor(batch.xi0, dtype=torch.float32, device="cuda")
+    line = np.stack([scenes.straight_line_coeffs(batch.start[p], batch.goal[p])
+                     for p in range(batch.n_problems)])[batch.traj_problem]
+    xi0_line = torch.as_tensor(scenes.f32(line), device="cuda")
+    forms = {"plain_fp32": ("fp32", xi0_rand)}
+    if wl == "config5":
+        forms["plain_fp32_straight"] = ("fp32", xi0_line)
+    if use_tc:
+        forms[f"plain_{tc}"] = (tc, xi0_rand)
     if ladder:
-        handles["fp32_ladder"] = trajbatch.from_batch(batch, precision="fp32")
-        handles["fp32_ladder"].set_launch_shape(shape["warps_per_block"], shape["blocks_per_sm"],
-                                                shape.get("warps_per_trajectory", 1))
-        handles["fp32_ladder"].set_rho_schedule(*ladder)
-        forms["plain_fp32_rho_ladder"] = ("fp32_ladder", None)
-        if "mixed" in handles:
-            handles["mixed_ladder"] = trajbatch.from_batch(batch, precision="mixed")
-            handles["mixed_ladder"].set_rho_schedule(*ladder)
+        forms["plain_fp32_rho_ladder"] = ("fp32_ladder", xi0_rand)
     ws = None
-    if args.workload == "config2" and not args.no_warmstart:
+    if use_ws:
         from paper_2408_10731_b300 import warmstart
-        ws, ws_info = warmstart.trained(seed=1000, n_scenes=args.ws_scenes, epochs=20)
-
+        ws, ws_info = warmstart.trained(seed=1000, n_scenes=args.ws_scenes, epochs=20,
+                                        max_rows=max(4096, batch.n_problems))
         staged = ws.stage(batch)  # the scenes resident on the device before the timed steps
 
         def ws_init(hh):
             prop = ws.propose(staged).reshape(batch.n_traj, 2, 11)
             hh.set_initial(None, prop)
         forms["warmstart_fp32"] = ("fp32", ws_init)
-        if "mixed" in handles:
-            forms["warmstart_mixed"] = ("mixed", ws_init)
-        if "mixed_ladder" in handles:
-            forms["warmstart_mixed_rho_ladder"] = ("mixed_ladder", ws_init)
-    xi0_dev = torch.as_tensor(batch.xi0, dtype=torch.float32, device="cuda")
+        if use_tc:
+            forms[f"warmstart_{tc}"] = (tc, ws_init)
+            if ladder:
+                forms[f"warmstart_{tc}_rho_ladder"] = (tc + "_ladder", ws_init)
 
-    def run_form(form, steps, timed):
+    def run_form(form, steps):
         key, init = form
         hh = handles[key]
-        if init is None:
-            hh.set_initial(None, xi0_dev)
+        if not callable(init):
+            hh.set_initial(None, init)
         step_ms, kern_ms, solved = [], [], []
         for _ in range(steps):
             flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            if init is not None:
+            if callable(init):
                 init(hh)
             hh.solve(args.max_iters, args.tol, stats=False)
             e1.record(stream)
@@ -727,16 +872,16 @@ def main():
     barrier()
     sampler.mark()
     for name, form in forms.items():
-        run_form(form, args.warmup, False)
+        run_form(form, args.warmup)
         barrier()
-        results[name] = run_form(form, args.steps, True)
+        results[name] = run_form(form, args.steps)
     barrier()
     sampler.mark()
     clocks = sampler.stop()
-    headline = next(f for f in ("warmstart_mixed", "warmstart_fp32", "plain_fp32") if f in results)
-    step_ms, kern_ms, solved, out = results["plain_fp32"]
+    headline = next(f for f in (f"warmstart_{tc}", f"plain_{tc}", "plain_fp32") if f in results)
     h_step_ms, h_kern_ms, h_solved, h_out = results[headline]
-    hh = handles[forms[headline][0]]
+    hkey = forms[headline][0]
+    hh = handles[hkey]
 
     # end to end through the public API with pinned host buffers (headline form)
     tp_h = batch.traj_problem.astype(np.int32)
@@ -746,7 +891,7 @@ def main():
         ("residual", (batch.n_traj, 3), torch.float32), ("iters", (batch.n_traj,), torch.int32),
         ("status", (batch.n_traj,), torch.int8))}
     e2e_s, e2e_solved = [], []
-    for _ in range(max(3, min(50, args.steps // 2))):
+    for _ in range(max(3, min(20, args.steps // 2))):
         flush.fill_(1.0); torch.cuda.synchronize()
         t0 = time.perf_counter()
         if headline.startswith("warmstart"):
@@ -771,48 +916,55 @@ def main():
     total_ms_max, n_solved_all, e2e_all = combine_ranks(
         dist if world > 1 else None, world, total_ms, n_solved, e2e_val, device="cuda")
     value = n_solved_all / (total_ms_max * 1e-3)
+
+    def kern_of(key):
+        prec = key.split("_ladder")[0]
+        return kernel_name(prec, shapes.get(key), int(batch.n_steps.max()))
+
     form_summary = {}
     for name, (sm, km, sv, o) in results.items():
         ok = o["status"] == 0
-        prec_f = forms[name][0].split("_")[0]
-        form_summary[name] = {"kernel": kernel_name(prec_f, shape if prec_f == args.precision
-                                                    else None, int(batch.n_steps.max())),
+        key = forms[name][0]
+        ops = algorithmic_ops(batch, o["iters"])
+        form_summary[name] = {"kernel": kern_of(key), "launch_shape": shapes.get(key),
                               "solved_per_s": float(np.sum(sv)) / (float(np.sum(sm)) * 1e-3),
                               "ms_per_batch_solve": float(np.mean(sm)),
                               "solve_kernel_ms": float(np.mean(km)),
                               "solved_per_step": float(np.mean(sv)),
                               "scenes_with_a_solution": float(ok.reshape(batch.n_problems, -1).any(1).mean()),
                               "iters_median_solved": float(np.median(o["iters"][ok])) if ok.any() else None,
-                              "solve_roofline_frac": (algorithmic_ops(batch, o["iters"]) /
-                                                      (float(np.mean(km)) * 1e-3) /
-                                                      (fp32_peak / 2.0)) if fp32_peak else None}
+                              "iters_p90_solved": float(np.percentile(o["iters"][ok], 90)) if ok.any() else None,
+                              "solve_roofline_frac": (ops / (float(np.mean(km)) * 1e-3) / (fp32_peak / 2.0))
+                              if fp32_peak else None}
 
     if rank == 0:
-        # roofline of the headline step's dominant kernel (the solve)
+        # roofline of the headline step's dominant kernel (the solve): FP32 lane operations
+        # against the measured FFMA rate, and MUFU operations against the measured rsqrtf rate
         ops = algorithmic_ops(batch, h_out["iters"])
+        mufu = algorithmic_mufu(batch, h_out["iters"])
         kern_s = float(np.mean(h_kern_ms)) * 1e-3
         achieved = ops / kern_s
         peak_ops = fp32_peak / 2.0  # FFMA rate in lane-operations/s (2 FLOP per FMA)
-        prec_h = forms[headline][0].split("_")[0]
-        kern = kernel_name(prec_h, shape if prec_h == args.precision else None,
-                           int(batch.n_steps.max()))
-        traffic = measured_traffic(kern, args.workload)
+        kern = kern_of(hkey)
+        wl_key = {"config5": "config5", "config2": "config2", "uneven": "uneven", "long": "long"}[wl]
+        traffic = measured_traffic(kern, wl_key)
+        workload = {"config5": WORKLOAD_CONFIG5.format(n=batch.n_problems, b=batch.n_traj),
+                    "config2": WORKLOAD, "uneven": WORKLOAD_UNEVEN, "long": WORKLOAD_LONG}[wl]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+bf16" if prec_h == "mixed" else "f32",
+            "dtype": "f32+bf16" if hkey != "fp32" else "f32",
             "data": "synthetic",
-            "config": {"workload": {"config2": WORKLOAD, "uneven": WORKLOAD_UNEVEN,
-                                    "long": WORKLOAD_LONG}[args.workload],
-                       "precision": args.precision, "launch_shape": shape,
+            "config": {"workload": workload, "precision": hkey, "launch_shape": shapes.get(hkey),
                        "l2": "flushed between timed steps (256 MB write, outside the events)",
                        "per_rank_batch": "seed + rank",
                        "rho_ladder_forms": (None if not ladder else
                                             {"levels": ladder[0], "growth": ladder[1],
                                              "every": ladder[2], "rho0": batch.rho})},
             "ms_per_batch_solve": float(np.mean(h_step_ms)),
-            "ms_per_batch_solve_plain_fp32": float(np.mean(step_ms)),
+            "ms_per_batch_solve_plain_fp32": float(np.mean(results["plain_fp32"][0])),
+            "solved_per_s_plain_fp32": form_summary["plain_fp32"]["solved_per_s"],
             "solved_per_step": float(np.mean(h_solved)), "trajectories_per_step": batch.n_traj,
             "iters": {"min": int(h_out["iters"].min()), "median": int(np.median(h_out["iters"])),
                       "max": int(h_out["iters"].max())},
@@ -821,7 +973,12 @@ def main():
                          "kernel": kern,
                          "peak_source": "measured FFMA microbenchmark "
                          "(traj_measure_fp32_peak), FP32 lane-ops/s",
-                         "algorithmic_ops_per_launch": ops},
+                         "algorithmic_ops_per_launch": ops,
+                         "mufu": {"achieved": mufu / kern_s / 1e12, "peak": mufu_peak / 1e12,
+                                  "unit": "T rsqrt/s", "frac": mufu / kern_s / mufu_peak,
+                                  "algorithmic_per_launch": mufu,
+                                  "peak_source": "measured rsqrtf microbenchmark "
+                                                 "(traj_measure_mufu_peak)"}},
             "e2e": {"value": e2e_all, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": args.steps * (7 if headline.startswith("warmstart") else 1),
@@ -829,14 +986,13 @@ def main():
             "headline_form": headline, "forms": form_summary,
             "source_digest": {k: source_digest(k) for k in KERNEL_SOURCES},
         }
-        if world == 1 and not args.no_cpu_baseline and args.workload in ("config2", "long"):
-            cb = cpu_baseline(args.seed, scenes_idx=range(16) if args.workload == "config2"
-                              else range(4), workload=batch)
-            cb.pop("seconds", None); cb.pop("solved", None)
-            line["cpu_baseline"] = cb
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_both(batch, wl)
         print(json.dumps(line), flush=True)
     for hx in handles.values():
         hx.close()
+    if ws is not None:
+        ws.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -65,11 +65,15 @@ enum {
 
 typedef enum {
   TRAJ_PREC_FP32 = 0, /* FP32 state and contractions; compensated FP32 QP step */
-  TRAJ_PREC_MIXED = 1 /* residual contraction F^T r on tcgen05 tensor cores (BF16 operands,
-                         FP32 accumulation in TMEM) plus one FP32 refinement pass when the
-                         residuals first meet the tolerance (the refined iterate must meet it
-                         too; it may add one iteration past the cap); residuals are always
-                         FP32. Needs one horizon (n_steps) for every problem of a batch. */
+  TRAJ_PREC_MIXED = 1, /* residual contraction F^T r on tcgen05 tensor cores (BF16 operands,
+                          FP32 accumulation in TMEM) plus one FP32 refinement pass when the
+                          residuals first meet the tolerance (the refined iterate must meet it
+                          too; it may add one iteration past the cap); residuals are always
+                          FP32. Horizons up to 256 grid points, at most 16 distinct ones per
+                          batch (uneven batches run in one launch). */
+  TRAJ_PREC_MIXED_SPLIT = 2 /* as TRAJ_PREC_MIXED with both operands split into BF16 hi/lo
+                               pairs (16 significant bits each): the basis's lo part doubles
+                               the MMAs, the residual's rides in spare rows of the same MMA */
 } traj_precision;
 
 typedef enum {
@@ -109,7 +113,8 @@ traj_status traj_batch_destroy(traj_batch *b);
  * n_p >= 2 (grid tau_t = t/(n_p-1)), duration[n_problems] horizon T > 0 in
  * seconds, start[n_problems][dim] and goal[n_problems][dim] positions (FP64).
  * The boundary rows are start position, zero start velocity and acceleration,
- * and the goal position (PRIEST eq. eq1_multiagent_1_priest). */
+ * and the goal position (PRIEST eq. eq1_multiagent_1_priest); traj_shift_horizon
+ * later gives the start a velocity and an acceleration. */
 traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
                               const double *duration, const double *start, const double *goal);
 
@@ -176,6 +181,16 @@ traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual,
  * over the grid (PRIEST's acceleration cost), FP32 [n_traj], host or device. */
 traj_status traj_get_accel_cost(traj_batch *b, float *cost);
 
+/* Homotopy signature of each trajectory of the last solve (2D, n_p <= 256): bit j
+ * (j < 64) is set when the trajectory passes obstacle j of its problem on the left
+ * of their relative motion, judged at the closest approach over the grid points
+ * (distances scaled by the semi-axes): the sign of (p - o_j) x (p' - v_j) there.
+ * Solutions of one problem with equal signatures pass every obstacle on the same
+ * side. Used to choose training labels of the learned warm start that cover
+ * different homotopy classes. sig: uint64 [n_traj], host or device. No paper
+ * counterpart. */
+traj_status traj_homotopy_signature(traj_batch *b, unsigned long long *sig);
+
 /* Solver state for checkpoint/resume and warm starts (nullable outputs):
  * multipliers lambda[n_traj][dim][11] and the last residual contraction
  * u = F^T (F xi - g) [n_traj][dim][11], FP32, host or device. Together with the
@@ -214,6 +229,32 @@ traj_status traj_set_rho_schedule(traj_batch *b, int levels, double growth, int 
  * paper counterpart as an interface. */
 traj_status traj_set_state(traj_batch *b, const float *coeffs, const float *lambda, const float *u);
 
+/* Receding-horizon step (Paper II's MPC: the batch optimizer runs once per control
+ * loop, and each loop's solve starts from the Lagrange multipliers of the previous
+ * one). After a solve, the robot has followed one planned trajectory per problem for
+ * `delta` seconds (0 < delta < T of every problem). This call prepares the next
+ * control loop's solve, on the device (FP64 where it forms new values):
+ *  - executed[n_problems] (host int, or NULL): the trajectory of each problem that
+ *    the robot followed; NULL picks, per problem, the trajectory with the smallest
+ *    worst-of-three residual of the last solve (ties to the lower index). Each
+ *    entry must be a trajectory of its problem (TRAJ_EINVAL otherwise).
+ *  - the executed plan's position, velocity and acceleration at delta become the
+ *    problem's start boundary rows (goal, horizon T and grid unchanged; the tracking
+ *    line x_des now runs from the new start);
+ *  - every obstacle moves on to c + v delta (its constant-velocity prediction);
+ *    traj_set_obstacles afterwards replaces them with fresh data if the caller has any;
+ *  - every trajectory's coefficients are re-expressed on the shifted window
+ *    [delta, delta + T] (the same polynomial, extrapolated past its old end) and
+ *    become the next initial iterate; the multipliers lambda are kept as they are;
+ *  - the FP64 set-up (KKT inverse, constants) is formed again for the moved
+ *    problems (synchronises).
+ * The next traj_solve projects the shifted iterate, so u is formed for the moved
+ * problem, with lambda0 = the carried multipliers instead of 0, then iterates as
+ * usual (iters counts from 0). traj_set_initial returns to fresh starts and
+ * traj_set_state to a resume. TRAJ_ESTATE before a solve has run; TRAJ_EINVAL in
+ * projection mode or for a delta outside (0, T). */
+traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed);
+
 /* Solve without allocating any memory, for callers that cannot allocate
  * device memory: code running under an allocator or memory pool owned by
  * another framework, plugins that may only use the buffers they are handed,
@@ -234,6 +275,11 @@ traj_status traj_set_state(traj_batch *b, const float *coeffs, const float *lamb
  *  - Limits: n_problems <= 256, N <= 8192 obstacles, n_traj <= 8192, n_p <=
  *    256, basis tables of the distinct horizons <= 160 KB; beyond them the
  *    call returns TRAJ_ESHAPE with the limit named in traj_last_error(NULL).
+ *  - Every traj_problem entry must lie in [0, n_problems): the entries are
+ *    range-checked on the device before any kernel indexes a problem with
+ *    them, and a bad one makes the call return TRAJ_EINVAL with no output
+ *    written. The device arrays must hold the sizes above; the library cannot
+ *    check the size of a device allocation.
  *  - Synchronous: returns after the solve has finished on the stream. The
  *    first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress), so make that first call before any stream capture.
@@ -254,13 +300,19 @@ traj_status traj_solve_noalloc(const traj_config *cfg, int n_problems, const int
  * default of the form), a cap on resident blocks per SM (0 = as many as
  * occupancy allows) and the warps that share one trajectory (1, 2 or 4,
  * dividing warps_per_block: timesteps interleaved across the warps, partial
- * contractions exchanged through shared memory; FP32 form only). The grid never exceeds what the batch needs. Results
- * are bitwise identical across shapes with the same warps per trajectory; across
- * those they differ only in the summation order of the contraction. */
+ * contractions exchanged through shared memory; FP32 form only). occupancy = 1
+ * selects the build whose registers are capped so that more warps stay resident
+ * (FP32 form: 128 registers, at most 4 warps per block; tensor-core forms: 170
+ * registers, at most 6), for one warp per trajectory and horizons up to 160 grid
+ * points; 0 leaves the registers unrestricted (the lowest latency per warp). The grid
+ * never exceeds what the batch needs. Results are bitwise identical across shapes and
+ * builds with the same warps per trajectory; across those they differ only in the
+ * summation order of the contraction. */
 typedef struct traj_launch_shape {
   int warps_per_block;
   int blocks_per_sm;
   int warps_per_trajectory;
+  int occupancy;
 } traj_launch_shape;
 
 /* Use this launch shape for later solves (default: FP32 form 4 warps per block,
@@ -268,9 +320,17 @@ typedef struct traj_launch_shape {
  * SMs; occupancy-bound blocks per SM). */
 traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape);
 
+/* The shape the last captured solve launch resolved to: warps per block, resident
+ * blocks per SM the launch counted on (after occupancy, shared memory and, in the
+ * tensor-core form, tensor-memory limits) and warps per trajectory, and the grid
+ * size (nullable outputs). TRAJ_ESTATE before the first solve. No paper counterpart. */
+traj_status traj_get_launch_info(traj_batch *b, traj_launch_shape *resolved, int *grid);
+
 /* Autotuner: times every candidate shape (warps per block in {0,1,2,4,8} x
  * blocks per SM in {occupancy,1,2,4} x warps per trajectory in {1,2,4}, the
- * latter in the FP32 form only) on this handle's own batch with `iters`
+ * latter in the FP32 form only, plus the register-capped build with one warp per
+ * trajectory and warps per block in {0,2,4} (tensor-core forms also 6) where the
+ * horizons allow it) on this handle's own batch with `iters`
  * fixed iterations, keeps the fastest for later solves and reports it in
  * *chosen and its time per solve in *best_ms (both nullable). Synchronises;
  * the previous solve's results are discarded. No paper counterpart. */
@@ -405,6 +465,14 @@ traj_status traj_warmstart_propose(traj_warmstart *w, int n_scenes, int n_obs, c
 traj_status traj_warmstart_gradients(traj_warmstart *w, int rows, const void *features,
                                      const float *targets, const int *n_labels, float *grads,
                                      float *loss);
+/* The same loss and gradients with every GEMM operand, activation and gradient in
+ * FP32 on the CUDA cores (no tensor cores, no BF16 rounding): the debug
+ * instantiation that checks the network's backward pass against an FP64
+ * reference to FP32 accuracy. Arguments as traj_warmstart_gradients (the BF16
+ * features are read as FP32 values); allocates its FP32 buffers on the first call. */
+traj_status traj_warmstart_gradients_fp32(traj_warmstart *w, int rows, const void *features,
+                                          const float *targets, const int *n_labels, float *grads,
+                                          float *loss);
 traj_status traj_warmstart_train_step(traj_warmstart *w, int rows, const void *features,
                                       const float *targets, const int *n_labels, float lr,
                                       float weight_decay, float *loss);
@@ -423,6 +491,13 @@ const char *traj_last_error(traj_batch *b);
  * (f32x2) on the stream and returns the better achieved FP32 FLOP/s (2 per
  * FMA), best of `reps` timed launches each. No paper counterpart (measurement). */
 traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_per_s);
+
+/* MUFU throughput microbenchmark, the denominator of the MUFU roofline: runs a
+ * kernel of independent rsqrtf chains (the special-function instruction the
+ * projections issue, once per point inside an obstacle and per velocity /
+ * acceleration bound test) and returns the achieved rsqrtf/s, best of `reps`
+ * timed launches. No paper counterpart (measurement). */
+traj_status traj_measure_mufu_peak(void *cuda_stream, int reps, double *rsqrt_per_s);
 
 /* ---- Joint multi-agent optimizer (Paper IV, Algorithm 5) ---------------------
  * A batch of independent scenes, each with n_agents agents solved jointly: every

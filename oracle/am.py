@@ -7,6 +7,10 @@ Parity status:
                fixed point equals the brute-force equality-constrained QP
   projection   pinned: dense-grid minimisation of each (alpha, beta, d)
                subproblem; closed form d = max(1, ||u||) (eq. d_max)
+  start state  pinned: with a start velocity and acceleration in the boundary
+  and carry    rows the obstacle-free fixed point is the brute-force QP with those
+               rows; one iteration from imported multipliers equals the
+               brute-force proximal QP step with them (tests/test_oracle_mpc.py)
   am_solve     pinned by invariants only (fixed point of a feasible QP optimum,
                A xi = b at every iterate, targets on/outside every ellipse,
                multiplier sign): the end-to-end iteration has no printed values
@@ -35,7 +39,8 @@ def _lib(real: str = "f64"):
             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp, _dp,
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
             ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, _ip, _dp, _dp, _dp,
-            _ip, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            _ip, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp,
+            _dp]
         lib.orc_kkt_flat.restype = ctypes.c_int
         lib.orc_kkt_flat.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -109,7 +114,7 @@ def solve(batch, max_iters: int, tol: float = -1.0, cost_mode: int = 0, w_smooth
           w_track: float = 1.0, iters_fixed=None, want_lambda: bool = False,
           want_hist: bool = False, n_threads: int = 0, real: str = "f64", xi0=None,
           rho_levels: int = 1, rho_growth: float = 1.0, rho_every: int = 0,
-          box_lo=None, box_hi=None):
+          box_lo=None, box_hi=None, start_va=None, lam0=None):
     """Run Algorithm 2 on every trajectory of a scenes.Batch.
 
     Returns dict(xi [B,dim,11], residual [B,3], iters [B], lam?, hist?).
@@ -117,6 +122,9 @@ def solve(batch, max_iters: int, tol: float = -1.0, cost_mode: int = 0, w_smooth
     iterations per trajectory (no stop test). rho_levels / rho_growth / rho_every:
     the penalty continuation of reading R10 (rho_levels = 1: a fixed rho).
     box_lo / box_hi [n_problems][dim]: workspace bounds of reading R11 (None: none).
+    start_va [n_problems][2][dim]: start velocity and acceleration of the boundary rows
+    (reading R12; None: at rest). lam0 [B][dim][11]: multipliers the loop starts from
+    (reading R12's carry; None: zero).
     """
     lib = _lib(real)
     dim = batch.dim
@@ -138,6 +146,8 @@ def solve(batch, max_iters: int, tol: float = -1.0, cost_mode: int = 0, w_smooth
         ro = np.zeros((idx.size, 3)); io = np.zeros(idx.size, np.int32)
         ho = np.full((idx.size, max_iters + 1, 3), np.nan) if want_hist else None
         fx = None if fixed_all is None else np.ascontiguousarray(fixed_all[idx])
+        sva = None if start_va is None else np.ascontiguousarray(start_va[p], np.float64)
+        l0 = None if lam0 is None else np.ascontiguousarray(np.asarray(lam0, np.float64)[idx])
         rc = lib.orc_am_solve_flat(
             dim, int(batch.n_steps[p]), float(batch.duration[p]), c.shape[0], _p(c), _p(a),
             _p(v), _p(st), _p(gl), float(batch.vmax), float(batch.amax), float(batch.rho),
@@ -145,7 +155,8 @@ def solve(batch, max_iters: int, tol: float = -1.0, cost_mode: int = 0, w_smooth
             float(tol), _p(fx, _ip), _p(xo), _p(lo), _p(ro), _p(io, _ip), _p(ho),
             int(n_threads), int(rho_levels), float(rho_growth), int(rho_every),
             _p(None if box_lo is None else np.ascontiguousarray(box_lo[p], np.float64)),
-            _p(None if box_hi is None else np.ascontiguousarray(box_hi[p], np.float64)))
+            _p(None if box_hi is None else np.ascontiguousarray(box_hi[p], np.float64)),
+            _p(sva), _p(l0))
         if rc:
             raise RuntimeError(f"oracle solve failed for problem {p}: {rc}")
         xi[idx] = xo; res[idx] = ro; its[idx] = io

@@ -41,6 +41,11 @@
  *     tau = [-lo; hi], slack s = max(0, tau - G xi) from the current iterate, and
  *     the rows' target e = tau - s; their residual norms join the obstacle group's
  *     maximum (column 0).
+ *  R12 receding horizon (Paper II's MPC: the multipliers carried from one control
+ *     loop to the next): the boundary rows take a start velocity and
+ *     acceleration (start_va, NULL = zero, as in R8), and the loop may start from
+ *     imported multipliers lam0 (NULL = 0): the initial projection is unchanged
+ *     and lam0 replaces lambda0 = 0.
  *  R10 penalty continuation (Paper I, Algorithm 1 line 9; Paper IV's ten cached
  *     KKT inverses): penalties rho growth^l, l = 0 .. levels-1, each with its own
  *     KKT inverse; after iteration k >= 1, if the trajectory has not stopped and k
@@ -160,6 +165,7 @@ typedef struct {
   int rho_levels;  /* penalty continuation (reading R10); 1 or 0: a fixed rho */
   double rho_growth;
   int rho_every;
+  const double *start_va; /* [2][dim] start velocity, then acceleration (R12), or NULL */
 } orc_problem;
 
 /* Dense F for one axis: (n_o + 2) n_p rows x 11 (F of Paper II without the
@@ -273,7 +279,8 @@ void orc_project_bound(int dim, const REAL *w, REAL bound, REAL *g) {
 /* ------------------------------------------------------------------------- */
 /* The AM loop (Algorithm 2) for n_traj trajectories of one problem.          */
 /*                                                                            */
-/* xi0[n_traj][dim][11]; outputs xi_out (same shape), lam_out (same shape,    */
+/* xi0[n_traj][dim][11]; lam0 (same shape, nullable: zero) the multipliers the */
+/* loop starts from; outputs xi_out (same shape), lam_out (same shape,        */
 /* nullable), residual_out[n_traj][3], iters_out[n_traj].                     */
 /* iters_fixed (nullable): run exactly iters_fixed[b] iterations, no test.    */
 /* Otherwise stop after the first iteration k >= 1 whose three residuals are  */
@@ -282,9 +289,10 @@ void orc_project_bound(int dim, const REAL *w, REAL bound, REAL *g) {
 /* [n_traj][max_iters + 1][3] (entries past the stop are left untouched).     */
 /* Returns 0, or a negative code for a singular KKT matrix / bad arguments.   */
 /* ------------------------------------------------------------------------- */
-int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_iters,
-                 double tol, const int *iters_fixed, double *xi_out, double *lam_out,
-                 double *residual_out, int *iters_out, double *hist, int n_threads) {
+int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, const double *lam0,
+                 int max_iters, double tol, const int *iters_fixed, double *xi_out,
+                 double *lam_out, double *residual_out, int *iters_out, double *hist,
+                 int n_threads) {
   const int dim = pr->dim, n_p = pr->n_p, n_o = pr->n_o, box = pr->box_lo != NULL;
   if (dim < 2 || dim > 3 || n_p < 2 || n_o < 0 || max_iters < 0) return -3;
   const size_t rows = (size_t)(n_o + 2 + 2 * box) * n_p;
@@ -303,7 +311,8 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
   }
 
   /* q per axis (eq. Q_matrix: q = -w_t P^T x_des, x_des the constant-velocity
-   * straight line); b per axis = (start, 0, 0, goal) (reading R8). */
+   * straight line); b per axis = (start, v0, a0, goal) with v0 = a0 = 0 (reading
+   * R8) unless a start state is given (reading R12). */
   double qa[3][NC], ba[3][NE];
   for (int a = 0; a < dim; ++a) {
     for (int i = 0; i < NC; ++i) {
@@ -315,7 +324,10 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
       }
       qa[a][i] = -pr->w_track * s;
     }
-    ba[a][0] = pr->start[a]; ba[a][1] = 0.0; ba[a][2] = 0.0; ba[a][3] = pr->goal[a];
+    ba[a][0] = pr->start[a];
+    ba[a][1] = pr->start_va ? pr->start_va[a] : 0.0;
+    ba[a][2] = pr->start_va ? pr->start_va[dim + a] : 0.0;
+    ba[a][3] = pr->goal[a];
   }
   double *tgrid = malloc(sizeof(double) * n_p);
   for (int t = 0; t < n_p; ++t) tgrid[t] = pr->T * (double)t / (double)(n_p - 1);
@@ -334,7 +346,10 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
     REAL *Kr = Kall;
     REAL rho = (REAL)rho_l[0];
     for (size_t k = 0; k < rows * NC; ++k) Fr[k] = (REAL)F[k];
-    for (int k = 0; k < dim * NC; ++k) { xi[k] = (REAL)xi0[(size_t)b * dim * NC + k]; lam[k] = 0; }
+    for (int k = 0; k < dim * NC; ++k) {
+      xi[k] = (REAL)xi0[(size_t)b * dim * NC + k];
+      lam[k] = lam0 ? (REAL)lam0[(size_t)b * dim * NC + k] : 0; /* R3, or R12's carry */
+    }
     /* projection mode (eq. matrix_vec): Q = I, q = -xi_sample, the trajectory's own xi0 */
     REAL q[3][NC];
     for (int a = 0; a < dim; ++a)
@@ -428,7 +443,8 @@ int orc_am_solve(const orc_problem *pr, int n_traj, const double *xi0, int max_i
           if (nrm > res[0]) res[0] = nrm;
         }
       /* Line 6 -- multiplier update lambda <- lambda - rho F^T (F xi - g) (reading R2).
-       * At k = 0 (initialisation) lambda0 = 0 and only g0 is formed (reading R3). */
+       * At k = 0 (initialisation) lambda keeps its initial value (0, or the carried
+       * multipliers of R12) and only g0 is formed (reading R3). */
       if (k > 0)
         for (int a = 0; a < dim; ++a)
           for (int i = 0; i < NC; ++i) {
@@ -469,18 +485,19 @@ int orc_am_solve_flat(int dim, int n_p, double T, int n_o, const double *centers
                       const double *xi0, int max_iters, double tol, const int *iters_fixed,
                       double *xi_out, double *lam_out, double *residual_out, int *iters_out,
                       double *hist, int n_threads, int rho_levels, double rho_growth,
-                      int rho_every, const double *box_lo, const double *box_hi) {
+                      int rho_every, const double *box_lo, const double *box_hi,
+                      const double *start_va, const double *lam0) {
   orc_problem pr = {dim, n_p, T, n_o, centers, semi_axes, velocities, start, goal,
                     vmax, amax, rho, w_smooth, w_track, cost_mode, box_lo, box_hi, rho_levels,
-                    rho_growth, rho_every};
-  return orc_am_solve(&pr, n_traj, xi0, max_iters, tol, iters_fixed, xi_out, lam_out,
+                    rho_growth, rho_every, start_va};
+  return orc_am_solve(&pr, n_traj, xi0, lam0, max_iters, tol, iters_fixed, xi_out, lam_out,
                       residual_out, iters_out, hist, n_threads);
 }
 
 int orc_kkt_flat(int dim, int n_p, double T, int n_o, double rho, double w_smooth,
                  double w_track, int cost_mode, double *K, double *Kinv) {
   orc_problem pr = {dim, n_p, T, n_o, NULL, NULL, NULL, NULL, NULL,
-                    0, 0, rho, w_smooth, w_track, cost_mode, NULL, NULL, 1, 1.0, 0};
+                    0, 0, rho, w_smooth, w_track, cost_mode, NULL, NULL, 1, 1.0, 0, NULL};
   return orc_kkt(&pr, K, Kinv);
 }
 

@@ -39,7 +39,7 @@ def tuned(handle, batch, precision="fp32", iters=20):
     if key in cache:
         e = cache[key]
         handle.set_launch_shape(e["warps_per_block"], e["blocks_per_sm"],
-                                e.get("warps_per_trajectory", 1))
+                                e.get("warps_per_trajectory", 1), e.get("occupancy", 0))
         return dict(e, cached=True)
     e = handle.autotune(iters)
     cache = _load()

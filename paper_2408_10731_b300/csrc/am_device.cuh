@@ -173,17 +173,19 @@ __device__ __forceinline__ bool rho_step(const SolveArgs &A, int k, int &level, 
   return true;
 }
 
-// Resume: the owner lanes' multipliers and last contraction of trajectory b from the
-// imported state (lane 16 a + i: axis a, coefficient i; axis 2 at lanes i, 16 + i).
+// Resume or carry: the owner lanes' multipliers of trajectory b from the imported
+// state, and its last contraction when one was imported (resume; a carried start
+// forms u with its initial projection) (lane 16 a + i: axis a, coefficient i; axis 2
+// at lanes i, 16 + i).
 template <int DIM>
 __device__ __forceinline__ void resume_state(const SolveArgs &A, int b, int oa, int ri, float &lam,
                                              float &lam2, float &uo, float &uo2) {
   const size_t base = (size_t)b * DIM * NC;
   lam = A.lam0[base + oa * NC + ri];
-  uo = A.u0[base + oa * NC + ri];
+  if (A.u0) uo = A.u0[base + oa * NC + ri];
   if constexpr (DIM == 3) {
     lam2 = A.lam0[base + 2 * NC + ri];
-    uo2 = A.u0[base + 2 * NC + ri];
+    if (A.u0) uo2 = A.u0[base + 2 * NC + ri];
   }
 }
 

@@ -79,9 +79,9 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
   float lam = 0.f, lam2 = 0.f, uo = 0.f, uo2 = 0.f;
   float mo, mv, ma;
   int k = 0;
-  if (A.lam0) { // resume from (xi, lambda, u) of an earlier solve: the next step is a QP step
+  if (A.lam0) { // resume from (xi, lambda, u) of an earlier solve, or carry lambda over a shift
     resume_state<DIM>(A, b, oa, ri, lam, lam2, uo, uo2);
-    k = 1;
+    k = A.u0 ? 1 : 0; // resume: the next step is a QP step; carry: project first
   }
   signed char st = 1;
   for (;; ++k) {
@@ -189,7 +189,7 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
   int k = 0, par = 0;
   if (A.lam0) {
     resume_state<DIM>(A, b, oa, ri, lam, lam2, uo, uo2);
-    k = 1;
+    k = A.u0 ? 1 : 0; // resume: the next step is a QP step; carry: project first
   }
   signed char st = 1;
   for (;; ++k) {
@@ -322,8 +322,10 @@ __device__ __forceinline__ void solve_nt(const SolveArgs &A, int b, const float 
   }
 }
 
-template <int DIM, int MAXNT>
-__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32, 1)
+// CAP: the occupancy build (at most 4 warps per block, 128 registers, four blocks
+// per SM); otherwise registers are unrestricted (one block of up to 8 warps).
+template <int DIM, int MAXNT, bool CAP = false>
+__global__ void __launch_bounds__(CAP ? 128 : MAX_WARPS_PER_BLOCK * 32, CAP ? 4 : 1)
 k_am_fp32(const __grid_constant__ SolveArgs A) {
   extern __shared__ float4 smem4[];
   const float4 *g4 = reinterpret_cast<const float4 *>(A.tables);
@@ -388,18 +390,18 @@ k_am_long(const __grid_constant__ SolveArgs A) {
 }
 
 template <int W> struct TeamKernel {
-  template <int DIM, int MAXNT> static constexpr auto get() { return k_am_team<DIM, (MAXNT + W - 1) / W, W>; }
+  template <int DIM, int MAXNT, bool CAP> static constexpr auto get() { return k_am_team<DIM, (MAXNT + W - 1) / W, W>; }
 };
 template <> struct TeamKernel<1> {
-  template <int DIM, int MAXNT> static constexpr auto get() { return k_am_fp32<DIM, MAXNT>; }
+  template <int DIM, int MAXNT, bool CAP> static constexpr auto get() { return k_am_fp32<DIM, MAXNT, CAP>; }
 };
 
-template <int DIM, int MAXNT, int W>
+template <int DIM, int MAXNT, int W, bool CAP = false>
 static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_sm,
                             cudaStream_t s, LaunchShape *used) {
-  auto kern = TeamKernel<W>::template get<DIM, MAXNT>();
+  auto kern = TeamKernel<W>::template get<DIM, MAXNT, CAP>();
   const int warps = shape.warps_per_block > 0 ? shape.warps_per_block : 4;
-  if (warps > MAX_WARPS_PER_BLOCK || warps % W != 0) return cudaErrorInvalidValue;
+  if (warps > (CAP ? 4 : MAX_WARPS_PER_BLOCK) || warps % W != 0) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * (size_t)a.table_floats_total +
                       (W > 1 ? (size_t)(warps / W) * (2 * W * XCH * sizeof(float) + sizeof(int)) : 0);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -413,7 +415,10 @@ static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_
   long long grid = (long long)n_sm * occ;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
-  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = W; }
+  if (used) {
+    used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = W;
+    used->occupancy = CAP ? 1 : 0;
+  }
   kern<<<(unsigned)grid, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -449,14 +454,15 @@ static cudaError_t launch_long(const SolveArgs &a, const LaunchShape &shape, int
   long long grid = (long long)n_sm * occ;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
-  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = 1; }
+  if (used) { used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = 1; used->occupancy = 0; }
   k_am_long<DIM><<<(unsigned)grid, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s, LaunchShape *used) {
-  if (precision == 1) return launch_am_mixed(dim, max_np, a, shape, n_sm, s, used);
+  if (precision == 1 || precision == 2)
+    return launch_am_mixed(dim, max_np, precision == 2, a, shape, n_sm, s, used);
   const int nt = (max_np + 31) / 32;
   if (nt > 8) { // long horizons: chunked, one warp per trajectory
     if (shape.team != 0 && shape.team != 1) return cudaErrorInvalidValue;
@@ -464,6 +470,13 @@ cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs 
   }
   const int team = shape.team;
   if (team != 0 && team != 1 && team != 2 && team != 4) return cudaErrorInvalidValue;
+  if (shape.occupancy) { // the register-capped build: one warp per trajectory, n_p <= 160
+    if (team > 1 || nt > 5) return cudaErrorInvalidValue;
+    if (dim == 2) return nt <= 4 ? launch_t<2, 4, 1, true>(a, shape, n_sm, s, used)
+                                 : launch_t<2, 5, 1, true>(a, shape, n_sm, s, used);
+    return nt <= 4 ? launch_t<3, 4, 1, true>(a, shape, n_sm, s, used)
+                   : launch_t<3, 5, 1, true>(a, shape, n_sm, s, used);
+  }
 #define TB_PICK(D, N)                                                                   \
   return team == 4 ? launch_t<D, N, 4>(a, shape, n_sm, s, used)                         \
        : team == 2 ? launch_t<D, N, 2>(a, shape, n_sm, s, used)                         \

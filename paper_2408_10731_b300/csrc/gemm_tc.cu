@@ -19,6 +19,7 @@
 // flag, skips the remaining work, still frees its TMEM and returns.
 #include "internal.cuh"
 #include "tcgen05.cuh"
+#include "gelu.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -46,17 +47,6 @@ struct GemmArgs {
   const float *aux;         // EPI_GELU_BWD: Z [M][ldo]
   int *err;                 // bit 0 set if a wait expired
 };
-
-__device__ __forceinline__ float gelu_tanh(float z) {
-  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-  return 0.5f * z * (1.f + tanhf(k0 * (z + k1 * z * z * z)));
-}
-
-__device__ __forceinline__ float gelu_tanh_grad(float z) {
-  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-  const float t = tanhf(k0 * (z + k1 * z * z * z));
-  return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * k0 * (1.f + 3.f * k1 * z * z);
-}
 
 template <int EPI, int GM_BN>
 __global__ void __launch_bounds__(128, 1)

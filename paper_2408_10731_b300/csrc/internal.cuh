@@ -13,6 +13,7 @@ constexpr int ROW = 12;     // padded row length (floats) of every 11-wide table
 constexpr int MAX_STEPS = 256;       // grid points per problem held in registers by a warp
 constexpr int MAX_STEPS_LONG = 1024; // batch handle, FP32 form: longer horizons run chunked
 constexpr int RHO_MAX_LEVELS = 10; // penalty levels of the continuation ladder
+constexpr int MAX_HZ = 16;         // distinct horizons of one batch in the tensor-core form
 
 // Per-problem record on the device (64 bytes).
 struct ProblemDev {
@@ -77,7 +78,8 @@ struct SolveArgs {
   const int *order;
   const float *xi0;
   const float *lam0;          // resume: multipliers and last contraction of the iterate in
-  const float *u0;            //   xi0 ([n_traj][dim][11]); both NULL for a fresh start
+  const float *u0;            //   xi0 ([n_traj][dim][11]); both NULL for a fresh start;
+                              //   carry (receding horizon): lam0 only, u0 NULL
   float *xi;
   float *lam;
   float *u;
@@ -100,6 +102,11 @@ struct SolveArgs {
   const float *rho_ladder;
   int rho_levels;
   int rho_every;
+  // distinct horizons of the batch (the tensor-core form builds one basis operand per
+  // horizon): n_p and basis-table offset of each, in table order
+  int hz_n;
+  int hz_np[MAX_HZ];
+  int hz_tbl[MAX_HZ];
 };
 
 // ---- compensated (double-float) helpers -----------------------------------
@@ -129,10 +136,33 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 namespace tb {
 cudaError_t launch_setup_tables(const int *d_horizons, const int *d_offsets, int n_horizons,
                                 float *d_tables, cudaStream_t s);
+// d_start_va [n_problems][2][dim]: start velocity and acceleration of the boundary rows
+// (NULL: at rest)
 cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const double *d_T,
-                                  const double *d_start, const double *d_goal, int dim,
-                                  double rho, double w_smooth, double w_track, int cost_mode,
-                                  int max_np, float *d_constants, cudaStream_t s);
+                                  const double *d_start, const double *d_goal,
+                                  const double *d_start_va, int dim, double rho, double w_smooth,
+                                  double w_track, int cost_mode, int max_np, float *d_constants,
+                                  cudaStream_t s);
+// Receding-horizon step (mpc.cu): executed [n_problems] device indices (or NULL: per
+// problem the trajectory with the smallest worst residual, chosen into exec_scratch);
+// every trajectory's xi re-expressed on the window shifted by delta seconds into xi0,
+// lam copied to lam0; the executed plans' state at delta into start / start_va; every
+// obstacle centre moved by v delta in the staged centres.
+struct ShiftArgs {
+  int dim, n_problems, n_traj, n_obs;
+  double delta;
+  const double *T;                 // [n_problems]
+  const int *traj_problem;         // [n_traj]
+  const float *xi, *lam, *res;     // last solve: [n_traj][dim][11] x2, [n_traj][3]
+  float *xi0, *lam0;               // next solve's start
+  const int *executed;             // [n_problems] or NULL
+  int *exec_scratch;               // [n_problems]
+  unsigned long long *key_scratch; // [n_problems]
+  double *start, *start_va;        // [n_problems][dim], [n_problems][2][dim]
+  float *centers;                  // staged obstacle centres [n_obs][dim]
+  const float *velocities;         // [n_obs][dim]
+};
+cudaError_t launch_mpc_shift(const ShiftArgs &a, cudaStream_t s);
 // Obstacle-pair records of all problems: n_slots = 2 x (total pair records); offsets
 // (CSR obstacle offsets, n_problems + 1) and pair_off (first record of each problem,
 // n_problems + 1) are device arrays.
@@ -148,11 +178,18 @@ struct LaunchShape {
   int blocks_per_sm;
   int grid; // filled in by the launcher
   int team; // warps per trajectory: 1 or 2
+  int occupancy; // 1: the build whose registers are capped for more resident warps
+                 // (FP32 form: 128 per thread, at most 4 warps per block; tensor-core
+                 // form: 170, at most 6 warps), one warp per trajectory, horizons up
+                 // to 160 grid points; 0: registers unrestricted
 };
-// tensor-core form (am_mixed.cu); every problem of the batch has n_p steps; the
-// shape's warps per block (0: the batch spread over all SMs) and blocks per SM apply
-cudaError_t launch_am_mixed(int dim, int n_p, const SolveArgs &a, const LaunchShape &shape,
-                            int n_sm, cudaStream_t s, LaunchShape *used);
+// tensor-core form (am_mixed.cu); horizons up to max_np <= 256, the distinct ones in
+// a.hz_*; split: hi/lo BF16 operand pairs; the shape's warps per block (0: the batch
+// spread over all SMs) and blocks per SM apply
+cudaError_t launch_am_mixed(int dim, int max_np, bool split, const SolveArgs &a,
+                            const LaunchShape &shape, int n_sm, cudaStream_t s, LaunchShape *used);
+// shared memory of one CTA of the tensor-core form with `warps` warps
+size_t mixed_smem_bytes(const SolveArgs &a, int dim, bool split, int warps);
 cudaError_t launch_am_solve(int dim, int max_np, int precision, const SolveArgs &a,
                             const LaunchShape &shape, int n_sm, cudaStream_t s,
                             LaunchShape *used);
@@ -181,6 +218,13 @@ cudaError_t launch_gemm_bf16(int epi, const void *A, const void *B, int M, int N
                              const float *aux, int *err, cudaStream_t s);
 cudaError_t launch_accel_cost(const float *xi, const int *traj_problem, const ProblemDev *problems,
                               const float *tables, int dim, int B, float *out, cudaStream_t s);
+// 2D homotopy signatures of the trajectories xi (homotopy.cu): bit j = obstacle j passed
+// on the left of the relative motion at the closest approach (j < 64)
+cudaError_t launch_homotopy(const float *xi, const int *traj_problem, const ProblemDev *problems,
+                            const float *tables, const float *centers, const float *axes,
+                            const float *vel, const int *obs_offsets, int n_traj,
+                            unsigned long long *sig, cudaStream_t s);
 cudaError_t launch_ffma_peak(float *out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_ffma2_peak(float *out, int blocks, int iters, cudaStream_t s);
+cudaError_t launch_rsqrt_peak(float *out, int blocks, int iters, cudaStream_t s);
 } // namespace tb

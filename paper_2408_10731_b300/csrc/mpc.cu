@@ -1,0 +1,117 @@
+// mpc.cu -- the receding-horizon step of Paper II's MPC use of Algorithm 2:
+// the robot has followed one planned trajectory per problem for delta seconds,
+// and the next control loop's solve starts from the previous one's multipliers
+// (the paper initialises the Lagrange multipliers with the preceding loop's
+// solution). On the device, in FP64:
+//
+//  * the executed plan of each problem: the caller's choice, or the trajectory
+//    with the smallest worst-of-three residual (ties to the lower index), found
+//    with a 64-bit atomic minimum of (residual bits, index): non-negative floats
+//    order as their bit patterns, and a NaN residual sorts after every number;
+//  * every trajectory's polynomial re-expressed on the shifted window: the
+//    coefficients of q(tau') = p(f + tau'), f = delta / T, are the blossom
+//    (polar form) of p at (f, ..., f, 1 + f, ..., 1 + f) with i arguments 1 + f
+//    for coefficient i, each evaluated by de Casteljau's scheme with one
+//    parameter per level; past the old end the polynomial is extrapolated;
+//  * the executed plan's position, velocity and acceleration at delta: the first
+//    three shifted coefficients give q(0), q'(0) = 10 (c1 - c0) and
+//    q''(0) = 90 (c2 - 2 c1 + c0), scaled by 1/T and 1/T^2;
+//  * every obstacle centre moved on to c + v delta (its constant-velocity
+//    prediction; multiply and add rounded separately, then rounded to FP32);
+//  * the multipliers copied unchanged.
+#include "internal.cuh"
+
+namespace tb {
+
+// Coefficient i of the polynomial with coefficients c re-expressed on [f, 1 + f].
+__device__ double blossom_shift(const double (&c)[NC], int i, double f) {
+  double w[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) w[j] = c[j];
+  for (int r = 1; r < NC; ++r) {
+    const double u = r <= NC - 1 - i ? f : 1.0 + f;
+    for (int j = 0; j < NC - r; ++j) w[j] = fma(u, w[j + 1] - w[j], w[j]);
+  }
+  return w[0];
+}
+
+__global__ void k_exec_clear(int n_problems, unsigned long long *key) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n_problems) key[p] = ~0ull;
+}
+
+__global__ void k_exec_pick(int n_traj, const int *traj_problem, const float *res,
+                            unsigned long long *key) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_traj) return;
+  const float r0 = res[b * 3 + 0], r1 = res[b * 3 + 1], r2 = res[b * 3 + 2];
+  const float r = fmaxf(fmaxf(r0, r1), r2);
+  const bool nan = isnan(r0) || isnan(r1) || isnan(r2); // fmaxf would drop a NaN operand
+  const unsigned bits = nan ? 0x7fc00000u : __float_as_uint(r);
+  atomicMin(&key[traj_problem[b]], ((unsigned long long)bits << 32) | (unsigned)b);
+}
+
+__global__ void k_exec_index(int n_problems, const unsigned long long *key, int *exec) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n_problems) exec[p] = key[p] == ~0ull ? -1 : (int)(unsigned)(key[p] & 0xffffffffull);
+}
+
+// One thread per (trajectory, axis): xi0 = shifted xi, lam0 = lam.
+__global__ void k_shift_traj(ShiftArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n_traj * a.dim) return;
+  const int b = e / a.dim;
+  const double f = a.delta / a.T[a.traj_problem[b]];
+  const float *x = a.xi + (size_t)e * NC;
+  double c[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) c[j] = (double)x[j];
+  for (int i = 0; i < NC; ++i) {
+    a.xi0[(size_t)e * NC + i] = (float)blossom_shift(c, i, f);
+    a.lam0[(size_t)e * NC + i] = a.lam[(size_t)e * NC + i];
+  }
+}
+
+// One thread per (problem, axis): the executed plan's state at delta becomes the start.
+__global__ void k_shift_start(ShiftArgs a, const int *exec) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n_problems * a.dim) return;
+  const int p = e / a.dim, ax = e % a.dim;
+  const int b = exec[p];
+  if (b < 0) return; // no trajectory of this problem: its start stays
+  const double T = a.T[p], f = a.delta / T;
+  const float *x = a.xi + ((size_t)b * a.dim + ax) * NC;
+  double c[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) c[j] = (double)x[j];
+  const double q0 = blossom_shift(c, 0, f), q1 = blossom_shift(c, 1, f), q2 = blossom_shift(c, 2, f);
+  const double v0 = 10.0 * (q1 - q0) / T, a0 = 90.0 * ((q2 - q1) - (q1 - q0)) / (T * T);
+  if (!isfinite(q0) || !isfinite(v0) || !isfinite(a0)) return; // a failed plan: keep the start
+  a.start[p * a.dim + ax] = q0;
+  a.start_va[(p * 2 + 0) * a.dim + ax] = v0;
+  a.start_va[(p * 2 + 1) * a.dim + ax] = a0;
+}
+
+__global__ void k_shift_obstacles(ShiftArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n_obs * a.dim) return;
+  a.centers[e] = (float)__dadd_rn((double)a.centers[e], __dmul_rn((double)a.velocities[e], a.delta));
+}
+
+cudaError_t launch_mpc_shift(const ShiftArgs &a, cudaStream_t s) {
+  const int *exec = a.executed;
+  if (!exec) {
+    k_exec_clear<<<(a.n_problems + 255) / 256, 256, 0, s>>>(a.n_problems, a.key_scratch);
+    k_exec_pick<<<(a.n_traj + 255) / 256, 256, 0, s>>>(a.n_traj, a.traj_problem, a.res,
+                                                        a.key_scratch);
+    k_exec_index<<<(a.n_problems + 255) / 256, 256, 0, s>>>(a.n_problems, a.key_scratch,
+                                                             a.exec_scratch);
+    exec = a.exec_scratch;
+  }
+  k_shift_start<<<(a.n_problems * a.dim + 127) / 128, 128, 0, s>>>(a, exec);
+  k_shift_traj<<<(a.n_traj * a.dim + 127) / 128, 128, 0, s>>>(a);
+  if (a.n_obs > 0) k_shift_obstacles<<<(a.n_obs * a.dim + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+} // namespace tb

@@ -78,10 +78,17 @@ cudaError_t scratch_address(int dev, unsigned char **out) {
   return cudaSuccess;
 }
 
-// order[k] = k (the queue runs the trajectories in index order).
-__global__ void k_noalloc_order(int n_traj, int *order) {
+// order[k] = k (the queue runs the trajectories in index order), and the range
+// check of the caller's trajectory -> problem map, which lives in device memory:
+// an entry outside [0, n_problems) sets bit 4 of *flags and nothing reads through it
+// (the host looks at the flag before it launches anything that would).
+__global__ void k_noalloc_order(int n_traj, const int *traj_problem, int n_problems, int *order,
+                                int *flags) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_traj) order[i] = i;
+  if (i >= n_traj) return;
+  order[i] = i;
+  const int p = traj_problem[i];
+  if (p < 0 || p >= n_problems) atomicOr(flags, 16);
 }
 
 traj_status err(traj_status s, const std::string &msg) {
@@ -194,13 +201,18 @@ extern "C" traj_status traj_solve_noalloc(
   NA_CK(cudaMemcpyAsync(d_offsets, obs_offsets, sizeof(int) * (n_problems + 1), cudaMemcpyHostToDevice, s));
   NA_CK(cudaMemcpyAsync(d_pair_off, pair_off, sizeof(int) * (n_problems + 1), cudaMemcpyHostToDevice, s));
   NA_CK(cudaMemsetAsync(d_words, 0, 64, s));
-  k_noalloc_order<<<(n_traj + 255) / 256, 256, 0, s>>>(n_traj, d_order);
+  k_noalloc_order<<<(n_traj + 255) / 256, 256, 0, s>>>(n_traj, traj_problem, n_problems, d_order,
+                                                         d_words + 1);
   NA_CK(cudaGetLastError());
+  int flags = 0;
+  NA_CK(cudaMemcpyAsync(&flags, d_words + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NA_CK(cudaStreamSynchronize(s));
+  if (flags & 16) return err(TRAJ_EINVAL, "traj_solve_noalloc: a traj_problem entry is outside [0, n_problems)");
   NA_CK(launch_setup_tables(d_hz, d_hoff, n_hz, d_tables, s));
   NA_CK(launch_pack_obstacles(D, n_problems, 2 * pair_off[n_problems], d_offsets, d_pair_off,
                               centers, semi_axes, velocities, d_obs, d_problems, s));
-  NA_CK(launch_setup_problems(d_problems, n_problems, d_T, d_start, d_goal, D, c.rho, c.w_smooth,
-                              c.w_track, c.cost_mode, max_np, d_const, s));
+  NA_CK(launch_setup_problems(d_problems, n_problems, d_T, d_start, d_goal, nullptr, D, c.rho,
+                              c.w_smooth, c.w_track, c.cost_mode, max_np, d_const, s));
   SolveArgs a{};
   a.problems = d_problems;
   a.obstacles = d_obs;
@@ -227,11 +239,14 @@ extern "C" traj_status traj_solve_noalloc(
   a.queue = d_words;
   a.flags = d_words + 1;
   a.t0 = reinterpret_cast<unsigned long long *>(d_words + 2);
-  NA_CK(launch_am_solve(D, max_np, TRAJ_PREC_FP32, a, LaunchShape{4, 0, 0}, n_sm, s, nullptr));
+  // four warps per block, one warp per trajectory
+  LaunchShape shape{};
+  shape.warps_per_block = 4;
+  shape.team = 1;
+  NA_CK(launch_am_solve(D, max_np, TRAJ_PREC_FP32, a, shape, n_sm, s, nullptr));
   // the host-side sources above live on this stack frame: finish before returning
+  NA_CK(cudaMemcpyAsync(&flags, d_words + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));
-  int flags = 0;
-  NA_CK(cudaMemcpy(&flags, d_words + 1, sizeof(int), cudaMemcpyDeviceToHost));
   if (flags & 2) return err(TRAJ_ENAN, "non-finite input in some trajectories");
   return TRAJ_OK;
 }

@@ -1,7 +1,7 @@
-// peak.cu -- FP32 FFMA throughput microbenchmark: the denominator of the ALU
-// roofline that the solve kernel is measured against (no FP32 figure exists in
-// the driver's measured peaks). Eight independent FMA chains per thread keep
-// the FMA pipes busy without memory traffic.
+// peak.cu -- FP32 FFMA and MUFU reciprocal-square-root throughput
+// microbenchmarks: the denominators of the ALU roofline that the solve kernels
+// are measured against (no FP32 or MUFU figure exists in the measured peaks).
+// Eight independent chains per thread keep the pipe busy without memory traffic.
 #include "internal.cuh"
 
 namespace tb {
@@ -39,6 +39,28 @@ __global__ void k_ffma2_peak(float *out, int iters) {
   const float s = a0.x + a1.x + a2.x + a3.x + a4.x + a5.x + a6.x + a7.x + a0.y + a1.y + a2.y +
                   a3.y + a4.y + a5.y + a6.y + a7.y;
   if (s == 123.456f) out[blockIdx.x] = s;
+}
+
+// Eight independent rsqrtf chains (x <- 1/sqrt(x), which stays in (0, inf) and
+// tends to 1): the same instruction the projections issue once per point inside an
+// obstacle and once per velocity / acceleration bound test.
+__global__ void k_rsqrt_peak(float *out, int iters) {
+  float a0 = 1.0f + threadIdx.x * 1e-3f, a1 = a0 + 0.1f, a2 = a0 + 0.2f, a3 = a0 + 0.3f;
+  float a4 = a0 + 0.4f, a5 = a0 + 0.5f, a6 = a0 + 0.6f, a7 = a0 + 0.7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      a0 = rsqrtf(a0); a1 = rsqrtf(a1); a2 = rsqrtf(a2); a3 = rsqrtf(a3);
+      a4 = rsqrtf(a4); a5 = rsqrtf(a5); a6 = rsqrtf(a6); a7 = rsqrtf(a7);
+    }
+  }
+  const float s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == 123.456f) out[blockIdx.x] = s;
+}
+
+cudaError_t launch_rsqrt_peak(float *out, int blocks, int iters, cudaStream_t s) {
+  k_rsqrt_peak<<<blocks, 256, 0, s>>>(out, iters);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ffma_peak(float *out, int blocks, int iters, cudaStream_t s) {

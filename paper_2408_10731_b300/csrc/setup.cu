@@ -5,7 +5,8 @@
 //  * KKT formation and inversion per problem (eqs. over_2, zeta_1_sepration_3,
 //    Q_matrix, matrix_vec): Q-bar = Q + rho F^T F with F^T F = n_o P^T P +
 //    Pd^T Pd + Pdd^T Pdd (the stacked F of Paper II is never formed), boundary
-//    rows A = [P_0; Pd_0; Pdd_0; P_{-1}], Gauss-Jordan with partial pivoting in
+//    rows A = [P_0; Pd_0; Pdd_0; P_{-1}] with b = (start, v0, a0, goal), v0 = a0 = 0
+//    unless a start state is given, Gauss-Jordan with partial pivoting in
 //    FP64, then the per-problem constants the FP32 loop needs, each split into
 //    an FP32 (hi, lo) pair: K11, G = rho K11 F^T F, c = K12 b, hq = K11 (-q) + c.
 //  * Obstacle packing: moving ellipses/ellipsoids into the float4 records the
@@ -46,8 +47,8 @@ static_assert(NC * NC + 3 * NC <= SETUP_THREADS, "one Gram / q element per threa
 
 __global__ void __launch_bounds__(SETUP_THREADS)
 k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
-                 const double *goal, int dim, double rho, double w_s, double w_t,
-                 int cost_mode, float *constants) {
+                 const double *goal, const double *start_va, int dim, double rho, double w_s,
+                 double w_t, int cost_mode, float *constants) {
   extern __shared__ double sm[];
   __shared__ double Q[NC * NC], M[NC * NC], qv[3 * NC];
   __shared__ double W[NK * 2 * NK];
@@ -188,7 +189,11 @@ k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
     int ax = e / ROW, i = e % ROW;
     double cval = 0, hq = 0;
     if (ax < dim && i < NC) {
-      double bb[NE] = {start[p * dim + ax], 0.0, 0.0, goal[p * dim + ax]};
+      // b = (start, v0, a0, goal): at rest unless a start state is given (the
+      // receding-horizon step moves the start onto the executed plan)
+      const double v0 = start_va ? start_va[(p * 2 + 0) * dim + ax] : 0.0;
+      const double a0 = start_va ? start_va[(p * 2 + 1) * dim + ax] : 0.0;
+      double bb[NE] = {start[p * dim + ax], v0, a0, goal[p * dim + ax]};
       for (int k = 0; k < NE; ++k) cval += K12[i * NE + k] * bb[k];
       hq = cval;
       for (int k = 0; k < NC; ++k) hq += K11[i * NC + k] * (-qv[ax * NC + k]);
@@ -247,7 +252,8 @@ cudaError_t launch_setup_tables(const int *d_horizons, const int *d_offsets, int
 }
 
 cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const double *d_T,
-                                  const double *d_start, const double *d_goal, int dim,
+                                  const double *d_start, const double *d_goal,
+                                  const double *d_start_va, int dim,
                                   double rho, double w_smooth, double w_track, int cost_mode,
                                   int max_np, float *d_constants, cudaStream_t s) {
   if (n_problems <= 0) return cudaSuccess;
@@ -256,9 +262,9 @@ cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const 
   cudaError_t e = cudaFuncSetAttribute(k_setup_problems,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_setup_problems<<<n_problems, SETUP_THREADS, smem, s>>>(d_problems, d_T, d_start, d_goal, dim,
-                                                           rho, w_smooth, w_track, cost_mode,
-                                                           d_constants);
+  k_setup_problems<<<n_problems, SETUP_THREADS, smem, s>>>(d_problems, d_T, d_start, d_goal,
+                                                           d_start_va, dim, rho, w_smooth, w_track,
+                                                           cost_mode, d_constants);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,10 @@ struct traj_batch {
   // device workspace
   ProblemDev *d_problems = nullptr;
   double *d_T = nullptr, *d_start = nullptr, *d_goal = nullptr;
+  double *d_start_va = nullptr;               // [P][2][dim] start velocity, acceleration
+  int *d_exec = nullptr;                      // receding-horizon step: executed plan per problem
+  unsigned long long *d_exec_key = nullptr;
+  unsigned long long *d_sig = nullptr;        // homotopy signatures [B]
   float *d_constants = nullptr;
   int const_levels = 1;                       // constants blocks allocated per problem
   // penalty continuation (traj_set_rho_schedule): levels, growth per level, switch period
@@ -48,6 +52,8 @@ struct traj_batch {
   float *d_xi0 = nullptr, *d_xi = nullptr, *d_lam = nullptr, *d_u = nullptr, *d_res = nullptr;
   float *d_lam0 = nullptr, *d_u0 = nullptr; // imported state (traj_set_state)
   bool resume = false;                       // the next solves continue the imported state
+  bool carry = false;                        // the next solves start from the shifted iterate
+                                             // and the carried multipliers
   int *d_iters = nullptr;
   signed char *d_status = nullptr;
   int *d_queue = nullptr, *d_flags = nullptr;
@@ -55,11 +61,12 @@ struct traj_batch {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // launch shape of the solve (set by traj_autotune / traj_set_launch_shape)
   LaunchShape shape{0, 0, 0, 1};
+  LaunchShape used{0, 0, 0, 0}; // what the last captured solve launch resolved the shape to
   // the solve captured as a CUDA graph, replayed while its key is unchanged
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_valid = false;
-  int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1, g_team = -1, g_resume = -1;
+  int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1, g_team = -1, g_resume = -1, g_occ = -1;
   float g_tol = 0.f;
   unsigned long long g_timeout = 0;
   std::vector<int> tbl_off; // per problem, float offset of its basis tables
@@ -103,7 +110,8 @@ template <class T> static cudaError_t dalloc(T **p, size_t n) {
 }
 
 static void free_all(traj_batch *b) {
-  void *ptrs[] = {b->d_problems, b->d_T, b->d_start, b->d_goal, b->d_constants, b->d_rho_ladder, b->d_tables,
+  void *ptrs[] = {b->d_problems, b->d_T, b->d_start, b->d_goal, b->d_start_va, b->d_exec,
+                  b->d_exec_key, b->d_sig, b->d_constants, b->d_rho_ladder, b->d_tables,
                   b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_index,
                   b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res, b->d_lam0, b->d_u0,
                   b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0, b->d_L, b->d_r,
@@ -159,7 +167,8 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
     g_create_error = "vmax, amax, rho must be positive and finite; weights non-negative";
     return TRAJ_EINVAL;
   }
-  if (c.precision != TRAJ_PREC_FP32 && c.precision != TRAJ_PREC_MIXED) {
+  if (c.precision != TRAJ_PREC_FP32 && c.precision != TRAJ_PREC_MIXED &&
+      c.precision != TRAJ_PREC_MIXED_SPLIT) {
     g_create_error = "unknown precision";
     return TRAJ_EINVAL;
   }
@@ -189,7 +198,9 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
     return bail("cudaDeviceGetAttribute", e);
   const size_t P = c.max_problems, B = c.max_traj, N = c.max_obstacles, D = c.dim;
   if ((e = dalloc(&b->d_problems, P)) || (e = dalloc(&b->d_T, P)) || (e = dalloc(&b->d_start, P * D)) ||
-      (e = dalloc(&b->d_goal, P * D)) || (e = dalloc(&b->d_constants, P * CONST_FLOATS)) ||
+      (e = dalloc(&b->d_goal, P * D)) || (e = dalloc(&b->d_start_va, P * 2 * D)) ||
+      (e = dalloc(&b->d_exec, P)) || (e = dalloc(&b->d_exec_key, P)) || (e = dalloc(&b->d_sig, B)) ||
+      (e = dalloc(&b->d_constants, P * CONST_FLOATS)) ||
       (e = dalloc(&b->d_rho_ladder, RHO_MAX_LEVELS)) ||
       (e = dalloc(&b->d_horizons, MAX_STEPS_LONG + 1)) || (e = dalloc(&b->d_hoffsets, MAX_STEPS_LONG + 1)) ||
       (e = dalloc(&b->d_obs, ((N + P) / 2 + 1) * pair_vec(c.dim))) ||
@@ -258,6 +269,7 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
   CK(b, cudaMemcpyAsync(b->d_T, duration, sizeof(double) * n_problems, cudaMemcpyHostToDevice, b->stream));
   CK(b, cudaMemcpyAsync(b->d_start, start, sizeof(double) * n_problems * D, cudaMemcpyHostToDevice, b->stream));
   CK(b, cudaMemcpyAsync(b->d_goal, goal, sizeof(double) * n_problems * D, cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemsetAsync(b->d_start_va, 0, sizeof(double) * n_problems * 2 * D, b->stream)); // at rest
   CK(b, launch_setup_tables(b->d_horizons, b->d_hoffsets, (int)hz.size(), b->d_tables, b->stream));
   CK(b, cudaStreamSynchronize(b->stream)); // host arrays may be reused by the caller
   b->n_steps.assign(n_steps, n_steps + n_problems);
@@ -299,7 +311,7 @@ static traj_status upload_problems(traj_batch *b) {
   CK(b, launch_pack_obstacles(D, P, 2 * index[2 * P + 1], b->d_obs_index, b->d_obs_index + P + 1,
                               st_c, st_a, st_v, b->d_obs, b->d_problems, b->stream));
   for (int l = 0; l < L; ++l)
-    CK(b, launch_setup_problems(b->d_problems, P, b->d_T, b->d_start, b->d_goal, D,
+    CK(b, launch_setup_problems(b->d_problems, P, b->d_T, b->d_start, b->d_goal, b->d_start_va, D,
                                 b->cfg.rho * std::pow(b->rho_growth, (double)l), b->cfg.w_smooth,
                                 b->cfg.w_track, b->cfg.cost_mode, b->max_np_used,
                                 b->d_constants + (size_t)l * CONST_FLOATS, b->stream));
@@ -371,8 +383,9 @@ traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
                              const float *coeffs0) {
   if (!b) return TRAJ_EINVAL;
   if (!b->have_obstacles) return fail(b, TRAJ_ESTATE, "traj_set_obstacles must come first");
-  if (b->resume) { // a fresh start from here on
+  if (b->resume || b->carry) { // a fresh start from here on
     b->resume = false;
+    b->carry = false;
     invalidate_graph(b);
   }
   if (!traj_problem && coeffs0 && b->have_initial && n_traj == b->n_traj) {
@@ -447,6 +460,10 @@ static traj_status solve_stats(traj_batch *b, traj_solve_stats *stats) {
   return s.n_solved == B ? TRAJ_OK : TRAJ_NOT_CONVERGED;
 }
 
+// How the solve starts: 0 fresh (project xi0, lambda0 = 0), 1 resume (QP step from
+// the imported xi, lambda, u), 2 carry (project the shifted xi0, lambda0 = carried).
+static int start_mode(const traj_batch *b) { return b->resume ? 1 : (b->carry ? 2 : 0); }
+
 traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
                        traj_solve_stats *stats) {
   tb::NvtxRange nvtx_range("traj_solve");
@@ -454,13 +471,9 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
   if (max_iters < 0) return fail(b, TRAJ_EINVAL, "max_iters must be >= 0");
   if (std::isnan(tol) || !(timeout_ms >= 0)) return fail(b, TRAJ_EINVAL, "bad tol or timeout");
-  if (b->cfg.precision == TRAJ_PREC_MIXED) {
-    for (int p = 1; p < b->n_problems; ++p)
-      if (b->n_steps[p] != b->n_steps[0])
-        return fail(b, TRAJ_ESHAPE, "the tensor-core form needs one horizon (n_steps) per batch");
-    if (b->max_np_used > MAX_STEPS)
-      return fail(b, TRAJ_ESHAPE, "the tensor-core form takes at most 256 grid points per problem");
-  }
+  const bool mixed = b->cfg.precision != TRAJ_PREC_FP32;
+  if (mixed && b->max_np_used > MAX_STEPS)
+    return fail(b, TRAJ_ESHAPE, "the tensor-core form takes at most 256 grid points per problem");
   if (b->max_np_used > MAX_STEPS && b->shape.team != 1)
     return fail(b, TRAJ_ESHAPE, "horizons above 256 grid points run one warp per trajectory "
                                 "(warps_per_trajectory 1)");
@@ -476,8 +489,8 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   a.traj_problem = b->d_traj_problem;
   a.order = b->d_order;
   a.xi0 = b->d_xi0;
-  a.lam0 = b->resume ? b->d_lam0 : nullptr;
-  a.u0 = b->resume ? b->d_u0 : nullptr;
+  a.lam0 = (b->resume || b->carry) ? b->d_lam0 : nullptr;
+  a.u0 = b->resume ? b->d_u0 : nullptr; // carry: u is formed by the initial projection
   a.xi = b->d_xi;
   a.lam = b->d_lam;
   a.u = b->d_u;
@@ -492,13 +505,34 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   a.amax = (float)b->cfg.amax;
   a.cost_mode = b->cfg.cost_mode;
   a.timeout_ns = timeout_ms > 0 ? (unsigned long long)(timeout_ms * 1e6) : 0ull;
+  {
+    // distinct horizons in table order (ascending n_p, as traj_set_problems laid them out)
+    std::vector<int> hz(b->n_steps);
+    std::sort(hz.begin(), hz.end());
+    hz.erase(std::unique(hz.begin(), hz.end()), hz.end());
+    if (mixed && (int)hz.size() > MAX_HZ)
+      return fail(b, TRAJ_ESHAPE, "the tensor-core form takes at most 16 distinct horizons per batch");
+    int off = 0;
+    a.hz_n = std::min((int)hz.size(), MAX_HZ);
+    for (int h = 0; h < a.hz_n; ++h) {
+      a.hz_np[h] = hz[h];
+      a.hz_tbl[h] = off;
+      off += table_floats(hz[h]);
+    }
+    a.table_floats_total = b->table_floats;
+    if (mixed && mixed_smem_bytes(a, b->cfg.dim, b->cfg.precision == TRAJ_PREC_MIXED_SPLIT, 1) >
+                     227 * 1024)
+      return fail(b, TRAJ_ESHAPE, "the tensor-core form's basis operands of these horizons exceed "
+                                  "the shared memory of one CTA");
+  }
   a.queue = b->d_queue;
   a.t0 = b->d_t0;
   a.flags = b->d_flags;
   const bool same = b->graph_valid && b->g_max_iters == max_iters && b->g_tol == tol &&
                     b->g_timeout == a.timeout_ns && b->g_n_traj == b->n_traj &&
                     b->g_warps == b->shape.warps_per_block && b->g_bps == b->shape.blocks_per_sm &&
-                    b->g_team == b->shape.team && b->g_resume == (int)b->resume;
+                    b->g_team == b->shape.team && b->g_occ == b->shape.occupancy &&
+                    b->g_resume == start_mode(b);
   if (!same) {
     // capture {clear counters; persistent solve} on the handle's capture stream
     invalidate_graph(b);
@@ -508,7 +542,8 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
     if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_flags, 0, sizeof(int), cs);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_t0, 0, sizeof(unsigned long long), cs);
     if (ce == cudaSuccess)
-      ce = launch_am_solve(b->cfg.dim, b->max_np_used, b->cfg.precision, a, b->shape, b->n_sm, cs, nullptr);
+      ce = launch_am_solve(b->cfg.dim, b->max_np_used, b->cfg.precision, a, b->shape, b->n_sm, cs,
+                           &b->used);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(cs, &g);
     if (ce == cudaSuccess) ce = ee;
@@ -522,7 +557,8 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
     b->g_max_iters = max_iters; b->g_tol = tol; b->g_timeout = a.timeout_ns;
     b->g_n_traj = b->n_traj; b->g_warps = b->shape.warps_per_block; b->g_bps = b->shape.blocks_per_sm;
     b->g_team = b->shape.team;
-    b->g_resume = (int)b->resume;
+    b->g_occ = b->shape.occupancy;
+    b->g_resume = start_mode(b);
   }
   CK(b, cudaEventRecord(b->ev0, b->stream));
   CK(b, cudaGraphLaunch(b->graph_exec, b->stream));
@@ -560,6 +596,21 @@ traj_status traj_get_accel_cost(traj_batch *b, float *cost) {
                           b->n_traj, b->d_r, b->stream));
   CK(b, cudaMemcpyAsync(cost, b->d_r, sizeof(float) * b->n_traj, cudaMemcpyDefault, b->stream));
   if (is_host_ptr(cost)) CK(b, cudaStreamSynchronize(b->stream));
+  return TRAJ_OK;
+}
+
+traj_status traj_homotopy_signature(traj_batch *b, unsigned long long *sig) {
+  if (!b || !sig) return TRAJ_EINVAL;
+  if (!b->have_result) return fail(b, TRAJ_ESTATE, "no solve has run");
+  if (b->cfg.dim != 2) return fail(b, TRAJ_EINVAL, "homotopy signatures are defined for 2D problems");
+  if (b->max_np_used > MAX_STEPS) return fail(b, TRAJ_ESHAPE, "homotopy signatures take n_p <= 256");
+  const int N = b->n_obs, D = b->cfg.dim;
+  const float *st_c = b->d_obs_stage, *st_a = st_c + (size_t)N * D, *st_v = st_a + (size_t)N * D;
+  CK(b, launch_homotopy(b->d_xi, b->d_traj_problem, b->d_problems, b->d_tables, st_c, st_a, st_v,
+                        b->d_obs_index, b->n_traj, b->d_sig, b->stream));
+  CK(b, cudaMemcpyAsync(sig, b->d_sig, sizeof(unsigned long long) * b->n_traj, cudaMemcpyDefault,
+                        b->stream));
+  if (is_host_ptr(sig)) CK(b, cudaStreamSynchronize(b->stream));
   return TRAJ_OK;
 }
 
@@ -632,26 +683,100 @@ traj_status traj_set_state(traj_batch *b, const float *coeffs, const float *lamb
   CK(b, cudaMemcpyAsync(b->d_lam0, lambda, sizeof(float) * n, cudaMemcpyDefault, b->stream));
   CK(b, cudaMemcpyAsync(b->d_u0, u, sizeof(float) * n, cudaMemcpyDefault, b->stream));
   if (is_host_ptr(coeffs) || is_host_ptr(lambda) || is_host_ptr(u)) CK(b, cudaStreamSynchronize(b->stream));
-  if (!b->resume) {
+  if (!b->resume || b->carry) {
     b->resume = true;
+    b->carry = false;
     invalidate_graph(b);
   }
   b->have_result = false;
   return TRAJ_OK;
 }
 
+traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed) {
+  tb::NvtxRange nvtx_range("traj_shift_horizon");
+  if (!b) return TRAJ_EINVAL;
+  if (!b->have_result) return fail(b, TRAJ_ESTATE, "traj_shift_horizon needs a finished solve");
+  if (b->cfg.cost_mode != TRAJ_COST_SMOOTH_TRACK)
+    return fail(b, TRAJ_EINVAL, "the receding-horizon step needs the smoothness/tracking cost");
+  const int P = b->n_problems, B = b->n_traj;
+  double tmin = b->duration[0];
+  for (int p = 1; p < P; ++p) tmin = std::min(tmin, b->duration[p]);
+  if (!(delta > 0) || !(delta < tmin) || !std::isfinite(delta))
+    return fail(b, TRAJ_EINVAL, "delta must lie in (0, T) for every problem");
+  if (executed) {
+    for (int p = 0; p < P; ++p)
+      if (executed[p] < 0 || executed[p] >= B || b->traj_problem[executed[p]] != p)
+        return fail(b, TRAJ_EINVAL, "executed[" + std::to_string(p) + "] is not a trajectory of problem " +
+                                        std::to_string(p));
+    CK(b, cudaMemcpyAsync(b->d_exec, executed, sizeof(int) * P, cudaMemcpyHostToDevice, b->stream));
+  }
+  ShiftArgs a{};
+  a.dim = b->cfg.dim;
+  a.n_problems = P;
+  a.n_traj = B;
+  a.n_obs = b->n_obs;
+  a.delta = delta;
+  a.T = b->d_T;
+  a.traj_problem = b->d_traj_problem;
+  a.xi = b->d_xi;
+  a.lam = b->d_lam;
+  a.res = b->d_res;
+  a.xi0 = b->d_xi0;
+  a.lam0 = b->d_lam0;
+  a.executed = executed ? b->d_exec : nullptr;
+  a.exec_scratch = b->d_exec;
+  a.key_scratch = b->d_exec_key;
+  a.start = b->d_start;
+  a.start_va = b->d_start_va;
+  a.centers = b->d_obs_stage;
+  a.velocities = b->d_obs_stage + (size_t)2 * b->n_obs * b->cfg.dim;
+  CK(b, launch_mpc_shift(a, b->stream));
+  traj_status rs = upload_problems(b); // re-pack the moved obstacles, FP64 set-up of every level
+  if (rs != TRAJ_OK) return rs;
+  if (!b->carry || b->resume) {
+    b->carry = true;
+    b->resume = false;
+    invalidate_graph(b);
+  }
+  b->have_result = false;
+  b->err.clear();
+  return TRAJ_OK;
+}
+
 traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape) {
   if (!b || !shape) return TRAJ_EINVAL;
+  const bool tc = b->cfg.precision != TRAJ_PREC_FP32;
   if (shape->warps_per_block < 0 || shape->warps_per_block > 8 || shape->blocks_per_sm < 0 ||
       (shape->warps_per_trajectory != 1 && shape->warps_per_trajectory != 2 &&
        shape->warps_per_trajectory != 4) ||
       (shape->warps_per_block % shape->warps_per_trajectory) != 0 ||
-      (b->cfg.precision == TRAJ_PREC_MIXED && shape->warps_per_trajectory != 1))
+      (tc && shape->warps_per_trajectory != 1))
     return fail(b, TRAJ_EINVAL, "warps_per_block in [0, 8] (0: default; a multiple of "
                                 "warps_per_trajectory), blocks_per_sm >= 0, warps_per_trajectory "
                                 "1, 2 or 4 (1 in the tensor-core form)");
-  b->shape = LaunchShape{shape->warps_per_block, shape->blocks_per_sm, 0, shape->warps_per_trajectory};
+  if (shape->occupancy != 0 && shape->occupancy != 1)
+    return fail(b, TRAJ_EINVAL, "occupancy must be 0 or 1");
+  if (shape->occupancy && (shape->warps_per_trajectory != 1 || shape->warps_per_block > (tc ? 6 : 4)))
+    return fail(b, TRAJ_EINVAL, "the register-capped build runs one warp per trajectory and at "
+                                "most 4 warps per block (6 in the tensor-core form)");
+  if (shape->occupancy && b->have_problems && b->max_np_used > 160)
+    return fail(b, TRAJ_ESHAPE, "the register-capped build takes horizons up to 160 grid points");
+  b->shape = LaunchShape{shape->warps_per_block, shape->blocks_per_sm, 0, shape->warps_per_trajectory,
+                         shape->occupancy};
   invalidate_graph(b);
+  return TRAJ_OK;
+}
+
+traj_status traj_get_launch_info(traj_batch *b, traj_launch_shape *resolved, int *grid) {
+  if (!b) return TRAJ_EINVAL;
+  if (!b->graph_valid) return fail(b, TRAJ_ESTATE, "no solve launch has been captured");
+  if (resolved) {
+    resolved->warps_per_block = b->used.warps_per_block;
+    resolved->blocks_per_sm = b->used.blocks_per_sm;
+    resolved->warps_per_trajectory = b->used.team;
+    resolved->occupancy = b->used.occupancy;
+  }
+  if (grid) *grid = b->used.grid;
   return TRAJ_OK;
 }
 
@@ -662,24 +787,30 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
   if (iters < 1) return fail(b, TRAJ_EINVAL, "iters must be >= 1");
   static const int cand_w[] = {0, 1, 2, 4, 8}; // 0: the form's default shape
   static const int cand_b[] = {0, 1, 2, 4};
-  LaunchShape best{4, 0, 0, 1};
+  const bool tc = b->cfg.precision != TRAJ_PREC_FP32;
+  std::vector<LaunchShape> cands;
+  for (int team = 1; team <= (tc ? 1 : 4); team *= 2)
+    for (int w : cand_w)
+      for (int bps : cand_b)
+        if (w % team == 0) cands.push_back(LaunchShape{w, bps, 0, team, 0});
+  if (b->max_np_used <= 160) // the register-capped build, one warp per trajectory
+    for (int w : {0, 2, 4, 6})
+      if (w <= (tc ? 6 : 4)) cands.push_back(LaunchShape{w, 0, 0, 1, 1});
+  LaunchShape best{4, 0, 0, 1, 0};
   float best_t = 1e30f;
-  for (int team = 1; team <= (b->cfg.precision == TRAJ_PREC_MIXED ? 1 : 4); team *= 2)
-  for (int w : cand_w)
-    for (int bps : cand_b) {
-      if (w % team != 0) continue;
-      b->shape = LaunchShape{w, bps, 0, team};
-      invalidate_graph(b);
-      float tot = 0.f;
-      bool ok = true;
-      for (int r = 0; r < 3 && ok; ++r) { // first run captures the graph, then two timed replays
-        traj_solve_stats st{};
-        traj_status rc = traj_solve(b, iters, -1.0f, 0.0, &st);
-        if (rc != TRAJ_OK && rc != TRAJ_NOT_CONVERGED) ok = false;
-        else if (r > 0) tot += st.gpu_ms;
-      }
-      if (ok && tot < best_t) { best_t = tot; best = b->shape; }
+  for (const LaunchShape &c : cands) {
+    b->shape = c;
+    invalidate_graph(b);
+    float tot = 0.f;
+    bool ok = true;
+    for (int r = 0; r < 3 && ok; ++r) { // first run captures the graph, then two timed replays
+      traj_solve_stats st{};
+      traj_status rc = traj_solve(b, iters, -1.0f, 0.0, &st);
+      if (rc != TRAJ_OK && rc != TRAJ_NOT_CONVERGED) ok = false;
+      else if (r > 0) tot += st.gpu_ms;
     }
+    if (ok && tot < best_t) { best_t = tot; best = b->shape; }
+  }
   b->shape = best;
   invalidate_graph(b);
   b->have_result = false;
@@ -687,6 +818,7 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
     chosen->warps_per_block = best.warps_per_block;
     chosen->blocks_per_sm = best.blocks_per_sm;
     chosen->warps_per_trajectory = best.team;
+    chosen->occupancy = best.occupancy;
   }
   if (best_ms) *best_ms = best_t / 2.f;
   if (best_t >= 1e30f) return fail(b, TRAJ_ECUDA, "no launch shape ran");
@@ -789,6 +921,40 @@ traj_status traj_measure_fp32_peak(void *cuda_stream, int reps, double *flops_pe
   cudaEventDestroy(e1);
   cudaFree(out);
   *flops_per_s = best;
+  return rc;
+}
+
+traj_status traj_measure_mufu_peak(void *cuda_stream, int reps, double *rsqrt_per_s) {
+  if (!rsqrt_per_s || reps < 1) return TRAJ_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TRAJ_ECUDA;
+  }
+  float *out = nullptr;
+  cudaEvent_t e0, e1;
+  if (cudaMalloc(&out, sizeof(float) * n_sm * 8) != cudaSuccess) return TRAJ_ENOMEM;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = n_sm * 8, iters = 1024;
+  const double ops = 8.0 * 16 * (double)iters * 256.0 * blocks; // rsqrtf per launch
+  double best = 0.0;
+  traj_status rc = TRAJ_OK;
+  for (int r = 0; r <= reps && rc == TRAJ_OK; ++r) {
+    cudaEventRecord(e0, s);
+    if (tb::launch_rsqrt_peak(out, blocks, iters, s) != cudaSuccess) rc = TRAJ_ECUDA;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = TRAJ_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0 && ms > 0) best = std::max(best, ops / (ms * 1e-3));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *rsqrt_per_s = best;
   return rc;
 }
 

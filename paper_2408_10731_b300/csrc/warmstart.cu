@@ -11,6 +11,7 @@
 //   averaged over the labels of the batch.
 #include "trajbatch.h"
 #include "internal.cuh"
+#include "gelu.cuh"
 #include "nvtx_range.h"
 
 #include <cuda_bf16.h>
@@ -219,6 +220,62 @@ __global__ void k_proposals(const float *Y, const float *line, int R, float *out
   out[e] = Y[e] + line[(size_t)s * D22 + (q % D22)];
 }
 
+// ---- FP32-operand debug path ------------------------------------------------------
+// C[m][n] = sum_k A(m, k) B(n, k) with every operand FP32 on the CUDA cores, the
+// operands addressed through strides (A(m, k) = A[m sAm + k sAk], likewise B) so
+// that the backward pass needs no transposed copies. Epilogues as the tensor-core
+// GEMM's, in FP32: 0 store; 1 Z = C + bias and H = GELU(Z); 2 C + bias; 3
+// C * GELU'(aux). 32 x 32 output tiles, K staged through shared memory in steps of 32.
+struct F32Gemm {
+  int M, N, K;
+  const float *A; long long sAm, sAk;
+  const float *B; long long sBn, sBk;
+  float *C; int ldc;
+  int epi;
+  const float *bias, *aux; // aux [M][ldc]
+  float *H;                // epilogue 1: GELU(Z) [M][ldc]
+};
+
+__global__ void k_gemm_f32(F32Gemm g) {
+  __shared__ float As[32][33], Bs[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y; // 32 x 8 threads, 4 rows each
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < g.K; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int m = m0 + r, n = n0 + r, k = k0 + tx;
+      As[r][tx] = (m < g.M && k < g.K) ? g.A[m * g.sAm + k * g.sAk] : 0.f;
+      Bs[r][tx] = (n < g.N && k < g.K) ? g.B[n * g.sBn + k * g.sBk] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float b = Bs[tx][k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = fmaf(As[ty + 8 * i][k], b, acc[i]);
+    }
+    __syncthreads();
+  }
+  const int n = n0 + tx;
+  if (n >= g.N) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 8 * i;
+    if (m >= g.M) continue;
+    const size_t o = (size_t)m * g.ldc + n;
+    float v = acc[i];
+    if (g.epi == 1 || g.epi == 2) v += g.bias[n];
+    if (g.epi == 3) v *= gelu_tanh_grad(g.aux[o]);
+    g.C[o] = v;
+    if (g.epi == 1) g.H[o] = gelu_tanh(v);
+  }
+}
+
+__global__ void k_bf16_to_f32(const __nv_bfloat16 *in, float *out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __bfloat162float(in[i]);
+}
+
 // padded <-> public parameter layouts (W1 rows 400 <-> 388)
 __global__ void k_params_pad(const float *u, float *p, int to_padded) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,6 +302,9 @@ struct traj_warmstart {
   __nv_bfloat16 *W1b, *W2b, *W3b, *W4b, *W2t, *W3t, *W4t;
   __nv_bfloat16 *Xt, *H1, *H2, *H3, *H1t, *H2t, *H3t, *dYb, *dYt, *dZ1, *dZ2, *dZ3, *dZ1t, *dZ2t, *dZ3t;
   float *Z1, *Z2, *Z3, *Y, *dYf, *total, *loss_tmp, *stage;
+  // FP32-operand debug path (allocated on its first use): features, activations and
+  // their gradients in FP32
+  float *f_X = nullptr, *f_H1, *f_H2, *f_H3, *f_dZ1, *f_dZ2, *f_dZ3;
   double *d_start = nullptr, *d_goal = nullptr;
   int *d_offsets = nullptr, *err = nullptr;
   int feat_cap = 0;
@@ -328,6 +388,59 @@ cudaError_t backward(traj_warmstart *w, int R, const void *X, const float *targe
       (e = transpose(reinterpret_cast<const __nv_bfloat16 *>(X), w->Xt, R, IN_PAD, s))) return e;
   if ((e = launch_gemm_bf16(0, w->dZ1t, w->Xt, HID, IN_PAD, R, g + P_W1, nullptr, IN_PAD, nullptr, nullptr, w->err, s))) return e;
   k_colsum<__nv_bfloat16><<<(HID + 127) / 128, 128, 0, s>>>(w->dZ1, R, HID, g + P_B1);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_f32(cudaStream_t s, int M, int N, int K, const float *A, long long sAm,
+                     long long sAk, const float *B, long long sBn, long long sBk, float *C, int ldc,
+                     int epi, const float *bias = nullptr, const float *aux = nullptr,
+                     float *H = nullptr) {
+  F32Gemm g{M, N, K, A, sAm, sAk, B, sBn, sBk, C, ldc, epi, bias, aux, H};
+  dim3 grid((N + 31) / 32, (M + 31) / 32), block(32, 8);
+  k_gemm_f32<<<grid, block, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// The loss and parameter gradients of one batch with every GEMM operand in FP32 (the
+// debug instantiation of backward(): same layers, loss and order, FP32 throughout).
+cudaError_t backward_f32(traj_warmstart *w, int R, const void *X, const float *targets,
+                         const int *n_labels, float *loss) {
+  cudaStream_t s = w->stream;
+  cudaError_t e;
+  const float *W = w->W;
+  float *g = w->g;
+  k_bf16_to_f32<<<(R * IN_PAD + 255) / 256, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(X),
+                                                         w->f_X, R * IN_PAD);
+  // forward: Z = H W^T + b, H' = GELU(Z); Y = H3 W4^T + b4
+  if ((e = gemm_f32(s, R, HID, IN_PAD, w->f_X, IN_PAD, 1, W + P_W1, IN_PAD, 1, w->Z1, HID, 1, W + P_B1,
+                    nullptr, w->f_H1))) return e;
+  if ((e = gemm_f32(s, R, HID, HID, w->f_H1, HID, 1, W + P_W2, HID, 1, w->Z2, HID, 1, W + P_B2,
+                    nullptr, w->f_H2))) return e;
+  if ((e = gemm_f32(s, R, HID, HID, w->f_H2, HID, 1, W + P_W3, HID, 1, w->Z3, HID, 1, W + P_B3,
+                    nullptr, w->f_H3))) return e;
+  if ((e = gemm_f32(s, R, OUT, HID, w->f_H3, HID, 1, W + P_W4, HID, 1, w->Y, OUT, 2, W + P_B4))) return e;
+  if ((e = cudaMemsetAsync(loss, 0, sizeof(float), s))) return e;
+  k_count_labels<<<1, 1024, 0, s>>>(n_labels, R, w->total);
+  k_loss_wta<<<(R + 127) / 128, 128, 0, s>>>(w->Y, targets, n_labels, R, w->total, w->dYf, w->dYb, loss);
+  if ((e = cudaGetLastError())) return e;
+  // layer 4: dW4 = dY^T H3, db4 = colsum dY, dZ3 = (dY W4) GELU'(Z3)
+  if ((e = gemm_f32(s, OUT, HID, R, w->dYf, 1, OUT, w->f_H3, 1, HID, g + P_W4, HID, 0))) return e;
+  k_colsum<float><<<(OUT + 127) / 128, 128, 0, s>>>(w->dYf, R, OUT, g + P_B4);
+  if ((e = gemm_f32(s, R, HID, OUT, w->dYf, OUT, 1, W + P_W4, 1, HID, w->f_dZ3, HID, 3, nullptr,
+                    w->Z3))) return e;
+  // layer 3
+  if ((e = gemm_f32(s, HID, HID, R, w->f_dZ3, 1, HID, w->f_H2, 1, HID, g + P_W3, HID, 0))) return e;
+  k_colsum<float><<<(HID + 127) / 128, 128, 0, s>>>(w->f_dZ3, R, HID, g + P_B3);
+  if ((e = gemm_f32(s, R, HID, HID, w->f_dZ3, HID, 1, W + P_W3, 1, HID, w->f_dZ2, HID, 3, nullptr,
+                    w->Z2))) return e;
+  // layer 2
+  if ((e = gemm_f32(s, HID, HID, R, w->f_dZ2, 1, HID, w->f_H1, 1, HID, g + P_W2, HID, 0))) return e;
+  k_colsum<float><<<(HID + 127) / 128, 128, 0, s>>>(w->f_dZ2, R, HID, g + P_B2);
+  if ((e = gemm_f32(s, R, HID, HID, w->f_dZ2, HID, 1, W + P_W2, 1, HID, w->f_dZ1, HID, 3, nullptr,
+                    w->Z1))) return e;
+  // layer 1 (the padding columns of W1 get the features' zero columns: zero gradient)
+  if ((e = gemm_f32(s, HID, IN_PAD, R, w->f_dZ1, 1, HID, w->f_X, 1, IN_PAD, g + P_W1, IN_PAD, 0))) return e;
+  k_colsum<float><<<(HID + 127) / 128, 128, 0, s>>>(w->f_dZ1, R, HID, g + P_B1);
   return cudaGetLastError();
 }
 
@@ -509,6 +622,31 @@ traj_status traj_warmstart_gradients(traj_warmstart *w, int rows, const void *fe
   traj_status rc = check_rows(w, rows);
   if (rc != TRAJ_OK) return rc;
   WS_CK(backward(w, rows, features, targets, n_labels, loss));
+  if (grads) {
+    k_params_pad<<<(P_TOTAL + 255) / 256, 256, 0, w->stream>>>(w->g, w->stage, 0);
+    WS_CK(cudaGetLastError());
+    WS_CK(cudaMemcpyAsync(grads, w->stage, sizeof(float) * U_TOTAL, cudaMemcpyDefault, w->stream));
+  }
+  return TRAJ_OK;
+}
+
+traj_status traj_warmstart_gradients_fp32(traj_warmstart *w, int rows, const void *features,
+                                          const float *targets, const int *n_labels, float *grads,
+                                          float *loss) {
+  if (!w || !features || !targets || !n_labels || !loss) return TRAJ_EINVAL;
+  traj_status rc = check_rows(w, rows);
+  if (rc != TRAJ_OK) return rc;
+  if (!w->f_X) {
+    const size_t R = w->max_rows;
+    if (!ws_alloc(w, &w->f_X, R * IN_PAD) || !ws_alloc(w, &w->f_H1, R * HID) ||
+        !ws_alloc(w, &w->f_H2, R * HID) || !ws_alloc(w, &w->f_H3, R * HID) ||
+        !ws_alloc(w, &w->f_dZ1, R * HID) || !ws_alloc(w, &w->f_dZ2, R * HID) ||
+        !ws_alloc(w, &w->f_dZ3, R * HID)) {
+      w->f_X = nullptr; // the buffers allocated so far are released by destroy
+      return ws_fail(TRAJ_ENOMEM, "cudaMalloc failed (FP32 debug buffers)");
+    }
+  }
+  WS_CK(backward_f32(w, rows, features, targets, n_labels, loss));
   if (grads) {
     k_params_pad<<<(P_TOTAL + 255) / 256, 256, 0, w->stream>>>(w->g, w->stage, 0);
     WS_CK(cudaGetLastError());

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "TRAJ_OK", 1: "TRAJ_NOT_CONVERGED", -1: "TRAJ_EINVAL", -2: "T
                 -3: "TRAJ_ECUDA", -4: "TRAJ_ESHAPE", -5: "TRAJ_ETIMEOUT", -6: "TRAJ_ENAN",
                 -7: "TRAJ_ESTATE"}
 TRAJ_CONVERGED, TRAJ_CAP, TRAJ_NAN, TRAJ_TIMEOUT = 0, 1, 2, 3
-PRECISION = {"fp32": 0, "mixed": 1}
+PRECISION = {"fp32": 0, "mixed": 1, "mixed_split": 2}
 COST_MODE = {"smooth_track": 0, "project": 1}
 
 
@@ -46,7 +46,7 @@ class SolveStats(ctypes.Structure):
 
 class LaunchShape(ctypes.Structure):
     _fields_ = [("warps_per_block", _c_int), ("blocks_per_sm", _c_int),
-                ("warps_per_trajectory", _c_int)]
+                ("warps_per_trajectory", _c_int), ("occupancy", _c_int)]
 
 
 class SamplerConfig(ctypes.Structure):
@@ -96,12 +96,16 @@ def load_library():
     lib.traj_set_state.argtypes = [_vp, _vp, _vp, _vp]
     lib.traj_set_rho_schedule.argtypes = [_vp, _c_int, _c_double, _c_int]
     lib.traj_set_workspace.argtypes = [_vp, _vp, _vp]
+    lib.traj_shift_horizon.argtypes = [_vp, _c_double, _vp]
+    lib.traj_homotopy_signature.argtypes = [_vp, _vp]
     lib.traj_status_string.argtypes = [_c_int]
     lib.traj_status_string.restype = ctypes.c_char_p
     lib.traj_last_error.argtypes = [_vp]
     lib.traj_last_error.restype = ctypes.c_char_p
     lib.traj_measure_fp32_peak.argtypes = [_vp, _c_int, ctypes.POINTER(_c_double)]
+    lib.traj_measure_mufu_peak.argtypes = [_vp, _c_int, ctypes.POINTER(_c_double)]
     lib.traj_set_launch_shape.argtypes = [_vp, ctypes.POINTER(LaunchShape)]
+    lib.traj_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchShape), ctypes.POINTER(_c_int)]
     lib.traj_autotune.argtypes = [_vp, _c_int, ctypes.POINTER(LaunchShape),
                                   ctypes.POINTER(_c_float)]
     lib.traj_sampler_step.argtypes = [_vp, ctypes.POINTER(SamplerConfig), _c_int, _vp, _vp, _vp,
@@ -114,8 +118,8 @@ def load_library():
                                        _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
                  "traj_set_obstacles", "traj_set_initial", "traj_solve", "traj_get_solve_stats",
-                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_set_rho_schedule", "traj_set_workspace", "traj_measure_fp32_peak",
-                 "traj_solve_noalloc", "traj_set_launch_shape", "traj_autotune",
+                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_set_rho_schedule", "traj_set_workspace", "traj_shift_horizon", "traj_homotopy_signature", "traj_measure_fp32_peak", "traj_measure_mufu_peak",
+                 "traj_solve_noalloc", "traj_set_launch_shape", "traj_get_launch_info", "traj_autotune",
                  "traj_sampler_step", "traj_sampler_step_multi", "traj_gemm_bf16"):
         getattr(lib, name).restype = _c_int
     _LIB = lib
@@ -158,6 +162,17 @@ def measure_fp32_peak(reps: int = 5, stream=None) -> float:
                                     ctypes.byref(out))
     if rc != 0:
         raise TrajBatchError(rc, "FFMA microbenchmark failed")
+    return out.value
+
+
+def measure_mufu_peak(reps: int = 5, stream=None) -> float:
+    """rsqrtf/s of the MUFU microbenchmark (traj_measure_mufu_peak)."""
+    lib = load_library()
+    out = ctypes.c_double(0.0)
+    rc = lib.traj_measure_mufu_peak(stream if stream is not None else _default_stream(), reps,
+                                    ctypes.byref(out))
+    if rc != 0:
+        raise TrajBatchError(rc, "MUFU microbenchmark failed")
     return out.value
 
 
@@ -249,10 +264,20 @@ class TrajBatch:
         self._check(self._lib.traj_get_trajectories(self._h, c, r, i, s))
         return dict(xi=coeffs, residual=residual, iters=iters, status=status)
 
-    def set_launch_shape(self, warps_per_block, blocks_per_sm=0, warps_per_trajectory=1):
+    def set_launch_shape(self, warps_per_block, blocks_per_sm=0, warps_per_trajectory=1,
+                         occupancy=0):
         self._check(self._lib.traj_set_launch_shape(
             self._h, ctypes.byref(LaunchShape(int(warps_per_block), int(blocks_per_sm),
-                                              int(warps_per_trajectory)))))
+                                              int(warps_per_trajectory), int(occupancy)))))
+
+    def launch_info(self):
+        """The shape the last solve launch resolved to (warps per block, resident blocks
+        per SM, warps per trajectory) and its grid."""
+        shape, grid = LaunchShape(), _c_int(0)
+        self._check(self._lib.traj_get_launch_info(self._h, ctypes.byref(shape), ctypes.byref(grid)))
+        return dict(warps_per_block=shape.warps_per_block, blocks_per_sm=shape.blocks_per_sm,
+                    warps_per_trajectory=shape.warps_per_trajectory, occupancy=shape.occupancy,
+                    grid=grid.value)
 
     def autotune(self, iters=20):
         """Time the candidate launch shapes on this batch; keep and return the fastest."""
@@ -260,7 +285,8 @@ class TrajBatch:
         self._check(self._lib.traj_autotune(self._h, int(iters), ctypes.byref(shape),
                                             ctypes.byref(ms)))
         return dict(warps_per_block=shape.warps_per_block, blocks_per_sm=shape.blocks_per_sm,
-                    warps_per_trajectory=shape.warps_per_trajectory, ms=ms.value)
+                    warps_per_trajectory=shape.warps_per_trajectory, occupancy=shape.occupancy,
+                    ms=ms.value)
 
     def sampler_step(self, cfg: dict, iteration, mu, sigma, best, z=None, trace=None,
                      n_dist=None):
@@ -307,6 +333,20 @@ class TrajBatch:
         `every`-th unconverged iteration (levels = 1: the fixed penalty)."""
         self._check(self._lib.traj_set_rho_schedule(self._h, int(levels), float(growth), int(every)))
 
+    def homotopy_signature(self):
+        """uint64 [n_traj]: bit j set when the trajectory passes obstacle j (j < 64) on the
+        left of their relative motion at the closest approach (2D)."""
+        sig = np.zeros(self.n_traj, np.uint64)
+        self._check(self._lib.traj_homotopy_signature(self._h, sig.ctypes.data))
+        return sig
+
+    def shift_horizon(self, delta, executed=None):
+        """Receding-horizon step: the robot followed executed[p] (None: per problem the
+        trajectory with the smallest worst residual) for delta seconds; the next solve
+        starts from the shifted iterate and the carried multipliers."""
+        ep, ke = (None, None) if executed is None else _ptr(np.asarray(executed), np.int32)
+        self._check(self._lib.traj_shift_horizon(self._h, float(delta), ep))
+
     def set_state(self, xi, lam, u):
         """Resume the next solves from an exported (xi, lambda, u) state."""
         xp, kx = _ptr(xi, np.float32)
@@ -332,7 +372,22 @@ def solve_noalloc(dim, vmax, amax, rho, n_steps, duration, start, goal, obs_offs
                   semi_axes, velocities, traj_problem, coeffs0, max_iters, tol, coeffs, residual,
                   iters, status, w_smooth=1.0, w_track=1.0, cost_mode="smooth_track", stream=None):
     """traj_solve_noalloc: the allocation-free solve. Obstacles, traj_problem, coeffs0 and
-    the four outputs must be CUDA tensors; the problem arrays are host arrays."""
+    the four outputs must be CUDA tensors of the sizes the problem arrays imply (the
+    kernels read and write them directly, so a host array or a short tensor would be an
+    out-of-bounds device access, not an error); the problem arrays are host arrays.
+    Raises ValueError before any call into the library when one is not."""
+    n_obs = int(np.asarray(obs_offsets)[-1])
+    n_traj = int(traj_problem.shape[0]) if hasattr(traj_problem, "shape") else len(traj_problem)
+    want = (("centers", centers, n_obs * dim), ("semi_axes", semi_axes, n_obs * dim),
+            ("velocities", velocities, n_obs * dim), ("traj_problem", traj_problem, n_traj),
+            ("coeffs0", coeffs0, n_traj * dim * 11), ("coeffs", coeffs, n_traj * dim * 11),
+            ("residual", residual, n_traj * 3), ("iters", iters, n_traj),
+            ("status", status, n_traj))
+    for name, x, n in want:
+        if not (hasattr(x, "is_cuda") and x.is_cuda):
+            raise ValueError(f"solve_noalloc: {name} must be a CUDA tensor")
+        if x.numel() < n:
+            raise ValueError(f"solve_noalloc: {name} holds {x.numel()} values, needs {n}")
     lib = load_library()
     cfg = TrajConfig(dim, 10, 0, 0, 0, 0, vmax, amax, rho, w_smooth, w_track, 0,
                      COST_MODE[cost_mode], stream if stream is not None else _default_stream())

@@ -40,6 +40,7 @@ def _lib():
         lib.traj_warmstart_forward.argtypes = [_vp, _ci, _vp, _vp, _vp]
         lib.traj_warmstart_propose.argtypes = [_vp, _ci, _ci] + [_vp] * 9
         lib.traj_warmstart_gradients.argtypes = [_vp, _ci, _vp, _vp, _vp, _vp, _vp]
+        lib.traj_warmstart_gradients_fp32.argtypes = [_vp, _ci, _vp, _vp, _vp, _vp, _vp]
         lib.traj_warmstart_train_step.argtypes = [_vp, _ci, _vp, _vp, _vp, _cf, _cf, _vp]
         lib.traj_warmstart_sync.argtypes = [_vp]
         lib.traj_warmstart_get_state.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(_ci)]
@@ -48,7 +49,8 @@ def _lib():
         for n in ("traj_warmstart_create", "traj_warmstart_destroy", "traj_warmstart_set_params",
                   "traj_warmstart_get_params", "traj_warmstart_features", "traj_warmstart_forward",
                   "traj_warmstart_propose",
-                  "traj_warmstart_gradients", "traj_warmstart_train_step", "traj_warmstart_sync",
+                  "traj_warmstart_gradients", "traj_warmstart_gradients_fp32",
+                  "traj_warmstart_train_step", "traj_warmstart_sync",
                   "traj_warmstart_get_state", "traj_warmstart_set_state", "traj_get_accel_cost"):
             getattr(lib, n).restype = _ci
         _READY = True
@@ -252,6 +254,17 @@ class WarmStart:
         _check(_lib().traj_warmstart_gradients(self._h, X.shape[0], X.data_ptr(),
                                                targets.data_ptr(), n_labels.data_ptr(),
                                                g.ctypes.data, self.loss.data_ptr()), "gradients")
+        self.sync()
+        return g, float(self.loss.item())
+
+    def gradients_fp32(self, X, targets, n_labels):
+        """Loss and gradients of the FP32-operand debug instantiation (CUDA-core FP32
+        GEMMs, FP32 activations)."""
+        g = np.zeros(num_params(), np.float32)
+        _check(_lib().traj_warmstart_gradients_fp32(self._h, X.shape[0], X.data_ptr(),
+                                                    targets.data_ptr(), n_labels.data_ptr(),
+                                                    g.ctypes.data, self.loss.data_ptr()),
+               "gradients_fp32")
         self.sync()
         return g, float(self.loss.item())
 

@@ -58,3 +58,31 @@ def test_no_cpu_fallback_without_device():
     with pytest.raises(tb.TrajBatchError) as e:
         tb.TrajBatch(2, 1, 4, 4, 50, 1.5, 2.0)
     assert e.value.code == -3  # TRAJ_ECUDA: no CPU path exists
+
+
+def test_solve_noalloc_refuses_host_arrays_and_short_tensors_before_the_library():
+    """The allocation-free solve hands its array arguments to the kernels as they
+    are; the binding refuses a numpy array or a CPU tensor (a host pointer the
+    kernels would dereference) with ValueError, before any call into the library."""
+    import numpy as np
+    import torch
+    from paper_2408_10731_b300 import scenes
+    b = scenes.config2(0, n_scenes=1, inits=2)
+    n_obs = int(b.offsets[-1])
+    args = dict(centers=torch.zeros(n_obs, 2), semi_axes=torch.zeros(n_obs, 2),
+                velocities=torch.zeros(n_obs, 2), traj_problem=torch.zeros(2, dtype=torch.int32),
+                coeffs0=torch.zeros(2, 2, 11), coeffs=torch.zeros(2, 2, 11),
+                residual=torch.zeros(2, 3), iters=torch.zeros(2, dtype=torch.int32),
+                status=torch.zeros(2, dtype=torch.int8))
+
+    def call(**over):
+        a = dict(args, **over)
+        tb.solve_noalloc(2, 1.5, 2.0, 1.0, b.n_steps, b.duration, b.start, b.goal, b.offsets,
+                         a["centers"], a["semi_axes"], a["velocities"], a["traj_problem"],
+                         a["coeffs0"], 10, 1e-3, a["coeffs"], a["residual"], a["iters"],
+                         a["status"])
+
+    with pytest.raises(ValueError, match="centers must be a CUDA tensor"):
+        call(centers=np.zeros((n_obs, 2), np.float32))
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        call()  # CPU tensors are host memory too

@@ -1,0 +1,142 @@
+"""GPU parity of the receding-horizon step (traj_shift_horizon, Paper II's MPC use
+of Algorithm 2: each control loop's solve starts from the previous loop's
+multipliers) against the FP64 oracle's step (oracle/mpc.py)."""
+import numpy as np
+import pytest
+
+from oracle import am, mpc
+from paper_2408_10731_b300 import scenes
+from tests.gpu_helpers import POS_TOL, position_error
+
+pytestmark = pytest.mark.gpu
+
+
+def _handle(batch, **kw):
+    from paper_2408_10731_b300 import trajbatch as tb
+    return tb.from_batch(batch, **kw)
+
+
+def test_three_receding_calls_of_ten_iterations_match_the_oracle():
+    """Each control loop is checked against the oracle's step from the GPU's own state
+    before it (coefficients and multipliers as the GPU left them), at the parity bar;
+    the oracle's own chain of three loops is followed beside it, where the FP32
+    rounding of each shifted iterate and start state compounds (bound 5e-5 m)."""
+    b = scenes.config2(5, n_scenes=6, inits=4)
+    executed = np.arange(b.n_problems) * 4 + 1  # the second plan of every scene
+    delta = 0.3
+    h = _handle(b)
+    try:
+        h.solve(30, -1.0)
+        g = h.get_trajectories()
+        o = am.solve(b, 30, tol=-1.0, want_lambda=True)
+        assert position_error(b, g["xi"], o["xi"]).max() <= POS_TOL
+        chain_xi, chain_lam, chain_b = o["xi"], o["lam"], b
+        cur = b
+        for step in range(3):
+            xi_g = g["xi"].astype(np.float64)
+            lam_g = h.get_state()["lam"].astype(np.float64)
+            h.shift_horizon(delta, executed)
+            h.solve(10, -1.0)
+            g = h.get_trajectories()
+            cur, va, o = mpc.solve_after_step(cur, xi_g, lam_g, executed, delta, 10)
+            err = position_error(cur, g["xi"], o["xi"])
+            assert err.max() <= POS_TOL, (step, err.max())
+            assert np.all(g["iters"] == 10)
+            scale = np.abs(o["lam"]).max()
+            assert np.abs(h.get_state()["lam"] - o["lam"]).max() <= 2e-4 * scale, step
+            np.testing.assert_allclose(g["residual"], o["residual"], atol=2e-5, rtol=1e-4)
+            # the new start is where the executed plan was delta seconds in
+            P, Pd, Pdd = am.bernstein(100, 10.0)
+            xg = g["xi"].astype(np.float64)
+            np.testing.assert_allclose(xg @ P[0], cur.start[cur.traj_problem], atol=2e-5)
+            np.testing.assert_allclose(xg @ Pd[0], va[cur.traj_problem, 0], atol=2e-5)
+            chain_b, _, co = mpc.solve_after_step(chain_b, chain_xi, chain_lam, executed, delta, 10)
+            chain_xi, chain_lam = co["xi"], co["lam"]
+            assert position_error(chain_b, g["xi"], chain_xi).max() <= 5e-5, step
+    finally:
+        h.close()
+
+
+def test_default_executed_plan_is_the_smallest_worst_residual():
+    b = scenes.config2(6, n_scenes=5, inits=6)
+    h1, h2 = _handle(b), _handle(b)
+    try:
+        h1.solve(40, 1e-3)
+        h2.solve(40, 1e-3)
+        res = h2.get_trajectories()["residual"]
+        worst = res.max(axis=1).reshape(b.n_problems, 6)
+        executed = np.argmin(worst, axis=1) + 6 * np.arange(b.n_problems)  # ties: lower index
+        h1.shift_horizon(0.2)
+        h2.shift_horizon(0.2, executed)
+        h1.solve(10, -1.0)
+        h2.solve(10, -1.0)
+        a, c = h1.get_trajectories(), h2.get_trajectories()
+        assert np.array_equal(a["xi"], c["xi"]) and np.array_equal(a["residual"], c["residual"])
+    finally:
+        h1.close()
+        h2.close()
+
+
+def test_fresh_start_after_a_shift_and_refused_calls():
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.config2(7, n_scenes=3, inits=2)
+    h = _handle(b)
+    try:
+        with pytest.raises(tb.TrajBatchError) as e:
+            h.shift_horizon(0.1)  # no solve yet
+        assert e.value.code == -7
+        h.solve(15, -1.0)
+        ref = h.get_trajectories()["xi"].copy()
+        for bad in (0.0, -0.1, 10.0, float("nan")):
+            with pytest.raises(tb.TrajBatchError) as e:
+                h.shift_horizon(bad)
+            assert e.value.code == -1
+        with pytest.raises(tb.TrajBatchError) as e:
+            h.shift_horizon(0.1, [0, 1, 2])  # trajectory 1 belongs to problem 0
+        assert e.value.code == -1
+        h.shift_horizon(0.1, [0, 2, 4])
+        h.solve(15, -1.0)
+        moved = h.get_trajectories()["xi"].copy()
+        assert not np.array_equal(moved, ref)
+        # traj_set_initial returns to fresh starts (of the moved problems)
+        h.set_initial(b.traj_problem, b.xi0)
+        h.solve(15, -1.0)
+        again = h.get_trajectories()["xi"]
+        assert not np.array_equal(again, moved)
+    finally:
+        h.close()
+    hp = _handle(b, cost_mode="project")
+    try:
+        hp.solve(5, -1.0)
+        with pytest.raises(tb.TrajBatchError) as e:
+            hp.shift_horizon(0.1)
+        assert e.value.code == -1
+    finally:
+        hp.close()
+
+
+def test_full_size_receding_step_sampled():
+    """The bench's MPC workload (125 scenes x 8 plans, 50 moving ellipses): a converged
+    plan, one shift of 0.1 s and 10 iterations; three scenes recomputed by the oracle
+    from the GPU's own state before the shift."""
+    b = scenes.config2(0, n_scenes=125, inits=8)
+    h = _handle(b)
+    try:
+        h.solve(500, 1e-3)
+        g0 = h.get_trajectories()
+        lam0 = h.get_state()["lam"]
+        worst = g0["residual"].max(axis=1).reshape(125, 8)
+        executed = np.argmin(worst, axis=1) + 8 * np.arange(125)
+        h.shift_horizon(0.1)
+        h.solve(10, -1.0)
+        g = h.get_trajectories()
+        for p in (0, 61, 124):
+            sub = b.select_problems([p])
+            idx = np.nonzero(b.traj_problem == p)[0]
+            moved, va, o = mpc.solve_after_step(sub, g0["xi"][idx].astype(np.float64),
+                                                lam0[idx].astype(np.float64),
+                                                [int(executed[p] - idx[0])], 0.1, 10)
+            err = position_error(moved, g["xi"][idx], o["xi"])
+            assert err.max() <= POS_TOL, (p, err.max())
+    finally:
+        h.close()

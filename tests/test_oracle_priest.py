@@ -71,6 +71,38 @@ def test_refit_uniform_weights_is_the_elite_sample_mean_and_covariance():
     np.testing.assert_array_equal(best, X[elite[0]])
 
 
+def test_refit_weights_favour_the_cheaper_elite_by_exp_of_the_cost_gap():
+    """Two elites whose augmented costs differ by gamma ln 3 carry weights 1 and 1/3
+    (the cheaper one heavier: Algorithm 3's update concentrates on good samples). With
+    sigma_lr = 1 the new mean is (3 x1 + x2) / 4 and, with d = x1 - x2, the new
+    covariance about it is (3 (d/4)(d/4)^T + (3d/4)(3d/4)^T) / 4 = 3/16 d d^T. The
+    printed exponent's sign would give (x1 + 3 x2) / 4 instead; this case tells the
+    two apart, where uniform weights cannot."""
+    rng = np.random.default_rng(5)
+    for gamma in (1.0, 0.37, 12.0):
+        X = rng.normal(size=(6, 5))
+        x1, x2 = X[4], X[1]
+        caug = rng.uniform(50, 60, 6)
+        caug[4] = 3.25
+        caug[1] = 3.25 + gamma * np.log(3.0)
+        elite = np.array([4, 1])  # ascending c_aug, as select() returns them
+        mu, sig, best, c = priest.refit(X, caug, elite, np.full(5, 9.0), 7 * np.eye(5),
+                                        gamma=gamma, sig=1.0)
+        d = x1 - x2
+        np.testing.assert_allclose(mu, (3 * x1 + x2) / 4, atol=1e-12)
+        np.testing.assert_allclose(sig, 3.0 / 16.0 * np.outer(d, d), atol=1e-12)
+        np.testing.assert_array_equal(best, x1)
+        assert c == 3.25
+        # half a step: the old moments enter with weight 1/2, the covariance is about
+        # the blended mean m, so each elite's deviation is x - m
+        mu_h, sig_h, _, _ = priest.refit(X, caug, elite, np.full(5, 9.0), 7 * np.eye(5),
+                                         gamma=gamma, sig=0.5)
+        m = 0.5 * 9.0 + 0.5 * (3 * x1 + x2) / 4
+        np.testing.assert_allclose(mu_h, m, atol=1e-12)
+        cov = (3 * np.outer(x1 - m, x1 - m) + np.outer(x2 - m, x2 - m)) / 4
+        np.testing.assert_allclose(sig_h, 3.5 * np.eye(5) + 0.5 * cov, atol=1e-12)
+
+
 def _fit(n_p, T, pos):
     """Degree-10 Bernstein coefficients [dim][11] of a polynomial sampled at the grid."""
     from oracle import am

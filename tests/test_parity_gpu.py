@@ -379,3 +379,28 @@ def test_workspace_bounds_parity():
     finally:
         h.close()
     assert position_error(b3, g3["xi"], o3["xi"]).max() <= POS_TOL
+
+
+@pytest.mark.parametrize("prec,batch", [("fp32", "uneven"), ("mixed", "uneven"),
+                                        ("mixed_split", "config2")])
+def test_register_capped_build_is_bitwise_the_default_one(prec, batch):
+    """The occupancy build (registers capped so that more warps stay resident) runs the
+    same arithmetic as the default build: identical results, bit for bit."""
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = reduced_config4(12, seed=5, inits=2) if batch == "uneven" else \
+        scenes.config2(8, n_scenes=6, inits=4)
+    h = tb.from_batch(b, precision=prec)
+    try:
+        out = {}
+        for occ in (0, 1):
+            h.set_launch_shape(4, 0, 1, occ)
+            h.solve(40, tol=1e-3)
+            out[occ] = h.get_trajectories()
+            info = h.launch_info()
+            assert info["occupancy"] == occ and info["warps_per_block"] == 4
+        for k in ("xi", "residual", "iters", "status"):
+            np.testing.assert_array_equal(out[0][k], out[1][k])
+        with pytest.raises(tb.TrajBatchError):
+            h.set_launch_shape(8, 0, 1, 1)  # more warps per block than the capped build takes
+    finally:
+        h.close()

@@ -90,6 +90,50 @@ def test_sampler_steps_match_oracle_stagewise():
         h.close()
 
 
+def test_refit_weights_follow_the_cost_gap_closed_form():
+    """Two elites whose augmented costs differ by gamma ln 3 weigh 1 and 1/3 (the
+    cheaper one heavier), so with sigma_lr = 1 the device refit must give the mean
+    (3 x1 + x2) / 4 and the covariance 3/16 d d^T, d = x1 - x2 (Algorithm 3's mean and
+    covariance update). The first step reads the GPU's two elites and their costs;
+    gamma is then set to their gap / ln 3 and the same step (same draws, so the same
+    projected samples and costs) is repeated."""
+    import torch
+    B = 64
+    c3, b, h = _handle(B, seed=3)
+    D = 33
+    z = _cuda(scenes.normal_draws(77, (B, D)))
+    cfg = dict(n_inner=10, n_proj=32, n_elite=2, gamma=1.0, sigma_lr=1.0, eps=1e-6, w_res=1.0,
+               seed=0)
+    try:
+        def run(gamma):
+            mu, sigma, best = _cuda(c3["mu0"]), _cuda(c3["sigma0"]), _cuda(np.zeros(D + 1))
+            tr = dict(projected=torch.zeros(B, D, device="cuda"),
+                      cost_aug=torch.zeros(B, device="cuda"),
+                      elite_idx=torch.zeros(2, dtype=torch.int32, device="cuda"))
+            h.sampler_step(dict(cfg, gamma=gamma), 0, mu, sigma, best, z=z, trace=tr)
+            return mu.cpu().numpy().astype(np.float64), sigma.cpu().numpy().astype(np.float64), \
+                {k: v.cpu().numpy() for k, v in tr.items()}
+        _, _, g = run(1.0)
+        e = g["elite_idx"]
+        c1, c2 = float(g["cost_aug"][e[0]]), float(g["cost_aug"][e[1]])
+        assert c2 > c1
+        gamma = (c2 - c1) / math.log(3.0)
+        mu, sigma, g2 = run(gamma)
+        np.testing.assert_array_equal(g2["elite_idx"], e)
+        np.testing.assert_array_equal(g2["cost_aug"], g["cost_aug"])
+        x1 = g2["projected"][e[0]].astype(np.float64)
+        x2 = g2["projected"][e[1]].astype(np.float64)
+        d = x1 - x2
+        scale = np.abs(x1).max()
+        np.testing.assert_allclose(mu, (3 * x1 + x2) / 4, atol=2e-6 * scale)
+        np.testing.assert_allclose(sigma, 3.0 / 16.0 * np.outer(d, d),
+                                   atol=2e-5 * max(1.0, np.abs(d).max() ** 2))
+        # the opposite sign of the exponent would put the mean at (x1 + 3 x2) / 4
+        assert np.abs(mu - (x1 + 3 * x2) / 4).max() > 100 * 2e-6 * scale
+    finally:
+        h.close()
+
+
 def test_full_size_sampler_run_invariants():
     """The 3D workload at full size: 4096 samples, 10 outer x 20 inner iterations,
     on-device Philox draws."""

@@ -91,6 +91,32 @@ def test_gradients_and_adamw_match_oracle():
     ws.close()
 
 
+def test_fp32_operand_gradients_match_oracle_to_1e4():
+    """The debug instantiation with FP32 operands (CUDA-core GEMMs, FP32 activations):
+    loss and every parameter tensor's gradient within 1e-4 relative of the FP64
+    oracle, tight enough that a dropped term on part of a tensor (a bias gradient
+    row, a GELU' factor) shows, where the BF16 check's 2e-2 could hide it."""
+    torch, warmstart, b, ws, params, X, line = _setup()
+    rng = np.random.default_rng(2)
+    P = b.n_problems
+    targets = rng.normal(0, 0.5, (P, 8, 22)).astype(np.float32)
+    n_labels = rng.integers(0, 9, P).astype(np.int32)
+    g, loss = ws.gradients_fp32(X, torch.as_tensor(targets, device="cuda"),
+                                torch.as_tensor(n_labels, device="cuda"))
+    Xo = X.float().cpu().numpy().astype(np.float64)[:, :mlp.IN]
+    lo, go = mlp.backward(params, Xo, targets.astype(np.float64), n_labels)
+    assert abs(loss - lo) <= 1e-5 * abs(lo), (loss, lo)
+    gd, od = mlp.unpack(g.astype(np.float64)), mlp.unpack(go)
+    for name, _ in mlp.SHAPES:
+        assert _rel(gd[name], od[name]) <= 1e-4, (name, _rel(gd[name], od[name]))
+        # per row as well: a wrong row of a matrix (one unit's gradient) cannot hide
+        rows = np.atleast_2d(gd[name])
+        orow = np.atleast_2d(od[name])
+        scale = np.abs(orow).max()
+        assert np.abs(rows - orow).max() <= 1e-4 * scale, (name, np.abs(rows - orow).max() / scale)
+    ws.close()
+
+
 def test_training_checkpoint_resumes_bitwise(tmp_path):
     """Train 3 AdamW steps, checkpoint (weights, moments, step) to a file, train 4
     more; a fresh handle that loads the file and trains the same 4 steps ends with

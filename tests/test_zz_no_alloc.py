@@ -50,15 +50,65 @@ def test_noalloc_matches_handle_solve_on_two_calls_in_a_row():
         np.testing.assert_array_equal(got["status"], ref["status"])
 
 
-def test_noalloc_rejects_sizes_beyond_its_limits():
+def _args(batch, n_traj):
     import torch
+    dev = torch.device("cuda", 0)
+    n_obs, D = int(batch.offsets[-1]), batch.dim
+    t = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    return dict(centers=t(batch.centers, torch.float32), semi_axes=t(batch.semi_axes, torch.float32),
+                velocities=t(batch.velocities, torch.float32),
+                traj_problem=torch.zeros(n_traj, dtype=torch.int32, device=dev),
+                coeffs0=torch.zeros(n_traj, D, 11, device=dev),
+                coeffs=torch.zeros(n_traj, D, 11, device=dev),
+                residual=torch.zeros(n_traj, 3, device=dev),
+                iters=torch.zeros(n_traj, dtype=torch.int32, device=dev),
+                status=torch.zeros(n_traj, dtype=torch.int8, device=dev))
+
+
+def _call(batch, a, iters=10, tol=1e-3):
+    from paper_2408_10731_b300 import trajbatch as tb
+    tb.solve_noalloc(batch.dim, batch.vmax, batch.amax, batch.rho, batch.n_steps, batch.duration,
+                     batch.start, batch.goal, batch.offsets, a["centers"], a["semi_axes"],
+                     a["velocities"], a["traj_problem"], a["coeffs0"], iters, tol, a["coeffs"],
+                     a["residual"], a["iters"], a["status"])
+
+
+def test_noalloc_rejects_sizes_beyond_its_limits():
     from paper_2408_10731_b300 import trajbatch as tb
     b = scenes.config2(0, n_scenes=1, inits=2)
-    dev = torch.device("cuda", 0)
-    dummy = torch.zeros(16, device=dev)
-    many = np.zeros(8193, np.int32)
     with pytest.raises(tb.TrajBatchError) as e:
-        tb.solve_noalloc(2, 1.5, 2.0, 1.0, b.n_steps, b.duration, b.start, b.goal, b.offsets,
-                         dummy, dummy, dummy, torch.as_tensor(many, device=dev), dummy, 10, 1e-3,
-                         dummy, dummy, dummy.int(), dummy.to(torch.int8))
+        _call(b, _args(b, 8193))
     assert e.value.code == -4 and "8192" in str(e.value)
+
+
+def test_noalloc_rejects_a_problem_index_out_of_range_on_the_device():
+    """traj_problem lives in device memory; an entry outside [0, n_problems) is found
+    by a range check on the device before any kernel indexes the problem records, and
+    the call returns TRAJ_EINVAL with the outputs untouched."""
+    import torch
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.config2(0, n_scenes=2, inits=2)
+    for bad in (2, -1, 255):
+        a = _args(b, 4)
+        a["traj_problem"] = torch.tensor([0, 1, bad, 0], dtype=torch.int32, device="cuda")
+        a["coeffs0"].copy_(torch.as_tensor(b.xi0, device="cuda"))
+        a["iters"].fill_(-7)
+        with pytest.raises(tb.TrajBatchError) as e:
+            _call(b, a)
+        assert e.value.code == -1 and "traj_problem" in str(e.value)
+        assert bool((a["iters"] == -7).all())
+    # a valid map right after works (the flag does not stick)
+    a = _args(b, 4)
+    a["traj_problem"] = torch.tensor([0, 1, 1, 0], dtype=torch.int32, device="cuda")
+    a["coeffs0"].copy_(torch.as_tensor(b.xi0, device="cuda"))
+    _call(b, a)
+    assert bool((a["iters"] >= 1).all())
+
+
+def test_noalloc_binding_refuses_a_short_output_tensor():
+    import torch
+    b = scenes.config2(0, n_scenes=1, inits=2)
+    a = _args(b, 2)
+    a["coeffs"] = torch.zeros(2, 2, 10, device="cuda")
+    with pytest.raises(ValueError, match="coeffs holds 40 values, needs 44"):
+        _call(b, a)
