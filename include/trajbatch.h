@@ -182,9 +182,9 @@ traj_status traj_get_trajectories(traj_batch *b, float *coeffs, float *residual,
 traj_status traj_get_accel_cost(traj_batch *b, float *cost);
 
 /* Homotopy signature of each trajectory of the last solve (2D, n_p <= 256): bit j
- * (j < 64) is set when the trajectory passes obstacle j of its problem on the left
- * of their relative motion, judged at the closest approach over the grid points
- * (distances scaled by the semi-axes): the sign of (p - o_j) x (p' - v_j) there.
+ * (j < 64) is set when obstacle j of its problem is on the trajectory's left as they
+ * pass, judged at the closest approach over the grid points (distances scaled by the
+ * semi-axes): (p - o_j) x (p' - v_j) > 0 there.
  * Solutions of one problem with equal signatures pass every obstacle on the same
  * side. Used to choose training labels of the learned warm start that cover
  * different homotopy classes. sig: uint64 [n_traj], host or device. No paper
@@ -297,8 +297,11 @@ traj_status traj_solve_noalloc(const traj_config *cfg, int n_problems, const int
                                signed char *status);
 
 /* CTA shape of the persistent solve launch: warps per block (1..8; 0 = the
- * default of the form), a cap on resident blocks per SM (0 = as many as
- * occupancy allows) and the warps that share one trajectory (1, 2 or 4,
+ * default of the form), resident blocks per SM (0 = as many as the occupancy
+ * query allows; a positive count caps it, and in the tensor-core forms it is also
+ * honoured above the query's answer, which is conservative for these kernels, as
+ * far as registers, shared memory, tensor memory and warp slots hold) and the warps
+ * that share one trajectory (1, 2 or 4,
  * dividing warps_per_block: timesteps interleaved across the warps, partial
  * contractions exchanged through shared memory; FP32 form only). occupancy = 1
  * selects the build whose registers are capped so that more warps stay resident
@@ -322,15 +325,18 @@ traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape)
 
 /* The shape the last captured solve launch resolved to: warps per block, resident
  * blocks per SM the launch counted on (after occupancy, shared memory and, in the
- * tensor-core form, tensor-memory limits) and warps per trajectory, and the grid
- * size (nullable outputs). TRAJ_ESTATE before the first solve. No paper counterpart. */
-traj_status traj_get_launch_info(traj_batch *b, traj_launch_shape *resolved, int *grid);
+ * tensor-core form, tensor-memory limits), warps per trajectory and build, the grid
+ * size, the kernel's registers per thread and its dynamic shared memory per block
+ * in bytes (nullable outputs; 0 registers for a long-horizon launch). TRAJ_ESTATE
+ * before the first solve. No paper counterpart. */
+traj_status traj_get_launch_info(traj_batch *b, traj_launch_shape *resolved, int *grid,
+                                 int *registers, int *shared_bytes);
 
 /* Autotuner: times every candidate shape (warps per block in {0,1,2,4,8} x
  * blocks per SM in {occupancy,1,2,4} x warps per trajectory in {1,2,4}, the
  * latter in the FP32 form only, plus the register-capped build with one warp per
- * trajectory and warps per block in {0,2,4} (tensor-core forms also 6) where the
- * horizons allow it) on this handle's own batch with `iters`
+ * trajectory, warps per block in {0,2,4} (tensor-core forms also 6) and blocks per
+ * SM in {occupancy,2,3} where the horizons allow it) on this handle's own batch with `iters`
  * fixed iterations, keeps the fastest for later solves and reports it in
  * *chosen and its time per solve in *best_ms (both nullable). Synchronises;
  * the previous solve's results are discarded. No paper counterpart. */

@@ -47,6 +47,7 @@
 #include "am_device.cuh"
 #include "tcgen05.cuh"
 #include <cuda_bf16.h>
+#include <algorithm>
 
 namespace tb {
 
@@ -322,17 +323,18 @@ __device__ __forceinline__ bool mixed_one(const SolveArgs &A, int b, const float
   return true;
 }
 
-// Per-trajectory specialisation on the number of 32-step slots (short horizons of an
-// uneven batch do not pay for the longest one's).
-template <int DIM, int NT, int MAXNT, bool SPLIT>
+// Per-trajectory specialisation on the number of 32-step slots, in the steps 2, 4, 5
+// and 8 (short horizons of an uneven batch do not pay for the longest one's).
+template <int DIM, int MAXNT, bool SPLIT>
 __device__ __forceinline__ bool mixed_nt(const SolveArgs &A, int b, const float *stab, int lane,
                                          unsigned long long deadline, MxWarp &W, int nt) {
-  if constexpr (NT >= MAXNT) {
-    return mixed_one<DIM, MAXNT, SPLIT>(A, b, stab, lane, deadline, W);
-  } else {
-    if (nt <= NT) return mixed_one<DIM, NT, SPLIT>(A, b, stab, lane, deadline, W);
-    return mixed_nt<DIM, NT + 1, MAXNT, SPLIT>(A, b, stab, lane, deadline, W, nt);
-  }
+  if constexpr (MAXNT > 2)
+    if (nt <= 2) return mixed_one<DIM, 2, SPLIT>(A, b, stab, lane, deadline, W);
+  if constexpr (MAXNT > 4)
+    if (nt <= 4) return mixed_one<DIM, 4, SPLIT>(A, b, stab, lane, deadline, W);
+  if constexpr (MAXNT > 5)
+    if (nt <= 5) return mixed_one<DIM, 5, SPLIT>(A, b, stab, lane, deadline, W);
+  return mixed_one<DIM, MAXNT, SPLIT>(A, b, stab, lane, deadline, W);
 }
 
 template <int DIM, int MAXNT, bool SPLIT, bool CAP = false>
@@ -422,7 +424,7 @@ k_am_mixed(const __grid_constant__ SolveArgs A) {
     if (item >= A.n_traj) break;
     const int b = A.order[item];
     const int nt = (A.problems[A.traj_problem[b]].n_p + 31) >> 5;
-    if (!mixed_nt<DIM, 1, MAXNT, SPLIT>(A, b, stab, lane, deadline, W, nt)) break;
+    if (!mixed_nt<DIM, MAXNT, SPLIT>(A, b, stab, lane, deadline, W, nt)) break;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -455,7 +457,20 @@ static cudaError_t launch_mx(const SolveArgs &a, const LaunchShape &shape, int n
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  if (shape.blocks_per_sm > 0 && shape.blocks_per_sm < occ) occ = shape.blocks_per_sm;
+  // A count of blocks per SM asked for explicitly is honoured up to what the SM's
+  // resources hold -- registers, shared memory (1 KB reserved per block), tensor memory
+  // and warp slots -- even where the occupancy query answers fewer for this kernel.
+  if (shape.blocks_per_sm > 0) {
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * warps;
+    int fit = 65536 / (regs_cta > 0 ? regs_cta : 1);
+    fit = std::min(fit, (int)((228 * 1024) / (smem + 1024)));
+    fit = std::min(fit, (int)(512u / mixed_tmem_cols(warps, mixed_n(DIM, SPLIT))));
+    fit = std::min(fit, 64 / warps);
+    occ = std::max(1, std::min(shape.blocks_per_sm, fit));
+  }
   // TMEM: every resident CTA holds mixed_tmem_cols of the SM's 512 columns
   while (occ > 1 && (uint32_t)occ * mixed_tmem_cols(warps, mixed_n(DIM, SPLIT)) > 512u) --occ;
   long long grid = (long long)n_sm * occ, want = ((long long)a.n_traj + warps - 1) / warps;
@@ -464,6 +479,9 @@ static cudaError_t launch_mx(const SolveArgs &a, const LaunchShape &shape, int n
   if (used) {
     used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = 1;
     used->occupancy = CAP ? 1 : 0;
+    cudaFuncAttributes fa{};
+    used->regs = cudaFuncGetAttributes(&fa, kern) == cudaSuccess ? fa.numRegs : 0;
+    used->smem = (int)smem;
   }
   kern<<<(unsigned)grid, warps * 32, smem, s>>>(a);
   return cudaGetLastError();

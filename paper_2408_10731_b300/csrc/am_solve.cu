@@ -418,6 +418,9 @@ static cudaError_t launch_t(const SolveArgs &a, const LaunchShape &shape, int n_
   if (used) {
     used->warps_per_block = warps; used->blocks_per_sm = occ; used->grid = (int)grid; used->team = W;
     used->occupancy = CAP ? 1 : 0;
+    cudaFuncAttributes fa{};
+    used->regs = cudaFuncGetAttributes(&fa, kern) == cudaSuccess ? fa.numRegs : 0;
+    used->smem = (int)smem;
   }
   kern<<<(unsigned)grid, warps * 32, smem, s>>>(a);
   return cudaGetLastError();

@@ -4,7 +4,7 @@
 //
 // For obstacle j moving as o_j(t) = c_j + v_j t, the trajectory's closest approach
 // (in coordinates scaled by the semi-axes, over the grid points) is at t*, and the
-// obstacle is passed on the left of the relative motion when the cross product
+// obstacle is on the trajectory's left as they pass when the cross product
 // (p - o_j)(t*) x (p' - v_j)(t*) is positive: bit j of the signature is then set.
 // Two trajectories of a problem that pass every obstacle on the same sides share
 // the signature. Obstacles past the 64th of a problem are not encoded.

@@ -182,6 +182,8 @@ struct LaunchShape {
                  // (FP32 form: 128 per thread, at most 4 warps per block; tensor-core
                  // form: 170, at most 6 warps), one warp per trajectory, horizons up
                  // to 160 grid points; 0: registers unrestricted
+  int regs;      // filled in by the launcher: registers per thread of the kernel,
+  int smem;      //   dynamic shared memory per block (bytes)
 };
 // tensor-core form (am_mixed.cu); horizons up to max_np <= 256, the distinct ones in
 // a.hz_*; split: hi/lo BF16 operand pairs; the shape's warps per block (0: the batch

@@ -767,7 +767,8 @@ traj_status traj_set_launch_shape(traj_batch *b, const traj_launch_shape *shape)
   return TRAJ_OK;
 }
 
-traj_status traj_get_launch_info(traj_batch *b, traj_launch_shape *resolved, int *grid) {
+traj_status traj_get_launch_info(traj_batch *b, traj_launch_shape *resolved, int *grid,
+                                 int *registers, int *shared_bytes) {
   if (!b) return TRAJ_EINVAL;
   if (!b->graph_valid) return fail(b, TRAJ_ESTATE, "no solve launch has been captured");
   if (resolved) {
@@ -777,6 +778,8 @@ traj_status traj_get_launch_info(traj_batch *b, traj_launch_shape *resolved, int
     resolved->occupancy = b->used.occupancy;
   }
   if (grid) *grid = b->used.grid;
+  if (registers) *registers = b->used.regs;
+  if (shared_bytes) *shared_bytes = b->used.smem;
   return TRAJ_OK;
 }
 
@@ -795,7 +798,8 @@ traj_status traj_autotune(traj_batch *b, int iters, traj_launch_shape *chosen, f
         if (w % team == 0) cands.push_back(LaunchShape{w, bps, 0, team, 0});
   if (b->max_np_used <= 160) // the register-capped build, one warp per trajectory
     for (int w : {0, 2, 4, 6})
-      if (w <= (tc ? 6 : 4)) cands.push_back(LaunchShape{w, 0, 0, 1, 1});
+      for (int bps : {0, 2, 3})
+        if (w <= (tc ? 6 : 4)) cands.push_back(LaunchShape{w, bps, 0, 1, 1});
   LaunchShape best{4, 0, 0, 1, 0};
   float best_t = 1e30f;
   for (const LaunchShape &c : cands) {

@@ -105,7 +105,8 @@ def load_library():
     lib.traj_measure_fp32_peak.argtypes = [_vp, _c_int, ctypes.POINTER(_c_double)]
     lib.traj_measure_mufu_peak.argtypes = [_vp, _c_int, ctypes.POINTER(_c_double)]
     lib.traj_set_launch_shape.argtypes = [_vp, ctypes.POINTER(LaunchShape)]
-    lib.traj_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchShape), ctypes.POINTER(_c_int)]
+    lib.traj_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchShape), ctypes.POINTER(_c_int),
+                                         ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]
     lib.traj_autotune.argtypes = [_vp, _c_int, ctypes.POINTER(LaunchShape),
                                   ctypes.POINTER(_c_float)]
     lib.traj_sampler_step.argtypes = [_vp, ctypes.POINTER(SamplerConfig), _c_int, _vp, _vp, _vp,
@@ -273,11 +274,12 @@ class TrajBatch:
     def launch_info(self):
         """The shape the last solve launch resolved to (warps per block, resident blocks
         per SM, warps per trajectory) and its grid."""
-        shape, grid = LaunchShape(), _c_int(0)
-        self._check(self._lib.traj_get_launch_info(self._h, ctypes.byref(shape), ctypes.byref(grid)))
+        shape, grid, regs, smem = LaunchShape(), _c_int(0), _c_int(0), _c_int(0)
+        self._check(self._lib.traj_get_launch_info(self._h, ctypes.byref(shape), ctypes.byref(grid),
+                                                   ctypes.byref(regs), ctypes.byref(smem)))
         return dict(warps_per_block=shape.warps_per_block, blocks_per_sm=shape.blocks_per_sm,
                     warps_per_trajectory=shape.warps_per_trajectory, occupancy=shape.occupancy,
-                    grid=grid.value)
+                    grid=grid.value, registers=regs.value, shared_bytes=smem.value)
 
     def autotune(self, iters=20):
         """Time the candidate launch shapes on this batch; keep and return the fastest."""
@@ -334,8 +336,8 @@ class TrajBatch:
         self._check(self._lib.traj_set_rho_schedule(self._h, int(levels), float(growth), int(every)))
 
     def homotopy_signature(self):
-        """uint64 [n_traj]: bit j set when the trajectory passes obstacle j (j < 64) on the
-        left of their relative motion at the closest approach (2D)."""
+        """uint64 [n_traj]: bit j set when obstacle j (j < 64) is on the trajectory's left
+        as they pass, at the closest approach (2D)."""
         sig = np.zeros(self.n_traj, np.uint64)
         self._check(self._lib.traj_homotopy_signature(self._h, sig.ctypes.data))
         return sig

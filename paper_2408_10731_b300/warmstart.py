@@ -6,7 +6,8 @@ module marshals arguments and orchestrates:
 
   make_labels  -- solve many scenes from random initialisations with the
                   optimizer itself and keep, per scene, up to 8 solved
-                  trajectories ranked by their acceleration cost;
+                  trajectories: one per homotopy class first (in order of
+                  acceleration cost), then the cheapest others;
   train        -- epochs of shuffled minibatches through traj_warmstart_train_step;
   proposals    -- features -> network -> K = 8 initial coefficient sets per scene.
 
@@ -280,10 +281,14 @@ class WarmStart:
 
 
 def make_labels(batch, n_inits=32, cap=300, tol=1e-3, max_labels=HEADS, seed=0,
-                chunk=2048):
+                chunk=2048, diverse=True):
     """Solve every scene of `batch` from n_inits random initialisations N(line, 0.5 m)
-    and keep up to max_labels solved trajectories per scene, lowest acceleration cost
-    first, as offsets from the straight line: (targets [P, 8, 22], n_labels [P])."""
+    and keep up to max_labels solved trajectories per scene as offsets from the
+    straight line: (targets [P, 8, 22], n_labels [P]). With `diverse`, the labels cover
+    the scene's homotopy classes first (traj_homotopy_signature: which side of every
+    obstacle a solution passes): the cheapest solution of each class in order of
+    acceleration cost, then the cheapest remaining ones; otherwise the cheapest
+    solutions overall."""
     P = batch.n_problems
     rng = np.random.default_rng(seed)
     targets = np.zeros((P, HEADS, D22), np.float32)
@@ -305,6 +310,7 @@ def make_labels(batch, n_inits=32, cap=300, tol=1e-3, max_labels=HEADS, seed=0,
             cost = np.zeros(sub.n_traj, np.float32)
             rc = _lib().traj_get_accel_cost(h._h, cost.ctypes.data)
             _check(rc, "accel cost")
+            sig = h.homotopy_signature() if diverse else None
         finally:
             h.close()
         ok = out["status"] == tb.TRAJ_CONVERGED
@@ -312,7 +318,16 @@ def make_labels(batch, n_inits=32, cap=300, tol=1e-3, max_labels=HEADS, seed=0,
             idx = np.nonzero(ok[k * n_inits:(k + 1) * n_inits])[0] + k * n_inits
             if idx.size == 0:
                 continue
-            idx = idx[np.argsort(cost[idx], kind="stable")][:max_labels]
+            idx = idx[np.argsort(cost[idx], kind="stable")]
+            if diverse:
+                first, seen = [], set()
+                for i in idx:
+                    if int(sig[i]) not in seen:
+                        seen.add(int(sig[i]))
+                        first.append(i)
+                rest = [i for i in idx if i not in set(first)]
+                idx = np.array(first + rest, dtype=idx.dtype)
+            idx = idx[:max_labels]
             targets[p0 + k, :idx.size] = (out["xi"][idx] - lines[k][None]).reshape(idx.size, D22)
             n_labels[p0 + k] = idx.size
     return targets, n_labels
@@ -354,20 +369,22 @@ def proposals(ws: WarmStart, batch):
 
 
 def trained(seed=1000, n_scenes=200000, epochs=20, lr=1e-3, weight_decay=1e-4, cache=None,
-            max_rows=4096):
-    """A WarmStart trained on n_scenes config-2-style scenes labelled by the optimizer,
-    cached as .npy parameters (keyed by the training settings)."""
+            max_rows=4096, diverse=True):
+    """A WarmStart trained on n_scenes config-2-style scenes labelled by the optimizer
+    (labels covering homotopy classes first when `diverse`), cached as .npy parameters
+    (keyed by the training settings)."""
     import os
     if cache is None:
+        tag = "_div" if diverse else ""
         cache = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib",
-                             f"warmstart_{seed}_{n_scenes}_{epochs}_{lr:g}_{weight_decay:g}.npy")
+                             f"warmstart_{seed}_{n_scenes}_{epochs}_{lr:g}_{weight_decay:g}{tag}.npy")
     ws = WarmStart(max_rows)
     if os.path.exists(cache):
         ws.set_params(np.load(cache))
         return ws, None
     import torch
     tr = scenes.ellipse_scenes(seed, n_scenes)
-    targets, n_labels = make_labels(tr, seed=seed + 1)
+    targets, n_labels = make_labels(tr, seed=seed + 1, diverse=diverse)
     ws.set_params(init_params(seed))
     X, _ = ws.features(tr)
     losses = train(ws, X, torch.as_tensor(targets, device="cuda"),

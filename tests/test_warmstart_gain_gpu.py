@@ -2,7 +2,8 @@
 network's K = 8 proposals versus the initialisations the optimizer uses without
 it -- the straight line (zero offsets, the fallback) and 8 random draws
 N(straight line, 0.5 m). The network is trained on the GPU by the library's own
-kernels on scenes that the optimizer itself solved."""
+kernels on scenes that the optimizer itself solved, with labels that cover each
+scene's homotopy classes first."""
 import dataclasses
 
 import numpy as np
@@ -54,8 +55,11 @@ def test_trained_network_gains_over_the_fallback_initialisation(capsys):
         # solves only the easy scenes)
         assert res["learned"]["scenes"] >= 1.3 * res["straight"]["scenes"], res
         assert res["learned"]["traj"] >= res["straight"]["traj"], res
-        # against random draws: at least as many trajectories solved (fewer scenes with
-        # a solution: the proposals cover fewer homotopies; recorded above)
-        assert res["learned"]["traj"] >= 0.95 * res["random"]["traj"], res
+        # against random draws: more trajectories solved and more solved per second (the
+        # share of scenes with at least one solution stays below the random draws':
+        # the eight heads cover fewer homotopy classes than eight independent draws,
+        # with or without class-diverse labels; recorded above)
+        assert res["learned"]["traj"] >= res["random"]["traj"], res
+        assert res["learned"]["solved_per_s"] >= res["random"]["solved_per_s"], res
     finally:
         ws.close()

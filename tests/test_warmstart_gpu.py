@@ -187,3 +187,64 @@ def test_device_propose_matches_host_path_and_flags_bad_offsets():
         ws.sync()
     ws.sync()  # the flag is cleared once reported
     ws.close()
+
+
+def test_homotopy_signature_tells_the_sides_apart():
+    """One static obstacle on the straight path from (0, 0) to (8, 8): a trajectory
+    bending through (5, 3) keeps it on its left (bit set), one through (3, 5) on its
+    right (bit clear); an obstacle far off the path's left is on the left of both.
+    Random trajectories against a host evaluation of the same definition."""
+    import dataclasses
+    from paper_2408_10731_b300 import trajbatch as tb
+    start, goal = np.array([0.0, 0.0]), np.array([8.0, 8.0])
+    line = scenes.straight_line_coeffs(start, goal)
+    bump = np.sin(np.pi * np.arange(11) / 10.0)  # zero at both ends
+    right = line + 1.5 * np.stack([bump, -bump])
+    left = line + 1.5 * np.stack([-bump, bump])
+    b = scenes.Batch(dim=2, n_steps=np.array([100], np.int32), duration=np.array([10.0]),
+                     start=start[None], goal=goal[None], offsets=np.array([0, 2], np.int32),
+                     centers=np.array([[4.0, 4.0], [1.0, 7.0]], np.float32),
+                     semi_axes=np.full((2, 2), 0.5, np.float32),
+                     velocities=np.zeros((2, 2), np.float32),
+                     traj_problem=np.zeros(2, np.int32),
+                     xi0=scenes.f32(np.stack([right, left])), vmax=1e6, amax=1e6, rho=1.0)
+    h = tb.from_batch(b)
+    try:
+        h.solve(0, -1.0)  # the initial coefficients are projected, not moved: compare as given
+        sig = h.homotopy_signature()
+        xi = h.get_trajectories()["xi"].astype(np.float64)
+    finally:
+        h.close()
+    assert int(sig[0]) & 1 == 1 and int(sig[1]) & 1 == 0, sig
+    assert int(sig[0]) & 2 == 2 and int(sig[1]) & 2 == 2, sig
+    # random scenes: the same definition evaluated on the host from the GPU's coefficients
+    rb = scenes.config2(4, n_scenes=4, inits=8)
+    h = tb.from_batch(rb)
+    try:
+        h.solve(30, -1.0)
+        sig = h.homotopy_signature()
+        xi = h.get_trajectories()["xi"].astype(np.float64)
+    finally:
+        h.close()
+    from oracle import am
+    P, Pd, _ = am.bernstein(100, 10.0)
+    t = np.linspace(0.0, 10.0, 100)
+    checked = 0
+    for k in range(rb.n_traj):
+        p_ = rb.traj_problem[k]
+        c, a, v = (np.asarray(x, np.float64) for x in rb.obstacles(p_))
+        pos, vel = xi[k] @ P.T, xi[k] @ Pd.T  # [2, n_p]
+        for j in range(c.shape[0]):
+            o = c[j][:, None] + v[j][:, None] * t[None]
+            d2 = (((pos - o) / a[j][:, None]) ** 2).sum(0)
+            order = np.argsort(d2)
+            if d2[order[1]] - d2[order[0]] < 1e-4 * max(1.0, d2[order[0]]):
+                continue  # a near tie of the closest grid point: FP32 may pick the other
+            ts = order[0]
+            d, r = pos[:, ts] - o[:, ts], vel[:, ts] - v[j]
+            cr = d[0] * r[1] - d[1] * r[0]
+            if abs(cr) < 1e-4 * (np.linalg.norm(d) * np.linalg.norm(r) + 1e-12):
+                continue
+            assert ((int(sig[k]) >> j) & 1) == (1 if cr > 0 else 0), (k, j, cr)
+            checked += 1
+    assert checked > 1000
