@@ -236,10 +236,10 @@ def cpu_baseline(seed=0, scenes_idx=range(16), max_iters=500, tol=1e-3, workload
 
 def cpu_baseline_both(batch, wl):
     """The oracle on the host: all cores on 32 scenes (256 trajectories; 4 scenes of the
-    long horizon), and one thread on 4 scenes (32 trajectories; 1 of the long horizon).
+    long horizon), and one thread on 8 scenes (64 trajectories; 1 of the long horizon).
     On the held-out scenes only about one trajectory in seven converges, so the samples
     are large enough to hold some; trajectory-iterations/s is reported beside."""
-    n_all, n_one = (4, 1) if wl == "long" else (32, 4)
+    n_all, n_one = (4, 1) if wl == "long" else (32, 8)
     allc = cpu_baseline(workload=batch, scenes_idx=range(n_all))
     one = cpu_baseline(workload=batch, scenes_idx=range(n_one), n_threads=1)
     for d in (allc, one):
