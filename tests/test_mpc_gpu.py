@@ -140,3 +140,44 @@ def test_full_size_receding_step_sampled():
             assert err.max() <= POS_TOL, (p, err.max())
     finally:
         h.close()
+
+
+def _step_against_oracle(batch, precision="fp32", shape=None, iters0=20, delta=0.1):
+    """Solve, shift by delta onto each problem's first plan, solve 10 iterations; the
+    oracle's step from the GPU's own state before the shift. Returns the error."""
+    h = _handle(batch, precision=precision)
+    try:
+        if shape:
+            h.set_launch_shape(*shape)
+        h.solve(iters0, -1.0)
+        xi = h.get_trajectories()["xi"].astype(np.float64)
+        lam = h.get_state()["lam"].astype(np.float64)
+        executed = [int(np.nonzero(batch.traj_problem == p)[0][0]) for p in range(batch.n_problems)]
+        h.shift_horizon(delta, executed)
+        h.solve(10, -1.0)
+        g = h.get_trajectories()
+    finally:
+        h.close()
+    moved, _, o = mpc.solve_after_step(batch, xi, lam, executed, delta, 10)
+    return position_error(moved, g["xi"], o["xi"])
+
+
+def test_receding_step_in_3d_and_with_a_team_of_warps():
+    """A 3D problem set (ellipsoids, start velocity and acceleration in three axes) in
+    the one-warp and the two-warp-team kernels."""
+    b = scenes.long_horizon(3, n_scenes=3, inits=4, n_steps=200, dim=3)
+    assert _step_against_oracle(b).max() <= POS_TOL
+    b2 = scenes.config2(9, n_scenes=4, inits=4)
+    assert _step_against_oracle(b2, shape=(4, 0, 2)).max() <= POS_TOL
+
+
+@pytest.mark.parametrize("prec,bound", [("mixed", 5e-2), ("mixed_split", 1e-3)])
+def test_receding_step_in_the_tensor_core_forms(prec, bound, capsys):
+    """The carried multipliers and the first projection of the shifted iterate in the
+    tensor-core kernel; error against the oracle's step reported and bounded as the
+    forms' error after 20 iterations."""
+    b = scenes.config2(9, n_scenes=4, inits=4)
+    err = _step_against_oracle(b, precision=prec)
+    with capsys.disabled():
+        print(f"\n{prec} receding step vs FP64: max {err.max():.2e} m")
+    assert err.max() <= bound
