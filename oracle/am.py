@@ -11,10 +11,15 @@ Parity status:
   and carry    rows the obstacle-free fixed point is the brute-force QP with those
                rows; one iteration from imported multipliers equals the
                brute-force proximal QP step with them (tests/test_oracle_mpc.py)
-  am_solve     pinned by invariants only (fixed point of a feasible QP optimum,
-               A xi = b at every iterate, targets on/outside every ellipse,
-               multiplier sign): the end-to-end iteration has no printed values
-               in the paper, so beyond those invariants it is parity unpinned.
+  am_solve     pinned: the first two iterations (moving obstacles, active
+               bounds, 2D and 3D) equal their step-by-step brute-force
+               composition -- targets from the dense-grid-pinned projections,
+               xi-steps as null-space QP solves on BPoly tables with a literal
+               stacked F, lambda <- lambda - rho F^T (F xi - g); plus the fixed
+               point of a feasible QP optimum, the obstacle-free QP optimum,
+               A xi = b at every iterate and the multiplier sign. The paper
+               prints no iterate values, so later iterates are checked only
+               through these steps.
 """
 from __future__ import annotations
 

@@ -254,3 +254,62 @@ def test_long_horizon_scenes_follow_their_recipe(dim, moving):
         assert np.all(speed <= 1.0 + 1e-6) and (moving or np.all(speed == 0))
         assert np.all((((b.start[p] - c) / a) ** 2).sum(1) > 1.0)
         assert np.all((((b.goal[p] - (c + v * b.duration[p])) / a) ** 2).sum(1) > 1.0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_first_iterations_equal_brute_force_composition(dim):
+    """Two full iterations on a small problem with moving obstacles and active bounds,
+    rebuilt step by step outside the oracle's loop: the targets g from the projection
+    functions (pinned against dense grids above) applied to each iterate, the
+    xi-steps as brute-force equality-constrained QPs (null-space method, BPoly
+    tables, a literal stacked F per axis), and the multiplier update
+    lambda <- lambda - rho F^T (F xi - g). A dropped term, a wrong sign, an index off
+    by one or a step out of Algorithm 2's order moves the result."""
+    n_p, T, rho, vmax, amax = 20, 4.0, 0.8, 1.2, 1.5
+    rng = np.random.default_rng(21 + dim)
+    start = rng.uniform(-1, 1, dim)
+    goal = start + rng.uniform(3, 5, dim)
+    n_o = 3
+    centers = start + (goal - start) * rng.uniform(0.3, 0.7, (n_o, 1)) + rng.normal(0, 0.2, (n_o, dim))
+    axes = rng.uniform(0.4, 0.8, (n_o, dim))
+    vel = rng.normal(0, 0.3, (n_o, dim))
+    xi0 = scenes.straight_line_coeffs(start, goal)[None] + rng.normal(0, 0.4, (2, dim, 11))
+    b = _single_problem(start, goal, n_p, T, centers, axes, vel=vel, B=2, xi0=xi0, vmax=vmax,
+                        amax=amax, rho=rho)
+    P, Pd, Pdd = _tables(n_p, T)
+    t = np.linspace(0.0, T, n_p)
+    F = np.vstack([P] * n_o + [Pd, Pdd])                  # one axis's stacked rows
+    Q = Pdd.T @ Pdd + P.T @ P
+    A = np.stack([P[0], Pd[0], Pdd[0], P[-1]])
+    tau = np.linspace(0, 1, n_p)
+
+    def targets(xi):  # g [dim][rows] for coefficients xi [dim][11]
+        pos, v, a = xi @ P.T, xi @ Pd.T, xi @ Pdd.T
+        g = np.zeros((dim, F.shape[0]))
+        for j in range(n_o):
+            o = centers[j][:, None] + vel[j][:, None] * t[None]
+            for k in range(n_p):
+                g[:, j * n_p + k] = o[:, k] + am.project_obstacle(pos[:, k] - o[:, k], axes[j])
+        for k in range(n_p):
+            g[:, n_o * n_p + k] = am.project_bound(v[:, k], vmax)
+            g[:, (n_o + 1) * n_p + k] = am.project_bound(a[:, k], amax)
+        return g
+
+    for kk in range(2):
+        xi, lam = xi0[kk].copy(), np.zeros((dim, 11))
+        g = targets(xi)
+        ref = []
+        for it in range(2):
+            new = np.zeros_like(xi)
+            for ax in range(dim):
+                q = -P.T @ (start[ax] + (goal[ax] - start[ax]) * tau)
+                new[ax] = _qp_bruteforce(Q + rho * F.T @ F, q - lam[ax] - rho * F.T @ g[ax], A,
+                                         np.array([start[ax], 0.0, 0.0, goal[ax]]))
+            xi = new
+            g = targets(xi)
+            lam = lam - rho * np.stack([F.T @ (F @ xi[ax] - g[ax]) for ax in range(dim)])
+            ref.append((xi.copy(), lam.copy()))
+        for it in (1, 2):
+            out = am.solve(b, it, iters_fixed=np.full(2, it), want_lambda=True)
+            np.testing.assert_allclose(out["xi"][kk], ref[it - 1][0], atol=1e-9, rtol=0)
+            np.testing.assert_allclose(out["lam"][kk], ref[it - 1][1], atol=1e-8, rtol=0)
