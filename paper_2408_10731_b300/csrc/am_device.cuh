@@ -9,6 +9,8 @@
 // the f32x2 FMA (__ffma2_rn: two IEEE fmas per instruction), and the obstacle
 // test runs on the two obstacles of a pair record at once.
 #pragma once
+#include <climits>
+
 #include "internal.cuh"
 
 namespace tb {
@@ -307,14 +309,14 @@ __device__ __forceinline__ void project_record(float4 (&o)[pair_vec(DIM)], const
       pair_project<DIM>(o, p2[m], t2[m], sm[m], acc[m], mo);
 }
 
-// Pair loop: all of the lane's timesteps against the problem's obstacle-pair
-// records, two records (four obstacles) per step, each with its own test. The
-// tests are branch-free and packed; the sign bits of all ||u||^2 - 1 of a record
-// are OR-ed, and only when one is negative (a point inside, a few percent of the
-// tests) does the warp take that record's projection branch.
+// Dense pair loop: all of the lane's timesteps against every obstacle-pair record
+// of the problem, two records (four obstacles) per step, each with its own test.
+// The tests are branch-free and packed; the sign bits of all ||u||^2 - 1 of a
+// record are OR-ed, and only when one is negative (a point inside, a few percent of
+// the tests) does the warp take that record's projection branch.
 // acc accumulates sum_j (g_j - p) (= -sum_j r_j); mo is the lane's max ||r_j||^2.
 template <int DIM, int MAXNT>
-__device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const float (&tm)[MAXNT],
+__device__ __forceinline__ void pair_loop_dense(const float (&pos)[MAXNT][DIM], const float (&tm)[MAXNT],
                                           const float4 *obs, int n_o, float (&acc)[MAXNT][DIM],
                                           float &mo) {
   constexpr int PV = pair_vec(DIM), PT = pair_test_vec(DIM);
@@ -362,6 +364,130 @@ __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const 
   }
 }
 
+// Order keys of floats for warp min/max reductions on the integer unit: the key
+// k = bits ^ ((bits >> 31) & 0x7fffffff) orders as a signed integer as the floats
+// do (the magnitude bits of a negative float reversed); the map is its own inverse.
+__device__ __forceinline__ int float_key(float f) {
+  const int b = __float_as_int(f);
+  return b ^ ((b >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7fffffff)); }
+
+// Culled pair loop: all of the lane's timesteps against the problem's obstacle-pair
+// records, culled and exact: the records are taken 32 at a time, one per lane, and
+// for every timestep slot the lane first bounds its record's normalised coordinate
+// u = fma(ia, p, fma(nv, t, nc)) over the slot's box (the warp's least and greatest
+// position per axis and time, over the slots' valid lanes) by evaluating that same
+// expression at the box's corners: round-to-nearest is monotone and ia > 0, so the
+// corner values bound the u that each lane's own test computes. Where u >= 1 or
+// u <= -1 on some axis for both obstacles of a record, no lane's ||u||^2 - 1 can come
+// out negative, so the record is left out of that slot (a ballot per slot). The
+// records kept are then tested as before, two per step: packed and branch-free,
+// and only when a sign bit is set (a point inside) does the warp take the
+// projection branch. The results are bitwise those of testing every record; the
+// records of a slot are visited in increasing order.
+// acc accumulates sum_j (g_j - p) (= -sum_j r_j); mo is the lane's max ||r_j||^2.
+template <int DIM, int MAXNT>
+__device__ __forceinline__ void pair_loop_culled(const float (&pos)[MAXNT][DIM], const float (&tm)[MAXNT],
+                                                 unsigned valid, const float4 *obs, int n_o,
+                                                 float (&acc)[MAXNT][DIM], float &mo) {
+  constexpr int PV = pair_vec(DIM), PT = pair_test_vec(DIM), IA = DIM;
+  const int n_pairs = pair_count(n_o);
+  const int lane = threadIdx.x & 31;
+  float2 p2[MAXNT][DIM], t2[MAXNT];
+#pragma unroll
+  for (int m = 0; m < MAXNT; ++m) {
+    t2[m] = make_float2(tm[m], tm[m]);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) p2[m][a] = make_float2(pos[m][a], pos[m][a]);
+  }
+  mo = 0.f;
+  for (int k0 = 0; k0 < n_pairs; k0 += 32) {
+    const int r = k0 + lane;
+    float4 o[PT];
+#pragma unroll
+    for (int k = 0; k < PT; ++k)
+      o[k] = r < n_pairs ? __ldg(&obs[PV * r + k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned keep[MAXNT];
+#pragma unroll
+    for (int m = 0; m < MAXNT; ++m) {
+      const bool v = (valid >> m) & 1u;
+      const int kt0 = __reduce_min_sync(0xffffffffu, v ? __float_as_int(tm[m]) : INT_MAX);
+      const int kt1 = __reduce_max_sync(0xffffffffu, v ? __float_as_int(tm[m]) : INT_MIN);
+      const float2 ta = make_float2(__int_as_float(kt0), __int_as_float(kt0));
+      const float2 tb = make_float2(__int_as_float(kt1), __int_as_float(kt1));
+      bool out0 = false, out1 = false;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const int key = float_key(pos[m][a]);
+        const float lo = key_float(__reduce_min_sync(0xffffffffu, v ? key : INT_MAX));
+        const float hi = key_float(__reduce_max_sync(0xffffffffu, v ? key : INT_MIN));
+        const float2 nc = make_float2(o[a].x, o[a].y), nv = make_float2(o[a].z, o[a].w);
+        float2 ia;
+        if constexpr (DIM == 2) ia = a == 0 ? make_float2(o[IA].x, o[IA].y) : make_float2(o[IA].z, o[IA].w);
+        else ia = a == 0 ? make_float2(o[IA].x, o[IA].y)
+                         : (a == 1 ? make_float2(o[IA].z, o[IA].w) : make_float2(o[IA + 1].x, o[IA + 1].y));
+        const float2 i0 = __ffma2_rn(nv, ta, nc), i1 = __ffma2_rn(nv, tb, nc);
+        const float2 umin = __ffma2_rn(ia, make_float2(lo, lo),
+                                       make_float2(fminf(i0.x, i1.x), fminf(i0.y, i1.y)));
+        const float2 umax = __ffma2_rn(ia, make_float2(hi, hi),
+                                       make_float2(fmaxf(i0.x, i1.x), fmaxf(i0.y, i1.y)));
+        out0 = out0 || umin.x >= 1.f || umax.x <= -1.f;
+        out1 = out1 || umin.y >= 1.f || umax.y <= -1.f;
+      }
+      // an empty slot (no valid lane) keeps nothing
+      keep[m] = __ballot_sync(0xffffffffu, kt0 != INT_MAX && r < n_pairs && !(out0 && out1));
+    }
+#pragma unroll
+    for (int m = 0; m < MAXNT; ++m) {
+      unsigned bits = keep[m];
+      while (bits) {
+        const int ra = k0 + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const bool two = bits != 0u;
+        const int rb = two ? k0 + __ffs(bits) - 1 : ra; // a lone last record pairs with itself
+        bits &= bits - 1u;
+        float4 oa[PV], ob[PV];
+#pragma unroll
+        for (int k = 0; k < PT; ++k) {
+          oa[k] = __ldg(&obs[PV * ra + k]);
+          ob[k] = __ldg(&obs[PV * rb + k]);
+        }
+        const float2 sa = pair_sm1<DIM>(oa, p2[m], t2[m]);
+        const float2 sb = pair_sm1<DIM>(ob, p2[m], t2[m]);
+        if ((int)(__float_as_uint(sa.x) | __float_as_uint(sa.y)) < 0) {
+#pragma unroll
+          for (int k = PT; k < PV; ++k) oa[k] = __ldg(&obs[PV * ra + k]);
+          pair_project<DIM>(oa, p2[m], t2[m], sa, acc[m], mo);
+        }
+        if (two && (int)(__float_as_uint(sb.x) | __float_as_uint(sb.y)) < 0) {
+#pragma unroll
+          for (int k = PT; k < PV; ++k) ob[k] = __ldg(&obs[PV * rb + k]);
+          pair_project<DIM>(ob, p2[m], t2[m], sb, acc[m], mo);
+        }
+      }
+    }
+  }
+}
+
+// Which loop a kernel runs is fixed when it is compiled. The cull's fixed cost per
+// timestep slot (the slot box's warp reductions, one record bound per lane and a
+// ballot, about 50 instructions) pays for itself where a slot's 32 lanes hold 32
+// consecutive grid points (one warp per trajectory) and the problem has more than
+// about 12 records (24 obstacles): each record a slot skips saves a packed test
+// (about 8 instructions). The timesteps of a team's warp span 32 W grid points,
+// whose box culls too little, and the long-horizon chunks serve problems with few
+// obstacles (n_o = 10 in Paper I); both run the dense loop.
+template <int DIM, int MAXNT, bool CULL>
+__device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const float (&tm)[MAXNT],
+                                          unsigned valid, const float4 *obs, int n_o,
+                                          float (&acc)[MAXNT][DIM], float &mo) {
+  if constexpr (CULL)
+    pair_loop_culled<DIM, MAXNT>(pos, tm, valid, obs, n_o, acc, mo);
+  else
+    pair_loop_dense<DIM, MAXNT>(pos, tm, obs, n_o, acc, mo);
+}
+
 // Workspace bounds (PRIEST's G xi <= tau, G = [-P; P] per axis, slack s = max(0, tau -
 // G xi)): the residual rows are max(lo - p, 0) and max(p - hi, 0), i.e. the point's
 // offset from the box, p - clamp(p, lo, hi), which joins the obstacle group's sum
@@ -390,11 +516,14 @@ __device__ __forceinline__ void box_residuals(const ProblemDev *pr, const float 
 
 // ---- evaluate / project / contract ---------------------------------------------------
 // Positions p(t) = P xi at the lane's timesteps t = t0 + ts m (padding slots get a far
-// sentinel, which is outside every obstacle).
+// sentinel, which is outside every obstacle); bit m of valid is set for a slot that
+// holds a grid point.
 template <int DIM, int MAXNT>
 __device__ __forceinline__ void eval_positions(const float2 (&xp)[DIM][6], const float *tP, int n_p,
                                                int nt, float dt, int t0, int ts,
-                                               float (&pos)[MAXNT][DIM], float (&tm)[MAXNT]) {
+                                               float (&pos)[MAXNT][DIM], float (&tm)[MAXNT],
+                                               unsigned &valid) {
+  valid = 0u;
 #pragma unroll
   for (int m = 0; m < MAXNT; ++m) {
     const int t = t0 + ts * m;
@@ -402,6 +531,7 @@ __device__ __forceinline__ void eval_positions(const float2 (&xp)[DIM][6], const
 #pragma unroll
     for (int a = 0; a < DIM; ++a) pos[m][a] = 1.0e18f;
     if (m < nt && t < n_p) {
+      valid |= 1u << m;
       float r[12];
       load_row(tP + t * ROW, r);
 #pragma unroll
@@ -438,21 +568,23 @@ __device__ __forceinline__ void bound_residuals(const float2 (&xp)[DIM][6], cons
 
 // Evaluate, project and contract one iterate (Algorithm 2 lines 4-6, minus the
 // multiplier update). The lane's timesteps are t = t0 + ts m (ts = 32 when one warp
-// owns a trajectory). Returns the per-lane partial contraction u = F^T r as
-// coefficient pairs up[DIM][6] and the lane maxima of ||r_j||^2, ||r_v||^2, ||r_a||^2.
-template <int DIM, int MAXNT>
+// owns a trajectory; the culled pair loop wants that). Returns the per-lane partial
+// contraction u = F^T r as coefficient pairs up[DIM][6] and the lane maxima of
+// ||r_j||^2, ||r_v||^2, ||r_a||^2.
+template <int DIM, int MAXNT, bool CULL>
 __device__ __forceinline__ void project_contract(
     const float2 (&xp)[DIM][6], const float *tP, const float *tD, const float *tA,
     const float4 *obs, const ProblemDev *pr, int n_p, int nt, float dt, float invT, float invT2,
     float vmax, float amax, int t0, float2 (&up)[DIM][6], float &mo, float &mv, float &ma,
     int ts = 32) {
   float pos[MAXNT][DIM], acc[MAXNT][DIM], tm[MAXNT];
-  eval_positions<DIM, MAXNT>(xp, tP, n_p, nt, dt, t0, ts, pos, tm);
+  unsigned valid;
+  eval_positions<DIM, MAXNT>(xp, tP, n_p, nt, dt, t0, ts, pos, tm, valid);
 #pragma unroll
   for (int m = 0; m < MAXNT; ++m)
 #pragma unroll
     for (int a = 0; a < DIM; ++a) acc[m][a] = 0.f;
-  pair_loop<DIM, MAXNT>(pos, tm, obs, pr->n_o, acc, mo);
+  pair_loop<DIM, MAXNT, CULL>(pos, tm, valid, obs, pr->n_o, acc, mo);
   if (pr->box) box_residuals<DIM, MAXNT>(pr, pos, t0, ts, n_p, nt, acc, mo);
 #pragma unroll
   for (int a = 0; a < DIM; ++a)
@@ -492,13 +624,14 @@ __device__ __forceinline__ void project_contract_chunked(
   for (int c0 = 0; c0 < n_p; c0 += 32 * CNT) {
     const int nt = min(CNT, (n_p - c0 + 31) >> 5);
     float pos[CNT][DIM], acc[CNT][DIM], tm[CNT];
-    eval_positions<DIM, CNT>(xp, tP, n_p, nt, dt, c0 + lane, 32, pos, tm);
+    unsigned valid;
+    eval_positions<DIM, CNT>(xp, tP, n_p, nt, dt, c0 + lane, 32, pos, tm, valid);
 #pragma unroll
     for (int m = 0; m < CNT; ++m)
 #pragma unroll
       for (int a = 0; a < DIM; ++a) acc[m][a] = 0.f;
     float moc;
-    pair_loop<DIM, CNT>(pos, tm, obs, pr->n_o, acc, moc);
+    pair_loop<DIM, CNT, false>(pos, tm, valid, obs, pr->n_o, acc, moc);
     mo = fmaxf(mo, moc);
     if (pr->box) box_residuals<DIM, CNT>(pr, pos, c0 + lane, 32, n_p, nt, acc, mo);
 #pragma unroll
@@ -519,7 +652,8 @@ __device__ __forceinline__ void project_contract_chunked(
 }
 
 // Evaluate and project one iterate without the contraction (the tensor-core form
-// contracts on the MMA): per lane and timestep slot, the residual vectors
+// contracts on the MMA; one warp per trajectory, the culled pair loop): per lane and
+// timestep slot, the residual vectors
 // Ro = sum_j r_j, Rv = r_v / T and Ra = r_a / T^2 (zero past the horizon) and the
 // lane maxima of ||r_j||^2, ||r_v||^2, ||r_a||^2.
 template <int DIM, int NT>
@@ -529,12 +663,13 @@ __device__ __forceinline__ void project_only(
     float vmax, float amax, int t0, float (&Ro)[NT][DIM], float (&Rv)[NT][DIM],
     float (&Ra)[NT][DIM], float &mo, float &mv, float &ma, int ts = 32) {
   float pos[NT][DIM], acc[NT][DIM], tm[NT];
-  eval_positions<DIM, NT>(xp, tP, n_p, NT, dt, t0, ts, pos, tm);
+  unsigned valid;
+  eval_positions<DIM, NT>(xp, tP, n_p, NT, dt, t0, ts, pos, tm, valid);
 #pragma unroll
   for (int m = 0; m < NT; ++m)
 #pragma unroll
     for (int a = 0; a < DIM; ++a) acc[m][a] = 0.f;
-  pair_loop<DIM, NT>(pos, tm, obs, pr->n_o, acc, mo);
+  pair_loop<DIM, NT, true>(pos, tm, valid, obs, pr->n_o, acc, mo);
   if (pr->box) box_residuals<DIM, NT>(pr, pos, t0, ts, n_p, NT, acc, mo);
   mv = 0.f; ma = 0.f;
 #pragma unroll

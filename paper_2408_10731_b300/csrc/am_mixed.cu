@@ -285,7 +285,7 @@ __device__ __forceinline__ bool mixed_one(const SolveArgs &A, int b, const float
         qp_step<DIM>(C, lane, rho, hq_hi, hq_lo, hq2_hi, hq2_lo, lam, lam2, uo, uo2, xo, xo2);
         ++k;
         broadcast_pairs<DIM>(xo, xo2, xp);
-        project_contract<DIM, NT>(xp, tP, tD, tA, obs, prp, n_p, NT, pr.dt, pr.invT,
+        project_contract<DIM, NT, true>(xp, tP, tD, tA, obs, prp, n_p, NT, pr.dt, pr.invT,
                                   pr.invT2, A.vmax, A.amax, lane, up, mo, mv, ma);
         scatter_pairs<DIM>(up, lane, uo, uo2);
         mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);

@@ -93,7 +93,7 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
       project_contract_chunked<DIM, MAXNT>(xp, tP, tD, tA, obs, A.problems + p, n_p, pr.dt,
                                            pr.invT, pr.invT2, A.vmax, A.amax, lane, up, mo, mv, ma);
     else
-      project_contract<DIM, MAXNT>(xp, tP, tD, tA, obs, A.problems + p, n_p, nt, pr.dt, pr.invT,
+      project_contract<DIM, MAXNT, true>(xp, tP, tD, tA, obs, A.problems + p, n_p, nt, pr.dt, pr.invT,
                                    pr.invT2, A.vmax, A.amax, lane, up, mo, mv, ma);
     scatter_pairs<DIM>(up, lane, uo, uo2);
     mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
@@ -197,7 +197,7 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
     float2 xp[DIM][6];
     broadcast_pairs<DIM>(xo, xo2, xp);
     float2 up[DIM][6];
-    project_contract<DIM, NT>(xp, tP, tD, tA, obs, A.problems + p, n_p, NT, pr.dt, pr.invT,
+    project_contract<DIM, NT, false>(xp, tP, tD, tA, obs, A.problems + p, n_p, NT, pr.dt, pr.invT,
                               pr.invT2, A.vmax, A.amax, W * lane + r, up, mo, mv, ma, 32 * W);
     float part = 0.f, part2 = 0.f;
     scatter_pairs<DIM>(up, lane, part, part2);

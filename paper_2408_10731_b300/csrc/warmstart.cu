@@ -28,6 +28,7 @@ namespace {
 
 constexpr int IN = 388, IN_PAD = 400, HID = 256, OUT = 176, HEADS = 8, D22 = 22, NEAR = 64;
 constexpr int MAX_OBS_PER_SCENE = 1024;
+static_assert(IN == 4 + 6 * NEAR, "features: 4 start/goal inputs + 6 per nearest obstacle");
 
 // padded flat parameter layout on the device (W1 padded to 400 columns)
 constexpr int P_W1 = 0, P_B1 = P_W1 + HID * IN_PAD, P_W2 = P_B1 + HID, P_B2 = P_W2 + HID * HID,
@@ -51,7 +52,7 @@ __global__ void k_features(const double *start, const double *goal, const int *o
     o0 = o1 = 0;
   }
   const int n = min(o1 - o0, MAX_OBS_PER_SCENE);
-  int np2 = 64;
+  int np2 = NEAR; // the sort covers at least the NEAR slots of the features
   while (np2 < n) np2 <<= 1;
   const float sx = (float)start[2 * s], sy = (float)start[2 * s + 1];
   const float gx = (float)goal[2 * s] - sx, gy = (float)goal[2 * s + 1] - sy;
