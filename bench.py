@@ -68,8 +68,8 @@ KERNEL_SOURCES = {
     "k_am_mixed": ("am_mixed.cu", "am_device.cuh", "internal.cuh", "tcgen05.cuh"),
 }
 MEASURED_TRAFFIC = {
-    ("k_am_fp32", "config5"): (8 * 2613248, "61689337027f52b3"),
-    ("k_am_mixed", "config5"): (8 * 2868992, "ee560481ab46f6f2"),
+    ("k_am_fp32", "config5"): (8 * 2618112, "b59aed157e53c81c"),
+    ("k_am_mixed", "config5"): (8 * 2680832, "4bfcc853a6ebff75"),
 }
 
 
@@ -145,18 +145,19 @@ def algorithmic_mufu(batch, iters):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms; mark() brackets the
-    timed region so that only the samples taken inside it are summarised."""
+    """nvidia-smi clocks / throttle reasons sampled every interval_ms (200 ms; shorter
+    for a timed region of well under a second); mark() brackets the timed region so
+    that only the samples taken inside it are summarised."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_id):
+    def __init__(self, gpu_id, interval_ms=200):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.marks = []
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
@@ -321,10 +322,14 @@ def run_priest(args, torch):
         run()
     torch.cuda.synchronize()
     ms = []
+    clk = ClockSampler(_pci_id(torch, 0), interval_ms=20)
+    clk.mark()
     for _ in range(args.steps):
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream); run(); e1.record(stream); e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+    clk.mark()
+    clocks = clk.stop()
     # D-PRIEST: 4 distributions of 1024 samples each refined in parallel, with the BARN
     # cost terms (curvature, distance to the straight path); same solve and launch shape
     nd = 4
@@ -381,7 +386,7 @@ def run_priest(args, torch):
             "config": {"workload": "3D: 256 spheres r~U(0.1,0.3) on 12 box surfaces in 20x20x5 m, "
                                    "n_p=100 over 20 s, B=4096, N_proj=2991, N_elite=410, gamma 1, "
                                    "sigma_lr 0.5", "launch_shape": shape},
-            "best_cost_aug": bc, "gpu_launches_per_step": c3["n_outer"] * 6,
+            "best_cost_aug": bc, "gpu_launches_per_step": c3["n_outer"] * 6, "clocks": clocks,
             "forms": {"d_priest_barn": dpriest, "workspace_bounds": wsb},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 2e12,
                          "unit": "Top/s", "frac": achieved / (fp32_peak / 2.0), "traffic": None,
@@ -614,7 +619,7 @@ def run_mpc(args, torch):
     for _ in range(args.warmup):
         control_step()
     ms, solved_frac, e2e = [], [], []
-    clk = ClockSampler(_pci_id(torch, 0))
+    clk = ClockSampler(_pci_id(torch, 0), interval_ms=20)
     clk.mark()
     k = 0
     while len(ms) < args.steps:
