@@ -632,7 +632,9 @@ traj_status traj_fp_set_initial(traj_fp_batch *b, int n_traj, const int *traj_pr
  * iteration whose four residuals (obstacle, speed, acceleration: L-infinity
  * distance to the feasible target over the grid; heading copy: max_t
  * ||(c, s) - (cos psi, sin psi)||) are <= tol (tol < 0: never). Asynchronous
- * unless stats is non-NULL (then synchronises). */
+ * unless stats is non-NULL (then synchronises). TRAJ_ESHAPE if a problem has
+ * more than 456 704 obstacles (the solve keeps one bit per obstacle of a
+ * problem in shared memory for its exact cull of the circle tests). */
 traj_status traj_fp_solve(traj_fp_batch *b, int max_iters, float tol, traj_fp_stats *stats);
 
 /* coeffs [n_traj][5][11] in the order x, c, y, s, psi; residual [n_traj][4];

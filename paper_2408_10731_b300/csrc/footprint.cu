@@ -24,6 +24,7 @@
 #include "linalg.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -47,6 +48,7 @@ struct FpProblemDev {
 
 struct FpArgs {
   int n_traj, n_c, max_iters;
+  int mask_words;        // 32-obstacle mask words per warp: ceil(max obstacles per problem / 32)
   float tol, rho, rho_psi, vmax, amax, r_circle;
   float offs[FP_MAX_CIRCLES];
   const int *traj_problem;
@@ -236,13 +238,28 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// Order keys for warp min/max on the integer unit: k = bits ^ ((bits >> 31) & 0x7fffffff)
+// orders as a signed integer as the floats do; the map is its own inverse.
+__device__ __forceinline__ int fp_key(float f) {
+  const int b = __float_as_int(f);
+  return b ^ ((b >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float fp_unkey(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7fffffff)); }
+__device__ __forceinline__ float fp_warp_min(float v, bool on) {
+  return fp_unkey(__reduce_min_sync(0xffffffffu, on ? fp_key(v) : INT_MAX));
+}
+__device__ __forceinline__ float fp_warp_max(float v, bool on) {
+  return fp_unkey(__reduce_max_sync(0xffffffffu, on ? fp_key(v) : INT_MIN));
+}
+
 template <int PPL>
 __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np) {
   extern __shared__ float smf[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int traj = blockIdx.x * FP_WARPS + w;
   if (traj >= A.n_traj) return; // whole warp; no block-wide barrier follows
-  float *ws = smf + w * WS_FLOATS;
+  float *ws = smf + w * (WS_FLOATS + A.mask_words);
+  unsigned *keep = reinterpret_cast<unsigned *>(ws + WS_FLOATS); // this slot's kept obstacles
   const FpProblemDev pr = A.problems[A.traj_problem[traj]];
   const int n_p = pr.n_p, n_o = pr.n_o, n_c = A.n_c;
   const float *tP = A.tables + pr.tbl_off, *tD = tP + n_p * ROW, *tA = tD + n_p * ROW;
@@ -274,6 +291,16 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
   // grid while F xi uses the copy coefficients. The contraction u = F^T (F xi - g) is
   // accumulated per lane over its points (44 partial sums) and reduced across the
   // warp into U.
+  // Culled and exact: per slot of 32 grid points the warp bounds every circle
+  // centre of its valid lanes by a box [fx_lo, fx_hi] x [fy_lo, fy_hi] and the
+  // times by [tA, tB]; lane j then bounds obstacle j's normalised offsets
+  // ux = (fx - fma(vx, t, cx)) * iax (and uy) over the box with the same rounded
+  // operations at its corners. Each is monotone (round-to-nearest, iax > 0), so an
+  // obstacle with ux >= 1 or ux <= -1 (or uy) over the whole box has fma(ux, ux, uy^2)
+  // >= 1 at every circle and point of the slot and cannot hold one; the circle loop
+  // visits only the obstacles kept, in increasing order, and the sums are bitwise
+  // those of visiting all of them.
+  const int n_rounds = (n_o + 31) >> 5;
   auto project = [&](bool init, float (&rmax)[4]) {
     rmax[0] = rmax[1] = rmax[2] = rmax[3] = 0.f;
     float acc[44];
@@ -281,9 +308,11 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
     for (int e = 0; e < 44; ++e) acc[e] = 0.f;
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
+      if (32 * q >= n_p) break; // warp-uniform: the slot holds at least one grid point
       const int t = lane + 32 * q;
-      if (t >= n_p) break;
-      const float *rp_ = tP + t * ROW, *rd = tD + t * ROW, *ra = tA + t * ROW;
+      const bool valid = t < n_p;
+      const int tv = valid ? t : n_p - 1; // idle lanes read the last row; results unused
+      const float *rp_ = tP + tv * ROW, *rd = tD + tv * ROW, *ra = tA + tv * ROW;
       const float x = dot11p(rp_, X, XLO), y = dot11p(rp_, X + FP_H, XLO);
       const float vx = dot11(rd, X), vy = dot11(rd, X + FP_H); // bound tests: hi part
       const float axx = dot11(ra, X), ayy = dot11(ra, X + FP_H);
@@ -294,33 +323,68 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
       // or cos / sin psi in the initial pass (reading H5)
       const float cF = dot11p(rp_, X + NC, XLO), sF = dot11p(rp_, X + FP_H + NC, XLO);
       const float c = init ? cp : cF, s = init ? sp : sF;
+      const float tt = (float)t * pr.T / (float)(n_p - 1);
+      { // the slot's kept obstacles
+        float flo = __int_as_float(0x7f800000), fhi = -flo, glo = flo, ghi = -flo;
+        for (int m = 0; m < n_c; ++m) {
+          const float r = A.offs[m];
+          const float fx = fmaf(r, c, x), fy = fmaf(r, s, y);
+          flo = fminf(flo, fx); fhi = fmaxf(fhi, fx);
+          glo = fminf(glo, fy); ghi = fmaxf(ghi, fy);
+        }
+        flo = fp_warp_min(flo, valid); fhi = fp_warp_max(fhi, valid);
+        glo = fp_warp_min(glo, valid); ghi = fp_warp_max(ghi, valid);
+        const float ta = __int_as_float(__reduce_min_sync(0xffffffffu, valid ? __float_as_int(tt) : INT_MAX));
+        const float tb = __int_as_float(__reduce_max_sync(0xffffffffu, valid ? __float_as_int(tt) : INT_MIN));
+        for (int k = 0; k < n_rounds; ++k) {
+          const int j = 32 * k + lane;
+          bool kept = false;
+          if (j < n_o) {
+            const float4 o = ob[j];
+            const float2 ia = oax[j];
+            const float cA = fmaf(o.z, ta, o.x), cB = fmaf(o.z, tb, o.x);
+            const float dA = fmaf(o.w, ta, o.y), dB = fmaf(o.w, tb, o.y);
+            const float uxl = (flo - fmaxf(cA, cB)) * ia.x, uxh = (fhi - fminf(cA, cB)) * ia.x;
+            const float uyl = (glo - fmaxf(dA, dB)) * ia.y, uyh = (ghi - fminf(dA, dB)) * ia.y;
+            kept = !(uxl >= 1.f || uxh <= -1.f || uyl >= 1.f || uyh <= -1.f);
+          }
+          const unsigned msk = __ballot_sync(0xffffffffu, kept);
+          if (lane == 0) keep[k] = msk;
+        }
+        __syncwarp();
+      }
+      if (valid) {
       float rvx, rvy, rax, ray;
       bound_res(vx, vy, A.vmax, rvx, rvy);
       bound_res(axx, ayy, A.amax, rax, ray);
       rmax[1] = fmaxf(rmax[1], sqrtf(rvx * rvx + rvy * rvy));
       rmax[2] = fmaxf(rmax[2], sqrtf(rax * rax + ray * ray));
-      const float tt = (float)t * pr.T / (float)(n_p - 1);
       float Rox = 0.f, Roy = 0.f, Rcx = 0.f, Rcy = 0.f;
       for (int m = 0; m < n_c; ++m) {
         const float r = A.offs[m];
         const float fx = fmaf(r, c, x), fy = fmaf(r, s, y);
         float sx = 0.f, sy = 0.f; // sum over obstacles of the circle's residuals
-        for (int j = 0; j < n_o; ++j) {
-          const float4 o = ob[j];
-          const float2 ia = oax[j]; // reciprocal inflated semi-axes
-          const float dx = fx - fmaf(o.z, tt, o.x), dy = fy - fmaf(o.w, tt, o.y);
-          const float ux = dx * ia.x, uy = dy * ia.y;
-          const float u2 = fmaf(ux, ux, uy * uy);
-          if (u2 < 1.f) { // inside: pushed out along the ray (d = 1)
-            float ex, ey;
-            if (u2 > 0.f) {
-              const float f = 1.f - 1.f / sqrtf(u2);
-              ex = dx * f;
-              ey = dy * f;
-            } else { ex = -1.f / ia.x; ey = 0.f; } // atan2(0, 0) = 0
-            rmax[0] = fmaxf(rmax[0], sqrtf(ex * ex + ey * ey));
-            sx += ex;
-            sy += ey;
+        for (int k = 0; k < n_rounds; ++k) {
+          unsigned bits = keep[k];
+          while (bits) {
+            const int j = 32 * k + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const float4 o = ob[j];
+            const float2 ia = oax[j]; // reciprocal inflated semi-axes
+            const float dx = fx - fmaf(o.z, tt, o.x), dy = fy - fmaf(o.w, tt, o.y);
+            const float ux = dx * ia.x, uy = dy * ia.y;
+            const float u2 = fmaf(ux, ux, uy * uy);
+            if (u2 < 1.f) { // inside: pushed out along the ray (d = 1)
+              float ex, ey;
+              if (u2 > 0.f) {
+                const float f = 1.f - 1.f / sqrtf(u2);
+                ex = dx * f;
+                ey = dy * f;
+              } else { ex = -1.f / ia.x; ey = 0.f; } // atan2(0, 0) = 0
+              rmax[0] = fmaxf(rmax[0], sqrtf(ex * ex + ey * ey));
+              sx += ex;
+              sy += ey;
+            }
           }
         }
         // F xi - g for the collision rows: (x + r cF) - target = e - r (c - cF)
@@ -340,6 +404,8 @@ __global__ void __launch_bounds__(FP_WARPS * 32) k_fp_solve(FpArgs A, int max_np
         acc[FP_H + kk] = fmaf(p0, Roy, fmaf(a0, ray, fmaf(d0, rvy, acc[FP_H + kk])));
         acc[FP_H + NC + kk] = fmaf(p0, qy, acc[FP_H + NC + kk]);
       }
+      } // valid
+      __syncwarp(); // the next slot rewrites the masks
     }
 #pragma unroll
     for (int e = 0; e < 44; ++e) {
@@ -461,7 +527,7 @@ struct traj_fp_batch {
   traj_fp_config cfg{};
   cudaStream_t stream = nullptr;
   std::string err;
-  int n_problems = 0, n_traj = 0, max_np = 0;
+  int n_problems = 0, n_traj = 0, max_np = 0, max_no = 0;
   bool have_problems = false, have_initial = false, have_result = false;
   FpProblemDev *d_problems = nullptr;
   float *d_tables = nullptr, *d_consts = nullptr, *d_offs = nullptr;
@@ -567,7 +633,7 @@ traj_status traj_fp_set_problems(traj_fp_batch *b, int n_problems, const int *n_
   std::vector<FpProblemDev> recs(n_problems);
   std::vector<double> psi(2 * n_problems);
   size_t tbl = 0;
-  int max_np = 0;
+  int max_np = 0, max_no = 0;
   for (int p = 0; p < n_problems; ++p) {
     if (n_steps[p] < 2 || n_steps[p] > c.max_steps) return fp_fail(b, TRAJ_ESHAPE, "n_steps out of range");
     if (!(duration[p] > 0) || !std::isfinite(duration[p])) return fp_fail(b, TRAJ_EINVAL, "bad duration");
@@ -587,6 +653,7 @@ traj_status traj_fp_set_problems(traj_fp_batch *b, int n_problems, const int *n_
     recs[p] = r;
     tbl += (size_t)3 * n_steps[p] * ROW;
     max_np = std::max(max_np, n_steps[p]);
+    max_no = std::max(max_no, r.n_o);
     psi[2 * p] = heading_start[p];
     psi[2 * p + 1] = heading_goal[p];
   }
@@ -631,6 +698,7 @@ traj_status traj_fp_set_problems(traj_fp_batch *b, int n_problems, const int *n_
   if (herr & 1) return fp_fail(b, TRAJ_EINVAL, "a problem's KKT matrix is singular");
   b->n_problems = n_problems;
   b->max_np = max_np;
+  b->max_no = max_no;
   b->have_problems = true;
   b->have_initial = false;
   b->have_result = false;
@@ -685,7 +753,10 @@ traj_status traj_fp_solve(traj_fp_batch *b, int max_iters, float tol, traj_fp_st
   A.res_out = b->d_res;
   A.iters_out = b->d_iters;
   const int max_np = b->max_np;
-  const size_t smem = sizeof(float) * FP_WARPS * WS_FLOATS;
+  A.mask_words = std::max(1, (b->max_no + 31) / 32);
+  const size_t smem = sizeof(float) * FP_WARPS * (WS_FLOATS + A.mask_words);
+  if (smem > 227 * 1024) // one 32-bit mask word per 32 obstacles of a problem, per warp
+    return fp_fail(b, TRAJ_ESHAPE, "a problem has more obstacles than the solve's shared memory covers (456 704)");
   const int grid = (b->n_traj + FP_WARPS - 1) / FP_WARPS;
   cudaStream_t s = b->stream;
   auto kern = max_np <= 64 ? k_fp_solve<2> : max_np <= 128 ? k_fp_solve<4> : k_fp_solve<8>;
