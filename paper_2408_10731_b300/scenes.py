@@ -269,6 +269,51 @@ def long_horizon(seed: int = 0, n_scenes: int = 16, inits: int = 8, n_steps=1000
                  name=f"long_horizon_{dim}d_seed{seed}")
 
 
+def grazing(seed: int = 0, n_obstacles=(1, 2, 7, 24, 63, 64, 65, 130), inits: int = 4,
+            n_steps=(33, 65, 100), dim: int = 2, noise: float = 0.02) -> Batch:
+    """Obstacles that graze the straight start->goal path: one problem per
+    (obstacle count, horizon) pair, obstacle j centred on the path at a uniform
+    fraction of it and moved sideways by its own semi-axis times U(0.9, 1.1) along
+    a random direction normal to the path (so that many grid points lie near an
+    ellipse boundary), some static, some moving along or across the path at up to
+    0.5 m/s; semi-axes U(0.2, 0.8) m, start at the origin, goal (8, 8) (3D: (8, 8,
+    2)), T = 0.1 n_p s. `inits` initialisations: the straight line plus N(0, noise)
+    on every coefficient."""
+    rng = np.random.default_rng(seed)
+    start = np.zeros(dim)
+    goal = np.array([8.0, 8.0] if dim == 2 else [8.0, 8.0, 2.0])
+    u = (goal - start) / np.linalg.norm(goal - start)
+    problems = [(int(no), int(npt)) for no in n_obstacles for npt in n_steps]
+    cen, ax, vel, offs, n_np, Ts = [], [], [], [0], [], []
+    for no, npt in problems:
+        T = 0.1 * npt
+        a = rng.uniform(0.2, 0.8, (no, dim))
+        frac = rng.uniform(0.05, 0.95, no)
+        side = rng.normal(size=(no, dim))
+        side -= (side @ u)[:, None] * u[None, :]
+        side /= np.maximum(np.linalg.norm(side, axis=1, keepdims=True), 1e-12)
+        # move by the semi-axis along the chosen direction (a point of the path then
+        # sits near the ellipse boundary)
+        reach = 1.0 / np.sqrt(((side / a) ** 2).sum(1))
+        c = start + frac[:, None] * (goal - start) + side * (reach * rng.uniform(0.9, 1.1, no))[:, None]
+        kind = rng.integers(0, 3, no)
+        speed = rng.uniform(0.0, 0.5, no)
+        v = np.where((kind == 0)[:, None], 0.0,
+                     np.where((kind == 1)[:, None], u[None, :] * speed[:, None], side * speed[:, None]))
+        c = c - v * (frac * T)[:, None]  # at the path point when the line passes it
+        cen.append(c); ax.append(a); vel.append(v)
+        offs.append(offs[-1] + no); n_np.append(npt); Ts.append(T)
+    P = len(problems)
+    line = straight_line_coeffs(start, goal)
+    xi0 = line[None] + rng.normal(0.0, noise, (P * inits, dim, N_COEFF))
+    return Batch(dim=dim, n_steps=np.array(n_np, np.int32), duration=np.array(Ts),
+                 start=np.tile(start, (P, 1)), goal=np.tile(goal, (P, 1)),
+                 offsets=np.array(offs, np.int32), centers=f32(np.concatenate(cen)),
+                 semi_axes=f32(np.concatenate(ax)), velocities=f32(np.concatenate(vel)),
+                 traj_problem=np.repeat(np.arange(P, dtype=np.int32), inits), xi0=f32(xi0),
+                 vmax=1.5, amax=2.0, name=f"grazing_seed{seed}_{dim}d")
+
+
 def config4(seed: int = 0, n_problems: int = 2048, inits: int = 8) -> Batch:
     """Uneven batch: n_o log-uniform in [4,256], n_p in {50,75,100,150}, T = 0.1 n_p."""
     rng = np.random.default_rng(seed)
