@@ -1002,6 +1002,10 @@ def run_solve(args, torch, dist, world, rank, local):
                          "peak_source": "measured FFMA microbenchmark "
                          "(traj_measure_fp32_peak), FP32 lane-ops/s",
                          "algorithmic_ops_per_launch": ops,
+                         "count": "the method's dense count: every trajectory x obstacle x grid "
+                                  "point test, including those the kernel's exact cull skips "
+                                  "(their projections are zero); ncu's FMA-pipe activity is the "
+                                  "executed share (profiles/)",
                          "mufu": {"achieved": mufu / kern_s / 1e12, "peak": mufu_peak / 1e12,
                                   "unit": "T rsqrt/s", "frac": mufu / kern_s / mufu_peak,
                                   "algorithmic_per_launch": mufu,
