@@ -302,8 +302,8 @@ traj_status traj_solve_noalloc(const traj_config *cfg, int n_problems, const int
  * honoured above the query's answer, which is conservative for these kernels, as
  * far as registers, shared memory, tensor memory and warp slots hold) and the warps
  * that share one trajectory (1, 2 or 4,
- * dividing warps_per_block: timesteps interleaved across the warps, partial
- * contractions exchanged through shared memory; FP32 form only). occupancy = 1
+ * dividing warps_per_block: the grid's 32-point blocks dealt round-robin to the
+ * warps, partial contractions exchanged through shared memory; FP32 form only). occupancy = 1
  * selects the build whose registers are capped so that more warps stay resident
  * (FP32 form: 128 registers, at most 4 warps per block; tensor-core forms: 170
  * registers, at most 6), for one warp per trajectory and horizons up to 160 grid

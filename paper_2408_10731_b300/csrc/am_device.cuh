@@ -473,11 +473,10 @@ __device__ __forceinline__ void pair_loop_culled(const float (&pos)[MAXNT][DIM],
 // Which loop a kernel runs is fixed when it is compiled. The cull's fixed cost per
 // timestep slot (the slot box's warp reductions, one record bound per lane and a
 // ballot, about 50 instructions) pays for itself where a slot's 32 lanes hold 32
-// consecutive grid points (one warp per trajectory) and the problem has more than
-// about 12 records (24 obstacles): each record a slot skips saves a packed test
-// (about 8 instructions). The timesteps of a team's warp span 32 W grid points,
-// whose box culls too little, and the long-horizon chunks serve problems with few
-// obstacles (n_o = 10 in Paper I); both run the dense loop.
+// consecutive grid points and the problem has more than about 12 records (24
+// obstacles): each record a slot skips saves a packed test (about 8 instructions).
+// The one-warp and team kernels run the culled loop; the long-horizon chunks serve
+// problems with few obstacles (n_o = 10 in Paper I) and run the dense one.
 template <int DIM, int MAXNT, bool CULL>
 __device__ __forceinline__ void pair_loop(const float (&pos)[MAXNT][DIM], const float (&tm)[MAXNT],
                                           unsigned valid, const float4 *obs, int n_o,

@@ -135,8 +135,10 @@ __device__ __noinline__ void solve_one(const SolveArgs &A, int b, const float *s
 }
 
 // ---- W warps per trajectory (W = 2 or 4) ---------------------------------------------
-// The team's warps r = 0 .. W-1 own timesteps t = W lane + r + 32 W m (interleaved,
-// so all carry the same share of a ragged horizon). Each evaluates, projects and
+// The team's warps r = 0 .. W-1 own the 32-point blocks W m + r of the grid,
+// t = 32 (W m + r) + lane: a slot holds 32 consecutive grid points, so the culled
+// pair loop bounds it as tightly as one warp's, and every warp runs at most
+// ceil(n_p / 32 W) slots, as an interleaved split would. Each evaluates, projects and
 // contracts its timesteps; the partial contractions (after each warp's
 // reduce-scatter) and the residual maxima are exchanged through double-buffered
 // shared memory with one named barrier per iteration, and every warp adds them in
@@ -197,8 +199,8 @@ __device__ __noinline__ void solve_team(const SolveArgs &A, int b, const float *
     float2 xp[DIM][6];
     broadcast_pairs<DIM>(xo, xo2, xp);
     float2 up[DIM][6];
-    project_contract<DIM, NT, false>(xp, tP, tD, tA, obs, A.problems + p, n_p, NT, pr.dt, pr.invT,
-                              pr.invT2, A.vmax, A.amax, W * lane + r, up, mo, mv, ma, 32 * W);
+    project_contract<DIM, NT, true>(xp, tP, tD, tA, obs, A.problems + p, n_p, NT, pr.dt, pr.invT,
+                                    pr.invT2, A.vmax, A.amax, 32 * r + lane, up, mo, mv, ma, 32 * W);
     float part = 0.f, part2 = 0.f;
     scatter_pairs<DIM>(up, lane, part, part2);
     mo = warp_max(mo); mv = warp_max(mv); ma = warp_max(ma);
