@@ -68,8 +68,8 @@ KERNEL_SOURCES = {
     "k_am_mixed": ("am_mixed.cu", "am_device.cuh", "internal.cuh", "tcgen05.cuh"),
 }
 MEASURED_TRAFFIC = {
-    ("k_am_fp32", "config5"): (8 * 2618112, "b59aed157e53c81c"),
-    ("k_am_mixed", "config5"): (8 * 2680832, "4bfcc853a6ebff75"),
+    ("k_am_fp32", "config5"): (8 * 2614784, "baee5c3137b7a167"),
+    ("k_am_mixed", "config5"): (8 * 2676992, "6d912bdce5370fd8"),
 }
 
 
