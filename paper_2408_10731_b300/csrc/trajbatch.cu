@@ -401,14 +401,22 @@ traj_status traj_set_initial(traj_batch *b, int n_traj, const int *traj_problem,
   for (int k = 0; k < n_traj; ++k)
     if (traj_problem[k] < 0 || traj_problem[k] >= b->n_problems)
       return fail(b, TRAJ_EINVAL, "traj_problem entry out of range");
-  // work-queue order: most expensive (n_o * n_p) first, stable
+  // work-queue order: by the number of 32-point slots (the kernels specialise their
+  // code on it), most first, so that the warps of an SM run one specialisation at a
+  // time instead of fetching several in turn; within it, most expensive (n_o * n_p)
+  // first; stable
   std::vector<int> order(n_traj);
   for (int k = 0; k < n_traj; ++k) order[k] = k;
   std::vector<long long> cost(b->n_problems);
-  for (int p = 0; p < b->n_problems; ++p)
+  std::vector<int> slots(b->n_problems);
+  for (int p = 0; p < b->n_problems; ++p) {
     cost[p] = (long long)(b->obs_offsets[p + 1] - b->obs_offsets[p] + 2) * b->n_steps[p];
+    slots[p] = (b->n_steps[p] + 31) / 32;
+  }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return cost[traj_problem[x]] > cost[traj_problem[y]];
+    const int px = traj_problem[x], py = traj_problem[y];
+    if (slots[px] != slots[py]) return slots[px] > slots[py];
+    return cost[px] > cost[py];
   });
   CK(b, cudaMemcpyAsync(b->d_xi0, coeffs0, sizeof(float) * n_traj * b->cfg.dim * NC, cudaMemcpyDefault, b->stream));
   CK(b, cudaMemcpyAsync(b->d_traj_problem, traj_problem, sizeof(int) * n_traj, cudaMemcpyHostToDevice, b->stream));
