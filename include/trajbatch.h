@@ -246,8 +246,14 @@ traj_status traj_set_state(traj_batch *b, const float *coeffs, const float *lamb
  *  - every trajectory's coefficients are re-expressed on the shifted window
  *    [delta, delta + T] (the same polynomial, extrapolated past its old end) and
  *    become the next initial iterate; the multipliers lambda are kept as they are;
- *  - the FP64 set-up (KKT inverse, constants) is formed again for the moved
- *    problems (synchronises).
+ *  - the constants that depend on the boundary values (K12 b and the tracking term
+ *    K11 q, eq. Q_matrix) are formed again in FP64; the KKT inverse itself (which the
+ *    shift leaves as it was: same n_p, T, obstacle count, rho and bounds) is not.
+ *    The first shift after traj_set_problems, traj_set_obstacles,
+ *    traj_set_rho_schedule or traj_set_workspace runs the full FP64 set-up once more
+ *    and keeps its FP64 blocks (allocated then: 1.5 KB per problem and penalty
+ *    level; TRAJ_ENOMEM if that fails) and synchronises; later shifts only launch
+ *    the obstacle packing and the boundary update, asynchronously.
  * The next traj_solve projects the shifted iterate, so u is formed for the moved
  * problem, with lambda0 = the carried multipliers instead of 0, then iterates as
  * usual (iters counts from 0). traj_set_initial returns to fresh starts and

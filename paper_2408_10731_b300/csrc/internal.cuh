@@ -138,10 +138,26 @@ cudaError_t launch_setup_tables(const int *d_horizons, const int *d_offsets, int
                                 float *d_tables, cudaStream_t s);
 // d_start_va [n_problems][2][dim]: start velocity and acceleration of the boundary rows
 // (NULL: at rest)
+// kkt_out (nullable): per problem p, FP64 K11 [11][11], K12 [11][4] and the basis
+// moments m0 = sum_t P_t (1 - tau_t), m1 = sum_t P_t tau_t [11] each, at
+// kkt_out + p * kkt_stride (KKT64_DOUBLES doubles), so that a change of the boundary
+// values alone (launch_setup_boundary) need not form and invert K again.
+constexpr int KKT64_DOUBLES = NC * NC + NC * NE + 2 * NC; // 187
 cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const double *d_T,
                                   const double *d_start, const double *d_goal,
                                   const double *d_start_va, int dim, double rho, double w_smooth,
                                   double w_track, int cost_mode, int max_np, float *d_constants,
+                                  cudaStream_t s, double *kkt_out = nullptr, size_t kkt_stride = 0);
+// The boundary-dependent constants alone (hq and c of the smoothness/tracking cost, eq.
+// Q_matrix's q = -w_t P^T x_des with x_des the start -> goal line, and K12 b with b =
+// (start, v0, a0, goal)) of every problem and penalty level, from the FP64 blocks that
+// launch_setup_problems stored: after a receding-horizon shift, which moves the start
+// state but leaves the KKT matrix (n_p, T, n_o, rho) unchanged. Level l of problem p:
+// kkt64 + (p * levels + l) * KKT64_DOUBLES, constants + p * CONST_FLOATS * levels +
+// l * CONST_FLOATS.
+cudaError_t launch_setup_boundary(int n_problems, int levels, const double *d_start,
+                                  const double *d_goal, const double *d_start_va, int dim,
+                                  double w_track, const double *kkt64, float *d_constants,
                                   cudaStream_t s);
 // Receding-horizon step (mpc.cu): executed [n_problems] device indices (or NULL: per
 // problem the trajectory with the smallest worst residual, chosen into exec_scratch);

@@ -48,7 +48,7 @@ static_assert(NC * NC + 3 * NC <= SETUP_THREADS, "one Gram / q element per threa
 __global__ void __launch_bounds__(SETUP_THREADS)
 k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
                  const double *goal, const double *start_va, int dim, double rho, double w_s,
-                 double w_t, int cost_mode, float *constants) {
+                 double w_t, int cost_mode, float *constants, double *kkt_out, size_t kkt_stride) {
   extern __shared__ double sm[];
   __shared__ double Q[NC * NC], M[NC * NC], qv[3 * NC];
   __shared__ double W[NK * 2 * NK];
@@ -70,7 +70,7 @@ k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
   const int qk = qrow ? el - NC * NC : 0, qax = qk / NC, qi = qk % NC;
   const double s0 = qrow && qax < dim ? start[p * dim + qax] : 0.0;
   const double g0 = qrow && qax < dim ? goal[p * dim + qax] : 0.0;
-  double pp = 0, dd = 0, aa = 0, sq = 0;
+  double pp = 0, dd = 0, aa = 0, sq = 0, mo0 = 0, mo1 = 0; // mo0 / mo1: basis moments
   for (int c0 = 0; c0 < n_p; c0 += CH) {
     const int nc = n_p - c0 < CH ? n_p - c0 : CH;
     __syncthreads(); // the previous chunk has been read
@@ -102,6 +102,8 @@ k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
       for (int t = 0; t < nc; ++t) {
         double tau = (double)(c0 + t) / (double)(n_p - 1);
         sq += P[t * NC + qi] * (s0 + (g0 - s0) * tau);
+        mo0 += P[t * NC + qi] * (1.0 - tau);
+        mo1 += P[t * NC + qi] * tau;
       }
     }
   }
@@ -201,6 +203,46 @@ k_setup_problems(ProblemDev *problems, const double *Tarr, const double *start,
     split_store(&C[C_HQ_HI + e], &C[C_HQ_LO + e], hq);
     split_store(&C[C_C_HI + e], &C[C_C_LO + e], cval);
   }
+  if (kkt_out) { // the blocks a boundary-only update needs (launch_setup_boundary)
+    double *K = kkt_out + (size_t)p * kkt_stride;
+    for (int e = threadIdx.x; e < NC * NC + NC * NE; e += blockDim.x)
+      K[e] = e < NC * NC ? K11[e] : K12[e - NC * NC];
+    if (qrow && qax == 0) {
+      K[NC * NC + NC * NE + qi] = mo0;
+      K[NC * NC + NC * NE + NC + qi] = mo1;
+    }
+  }
+}
+
+// One thread per (problem, level, constants entry of the hq / c blocks): hq and c from
+// the stored FP64 blocks, in the full set-up's order of operations except q, which is
+// formed from the basis moments (q_i = -w_t (s0 m0_i + g0 m1_i), the same sum
+// regrouped).
+__global__ void k_setup_boundary(int n_problems, int levels, const double *start,
+                                 const double *goal, const double *start_va, int dim,
+                                 double w_t, const double *kkt64, float *constants) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)n_problems * levels * 3 * ROW;
+  if (id >= total) return;
+  const int e = (int)(id % (3 * ROW));
+  const long long pl = id / (3 * ROW);
+  const int l = (int)(pl % levels), p = (int)(pl / levels);
+  const double *K = kkt64 + (size_t)pl * KKT64_DOUBLES;
+  const double *K11 = K, *K12 = K + NC * NC, *m0 = K12 + NC * NE, *m1 = m0 + NC;
+  float *C = constants + (size_t)p * CONST_FLOATS * levels + (size_t)l * CONST_FLOATS;
+  const int ax = e / ROW, i = e % ROW;
+  double cval = 0, hq = 0;
+  if (ax < dim && i < NC) {
+    const double s0 = start[p * dim + ax], g0 = goal[p * dim + ax];
+    const double v0 = start_va ? start_va[(p * 2 + 0) * dim + ax] : 0.0;
+    const double a0 = start_va ? start_va[(p * 2 + 1) * dim + ax] : 0.0;
+    const double bb[NE] = {s0, v0, a0, g0};
+    for (int k = 0; k < NE; ++k) cval += K12[i * NE + k] * bb[k];
+    hq = cval;
+    for (int k = 0; k < NC; ++k) hq += K11[i * NC + k] * (w_t * (s0 * m0[k] + g0 * m1[k]));
+  }
+  split_store(&C[C_HQ_HI + e], &C[C_HQ_LO + e], hq);
+  split_store(&C[C_C_HI + e], &C[C_C_LO + e], cval);
 }
 
 // One thread per half of a pair record (see the layout in internal.cuh): problem p
@@ -255,7 +297,8 @@ cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const 
                                   const double *d_start, const double *d_goal,
                                   const double *d_start_va, int dim,
                                   double rho, double w_smooth, double w_track, int cost_mode,
-                                  int max_np, float *d_constants, cudaStream_t s) {
+                                  int max_np, float *d_constants, cudaStream_t s, double *kkt_out,
+                                  size_t kkt_stride) {
   if (n_problems <= 0) return cudaSuccess;
   const int ch = max_np < SETUP_CHUNK ? max_np : SETUP_CHUNK;
   size_t smem = sizeof(double) * 3 * (size_t)ch * NC;
@@ -264,7 +307,19 @@ cudaError_t launch_setup_problems(ProblemDev *d_problems, int n_problems, const 
   if (e != cudaSuccess) return e;
   k_setup_problems<<<n_problems, SETUP_THREADS, smem, s>>>(d_problems, d_T, d_start, d_goal,
                                                            d_start_va, dim, rho, w_smooth, w_track,
-                                                           cost_mode, d_constants);
+                                                           cost_mode, d_constants, kkt_out,
+                                                           kkt_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_boundary(int n_problems, int levels, const double *d_start,
+                                  const double *d_goal, const double *d_start_va, int dim,
+                                  double w_track, const double *kkt64, float *d_constants,
+                                  cudaStream_t s) {
+  if (n_problems <= 0 || levels <= 0) return cudaSuccess;
+  const long long total = (long long)n_problems * levels * 3 * ROW;
+  k_setup_boundary<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      n_problems, levels, d_start, d_goal, d_start_va, dim, w_track, kkt64, d_constants);
   return cudaGetLastError();
 }
 

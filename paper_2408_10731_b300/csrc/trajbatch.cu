@@ -35,6 +35,12 @@ struct traj_batch {
   unsigned long long *d_sig = nullptr;        // homotopy signatures [B]
   float *d_constants = nullptr;
   int const_levels = 1;                       // constants blocks allocated per problem
+  // FP64 K11, K12 and basis moments per problem and level (receding-horizon shifts:
+  // allocated at the first one; valid while the problems, obstacles, penalties and
+  // workspace bounds stay as they were set up)
+  double *d_kkt64 = nullptr;
+  size_t kkt64_cap = 0;
+  bool kkt_valid = false;
   // penalty continuation (traj_set_rho_schedule): levels, growth per level, switch period
   int rho_levels = 1, rho_every = 0;
   double rho_growth = 1.0;
@@ -115,7 +121,7 @@ static void free_all(traj_batch *b) {
                   b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_index,
                   b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res, b->d_lam0, b->d_u0,
                   b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0, b->d_L, b->d_r,
-                  b->d_caug, b->d_proj, b->d_elite, b->d_sflag};
+                  b->d_caug, b->d_proj, b->d_elite, b->d_sflag, b->d_kkt64};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (b->ev0) cudaEventDestroy(b->ev0);
@@ -275,6 +281,7 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
   b->n_steps.assign(n_steps, n_steps + n_problems);
   b->duration.assign(duration, duration + n_problems);
   b->n_problems = n_problems;
+  b->kkt_valid = false; // new problems: the next shift sets up in full
   b->max_np_used = max_np;
   b->have_problems = true;
   invalidate_graph(b);
@@ -289,8 +296,21 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
 // Upload the problem records (constants offsets for the current number of penalty
 // levels), pack the staged obstacles into pair records (which also flags bad
 // obstacle data) and form the FP64 set-up of every penalty level; synchronises.
-static traj_status upload_problems(traj_batch *b) {
+// keep_kkt: also store the FP64 blocks that later boundary-only updates
+// (traj_shift_horizon) start from
+static traj_status upload_problems(traj_batch *b, bool keep_kkt = false) {
   const int P = b->n_problems, D = b->cfg.dim, N = b->n_obs, L = b->rho_levels;
+  b->kkt_valid = false;
+  if (keep_kkt && b->kkt64_cap < (size_t)P * L * KKT64_DOUBLES) {
+    CK(b, cudaStreamSynchronize(b->stream));
+    if (b->d_kkt64) cudaFree(b->d_kkt64);
+    b->d_kkt64 = nullptr;
+    b->kkt64_cap = 0;
+    cudaError_t e = dalloc(&b->d_kkt64, (size_t)P * L * KKT64_DOUBLES);
+    if (e != cudaSuccess) return fail(b, e == cudaErrorMemoryAllocation ? TRAJ_ENOMEM : TRAJ_ECUDA,
+                                      std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    b->kkt64_cap = (size_t)P * L * KKT64_DOUBLES;
+  }
   const bool box = !b->box_lo.empty();
   for (int p = 0; p < P; ++p) {
     b->recs[p].const_off = p * CONST_FLOATS * L;
@@ -314,8 +334,25 @@ static traj_status upload_problems(traj_batch *b) {
     CK(b, launch_setup_problems(b->d_problems, P, b->d_T, b->d_start, b->d_goal, b->d_start_va, D,
                                 b->cfg.rho * std::pow(b->rho_growth, (double)l), b->cfg.w_smooth,
                                 b->cfg.w_track, b->cfg.cost_mode, b->max_np_used,
-                                b->d_constants + (size_t)l * CONST_FLOATS, b->stream));
+                                b->d_constants + (size_t)l * CONST_FLOATS, b->stream,
+                                keep_kkt ? b->d_kkt64 + (size_t)l * KKT64_DOUBLES : nullptr,
+                                (size_t)L * KKT64_DOUBLES));
   CK(b, cudaStreamSynchronize(b->stream));
+  b->kkt_valid = keep_kkt;
+  return TRAJ_OK;
+}
+
+// After a receding-horizon shift with the FP64 blocks at hand: the moved obstacles
+// re-packed, and only the boundary-dependent constants (hq, c) of every level
+// recomputed; the KKT matrix (n_p, T, n_o, rho, bounds) is the one set up before.
+static traj_status shift_boundary(traj_batch *b) {
+  const int P = b->n_problems, D = b->cfg.dim, N = b->n_obs, L = b->rho_levels;
+  const float *st_c = b->d_obs_stage, *st_a = st_c + (size_t)N * D, *st_v = st_a + (size_t)N * D;
+  const int *index = b->pair_index.data();
+  CK(b, launch_pack_obstacles(D, P, 2 * index[2 * P + 1], b->d_obs_index, b->d_obs_index + P + 1,
+                              st_c, st_a, st_v, b->d_obs, b->d_problems, b->stream));
+  CK(b, launch_setup_boundary(P, L, b->d_start, b->d_goal, b->d_start_va, D, b->cfg.w_track,
+                              b->d_kkt64, b->d_constants, b->stream));
   return TRAJ_OK;
 }
 
@@ -739,7 +776,10 @@ traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed)
   a.centers = b->d_obs_stage;
   a.velocities = b->d_obs_stage + (size_t)2 * b->n_obs * b->cfg.dim;
   CK(b, launch_mpc_shift(a, b->stream));
-  traj_status rs = upload_problems(b); // re-pack the moved obstacles, FP64 set-up of every level
+  // re-pack the moved obstacles and set up the new boundary values: the first shift
+  // after a set-up runs the FP64 set-up of every level and keeps its blocks, later ones
+  // recompute the boundary-dependent constants from them
+  traj_status rs = b->kkt_valid ? shift_boundary(b) : upload_problems(b, true);
   if (rs != TRAJ_OK) return rs;
   if (!b->carry || b->resume) {
     b->carry = true;
