@@ -24,12 +24,14 @@
 namespace tb {
 
 // Coefficient i of the polynomial with coefficients c re-expressed on [f, 1 + f].
-__device__ double blossom_shift(const double (&c)[NC], int i, double f) {
+__device__ __forceinline__ double blossom_shift(const double (&c)[NC], int i, double f) {
   double w[NC];
 #pragma unroll
   for (int j = 0; j < NC; ++j) w[j] = c[j];
+#pragma unroll
   for (int r = 1; r < NC; ++r) {
     const double u = r <= NC - 1 - i ? f : 1.0 + f;
+#pragma unroll
     for (int j = 0; j < NC - r; ++j) w[j] = fma(u, w[j + 1] - w[j], w[j]);
   }
   return w[0];
@@ -56,20 +58,19 @@ __global__ void k_exec_index(int n_problems, const unsigned long long *key, int 
   if (p < n_problems) exec[p] = key[p] == ~0ull ? -1 : (int)(unsigned)(key[p] & 0xffffffffull);
 }
 
-// One thread per (trajectory, axis): xi0 = shifted xi, lam0 = lam.
+// One thread per (trajectory, axis, coefficient): xi0 = shifted xi, lam0 = lam.
 __global__ void k_shift_traj(ShiftArgs a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.n_traj * a.dim) return;
-  const int b = e / a.dim;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; // (trajectory, axis, i)
+  if (e >= (long long)a.n_traj * a.dim * NC) return;
+  const long long row = e / NC;
+  const int i = (int)(e - row * NC), b = (int)(row / a.dim);
   const double f = a.delta / a.T[a.traj_problem[b]];
-  const float *x = a.xi + (size_t)e * NC;
+  const float *x = a.xi + (size_t)row * NC;
   double c[NC];
 #pragma unroll
   for (int j = 0; j < NC; ++j) c[j] = (double)x[j];
-  for (int i = 0; i < NC; ++i) {
-    a.xi0[(size_t)e * NC + i] = (float)blossom_shift(c, i, f);
-    a.lam0[(size_t)e * NC + i] = a.lam[(size_t)e * NC + i];
-  }
+  a.xi0[e] = (float)blossom_shift(c, i, f);
+  a.lam0[e] = a.lam[e];
 }
 
 // One thread per (problem, axis): the executed plan's state at delta becomes the start.
@@ -109,7 +110,8 @@ cudaError_t launch_mpc_shift(const ShiftArgs &a, cudaStream_t s) {
     exec = a.exec_scratch;
   }
   k_shift_start<<<(a.n_problems * a.dim + 127) / 128, 128, 0, s>>>(a, exec);
-  k_shift_traj<<<(a.n_traj * a.dim + 127) / 128, 128, 0, s>>>(a);
+  const long long n_coef = (long long)a.n_traj * a.dim * NC;
+  k_shift_traj<<<(unsigned)((n_coef + 127) / 128), 128, 0, s>>>(a);
   if (a.n_obs > 0) k_shift_obstacles<<<(a.n_obs * a.dim + 255) / 256, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
