@@ -396,6 +396,9 @@ def run_priest(args, torch):
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 2e12,
                          "unit": "Top/s", "frac": achieved / (fp32_peak / 2.0), "traffic": None,
                          "kernel": kernel_name("fp32", shape) + " (3D, projection mode; whole run timed)",
+                         "count": "the method's dense count: every sample x sphere x grid point "
+                                  "test, including those the kernel's exact cull skips (their "
+                                  "projections are zero)",
                          "peak_source": "measured FFMA microbenchmark (traj_measure_fp32_peak), "
                                         "FP32 lane-ops/s",
                          "algorithmic_ops_per_run": ops}}

@@ -114,13 +114,15 @@ __global__ void k_sample(const float *mu, const float *L, int D, int B, int Bg, 
 // c_1 = sum_t ||p''||^2 + w_curv c_kappa + w_path c_p on the grid (PRIEST's BARN cost):
 // c_kappa = ||p' x p''||^2 / ||p'||^6, the squared curvature (0 below a speed of 1e-3 m/s),
 // c_p = distance of p(t) from its projection onto the segment start -> goal of the
-// problem (start, goal: FP64 [dim]).
+// problem (start, goal: FP64 [dim]). One warp per sample: the lanes take the grid
+// points t = lane + 32 m and the warp sums their terms (butterfly order).
 __global__ void k_cost(const float *xi, const float *res, const float *tables, int tbl_off,
                        int n_p, float invT, float invT2, int dim, int B, float w_r, float w_curv,
                        float w_path, const double *start, const double *goal, float *r_out,
                        float *caug_out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B) return;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= B) return; // whole warps
   const float *tP = tables + tbl_off, *tD = tP + n_p * ROW, *tA = tD + n_p * ROW;
   float sv[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f};
   for (int a = 0; a < dim; ++a) {
@@ -129,16 +131,23 @@ __global__ void k_cost(const float *xi, const float *res, const float *tables, i
   }
   float L2 = 0.f;
   for (int a = 0; a < dim; ++a) L2 = fmaf(gv[a], gv[a], L2);
+  float x[3][NC];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) x[a][k] = a < dim ? xi[((size_t)i * dim + a) * NC + k] : 0.f;
   float c1 = 0.f;
-  for (int t = 0; t < n_p; ++t) {
+  for (int t = lane; t < n_p; t += 32) {
     float pos[3] = {0.f, 0.f, 0.f}, vel[3] = {0.f, 0.f, 0.f}, acc[3] = {0.f, 0.f, 0.f};
-    for (int a = 0; a < dim; ++a) {
-      const float *x = xi + ((size_t)i * dim + a) * NC;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= dim) break;
       float sp = 0.f, sd = 0.f, sa = 0.f;
+#pragma unroll
       for (int k = 0; k < NC; ++k) {
-        sp = fmaf(tP[t * ROW + k], x[k], sp);
-        sd = fmaf(tD[t * ROW + k], x[k], sd);
-        sa = fmaf(tA[t * ROW + k], x[k], sa);
+        sp = fmaf(tP[t * ROW + k], x[a][k], sp);
+        sd = fmaf(tD[t * ROW + k], x[a][k], sd);
+        sa = fmaf(tA[t * ROW + k], x[a][k], sa);
       }
       pos[a] = sp; vel[a] = sd * invT; acc[a] = sa * invT2;
     }
@@ -166,10 +175,14 @@ __global__ void k_cost(const float *xi, const float *res, const float *tables, i
     }
     c1 += c;
   }
-  float r = fmaxf(res[i * 3 + 0], fmaxf(res[i * 3 + 1], res[i * 3 + 2]));
-  if (!(r == r)) r = __int_as_float(0x7f800000); // NaN ranks last
-  r_out[i] = r;
-  caug_out[i] = c1 + w_r * r;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+  if (lane == 0) {
+    float r = fmaxf(res[i * 3 + 0], fmaxf(res[i * 3 + 1], res[i * 3 + 2]));
+    if (!(r == r)) r = __int_as_float(0x7f800000); // NaN ranks last
+    r_out[i] = r;
+    caug_out[i] = c1 + w_r * r;
+  }
 }
 
 // Ascending bitonic sort of (key, index) pairs in shared memory; ties by index.
@@ -223,10 +236,14 @@ __global__ void k_select(const float *r, const float *caug, int B, int n_proj, i
 }
 
 // Weighted refit (eqs. update_mean, update_covariance) and the best elite. One CTA
-// per group g = blockIdx.x of Bg samples.
+// per group g = blockIdx.x of Bg samples. stage: the elites' coefficients are first
+// copied to dynamic shared memory ([n_elite][D]), so that the sums over the elites read
+// them there (same order of operations either way).
 __global__ void k_refit(const float *xi, const float *caug, const int *elite, int Bg, int n_elite,
-                        int D, float gamma, float sig, float *mu, float *sigma, float *best) {
+                        int D, float gamma, float sig, float *mu, float *sigma, float *best,
+                        int stage) {
   __shared__ float w_s[8192];
+  extern __shared__ float xs[];
   const size_t g = blockIdx.x;
   xi += g * Bg * D;
   caug += g * Bg;
@@ -248,9 +265,15 @@ __global__ void k_refit(const float *xi, const float *caug, const int *elite, in
   __syncthreads();
   float S = 0.f;
   for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) S += red[k];
+  if (stage) {
+    for (int e = threadIdx.x; e < n_elite * D; e += blockDim.x)
+      xs[e] = xi[(size_t)elite[e / D] * D + e % D];
+    __syncthreads();
+  }
   for (int d = threadIdx.x; d < D; d += blockDim.x) {
     float s = 0.f;
-    for (int m = 0; m < n_elite; ++m) s = fmaf(w_s[m], xi[(size_t)elite[m] * D + d], s);
+    for (int m = 0; m < n_elite; ++m)
+      s = fmaf(w_s[m], stage ? xs[m * D + d] : xi[(size_t)elite[m] * D + d], s);
     mu_new[d] = (1.f - sig) * mu[d] + sig * (s / S);
   }
   __syncthreads();
@@ -258,7 +281,7 @@ __global__ void k_refit(const float *xi, const float *caug, const int *elite, in
     const int i = e / D, j = e % D;
     float s = 0.f;
     for (int m = 0; m < n_elite; ++m) {
-      const float *x = xi + (size_t)elite[m] * D;
+      const float *x = stage ? xs + m * D : xi + (size_t)elite[m] * D;
       s = fmaf(w_s[m] * (x[i] - mu_new[i]), x[j] - mu_new[j], s);
     }
     sigma[e] = (1.f - sig) * sigma[e] + sig * (s / S);
@@ -316,7 +339,8 @@ cudaError_t launch_sampler_back(const float *xi, const float *res, const float *
                                 float gamma, float sig, float *r_out, float *caug_out,
                                 int *proj_idx, int *elite_idx, float *mu, float *sigma,
                                 float *best, cudaStream_t s) {
-  k_cost<<<(B + 127) / 128, 128, 0, s>>>(xi, res, tables, tbl_off, n_p, invT, invT2, dim, B,
+  k_cost<<<(unsigned)(((long long)B * 32 + 255) / 256), 256, 0, s>>>(xi, res, tables, tbl_off, n_p,
+                                                                     invT, invT2, dim, B,
                                          cost.w_res, cost.w_curv, cost.w_path, cost.start,
                                          cost.goal, r_out, caug_out);
   cudaError_t e = cudaGetLastError();
@@ -329,8 +353,14 @@ cudaError_t launch_sampler_back(const float *xi, const float *res, const float *
   if (e != cudaSuccess) return e;
   k_select<<<n_dist, 1024, smem, s>>>(r_out, caug_out, Bg, n_proj, n_elite, proj_idx, elite_idx);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_refit<<<n_dist, 1024, 0, s>>>(xi, caug_out, elite_idx, Bg, n_elite, dim * NC, gamma, sig, mu,
-                                  sigma, best);
+  // the elites' coefficients in shared memory when they fit beside the 32 KB of weights
+  const size_t xs_bytes = sizeof(float) * (size_t)n_elite * dim * NC;
+  const int stage = xs_bytes <= 160 * 1024 ? 1 : 0;
+  if (stage && (e = cudaFuncSetAttribute(k_refit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)xs_bytes)) != cudaSuccess)
+    return e;
+  k_refit<<<n_dist, 1024, stage ? xs_bytes : 0, s>>>(xi, caug_out, elite_idx, Bg, n_elite, dim * NC,
+                                                     gamma, sig, mu, sigma, best, stage);
   return cudaGetLastError();
 }
 
