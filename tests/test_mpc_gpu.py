@@ -57,6 +57,42 @@ def test_three_receding_calls_of_ten_iterations_match_the_oracle():
         h.close()
 
 
+def test_new_obstacles_between_shifts_set_the_problems_up_again():
+    """A shift keeps each problem's KKT inverse and forms again only the constants that
+    depend on the boundary values; new obstacles (here a different number per scene,
+    which changes F^T F) must make the next shift set the problems up in full. Four
+    control loops; after the second shift the obstacles are replaced before its solve,
+    so the third shift starts from the new ones: every loop against the oracle's step
+    from the GPU's own state."""
+    import dataclasses
+    b = scenes.config2(7, n_scenes=4, inits=4)
+    new = scenes.config2(8, n_scenes=4, inits=4, n_obstacles=30)
+    executed = np.arange(b.n_problems) * 4 + 2
+    delta = 0.25
+    h = _handle(b)
+    try:
+        h.solve(30, -1.0)
+        g = h.get_trajectories()
+        cur = b
+        for step in range(4):
+            xi_g = g["xi"].astype(np.float64)
+            lam_g = h.get_state()["lam"].astype(np.float64)
+            h.shift_horizon(delta, executed)
+            moved, va, xi0, lam0 = mpc.mpc_step(cur, xi_g, lam_g, executed, delta)
+            if step == 1:  # fresh obstacle data, 30 instead of 50 per scene
+                h.set_obstacles(new.offsets, new.centers, new.semi_axes, new.velocities)
+                moved = dataclasses.replace(moved, offsets=new.offsets, centers=new.centers,
+                                            semi_axes=new.semi_axes, velocities=new.velocities)
+            h.solve(10, -1.0)
+            g = h.get_trajectories()
+            o = am.solve(moved, 10, xi0=xi0, start_va=va, lam0=lam0, want_lambda=True)
+            err = position_error(moved, g["xi"], o["xi"])
+            assert err.max() <= POS_TOL, (step, err.max())
+            cur = moved
+    finally:
+        h.close()
+
+
 def test_default_executed_plan_is_the_smallest_worst_residual():
     b = scenes.config2(6, n_scenes=5, inits=6)
     h1, h2 = _handle(b), _handle(b)
