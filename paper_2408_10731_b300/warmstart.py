@@ -188,14 +188,22 @@ class WarmStart:
         self.set_state(p, m, v, step)
         return meta
 
-    def features(self, batch):
-        """BF16 features [P, 400] and straight-line coefficients [P, 22] (CUDA tensors)."""
+    def features(self, batch, host=None):
+        """BF16 features [P, 400] and straight-line coefficients [P, 22] (CUDA tensors).
+        host: optional FP32 CPU tensors (pinned for asynchronous copies) holding the
+        batch's "centers", "semi_axes" and "velocities", copied to the device on the
+        current stream instead of the batch's numpy arrays."""
         torch = self.torch
         P = batch.n_problems
         dev = torch.device("cuda")
-        cen = torch.as_tensor(batch.centers, dtype=torch.float32, device=dev).contiguous()
-        ax = torch.as_tensor(batch.semi_axes, dtype=torch.float32, device=dev).contiguous()
-        vel = torch.as_tensor(batch.velocities, dtype=torch.float32, device=dev).contiguous()
+        if host is not None:  # copied on the handle's stream, ahead of the features kernel
+            with torch.cuda.stream(torch.cuda.ExternalStream(self.stream)):
+                cen, ax, vel = (host[k].to(dev, non_blocking=True)
+                                for k in ("centers", "semi_axes", "velocities"))
+        else:
+            cen = torch.as_tensor(batch.centers, dtype=torch.float32, device=dev).contiguous()
+            ax = torch.as_tensor(batch.semi_axes, dtype=torch.float32, device=dev).contiguous()
+            vel = torch.as_tensor(batch.velocities, dtype=torch.float32, device=dev).contiguous()
         X = torch.zeros(P, IN_PAD, dtype=torch.bfloat16, device=dev)
         line = torch.zeros(P, D22, dtype=torch.float32, device=dev)
         st = np.ascontiguousarray(batch.start, np.float64)
