@@ -77,32 +77,40 @@ __global__ void k_cholesky(const float *sigma, int D, float eps, float *L, int *
 // xi_i = mu_g + L_g z_i for sample i of group g = i / Bg. z from `z` ([B][D]) or,
 // when z == nullptr, Philox with counter (i, iteration, pair, 0) and key (seed lo,
 // seed hi); Box-Muller pairs.
+// One warp per sample (SAMPLE_WARPS per block): the lanes share its Philox calls (lane l
+// takes the call of counter q = 2 l), then its output rows (d = lane, lane + 32),
+// each row summed in the same order as a single thread would.
+constexpr int SAMPLE_WARPS = 4;
 __global__ void k_sample(const float *mu, const float *L, int D, int B, int Bg, const float *z,
                          unsigned long long seed, int iteration, float *xi0, float *samples_out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B) return;
+  __shared__ float zs[SAMPLE_WARPS][48];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * SAMPLE_WARPS + w;
+  if (i >= B) return; // whole warps
   const int g = i / Bg;
   mu += (size_t)g * D;
   L += (size_t)g * D * D;
-  float zz[48];
+  float *zz = zs[w];
   if (z) {
-    for (int d = 0; d < D; ++d) zz[d] = z[(size_t)i * D + d];
+    for (int d = lane; d < D; d += 32) zz[d] = z[(size_t)i * D + d];
   } else {
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    for (int q = 0; 2 * q < D; q += 2) { // one Philox call -> two Box-Muller pairs
+    const int q = 2 * lane; // one Philox call -> two Box-Muller pairs
+    if (2 * q < D) {
       const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)iteration, (uint32_t)q, 0u), key);
-      const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+      const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
       for (int h = 0; h < 2; ++h) {
-        const float rad = sqrtf(-2.f * logf(u01(w[2 * h])));
+        const float rad = sqrtf(-2.f * logf(u01(wv[2 * h])));
         float sn, cs;
-        sincospif(2.f * u01(w[2 * h + 1]), &sn, &cs);
+        sincospif(2.f * u01(wv[2 * h + 1]), &sn, &cs);
         const int d0 = 2 * (q + h);
         if (d0 < D) zz[d0] = rad * cs;
         if (d0 + 1 < D) zz[d0 + 1] = rad * sn;
       }
     }
   }
-  for (int d = 0; d < D; ++d) {
+  __syncwarp();
+  for (int d = lane; d < D; d += 32) {
     float s = mu[d];
     for (int k = 0; k <= d; ++k) s = fmaf(L[d * D + k], zz[k], s);
     xi0[(size_t)i * D + d] = s;
@@ -328,8 +336,8 @@ cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int
   k_cholesky<<<n_dist, 64, 0, s>>>(sigma, D, eps, L_scratch, flag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sample<<<(B + 127) / 128, 128, 0, s>>>(mu, L_scratch, D, B, B / n_dist, z, seed, iteration, xi0,
-                                           samples_out);
+  k_sample<<<(B + SAMPLE_WARPS - 1) / SAMPLE_WARPS, 32 * SAMPLE_WARPS, 0, s>>>(
+      mu, L_scratch, D, B, B / n_dist, z, seed, iteration, xi0, samples_out);
   return cudaGetLastError();
 }
 
