@@ -362,7 +362,7 @@ def run_priest(args, torch):
     dpriest = {"ms_per_run": float(np.mean(msd)), "distributions": nd, "samples_per_distribution": 1024,
                "best_cost_aug": [float(x) for x in bests[:, D].cpu()],
                "cost": "sum_t ||p''||^2 + 0.05 curvature^2 + 0.5 path distance + residual",
-               "launches_per_run": c3["n_outer"] * 6}
+               "launches_per_run": c3["n_outer"] * 8}
     # PRIEST's workspace bounds (the 20 x 20 x 5 m box of the scene) as extra rows of F
     h.set_workspace([[0.0, 0.0, 0.0]], [[20.0, 20.0, 5.0]])
     for _ in range(args.warmup):
@@ -391,7 +391,7 @@ def run_priest(args, torch):
             "config": {"workload": "3D: 256 spheres r~U(0.1,0.3) on 12 box surfaces in 20x20x5 m, "
                                    "n_p=100 over 20 s, B=4096, N_proj=2991, N_elite=410, gamma 1, "
                                    "sigma_lr 0.5", "launch_shape": shape},
-            "best_cost_aug": bc, "gpu_launches_per_step": c3["n_outer"] * 6, "clocks": clocks,
+            "best_cost_aug": bc, "gpu_launches_per_step": c3["n_outer"] * 8, "clocks": clocks,
             "forms": {"d_priest_barn": dpriest, "workspace_bounds": wsb},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 2e12,
                          "unit": "Top/s", "frac": achieved / (fp32_peak / 2.0), "traffic": None,

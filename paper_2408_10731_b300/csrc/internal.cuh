@@ -219,6 +219,9 @@ cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int
                                  cudaStream_t s);
 // cost terms: c_aug = sum_t (||p''||^2 + w_curv c_kappa + w_path c_p) + w_res r, with the
 // path from start to goal (device FP64 [dim])
+// refit_scratch: 2 * n_dist * ((n_elite * D + 3) & ~3) + n_dist * (D + 1) floats, 16-byte
+// aligned (the elites' weighted and centred coefficients, and the refit's new means and
+// weight sums).
 struct SamplerCost {
   float w_res, w_curv, w_path;
   const double *start, *goal;
@@ -227,8 +230,8 @@ cudaError_t launch_sampler_back(const float *xi, const float *res, const float *
                                 int tbl_off, int n_p, float invT, float invT2, int dim, int B,
                                 int n_dist, const SamplerCost &cost, int n_proj, int n_elite,
                                 float gamma, float sig, float *r_out, float *caug_out,
-                                int *proj_idx, int *elite_idx, float *mu, float *sigma,
-                                float *best, cudaStream_t s);
+                                int *proj_idx, int *elite_idx, float *refit_scratch, float *mu,
+                                float *sigma, float *best, cudaStream_t s);
 // tcgen05 BF16 GEMM C = A B^T (gemm_tc.cu); epi: 0 FP32 store, 1 bias+GELU (Z f32 and
 // GELU(Z) bf16), 2 bias FP32, 3 C * GELU'(aux) -> bf16.
 cudaError_t launch_gemm_bf16(int epi, const void *A, const void *B, int M, int N, int K,

@@ -11,15 +11,17 @@
 //      cost c_aug = c_1 + w_r r with c_1 = sum_t ||p''(t)||^2 (Algorithm 3), plus
 //      optional curvature and path-distance terms (the BARN cost of Section 5);
 //   4. ConstraintEliteSet: the N_proj lowest r; EliteSet: the N_elite lowest
-//      c_aug among them (deterministic bitonic sorts on (key, index));
+//      c_aug among them (exact ranks of the (key, index) pairs, counted over
+//      many CTAs);
 //   5. weights c_m = exp(-(c_aug,m - delta)/gamma), delta = min c_aug, and the
 //      updates of eqs. update_mean and update_covariance (the covariance uses
 //      the new mean). The sign of the exponent follows the reading that good
 //      samples weigh more.
 // Decentralised form (D-PRIEST): the batch splits into n_dist contiguous groups
-// of B / n_dist samples, each with its own mean and covariance. The Cholesky,
-// selection and refit kernels take one CTA per group, so every stage is one
-// launch for all distributions; the projection solve is one launch as before.
+// of B / n_dist samples, each with its own mean and covariance. The Cholesky and
+// refit kernels take one CTA per group and the selections one row of CTAs per
+// group, so every stage is one launch for all distributions; the projection solve
+// is one launch as before.
 #include "internal.cuh"
 #include <math.h>
 
@@ -45,33 +47,44 @@ __device__ __forceinline__ float u01(uint32_t x) { return ((float)x + 0.5f) * 2.
 // Cholesky of Sigma_g + eps I (D x D, D <= 48) into L_g (lower, row-major). One
 // CTA per distribution g = blockIdx.x.
 __global__ void k_cholesky(const float *sigma, int D, float eps, float *L, int *flag) {
-  __shared__ float A[48 * 48];
+  // thread i holds row i in registers (loops unrolled to the 48-column bound, so every
+  // index is a constant); the finished entries of each row are published in shared
+  // memory for the rows below. The sums run in the column-by-column order of the
+  // textbook algorithm.
+  __shared__ float Ls[48 * 48];
   sigma += (size_t)blockIdx.x * D * D;
   L += (size_t)blockIdx.x * D * D;
-  for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
-    const int i = e / D, j = e % D;
-    A[e] = 0.5f * (sigma[i * D + j] + sigma[j * D + i]) + (i == j ? eps : 0.f);
-  }
-  __syncthreads();
-  for (int j = 0; j < D; ++j) {
-    if (threadIdx.x == 0) {
-      float d = A[j * D + j];
-      for (int k = 0; k < j; ++k) d -= A[j * D + k] * A[j * D + k];
+  const int i = threadIdx.x;
+  const bool mine = i < D;
+  float row[48];
+#pragma unroll
+  for (int k = 0; k < 48; ++k)
+    row[k] = mine && k < D ? 0.5f * (sigma[i * D + k] + sigma[k * D + i]) + (i == k ? eps : 0.f) : 0.f;
+#pragma unroll
+  for (int j = 0; j < 48; ++j) {
+    if (j >= D) break;
+    if (i == j) {
+      float d = row[j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) d -= row[k] * row[k];
       if (!(d > 0.f)) { atomicOr(flag, 4); d = 1e-30f; }
-      A[j * D + j] = sqrtf(d);
+      row[j] = sqrtf(d);
+      Ls[j * 48 + j] = row[j];
     }
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < D; i += blockDim.x) {
-      float s = A[i * D + j];
-      for (int k = 0; k < j; ++k) s -= A[i * D + k] * A[j * D + k];
-      A[i * D + j] = s / A[j * D + j];
+    if (mine && i > j) {
+      float s = row[j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= row[k] * Ls[j * 48 + k];
+      row[j] = s / Ls[j * 48 + j];
+      Ls[i * 48 + j] = row[j];
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
-    const int i = e / D, j = e % D;
-    L[e] = j <= i ? A[e] : 0.f;
-  }
+  if (mine)
+#pragma unroll
+    for (int k = 0; k < 48; ++k)
+      if (k < D) L[i * D + k] = k <= i ? row[k] : 0.f;
 }
 
 // xi_i = mu_g + L_g z_i for sample i of group g = i / Bg. z from `z` ([B][D]) or,
@@ -124,21 +137,41 @@ __global__ void k_sample(const float *mu, const float *L, int D, int B, int Bg, 
 // c_p = distance of p(t) from its projection onto the segment start -> goal of the
 // problem (start, goal: FP64 [dim]). One warp per sample: the lanes take the grid
 // points t = lane + 32 m and the warp sums their terms (butterfly order).
-__global__ void k_cost(const float *xi, const float *res, const float *tables, int tbl_off,
-                       int n_p, float invT, float invT2, int dim, int B, float w_r, float w_curv,
-                       float w_path, const double *start, const double *goal, float *r_out,
-                       float *caug_out) {
+constexpr int COST_WARPS = 16;
+
+__global__ void __launch_bounds__(32 * COST_WARPS) k_cost(const float *xi, const float *res,
+                                                          const float *tables, int tbl_off,
+                                                          int n_p, float invT, float invT2,
+                                                          int dim, int B, float w_r,
+                                                          float w_curv, float w_path,
+                                                          const double *start,
+                                                          const double *goal, float *r_out,
+                                                          float *caug_out, int stage) {
+  // stage: the three basis tables are first copied to shared memory as [3][n_p][NC] (an
+  // odd row stride, so that the lanes' different grid points fall in different banks)
+  extern __shared__ float tab_s[];
+  const float *tab = tables + tbl_off;
+  int rs = ROW;
+  if (stage) {
+    for (int e = threadIdx.x; e < 3 * n_p * NC; e += blockDim.x)
+      tab_s[e] = tab[(e / NC) * ROW + e % NC];
+    __syncthreads();
+    tab = tab_s;
+    rs = NC;
+  }
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= B) return; // whole warps
-  const float *tP = tables + tbl_off, *tD = tP + n_p * ROW, *tA = tD + n_p * ROW;
+  const float *tP = tab, *tD = tP + n_p * rs, *tA = tD + n_p * rs;
   float sv[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f};
-  for (int a = 0; a < dim; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) if (a < dim) {
     sv[a] = (float)start[a];
     gv[a] = (float)(goal[a] - start[a]);
   }
   float L2 = 0.f;
-  for (int a = 0; a < dim; ++a) L2 = fmaf(gv[a], gv[a], L2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) if (a < dim) L2 = fmaf(gv[a], gv[a], L2);
   float x[3][NC];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -153,14 +186,15 @@ __global__ void k_cost(const float *xi, const float *res, const float *tables, i
       float sp = 0.f, sd = 0.f, sa = 0.f;
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        sp = fmaf(tP[t * ROW + k], x[a][k], sp);
-        sd = fmaf(tD[t * ROW + k], x[a][k], sd);
-        sa = fmaf(tA[t * ROW + k], x[a][k], sa);
+        sp = fmaf(tP[t * rs + k], x[a][k], sp);
+        sd = fmaf(tD[t * rs + k], x[a][k], sd);
+        sa = fmaf(tA[t * rs + k], x[a][k], sa);
       }
       pos[a] = sp; vel[a] = sd * invT; acc[a] = sa * invT2;
     }
     float a2 = 0.f;
-    for (int a = 0; a < dim; ++a) a2 = fmaf(acc[a], acc[a], a2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) if (a < dim) a2 = fmaf(acc[a], acc[a], a2);
     float c = a2;
     if (w_curv != 0.f) {
       const float cx = vel[1] * acc[2] - vel[2] * acc[1], cy = vel[2] * acc[0] - vel[0] * acc[2],
@@ -171,11 +205,13 @@ __global__ void k_cost(const float *xi, const float *res, const float *tables, i
     if (w_path != 0.f) {
       float u = 0.f;
       if (L2 > 0.f) {
-        for (int a = 0; a < dim; ++a) u = fmaf(pos[a] - sv[a], gv[a], u);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (a < dim) u = fmaf(pos[a] - sv[a], gv[a], u);
         u = fminf(fmaxf(u / L2, 0.f), 1.f);
       }
       float d2 = 0.f;
-      for (int a = 0; a < dim; ++a) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) if (a < dim) {
         const float d = pos[a] - (sv[a] + u * gv[a]);
         d2 = fmaf(d, d, d2);
       }
@@ -193,74 +229,111 @@ __global__ void k_cost(const float *xi, const float *res, const float *tables, i
   }
 }
 
-// Ascending bitonic sort of (key, index) pairs in shared memory; ties by index.
-__device__ void bitonic(float *key, int *idx, int n) {
-  for (int k = 2; k <= n; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int p = t ^ j;
-        if (p > t) {
-          const bool up = (t & k) == 0;
-          const float a = key[t], b = key[p];
-          const int ia = idx[t], ib = idx[p];
-          const bool gt = (a > b) || (a == b && ia > ib);
-          if (gt == up) { key[t] = b; key[p] = a; idx[t] = ib; idx[p] = ia; }
-        }
-      }
-      __syncthreads();
-    }
+// Selection key: an order-preserving map of the float to 32 unsigned bits (-0 taken
+// as +0, every NaN above +inf), with the sample index in the low word, so that the
+// composites are distinct and their order is the float order with ties broken by the
+// lower index.
+__device__ __forceinline__ unsigned long long sel_key(float x, int id) {
+  unsigned b = __float_as_uint(x);
+  if (b == 0x80000000u) b = 0u;
+  if ((b & 0x7fffffffu) > 0x7f800000u) b = 0x7fffffffu;
+  b ^= (b & 0x80000000u) ? 0xffffffffu : 0x80000000u;
+  return ((unsigned long long)b << 32) | (unsigned)id;
 }
 
-// Two-stage top-k: the n_proj lowest r, then the n_elite lowest c_aug among them.
-// One CTA per group g = blockIdx.x over its B samples (B <= 8192, padded to a power
-// of two with +inf keys); indices are local to the group.
-__global__ void k_select(const float *r, const float *caug, int B, int n_proj, int n_elite,
-                         int *proj_idx, int *elite_idx) {
-  extern __shared__ unsigned char sm_raw[];
-  r += (size_t)blockIdx.x * B;
-  caug += (size_t)blockIdx.x * B;
-  proj_idx += (size_t)blockIdx.x * n_proj;
-  elite_idx += (size_t)blockIdx.x * n_elite;
-  int n = 1;
-  while (n < B) n <<= 1;
-  float *key = reinterpret_cast<float *>(sm_raw);
-  int *idx = reinterpret_cast<int *>(key + n);
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    key[t] = t < B ? r[t] : __int_as_float(0x7f800000);
-    idx[t] = t < B ? t : 0x7fffffff;
+constexpr int RANK_THREADS = 256;
+constexpr int RANK_SLICES = 8;                           // threads counting for one element
+constexpr int RANK_ELEMS = RANK_THREADS / RANK_SLICES;  // elements per CTA
+
+// Top-k by rank counting, one stage of ConstraintEliteSet / EliteSet. Group g =
+// blockIdx.y has n candidates: candidate e is the sample id = ids[e] (e itself when
+// ids is null) with key x[id]. Its rank is the number of candidates whose (key, id)
+// comes first; every rank is distinct, and rank < n_out puts id at out[rank], so out
+// holds the n_out first candidates in ascending order (the result of sorting the
+// pairs). Each CTA stages all n composites of its group in shared memory and ranks
+// RANK_ELEMS candidates, RANK_SLICES threads each counting over every
+// RANK_SLICES-th composite.
+__global__ void __launch_bounds__(RANK_THREADS) k_rank_select(const float *x, int x_stride,
+                                                              const int *ids, int ids_stride,
+                                                              int n, int n_out, int *out,
+                                                              int out_stride) {
+  extern __shared__ unsigned long long comp[];
+  const int g = blockIdx.y;
+  x += (size_t)g * x_stride;
+  if (ids) ids += (size_t)g * ids_stride;
+  out += (size_t)g * out_stride;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int id = ids ? ids[e] : e;
+    comp[e] = sel_key(x[id], id);
   }
   __syncthreads();
-  bitonic(key, idx, n);
-  for (int t = threadIdx.x; t < n_proj; t += blockDim.x) proj_idx[t] = idx[t];
-  __syncthreads();
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    const int id = t < n_proj ? proj_idx[t] : 0x7fffffff;
-    key[t] = t < n_proj ? caug[id] : __int_as_float(0x7f800000);
-    idx[t] = id;
+  const int e = blockIdx.x * RANK_ELEMS + threadIdx.x / RANK_SLICES;
+  const int sl = threadIdx.x % RANK_SLICES;
+  const unsigned long long mine = e < n ? comp[e] : 0ull;
+  int c0 = 0, c1 = 0;
+  int m = sl;
+  for (; m + RANK_SLICES < n; m += 2 * RANK_SLICES) {
+    c0 += comp[m] < mine;
+    c1 += comp[m + RANK_SLICES] < mine;
   }
-  __syncthreads();
-  bitonic(key, idx, n);
-  for (int t = threadIdx.x; t < n_elite; t += blockDim.x) elite_idx[t] = idx[t];
+  if (m < n) c0 += comp[m] < mine;
+  int cnt = c0 + c1;
+#pragma unroll
+  for (int o = RANK_SLICES / 2; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (sl == 0 && e < n && cnt < n_out) out[cnt] = (int)(unsigned)(mine & 0xffffffffull);
 }
 
-// Weighted refit (eqs. update_mean, update_covariance) and the best elite. One CTA
-// per group g = blockIdx.x of Bg samples. stage: the elites' coefficients are first
-// copied to dynamic shared memory ([n_elite][D]), so that the sums over the elites read
-// them there (same order of operations either way).
-__global__ void k_refit(const float *xi, const float *caug, const int *elite, int Bg, int n_elite,
-                        int D, float gamma, float sig, float *mu, float *sigma, float *best,
-                        int stage) {
+// Weighted refit (eqs. update_mean, update_covariance) and the best elite, in two
+// kernels. k_refit_mean, one CTA of 1024 threads per group g = blockIdx.x of Bg
+// samples: the weights c_m, their sum S, the new mean (aux[g] = [mu_new, S]) and the
+// best elite, and for the covariance the elites' centred coefficients xc[m][d] =
+// x_m,d - mu_new,d and weighted ones wx[m][d] = c_m xc[m][d], stored contiguously.
+// k_refit_cov, a row of CTAs per group: one covariance entry per thread, the sum of
+// wx[m][i] xc[m][j] over the elites in order m = 0, 1, ...; the CTA with blockIdx.x
+// == 0 then stores mu_new into mu (no other kernel of the step reads mu after
+// k_refit_mean). stage: the elites' coefficients are first gathered into dynamic
+// shared memory ([n_elite][D]). The operations and their order are those of the
+// update equations written out entry by entry, whichever path runs.
+constexpr int REFIT_THREADS = 1024;
+constexpr int COV_THREADS = 256;
+constexpr int GATHER_BATCH = 8;  // gathers in flight per thread
+
+__global__ void __launch_bounds__(REFIT_THREADS) k_refit_mean(const float *xi, const float *caug,
+                                                              const int *elite, int Bg,
+                                                              int n_elite, int D, int ne_pad,
+                                                              float gamma, float sig,
+                                                              const float *mu,
+                                                              float *best, float *aux,
+                                                              float *wx, float *xc, int stage) {
   __shared__ float w_s[8192];
+  __shared__ float red[32];
+  __shared__ float mu_new[48];
   extern __shared__ float xs[];
   const size_t g = blockIdx.x;
   xi += g * Bg * D;
   caug += g * Bg;
   elite += g * n_elite;
   mu += g * D;
-  sigma += g * D * D;
   best += g * (D + 1);
-  __shared__ float mu_new[48];
-  __shared__ float red[32];
+  aux += g * (D + 1);
+  wx += g * ne_pad;
+  xc += g * ne_pad;
+  const int n = n_elite * D;
+  if (stage) {  // the gathers of a batch are issued before any is stored
+    for (int e0 = threadIdx.x; e0 < n; e0 += GATHER_BATCH * blockDim.x) {
+      float v[GATHER_BATCH];
+#pragma unroll
+      for (int u = 0; u < GATHER_BATCH; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = e < n ? __ldg(xi + (size_t)__ldg(elite + e / D) * D + e % D) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < GATHER_BATCH; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < n) xs[e] = v[u];
+      }
+    }
+  }
   const float delta = caug[elite[0]];
   float part = 0.f;
   for (int m = threadIdx.x; m < n_elite; m += blockDim.x) {
@@ -273,33 +346,74 @@ __global__ void k_refit(const float *xi, const float *caug, const int *elite, in
   __syncthreads();
   float S = 0.f;
   for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) S += red[k];
-  if (stage) {
-    for (int e = threadIdx.x; e < n_elite * D; e += blockDim.x)
-      xs[e] = xi[(size_t)elite[e / D] * D + e % D];
-    __syncthreads();
-  }
   for (int d = threadIdx.x; d < D; d += blockDim.x) {
     float s = 0.f;
+#pragma unroll 8
     for (int m = 0; m < n_elite; ++m)
       s = fmaf(w_s[m], stage ? xs[m * D + d] : xi[(size_t)elite[m] * D + d], s);
-    mu_new[d] = (1.f - sig) * mu[d] + sig * (s / S);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
-    const int i = e / D, j = e % D;
-    float s = 0.f;
-    for (int m = 0; m < n_elite; ++m) {
-      const float *x = stage ? xs + m * D : xi + (size_t)elite[m] * D;
-      s = fmaf(w_s[m] * (x[i] - mu_new[i]), x[j] - mu_new[j], s);
-    }
-    sigma[e] = (1.f - sig) * sigma[e] + sig * (s / S);
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < D; d += blockDim.x) {
-    mu[d] = mu_new[d];
+    const float mn = (1.f - sig) * mu[d] + sig * (s / S);
+    mu_new[d] = mn;
+    aux[d] = mn;
     best[d] = xi[(size_t)elite[0] * D + d];
   }
-  if (threadIdx.x == 0) best[D] = delta;
+  if (threadIdx.x == 0) {
+    aux[D] = S;
+    best[D] = delta;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int m = e / D, d = e % D;
+    const float c = (stage ? xs[e] : xi[(size_t)elite[m] * D + d]) - mu_new[d];
+    xc[e] = c;
+    wx[e] = w_s[m] * c;
+  }
+}
+
+__global__ void __launch_bounds__(COV_THREADS) k_refit_cov(int n_elite, int D, int ne_pad,
+                                                           float sig,
+                                                           const float *__restrict__ wx,
+                                                           const float *__restrict__ xc,
+                                                           const float *aux, float *mu,
+                                                           float *sigma, int stage) {
+  extern __shared__ float4 cov_s[];  // [wx | xc], ne_pad floats each
+  const size_t g = blockIdx.y;
+  wx += g * ne_pad;
+  xc += g * ne_pad;
+  aux += g * (D + 1);
+  mu += g * D;
+  sigma += g * D * D;
+  const float *w_src = wx, *x_src = xc;
+  if (stage) {  // 16-byte loads, a batch of them issued before any is stored
+    const int n4 = ne_pad / 4;
+    const float4 *src0 = reinterpret_cast<const float4 *>(wx);
+    const float4 *src1 = reinterpret_cast<const float4 *>(xc);
+    for (int q0 = threadIdx.x; q0 < 2 * n4; q0 += GATHER_BATCH * blockDim.x) {
+      float4 v[GATHER_BATCH];
+#pragma unroll
+      for (int u = 0; u < GATHER_BATCH; ++u) {
+        const int q = q0 + u * blockDim.x;
+        v[u] = q < n4 ? __ldg(src0 + q) : q < 2 * n4 ? __ldg(src1 + (q - n4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < GATHER_BATCH; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < 2 * n4) cov_s[q] = v[u];
+      }
+    }
+    __syncthreads();
+    w_src = reinterpret_cast<const float *>(cov_s);
+    x_src = w_src + ne_pad;
+  }
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < D * D) {
+    const int i = e / D, j = e % D;
+    float s = 0.f;
+#pragma unroll 8
+    for (int m = 0; m < n_elite; ++m) s = fmaf(w_src[m * D + i], x_src[m * D + j], s);
+    sigma[e] = (1.f - sig) * sigma[e] + sig * (s / aux[D]);
+  }
+  if (blockIdx.x == 0)
+    for (int d = threadIdx.x; d < D; d += blockDim.x) mu[d] = aux[d];
 }
 
 // c_1 = sum_t ||p''(t)||^2 of every trajectory of a batch (each with its own problem).
@@ -345,30 +459,56 @@ cudaError_t launch_sampler_back(const float *xi, const float *res, const float *
                                 int tbl_off, int n_p, float invT, float invT2, int dim, int B,
                                 int n_dist, const SamplerCost &cost, int n_proj, int n_elite,
                                 float gamma, float sig, float *r_out, float *caug_out,
-                                int *proj_idx, int *elite_idx, float *mu, float *sigma,
-                                float *best, cudaStream_t s) {
-  k_cost<<<(unsigned)(((long long)B * 32 + 255) / 256), 256, 0, s>>>(xi, res, tables, tbl_off, n_p,
-                                                                     invT, invT2, dim, B,
-                                         cost.w_res, cost.w_curv, cost.w_path, cost.start,
-                                         cost.goal, r_out, caug_out);
-  cudaError_t e = cudaGetLastError();
+                                int *proj_idx, int *elite_idx, float *refit_scratch, float *mu,
+                                float *sigma, float *best, cudaStream_t s) {
+  const size_t tab_bytes = sizeof(float) * 3 * (size_t)n_p * NC;
+  const int tab_stage = tab_bytes <= 160 * 1024 ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  if (tab_stage && (e = cudaFuncSetAttribute(k_cost, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tab_bytes)) != cudaSuccess)
+    return e;
+  k_cost<<<(B + COST_WARPS - 1) / COST_WARPS, 32 * COST_WARPS, tab_stage ? tab_bytes : 0, s>>>(
+      xi, res, tables, tbl_off, n_p, invT, invT2, dim, B, cost.w_res, cost.w_curv, cost.w_path,
+      cost.start, cost.goal, r_out, caug_out, tab_stage);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int Bg = B / n_dist;
-  int n = 1;
-  while (n < Bg) n <<= 1;
-  const size_t smem = (size_t)n * (sizeof(float) + sizeof(int));
-  e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // ConstraintEliteSet: the n_proj lowest r of each group; EliteSet: the n_elite
+  // lowest c_aug among them
+  e = cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(unsigned long long) * Bg));
   if (e != cudaSuccess) return e;
-  k_select<<<n_dist, 1024, smem, s>>>(r_out, caug_out, Bg, n_proj, n_elite, proj_idx, elite_idx);
+  k_rank_select<<<dim3((Bg + RANK_ELEMS - 1) / RANK_ELEMS, n_dist), RANK_THREADS,
+                  sizeof(unsigned long long) * Bg, s>>>(r_out, Bg, nullptr, 0, Bg, n_proj,
+                                                        proj_idx, n_proj);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_rank_select<<<dim3((n_proj + RANK_ELEMS - 1) / RANK_ELEMS, n_dist), RANK_THREADS,
+                  sizeof(unsigned long long) * n_proj, s>>>(caug_out, Bg, proj_idx, n_proj,
+                                                            n_proj, n_elite, elite_idx, n_elite);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the elites' coefficients in shared memory when they fit beside the 32 KB of weights
-  const size_t xs_bytes = sizeof(float) * (size_t)n_elite * dim * NC;
+  const int D = dim * NC;
+  const size_t xs_bytes = sizeof(float) * (size_t)n_elite * D;
   const int stage = xs_bytes <= 160 * 1024 ? 1 : 0;
-  if (stage && (e = cudaFuncSetAttribute(k_refit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (stage && (e = cudaFuncSetAttribute(k_refit_mean, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)xs_bytes)) != cudaSuccess)
     return e;
-  k_refit<<<n_dist, 1024, stage ? xs_bytes : 0, s>>>(xi, caug_out, elite_idx, Bg, n_elite, dim * NC,
-                                                     gamma, sig, mu, sigma, best, stage);
+  // per group, n_elite * D weighted and centred coefficients rounded up to a multiple of
+  // 4 floats, so that every group's arrays start on a 16-byte boundary
+  const int ne_pad = (n_elite * D + 3) & ~3;
+  float *wx = refit_scratch, *xc = wx + (size_t)n_dist * ne_pad;
+  float *aux = xc + (size_t)n_dist * ne_pad;
+  k_refit_mean<<<n_dist, REFIT_THREADS, stage ? xs_bytes : 0, s>>>(
+      xi, caug_out, elite_idx, Bg, n_elite, D, ne_pad, gamma, sig, mu, best, aux, wx, xc, stage);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t cov_bytes = sizeof(float) * 2 * (size_t)ne_pad;
+  const int cov_stage = cov_bytes <= 200 * 1024 ? 1 : 0;
+  if (cov_stage && (e = cudaFuncSetAttribute(k_refit_cov, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)cov_bytes)) != cudaSuccess)
+    return e;
+  k_refit_cov<<<dim3((D * D + COV_THREADS - 1) / COV_THREADS, n_dist), COV_THREADS,
+                cov_stage ? cov_bytes : 0, s>>>(n_elite, D, ne_pad, sig, wx, xc, aux, mu, sigma,
+                                                cov_stage);
   return cudaGetLastError();
 }
 

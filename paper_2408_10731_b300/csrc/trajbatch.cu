@@ -77,7 +77,7 @@ struct traj_batch {
   unsigned long long g_timeout = 0;
   std::vector<int> tbl_off; // per problem, float offset of its basis tables
   // sampler scratch (allocated at creation from max_traj)
-  float *d_L = nullptr, *d_r = nullptr, *d_caug = nullptr;
+  float *d_L = nullptr, *d_r = nullptr, *d_caug = nullptr, *d_refit = nullptr;
   int *d_proj = nullptr, *d_elite = nullptr, *d_sflag = nullptr;
 };
 
@@ -121,7 +121,7 @@ static void free_all(traj_batch *b) {
                   b->d_horizons, b->d_hoffsets, b->d_obs, b->d_obs_stage, b->d_obs_index,
                   b->d_traj_problem, b->d_order, b->d_xi0, b->d_xi, b->d_lam, b->d_u, b->d_res, b->d_lam0, b->d_u0,
                   b->d_iters, b->d_status, b->d_queue, b->d_flags, b->d_t0, b->d_L, b->d_r,
-                  b->d_caug, b->d_proj, b->d_elite, b->d_sflag, b->d_kkt64};
+                  b->d_caug, b->d_proj, b->d_elite, b->d_sflag, b->d_kkt64, b->d_refit};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (b->ev0) cudaEventDestroy(b->ev0);
@@ -218,7 +218,8 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
       (e = dalloc(&b->d_iters, B)) || (e = dalloc(&b->d_status, B)) || (e = dalloc(&b->d_queue, 1)) ||
       (e = dalloc(&b->d_flags, 1)) || (e = dalloc(&b->d_t0, 1)) || (e = dalloc(&b->d_L, TRAJ_SAMPLER_MAX_DIST * (D * NC) * (D * NC))) ||
       (e = dalloc(&b->d_r, B)) || (e = dalloc(&b->d_caug, B)) || (e = dalloc(&b->d_proj, B)) ||
-      (e = dalloc(&b->d_elite, B)) || (e = dalloc(&b->d_sflag, 1)))
+      (e = dalloc(&b->d_elite, B)) || (e = dalloc(&b->d_sflag, 1)) ||
+      (e = dalloc(&b->d_refit, TRAJ_SAMPLER_MAX_DIST * (D * NC + 7) + 2 * B * D * NC)))
     return bail("cudaMalloc", e);
   if ((e = cudaEventCreate(&b->ev0)) || (e = cudaEventCreate(&b->ev1))) return bail("cudaEventCreate", e);
   if ((e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking)))
@@ -908,7 +909,7 @@ traj_status traj_sampler_step_multi(traj_batch *b, const traj_sampler_config *sc
   CK(b, launch_sampler_back(b->d_xi, b->d_res, b->d_tables, b->tbl_off[0], n_p, (float)(1.0 / T),
                             (float)(1.0 / (T * T)), b->cfg.dim, B, n_dist, cost, sc->n_proj,
                             sc->n_elite, sc->gamma, sc->sigma_lr, b->d_r, b->d_caug, b->d_proj,
-                            b->d_elite, mu, sigma, best, b->stream));
+                            b->d_elite, b->d_refit, mu, sigma, best, b->stream));
   if (trace) {
     const size_t np = (size_t)n_dist * sc->n_proj, ne = (size_t)n_dist * sc->n_elite;
     if (trace->projected) CK(b, cudaMemcpyAsync(trace->projected, b->d_xi, sizeof(float) * B * D, cudaMemcpyDeviceToDevice, b->stream));
