@@ -68,8 +68,8 @@ KERNEL_SOURCES = {
     "k_am_mixed": ("am_mixed.cu", "am_device.cuh", "internal.cuh", "tcgen05.cuh"),
 }
 MEASURED_TRAFFIC = {
-    ("k_am_fp32", "config5"): (8 * 2615552, "fd606b37739c0aed"),
-    ("k_am_mixed", "config5"): (8 * 2676224, "23754c10d4e6ced0"),
+    ("k_am_fp32", "config5"): (8 * 2865664, "0b4f1a0787df6ca5"),
+    ("k_am_mixed", "config5"): (8 * 2802432, "96366f47fb100bee"),
 }
 
 
