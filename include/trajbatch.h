@@ -249,17 +249,32 @@ traj_status traj_set_state(traj_batch *b, const float *coeffs, const float *lamb
  *  - the constants that depend on the boundary values (K12 b and the tracking term
  *    K11 q, eq. Q_matrix) are formed again in FP64; the KKT inverse itself (which the
  *    shift leaves as it was: same n_p, T, obstacle count, rho and bounds) is not.
- *    The first shift after traj_set_problems, traj_set_obstacles,
- *    traj_set_rho_schedule or traj_set_workspace runs the full FP64 set-up once more
- *    and keeps its FP64 blocks (allocated then: 1.5 KB per problem and penalty
- *    level; TRAJ_ENOMEM if that fails) and synchronises; later shifts only launch
- *    the obstacle packing and the boundary update, asynchronously.
+ *    The FP64 set-up of traj_set_obstacles, traj_set_rho_schedule and
+ *    traj_set_workspace keeps its FP64 blocks (1.5 KB per problem and penalty level,
+ *    allocated then; TRAJ_ENOMEM if that fails), so every shift only launches the
+ *    obstacle packing and the boundary update, asynchronously.
  * The next traj_solve projects the shifted iterate, so u is formed for the moved
  * problem, with lambda0 = the carried multipliers instead of 0, then iterates as
  * usual (iters counts from 0). traj_set_initial returns to fresh starts and
  * traj_set_state to a resume. TRAJ_ESTATE before a solve has run; TRAJ_EINVAL in
  * projection mode or for a delta outside (0, T). */
 traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed);
+
+/* One receding-horizon control step: traj_shift_horizon(delta, executed) followed by
+ * traj_solve(max_iters, tol, timeout_ms, NULL), with the same results bit for bit,
+ * replayed as one CUDA graph on the handle's stream (the shift's kernels, the
+ * obstacle packing, the boundary update, the counters' reset and the persistent
+ * solve). The graph is captured at the first call and again when delta, whether
+ * executed is given, the solve's arguments or the launch shape change, or after any
+ * traj_set_* call; executed (host int[n_problems], or NULL for each problem's
+ * smallest worst residual) is checked on the host and copied before the replay.
+ * Asynchronous; traj_get_solve_stats afterwards reports the step's GPU time (shift and
+ * solve). Errors as the two calls it stands for, and TRAJ_ECUDA if the capture fails.
+ * Without kept FP64 blocks (a handle whose set-up has not run with its obstacles) it
+ * makes the two calls instead. Passage: Paper II, the MPC use of Algorithm 2
+ * (warm-started iterations per control loop). */
+traj_status traj_mpc_step(traj_batch *b, double delta, const int *executed, int max_iters,
+                          float tol, double timeout_ms);
 
 /* Solve without allocating any memory, for callers that cannot allocate
  * device memory: code running under an allocator or memory pool owned by

@@ -15,6 +15,18 @@
 
 using namespace tb;
 
+// What a captured solve graph was built for; the graph is replayed while it matches.
+struct GraphKey {
+  int max_iters = -1, n_traj = -1, warps = -1, bps = -1, team = -1, occ = -1, resume = -1;
+  float tol = 0.f;
+  unsigned long long timeout = 0;
+  bool operator==(const GraphKey &o) const {
+    return max_iters == o.max_iters && n_traj == o.n_traj && warps == o.warps && bps == o.bps &&
+           team == o.team && occ == o.occ && resume == o.resume && tol == o.tol &&
+           timeout == o.timeout;
+  }
+};
+
 struct traj_batch {
   traj_config cfg{};
   cudaStream_t stream = nullptr;
@@ -72,9 +84,13 @@ struct traj_batch {
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_valid = false;
-  int g_max_iters = -1, g_n_traj = -1, g_warps = -1, g_bps = -1, g_team = -1, g_resume = -1, g_occ = -1;
-  float g_tol = 0.f;
-  unsigned long long g_timeout = 0;
+  GraphKey g_key;
+  // one receding-horizon control step (shift, boundary update, solve) as a CUDA graph
+  cudaGraphExec_t mpc_exec = nullptr;
+  bool mpc_valid = false;
+  GraphKey mpc_key;
+  double mpc_delta = 0.0;
+  bool mpc_given = false;
   std::vector<int> tbl_off; // per problem, float offset of its basis tables
   // sampler scratch (allocated at creation from max_traj)
   float *d_L = nullptr, *d_r = nullptr, *d_caug = nullptr, *d_refit = nullptr;
@@ -127,13 +143,19 @@ static void free_all(traj_batch *b) {
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->mpc_exec) cudaGraphExecDestroy(b->mpc_exec);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
 }
 
+// Drop the captured graphs (the solve's and the control step's): their nodes hold the
+// buffers and arguments of the handle's state at capture.
 static void invalidate_graph(traj_batch *b) {
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   b->graph_exec = nullptr;
   b->graph_valid = false;
+  if (b->mpc_exec) cudaGraphExecDestroy(b->mpc_exec);
+  b->mpc_exec = nullptr;
+  b->mpc_valid = false;
 }
 
 extern "C" {
@@ -282,7 +304,7 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
   b->n_steps.assign(n_steps, n_steps + n_problems);
   b->duration.assign(duration, duration + n_problems);
   b->n_problems = n_problems;
-  b->kkt_valid = false; // new problems: the next shift sets up in full
+  b->kkt_valid = false; // new problems: the set-up with their obstacles keeps new blocks
   b->max_np_used = max_np;
   b->have_problems = true;
   invalidate_graph(b);
@@ -297,12 +319,12 @@ traj_status traj_set_problems(traj_batch *b, int n_problems, const int *n_steps,
 // Upload the problem records (constants offsets for the current number of penalty
 // levels), pack the staged obstacles into pair records (which also flags bad
 // obstacle data) and form the FP64 set-up of every penalty level; synchronises.
-// keep_kkt: also store the FP64 blocks that later boundary-only updates
-// (traj_shift_horizon) start from
-static traj_status upload_problems(traj_batch *b, bool keep_kkt = false) {
+// The FP64 blocks (K11, K12 and the basis moments of every problem and level) are
+// kept, so that receding-horizon shifts update only the boundary-dependent constants.
+static traj_status upload_problems(traj_batch *b) {
   const int P = b->n_problems, D = b->cfg.dim, N = b->n_obs, L = b->rho_levels;
   b->kkt_valid = false;
-  if (keep_kkt && b->kkt64_cap < (size_t)P * L * KKT64_DOUBLES) {
+  if (b->kkt64_cap < (size_t)P * L * KKT64_DOUBLES) {
     CK(b, cudaStreamSynchronize(b->stream));
     if (b->d_kkt64) cudaFree(b->d_kkt64);
     b->d_kkt64 = nullptr;
@@ -336,24 +358,24 @@ static traj_status upload_problems(traj_batch *b, bool keep_kkt = false) {
                                 b->cfg.rho * std::pow(b->rho_growth, (double)l), b->cfg.w_smooth,
                                 b->cfg.w_track, b->cfg.cost_mode, b->max_np_used,
                                 b->d_constants + (size_t)l * CONST_FLOATS, b->stream,
-                                keep_kkt ? b->d_kkt64 + (size_t)l * KKT64_DOUBLES : nullptr,
+                                b->d_kkt64 + (size_t)l * KKT64_DOUBLES,
                                 (size_t)L * KKT64_DOUBLES));
   CK(b, cudaStreamSynchronize(b->stream));
-  b->kkt_valid = keep_kkt;
+  b->kkt_valid = true;
   return TRAJ_OK;
 }
 
 // After a receding-horizon shift with the FP64 blocks at hand: the moved obstacles
 // re-packed, and only the boundary-dependent constants (hq, c) of every level
 // recomputed; the KKT matrix (n_p, T, n_o, rho, bounds) is the one set up before.
-static traj_status shift_boundary(traj_batch *b) {
+static traj_status shift_boundary(traj_batch *b, cudaStream_t s) {
   const int P = b->n_problems, D = b->cfg.dim, N = b->n_obs, L = b->rho_levels;
   const float *st_c = b->d_obs_stage, *st_a = st_c + (size_t)N * D, *st_v = st_a + (size_t)N * D;
   const int *index = b->pair_index.data();
   CK(b, launch_pack_obstacles(D, P, 2 * index[2 * P + 1], b->d_obs_index, b->d_obs_index + P + 1,
-                              st_c, st_a, st_v, b->d_obs, b->d_problems, b->stream));
+                              st_c, st_a, st_v, b->d_obs, b->d_problems, s));
   CK(b, launch_setup_boundary(P, L, b->d_start, b->d_goal, b->d_start_va, D, b->cfg.w_track,
-                              b->d_kkt64, b->d_constants, b->stream));
+                              b->d_kkt64, b->d_constants, s));
   return TRAJ_OK;
 }
 
@@ -510,10 +532,9 @@ static traj_status solve_stats(traj_batch *b, traj_solve_stats *stats) {
 // the imported xi, lambda, u), 2 carry (project the shifted xi0, lambda0 = carried).
 static int start_mode(const traj_batch *b) { return b->resume ? 1 : (b->carry ? 2 : 0); }
 
-traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
-                       traj_solve_stats *stats) {
-  tb::NvtxRange nvtx_range("traj_solve");
-  if (!b) return TRAJ_EINVAL;
+// The solve's arguments from the handle's state, after checking the call.
+static traj_status solve_args(traj_batch *b, int max_iters, float tol, double timeout_ms,
+                              SolveArgs &a) {
   if (!b->have_initial) return fail(b, TRAJ_ESTATE, "traj_set_initial must come first");
   if (max_iters < 0) return fail(b, TRAJ_EINVAL, "max_iters must be >= 0");
   if (std::isnan(tol) || !(timeout_ms >= 0)) return fail(b, TRAJ_EINVAL, "bad tol or timeout");
@@ -523,7 +544,7 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   if (b->max_np_used > MAX_STEPS && b->shape.team != 1)
     return fail(b, TRAJ_ESHAPE, "horizons above 256 grid points run one warp per trajectory "
                                 "(warps_per_trajectory 1)");
-  SolveArgs a{};
+  a = SolveArgs{};
   a.problems = b->d_problems;
   a.obstacles = b->d_obs;
   a.constants = b->d_constants;
@@ -574,22 +595,44 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   a.queue = b->d_queue;
   a.t0 = b->d_t0;
   a.flags = b->d_flags;
-  const bool same = b->graph_valid && b->g_max_iters == max_iters && b->g_tol == tol &&
-                    b->g_timeout == a.timeout_ns && b->g_n_traj == b->n_traj &&
-                    b->g_warps == b->shape.warps_per_block && b->g_bps == b->shape.blocks_per_sm &&
-                    b->g_team == b->shape.team && b->g_occ == b->shape.occupancy &&
-                    b->g_resume == start_mode(b);
-  if (!same) {
+  return TRAJ_OK;
+}
+
+// One solve on stream cs (also while it is capturing): clear the counters, then the
+// persistent solve launch.
+static cudaError_t record_solve(traj_batch *b, const SolveArgs &a, cudaStream_t cs) {
+  cudaError_t ce = cudaMemsetAsync(b->d_queue, 0, sizeof(int), cs);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_flags, 0, sizeof(int), cs);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_t0, 0, sizeof(unsigned long long), cs);
+  if (ce == cudaSuccess)
+    ce = launch_am_solve(b->cfg.dim, b->max_np_used, b->cfg.precision, a, b->shape, b->n_sm, cs,
+                         &b->used);
+  return ce;
+}
+
+// The key of a captured solve: the arguments that reach the graph's nodes by value.
+static GraphKey graph_key(const traj_batch *b, int max_iters, float tol, const SolveArgs &a) {
+  GraphKey k;
+  k.max_iters = max_iters; k.tol = tol; k.timeout = a.timeout_ns; k.n_traj = b->n_traj;
+  k.warps = b->shape.warps_per_block; k.bps = b->shape.blocks_per_sm; k.team = b->shape.team;
+  k.occ = b->shape.occupancy; k.resume = start_mode(b);
+  return k;
+}
+
+traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_ms,
+                       traj_solve_stats *stats) {
+  tb::NvtxRange nvtx_range("traj_solve");
+  if (!b) return TRAJ_EINVAL;
+  SolveArgs a;
+  traj_status rs = solve_args(b, max_iters, tol, timeout_ms, a);
+  if (rs != TRAJ_OK) return rs;
+  const GraphKey key = graph_key(b, max_iters, tol, a);
+  if (!(b->graph_valid && b->g_key == key)) {
     // capture {clear counters; persistent solve} on the handle's capture stream
     invalidate_graph(b);
     cudaStream_t cs = b->capture_stream;
     CK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaMemsetAsync(b->d_queue, 0, sizeof(int), cs);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_flags, 0, sizeof(int), cs);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_t0, 0, sizeof(unsigned long long), cs);
-    if (ce == cudaSuccess)
-      ce = launch_am_solve(b->cfg.dim, b->max_np_used, b->cfg.precision, a, b->shape, b->n_sm, cs,
-                           &b->used);
+    cudaError_t ce = record_solve(b, a, cs);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(cs, &g);
     if (ce == cudaSuccess) ce = ee;
@@ -600,11 +643,7 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
       return fail(b, TRAJ_ECUDA, std::string("solve graph capture: ") + cudaGetErrorString(ce));
     }
     b->graph_valid = true;
-    b->g_max_iters = max_iters; b->g_tol = tol; b->g_timeout = a.timeout_ns;
-    b->g_n_traj = b->n_traj; b->g_warps = b->shape.warps_per_block; b->g_bps = b->shape.blocks_per_sm;
-    b->g_team = b->shape.team;
-    b->g_occ = b->shape.occupancy;
-    b->g_resume = start_mode(b);
+    b->g_key = key;
   }
   CK(b, cudaEventRecord(b->ev0, b->stream));
   CK(b, cudaGraphLaunch(b->graph_exec, b->stream));
@@ -738,9 +777,9 @@ traj_status traj_set_state(traj_batch *b, const float *coeffs, const float *lamb
   return TRAJ_OK;
 }
 
-traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed) {
-  tb::NvtxRange nvtx_range("traj_shift_horizon");
-  if (!b) return TRAJ_EINVAL;
+// Check a receding-horizon step and fill its arguments; a given executed array is
+// copied to the device on the handle's stream.
+static traj_status shift_args(traj_batch *b, double delta, const int *executed, ShiftArgs &a) {
   if (!b->have_result) return fail(b, TRAJ_ESTATE, "traj_shift_horizon needs a finished solve");
   if (b->cfg.cost_mode != TRAJ_COST_SMOOTH_TRACK)
     return fail(b, TRAJ_EINVAL, "the receding-horizon step needs the smoothness/tracking cost");
@@ -756,7 +795,7 @@ traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed)
                                         std::to_string(p));
     CK(b, cudaMemcpyAsync(b->d_exec, executed, sizeof(int) * P, cudaMemcpyHostToDevice, b->stream));
   }
-  ShiftArgs a{};
+  a = ShiftArgs{};
   a.dim = b->cfg.dim;
   a.n_problems = P;
   a.n_traj = B;
@@ -776,18 +815,88 @@ traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed)
   a.start_va = b->d_start_va;
   a.centers = b->d_obs_stage;
   a.velocities = b->d_obs_stage + (size_t)2 * b->n_obs * b->cfg.dim;
-  CK(b, launch_mpc_shift(a, b->stream));
-  // re-pack the moved obstacles and set up the new boundary values: the first shift
-  // after a set-up runs the FP64 set-up of every level and keeps its blocks, later ones
-  // recompute the boundary-dependent constants from them
-  traj_status rs = b->kkt_valid ? shift_boundary(b) : upload_problems(b, true);
-  if (rs != TRAJ_OK) return rs;
+  return TRAJ_OK;
+}
+
+// After a shift the next solves start from the shifted iterate and the carried
+// multipliers.
+static void shift_state(traj_batch *b) {
   if (!b->carry || b->resume) {
     b->carry = true;
     b->resume = false;
     invalidate_graph(b);
   }
   b->have_result = false;
+}
+
+traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed) {
+  tb::NvtxRange nvtx_range("traj_shift_horizon");
+  if (!b) return TRAJ_EINVAL;
+  ShiftArgs a;
+  traj_status rs = shift_args(b, delta, executed, a);
+  if (rs != TRAJ_OK) return rs;
+  CK(b, launch_mpc_shift(a, b->stream));
+  // re-pack the moved obstacles and recompute the boundary-dependent constants of every
+  // level from the FP64 blocks that the last set-up kept (a full set-up only if none
+  // has been kept)
+  rs = b->kkt_valid ? shift_boundary(b, b->stream) : upload_problems(b);
+  if (rs != TRAJ_OK) return rs;
+  shift_state(b);
+  b->err.clear();
+  return TRAJ_OK;
+}
+
+traj_status traj_mpc_step(traj_batch *b, double delta, const int *executed, int max_iters,
+                          float tol, double timeout_ms) {
+  tb::NvtxRange nvtx_range("traj_mpc_step");
+  if (!b) return TRAJ_EINVAL;
+  if (!b->kkt_valid) { // no FP64 blocks kept: the shift sets up in full and synchronises
+    traj_status rs = traj_shift_horizon(b, delta, executed);
+    return rs != TRAJ_OK ? rs : traj_solve(b, max_iters, tol, timeout_ms, nullptr);
+  }
+  // check the solve first, as it will run from the shifted state
+  const bool carry0 = b->carry, resume0 = b->resume;
+  b->carry = true;
+  b->resume = false;
+  SolveArgs a;
+  traj_status rs = solve_args(b, max_iters, tol, timeout_ms, a);
+  b->carry = carry0;
+  b->resume = resume0;
+  if (rs != TRAJ_OK) return rs;
+  ShiftArgs sa;
+  if ((rs = shift_args(b, delta, executed, sa)) != TRAJ_OK) return rs;
+  shift_state(b);
+  const GraphKey key = graph_key(b, max_iters, tol, a);
+  const bool given = executed != nullptr;
+  if (!(b->mpc_valid && b->mpc_key == key && b->mpc_delta == delta && b->mpc_given == given)) {
+    // capture {shift; obstacle packing; boundary update; clear counters; solve}
+    if (b->mpc_exec) cudaGraphExecDestroy(b->mpc_exec);
+    b->mpc_exec = nullptr;
+    b->mpc_valid = false;
+    cudaStream_t cs = b->capture_stream;
+    CK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = launch_mpc_shift(sa, cs);
+    if (ce == cudaSuccess && shift_boundary(b, cs) != TRAJ_OK) ce = cudaErrorUnknown;
+    if (ce == cudaSuccess) ce = record_solve(b, a, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->mpc_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      if (b->mpc_exec) cudaGraphExecDestroy(b->mpc_exec);
+      b->mpc_exec = nullptr;
+      return fail(b, TRAJ_ECUDA, std::string("control step graph capture: ") + cudaGetErrorString(ce));
+    }
+    b->mpc_valid = true;
+    b->mpc_key = key;
+    b->mpc_delta = delta;
+    b->mpc_given = given;
+  }
+  CK(b, cudaEventRecord(b->ev0, b->stream));
+  CK(b, cudaGraphLaunch(b->mpc_exec, b->stream));
+  CK(b, cudaEventRecord(b->ev1, b->stream));
+  b->have_result = true;
   b->err.clear();
   return TRAJ_OK;
 }

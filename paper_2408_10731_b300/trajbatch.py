@@ -97,6 +97,7 @@ def load_library():
     lib.traj_set_rho_schedule.argtypes = [_vp, _c_int, _c_double, _c_int]
     lib.traj_set_workspace.argtypes = [_vp, _vp, _vp]
     lib.traj_shift_horizon.argtypes = [_vp, _c_double, _vp]
+    lib.traj_mpc_step.argtypes = [_vp, _c_double, _vp, _c_int, _c_float, _c_double]
     lib.traj_homotopy_signature.argtypes = [_vp, _vp]
     lib.traj_status_string.argtypes = [_c_int]
     lib.traj_status_string.restype = ctypes.c_char_p
@@ -119,7 +120,7 @@ def load_library():
                                        _vp, _vp, _vp, _vp]
     for name in ("traj_batch_create", "traj_batch_destroy", "traj_set_problems",
                  "traj_set_obstacles", "traj_set_initial", "traj_solve", "traj_get_solve_stats",
-                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_set_rho_schedule", "traj_set_workspace", "traj_shift_horizon", "traj_homotopy_signature", "traj_measure_fp32_peak", "traj_measure_mufu_peak",
+                 "traj_get_trajectories", "traj_get_state", "traj_set_state", "traj_set_rho_schedule", "traj_set_workspace", "traj_shift_horizon", "traj_mpc_step", "traj_homotopy_signature", "traj_measure_fp32_peak", "traj_measure_mufu_peak",
                  "traj_solve_noalloc", "traj_set_launch_shape", "traj_get_launch_info", "traj_autotune",
                  "traj_sampler_step", "traj_sampler_step_multi", "traj_gemm_bf16"):
         getattr(lib, name).restype = _c_int
@@ -348,6 +349,13 @@ class TrajBatch:
         starts from the shifted iterate and the carried multipliers."""
         ep, ke = (None, None) if executed is None else _ptr(np.asarray(executed), np.int32)
         self._check(self._lib.traj_shift_horizon(self._h, float(delta), ep))
+
+    def mpc_step(self, delta, max_iters, tol=1e-3, executed=None, timeout_ms=0.0):
+        """One control step, shift_horizon(delta, executed) then solve(max_iters, tol)
+        without statistics, replayed as one CUDA graph (bitwise the two calls)."""
+        ep, ke = (None, None) if executed is None else _ptr(np.asarray(executed), np.int32)
+        self._check(self._lib.traj_mpc_step(self._h, float(delta), ep, int(max_iters),
+                                            float(tol), float(timeout_ms)))
 
     def set_state(self, xi, lam, u):
         """Resume the next solves from an exported (xi, lambda, u) state."""

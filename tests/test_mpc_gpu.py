@@ -60,10 +60,10 @@ def test_three_receding_calls_of_ten_iterations_match_the_oracle():
 def test_new_obstacles_between_shifts_set_the_problems_up_again():
     """A shift keeps each problem's KKT inverse and forms again only the constants that
     depend on the boundary values; new obstacles (here a different number per scene,
-    which changes F^T F) must make the next shift set the problems up in full. Four
-    control loops; after the second shift the obstacles are replaced before its solve,
-    so the third shift starts from the new ones: every loop against the oracle's step
-    from the GPU's own state."""
+    which changes F^T F) are set up in full, and the next shift must start from the
+    blocks that set-up kept. Four control loops; after the second shift the obstacles
+    are replaced before its solve, so the third shift starts from the new ones: every
+    loop against the oracle's step from the GPU's own state."""
     import dataclasses
     b = scenes.config2(7, n_scenes=4, inits=4)
     new = scenes.config2(8, n_scenes=4, inits=4, n_obstacles=30)
@@ -217,3 +217,59 @@ def test_receding_step_in_the_tensor_core_forms(prec, bound, capsys):
     with capsys.disabled():
         print(f"\n{prec} receding step vs FP64: max {err.max():.2e} m")
     assert err.max() <= bound
+
+
+def test_mpc_step_graph_is_bitwise_the_shift_and_solve_calls():
+    """traj_mpc_step replays the shift, the boundary update and the solve as one CUDA
+    graph. Over control loops with the default executed plan, a given one, a new delta
+    (the graph captured again) and obstacles replaced between loops (the graph dropped
+    with the set-up), it gives bitwise the iterates, multipliers, residuals, iteration
+    counts and statuses of traj_shift_horizon followed by traj_solve."""
+    b = scenes.config2(11, n_scenes=6, inits=4)
+    new = scenes.config2(12, n_scenes=6, inits=4, n_obstacles=30)
+    h1, h2 = _handle(b), _handle(b)
+    try:
+        for h in (h1, h2):
+            h.solve(40, 1e-3, stats=False)
+        given = np.arange(b.n_problems) * 4 + 1
+        plan = [(0.1, None), (0.1, None), (0.1, given), (0.2, None), ("obstacles", None),
+                (0.2, None), (0.2, given), (0.1, None)]
+        for step, (delta, ex) in enumerate(plan):
+            if delta == "obstacles":
+                for h in (h1, h2):
+                    h.set_obstacles(new.offsets, new.centers, new.semi_axes, new.velocities)
+                    h.solve(10, 1e-3, stats=False)
+                continue
+            h1.shift_horizon(delta, ex)
+            h1.solve(10, 1e-3, stats=False)
+            h2.mpc_step(delta, 10, 1e-3, executed=ex)
+            g1, g2 = h1.get_trajectories(), h2.get_trajectories()
+            for k in ("xi", "residual", "iters", "status"):
+                assert np.array_equal(g1[k], g2[k]), (step, k)
+            assert np.array_equal(h1.get_state()["lam"], h2.get_state()["lam"]), step
+        st = h2.last_stats()
+        assert st["gpu_ms"] > 0 and st["n_traj"] == b.n_traj
+    finally:
+        h1.close()
+        h2.close()
+
+
+def test_mpc_step_refusals():
+    from paper_2408_10731_b300 import trajbatch as tb
+    b = scenes.config2(13, n_scenes=2, inits=2)
+    h = _handle(b)
+    try:
+        with pytest.raises(tb.TrajBatchError) as e:
+            h.mpc_step(0.1, 10)  # no solve has run
+        assert e.value.code == -7
+        h.solve(5, 1e-3, stats=False)
+        with pytest.raises(tb.TrajBatchError) as e:
+            h.mpc_step(100.0, 10)  # delta beyond the horizon
+        assert e.value.code == -1
+        with pytest.raises(tb.TrajBatchError) as e:
+            h.mpc_step(0.1, 10, executed=[1, 0])  # not a trajectory of its problem
+        assert e.value.code == -1
+        h.mpc_step(0.1, 10)  # the handle is still usable
+        assert np.all(np.isfinite(h.get_trajectories()["xi"]))
+    finally:
+        h.close()
