@@ -679,7 +679,7 @@ def run_mpc(args, torch):
             "scenes_with_a_solved_plan": float(np.mean(solved_frac)),
             "e2e": {"value": 1e3 * float(np.mean(e2e)), "unit": "ms", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(coeffs.numel() * 4 + res.numel() * 4)},
-            "gpu_launches": 9,  # 6 shift kernels, obstacle packing, boundary update, solve
+            "gpu_launches": 6,  # 3 shift kernels, obstacle packing, boundary update, solve
             "clocks": clocks,
             "forms": {"separate_calls": {
                 "ms_per_step": float(np.mean(ms_calls)), "e2e_ms": 1e3 * float(np.mean(e2e_calls)),

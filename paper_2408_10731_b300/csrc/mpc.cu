@@ -37,11 +37,6 @@ __device__ __forceinline__ double blossom_shift(const double (&c)[NC], int i, do
   return w[0];
 }
 
-__global__ void k_exec_clear(int n_problems, unsigned long long *key) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n_problems) key[p] = ~0ull;
-}
-
 __global__ void k_exec_pick(int n_traj, const int *traj_problem, const float *res,
                             unsigned long long *key) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,15 +48,18 @@ __global__ void k_exec_pick(int n_traj, const int *traj_problem, const float *re
   atomicMin(&key[traj_problem[b]], ((unsigned long long)bits << 32) | (unsigned)b);
 }
 
-__global__ void k_exec_index(int n_problems, const unsigned long long *key, int *exec) {
+// The executed plan of every problem from its key, which is then cleared for the next
+// step (the keys start cleared when the handle is created).
+__global__ void k_exec_index(int n_problems, unsigned long long *key, int *exec) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n_problems) exec[p] = key[p] == ~0ull ? -1 : (int)(unsigned)(key[p] & 0xffffffffull);
+  if (p >= n_problems) return;
+  const unsigned long long k = key[p];
+  exec[p] = k == ~0ull ? -1 : (int)(unsigned)(k & 0xffffffffull);
+  key[p] = ~0ull;
 }
 
 // One thread per (trajectory, axis, coefficient): xi0 = shifted xi, lam0 = lam.
-__global__ void k_shift_traj(ShiftArgs a) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; // (trajectory, axis, i)
-  if (e >= (long long)a.n_traj * a.dim * NC) return;
+__device__ __forceinline__ void shift_traj(const ShiftArgs &a, long long e) {
   const long long row = e / NC;
   const int i = (int)(e - row * NC), b = (int)(row / a.dim);
   const double f = a.delta / a.T[a.traj_problem[b]];
@@ -74,9 +72,7 @@ __global__ void k_shift_traj(ShiftArgs a) {
 }
 
 // One thread per (problem, axis): the executed plan's state at delta becomes the start.
-__global__ void k_shift_start(ShiftArgs a, const int *exec) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.n_problems * a.dim) return;
+__device__ __forceinline__ void shift_start(const ShiftArgs &a, const int *exec, int e) {
   const int p = e / a.dim, ax = e % a.dim;
   const int b = exec[p];
   if (b < 0) return; // no trajectory of this problem: its start stays
@@ -93,26 +89,41 @@ __global__ void k_shift_start(ShiftArgs a, const int *exec) {
   a.start_va[(p * 2 + 1) * a.dim + ax] = a0;
 }
 
-__global__ void k_shift_obstacles(ShiftArgs a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.n_obs * a.dim) return;
-  a.centers[e] = (float)__dadd_rn((double)a.centers[e], __dmul_rn((double)a.velocities[e], a.delta));
+// The three independent parts of the shift in one launch of small blocks, so that the
+// FP64 work spreads over every SM: blocks [0, nb_start) the start states (three blossoms
+// each), then the iterates, then the obstacle centres.
+constexpr int SHIFT_THREADS = 32;
+
+__global__ void __launch_bounds__(SHIFT_THREADS) k_shift(ShiftArgs a, const int *exec,
+                                                         int nb_start, int nb_traj) {
+  const int blk = blockIdx.x;
+  if (blk < nb_start) {
+    const int e = blk * SHIFT_THREADS + threadIdx.x;
+    if (e < a.n_problems * a.dim) shift_start(a, exec, e);
+  } else if (blk < nb_start + nb_traj) {
+    const long long e = (long long)(blk - nb_start) * SHIFT_THREADS + threadIdx.x;
+    if (e < (long long)a.n_traj * a.dim * NC) shift_traj(a, e);
+  } else {
+    const int e = (blk - nb_start - nb_traj) * SHIFT_THREADS + threadIdx.x;
+    if (e < a.n_obs * a.dim)
+      a.centers[e] = (float)__dadd_rn((double)a.centers[e], __dmul_rn((double)a.velocities[e], a.delta));
+  }
 }
 
 cudaError_t launch_mpc_shift(const ShiftArgs &a, cudaStream_t s) {
   const int *exec = a.executed;
   if (!exec) {
-    k_exec_clear<<<(a.n_problems + 255) / 256, 256, 0, s>>>(a.n_problems, a.key_scratch);
     k_exec_pick<<<(a.n_traj + 255) / 256, 256, 0, s>>>(a.n_traj, a.traj_problem, a.res,
                                                         a.key_scratch);
     k_exec_index<<<(a.n_problems + 255) / 256, 256, 0, s>>>(a.n_problems, a.key_scratch,
                                                              a.exec_scratch);
     exec = a.exec_scratch;
   }
-  k_shift_start<<<(a.n_problems * a.dim + 127) / 128, 128, 0, s>>>(a, exec);
+  const int nb_start = (a.n_problems * a.dim + SHIFT_THREADS - 1) / SHIFT_THREADS;
   const long long n_coef = (long long)a.n_traj * a.dim * NC;
-  k_shift_traj<<<(unsigned)((n_coef + 127) / 128), 128, 0, s>>>(a);
-  if (a.n_obs > 0) k_shift_obstacles<<<(a.n_obs * a.dim + 255) / 256, 256, 0, s>>>(a);
+  const int nb_traj = (int)((n_coef + SHIFT_THREADS - 1) / SHIFT_THREADS);
+  const int nb_obs = (a.n_obs * a.dim + SHIFT_THREADS - 1) / SHIFT_THREADS;
+  k_shift<<<nb_start + nb_traj + nb_obs, SHIFT_THREADS, 0, s>>>(a, exec, nb_start, nb_traj);
   return cudaGetLastError();
 }
 

@@ -243,6 +243,10 @@ traj_status traj_batch_create(const traj_config *cfg, traj_batch **out) {
       (e = dalloc(&b->d_elite, B)) || (e = dalloc(&b->d_sflag, 1)) ||
       (e = dalloc(&b->d_refit, TRAJ_SAMPLER_MAX_DIST * (D * NC + 7) + 2 * B * D * NC)))
     return bail("cudaMalloc", e);
+  // the executed-plan keys start cleared; each receding-horizon step clears them again
+  // after reading them
+  if ((e = cudaMemset(b->d_exec_key, 0xff, sizeof(unsigned long long) * P)) != cudaSuccess)
+    return bail("cudaMemset", e);
   if ((e = cudaEventCreate(&b->ev0)) || (e = cudaEventCreate(&b->ev1))) return bail("cudaEventCreate", e);
   if ((e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking)))
     return bail("cudaStreamCreateWithFlags", e);
