@@ -253,3 +253,36 @@ def test_decentralised_sampler_with_one_distribution_is_the_plain_step():
             h.close()
     for a, c in zip(*outs):
         np.testing.assert_array_equal(a, c)
+
+
+def test_selections_break_exact_ties_by_the_lower_index():
+    """Every normal draw used twice (at random positions): the two copies project to
+    bitwise the same trajectory, so every residual and cost ties with another sample's.
+    ConstraintEliteSet and EliteSet must still equal the oracle's stable selection (the
+    lower index first), including the ties that straddle N_proj and N_elite."""
+    import torch
+    B, D = 256, 33
+    c3, b, h = _handle(B)
+    cfg = dict(n_inner=20, n_proj=math.ceil(0.73 * B), n_elite=math.ceil(0.10 * B), gamma=1.0,
+               sigma_lr=0.5, eps=1e-6, w_res=1.0, seed=0)
+    mu, sigma, best = _cuda(c3["mu0"]), _cuda(c3["sigma0"]), _cuda(np.zeros(D + 1))
+    half = scenes.normal_draws(321, (B // 2, D))
+    order = np.random.default_rng(5).permutation(B)
+    z = np.empty((B, D))
+    z[order] = np.concatenate([half, half])
+    try:
+        tr = dict(residual=torch.zeros(B, device="cuda"), cost_aug=torch.zeros(B, device="cuda"),
+                  proj_idx=torch.zeros(cfg["n_proj"], dtype=torch.int32, device="cuda"),
+                  elite_idx=torch.zeros(cfg["n_elite"], dtype=torch.int32, device="cuda"))
+        h.sampler_step(cfg, 0, mu, sigma, best, z=_cuda(z), trace=tr)
+        g = {k: v.cpu().numpy() for k, v in tr.items()}
+        twin = np.empty(B, dtype=np.int64)
+        twin[order[:B // 2]] = order[B // 2:]
+        twin[order[B // 2:]] = order[:B // 2]
+        assert np.array_equal(g["residual"], g["residual"][twin])
+        assert np.array_equal(g["cost_aug"], g["cost_aug"][twin])
+        p_o, e_o = priest.select(g["residual"], g["cost_aug"], cfg["n_proj"], cfg["n_elite"])
+        np.testing.assert_array_equal(g["proj_idx"], p_o)
+        np.testing.assert_array_equal(g["elite_idx"], e_o)
+    finally:
+        h.close()
