@@ -147,12 +147,16 @@ static void free_all(traj_batch *b) {
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
 }
 
-// Drop the captured graphs (the solve's and the control step's): their nodes hold the
-// buffers and arguments of the handle's state at capture.
-static void invalidate_graph(traj_batch *b) {
+static void drop_solve_graph(traj_batch *b) {
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   b->graph_exec = nullptr;
   b->graph_valid = false;
+}
+
+// Drop the captured graphs (the solve's and the control step's): their nodes hold the
+// buffers and arguments of the handle's state at capture.
+static void invalidate_graph(traj_batch *b) {
+  drop_solve_graph(b);
   if (b->mpc_exec) cudaGraphExecDestroy(b->mpc_exec);
   b->mpc_exec = nullptr;
   b->mpc_valid = false;
@@ -633,7 +637,7 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
   const GraphKey key = graph_key(b, max_iters, tol, a);
   if (!(b->graph_valid && b->g_key == key)) {
     // capture {clear counters; persistent solve} on the handle's capture stream
-    invalidate_graph(b);
+    drop_solve_graph(b);
     cudaStream_t cs = b->capture_stream;
     CK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = record_solve(b, a, cs);
@@ -643,7 +647,7 @@ traj_status traj_solve(traj_batch *b, int max_iters, float tol, double timeout_m
     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->graph_exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (ce != cudaSuccess) {
-      invalidate_graph(b);
+      drop_solve_graph(b);
       return fail(b, TRAJ_ECUDA, std::string("solve graph capture: ") + cudaGetErrorString(ce));
     }
     b->graph_valid = true;
