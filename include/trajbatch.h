@@ -269,7 +269,8 @@ traj_status traj_shift_horizon(traj_batch *b, double delta, const int *executed)
  * traj_set_* call; executed (host int[n_problems], or NULL for each problem's
  * smallest worst residual) is checked on the host and copied before the replay.
  * Asynchronous; traj_get_solve_stats afterwards reports the step's GPU time (shift and
- * solve). Errors as the two calls it stands for, and TRAJ_ECUDA if the capture fails.
+ * solve). Errors as the two calls it stands for, and TRAJ_ECUDA if the capture fails
+ * (then nothing of the step has run and the handle is as before the call).
  * Without kept FP64 blocks (a handle whose set-up has not run with its obstacles) it
  * makes the two calls instead. Passage: Paper II, the MPC use of Algorithm 2
  * (warm-started iterations per control loop). */

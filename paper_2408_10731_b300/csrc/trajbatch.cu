@@ -891,9 +891,12 @@ traj_status traj_mpc_step(traj_batch *b, double delta, const int *executed, int 
     if (ce == cudaSuccess) ce = ee;
     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->mpc_exec, g, 0);
     if (g) cudaGraphDestroy(g);
-    if (ce != cudaSuccess) {
+    if (ce != cudaSuccess) { // nothing of the step ran: the handle stays as it was
       if (b->mpc_exec) cudaGraphExecDestroy(b->mpc_exec);
       b->mpc_exec = nullptr;
+      b->carry = carry0;
+      b->resume = resume0;
+      b->have_result = true;
       return fail(b, TRAJ_ECUDA, std::string("control step graph capture: ") + cudaGetErrorString(ce));
     }
     b->mpc_valid = true;
