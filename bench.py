@@ -630,6 +630,34 @@ def run_mpc(args, torch):
         h.shift_horizon(delta)
         h.solve(iters, 1e-3, stats=False)
 
+    def shape_of(w, bps, team):
+        return {"warps_per_block": w, "blocks_per_sm": bps, "warps_per_trajectory": team}
+
+    # launch shape of the solve: the caller's, else the one whose control steps ran
+    # fastest over a short trial of each candidate (outside the timed region)
+    if args.shape:
+        w, bps, team = (int(x) for x in args.shape.split(","))
+        h.set_launch_shape(w, bps, team)
+        shape = dict(shape_of(w, bps, team), fixed=True)
+    else:
+        trial = {}
+        for w, bps, team in ((0, 0, 1), (1, 0, 1), (2, 0, 1), (8, 0, 1), (2, 0, 2), (4, 0, 2)):
+            h.set_launch_shape(w, bps, team)
+            start_episode()
+            for _ in range(3):
+                control_step()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                control_step()
+            e1.record(stream); e1.synchronize()
+            trial[(w, bps, team)] = e0.elapsed_time(e1) / 5
+        best = min(trial, key=trial.get)
+        h.set_launch_shape(*best)
+        shape = dict(shape_of(*best), tuned_on="5 control steps per candidate",
+                     trial_ms={f"{w},{bps},{t}": round(v, 4) for (w, bps, t), v in trial.items()})
+
     def episodes(step_fn, clk=None):
         start_episode()
         for _ in range(args.warmup):
@@ -675,7 +703,8 @@ def run_mpc(args, torch):
                                    "episodes of 10 control steps from a converged plan",
                        "l2": "state and inputs stay on the device; each control step is one "
                              "CUDA graph launch (traj_mpc_step: shift kernels, obstacle "
-                             "packing, boundary update, solve)"},
+                             "packing, boundary update, solve)",
+                       "launch_shape": shape},
             "scenes_with_a_solved_plan": float(np.mean(solved_frac)),
             "e2e": {"value": 1e3 * float(np.mean(e2e)), "unit": "ms", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(coeffs.numel() * 4 + res.numel() * 4)},
