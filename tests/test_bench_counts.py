@@ -52,3 +52,20 @@ def test_measured_traffic_holds_only_for_the_captured_sources(monkeypatch):
         monkeypatch.setitem(bench.MEASURED_TRAFFIC, (kernel, "config5"), (1234, "0" * 16))
         assert bench.measured_traffic(kernel, "config5") is None
     assert bench.measured_traffic("k_am_fp32", "no such workload") is None
+
+
+def test_single_thread_baseline_spans_every_scene_of_the_all_core_sample():
+    """The one-thread oracle run takes every 4th trajectory of the all-core sample's
+    scenes, so that it covers the same scenes (two trajectories each of eight)."""
+    b = scenes.config2(0, n_scenes=4, inits=8)
+    one = bench.cpu_baseline(workload=b, scenes_idx=range(4), n_threads=1, traj_stride=4,
+                             max_iters=3)
+    assert one["cores"] == 1 and one["kind"] == "oracle"
+    assert one["sample"].startswith("8 trajectories (scenes 0..3 of the workload, every 4th "
+                                    "trajectory)")
+    assert 0 <= one["solved"] <= 8 and one["trajectory_iterations_per_s"] > 0
+    sub = b.select_problems(range(4)).subset(range(0, 32, 4))
+    assert sorted(set(sub.traj_problem.tolist())) == [0, 1, 2, 3]
+    allc = bench.cpu_baseline(workload=b, scenes_idx=range(4), max_iters=3)
+    assert allc["sample"].startswith("32 trajectories (scenes 0..3 of the workload, all "
+                                     "initialisations)")
