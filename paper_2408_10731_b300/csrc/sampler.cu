@@ -44,47 +44,45 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 __device__ __forceinline__ float u01(uint32_t x) { return ((float)x + 0.5f) * 2.3283064365386963e-10f; }
 
 // ---- kernels ----------------------------------------------------------------
-// Cholesky of Sigma_g + eps I (D x D, D <= 48) into L_g (lower, row-major). One
+// Cholesky of Sigma_g + eps I (D x D, D = 11 dim) into L_g (lower, row-major). One
 // CTA per distribution g = blockIdx.x.
-__global__ void k_cholesky(const float *sigma, int D, float eps, float *L, int *flag) {
-  // thread i holds row i in registers (loops unrolled to the 48-column bound, so every
-  // index is a constant); the finished entries of each row are published in shared
-  // memory for the rows below. The sums run in the column-by-column order of the
-  // textbook algorithm.
-  __shared__ float Ls[48 * 48];
+template <int D>
+__global__ void k_cholesky(const float *sigma, float eps, float *L, int *flag) {
+  // thread i holds row i in registers (loops unrolled to D, so every index is a
+  // constant); the finished entries of each row are published in shared memory for the
+  // rows below. The sums run in the column-by-column order of the textbook algorithm.
+  __shared__ float Ls[D * D];
   sigma += (size_t)blockIdx.x * D * D;
   L += (size_t)blockIdx.x * D * D;
   const int i = threadIdx.x;
   const bool mine = i < D;
-  float row[48];
+  float row[D];
 #pragma unroll
-  for (int k = 0; k < 48; ++k)
-    row[k] = mine && k < D ? 0.5f * (sigma[i * D + k] + sigma[k * D + i]) + (i == k ? eps : 0.f) : 0.f;
+  for (int k = 0; k < D; ++k)
+    row[k] = mine ? 0.5f * (sigma[i * D + k] + sigma[k * D + i]) + (i == k ? eps : 0.f) : 0.f;
 #pragma unroll
-  for (int j = 0; j < 48; ++j) {
-    if (j >= D) break;
+  for (int j = 0; j < D; ++j) {
     if (i == j) {
       float d = row[j];
 #pragma unroll
       for (int k = 0; k < j; ++k) d -= row[k] * row[k];
       if (!(d > 0.f)) { atomicOr(flag, 4); d = 1e-30f; }
       row[j] = sqrtf(d);
-      Ls[j * 48 + j] = row[j];
+      Ls[j * D + j] = row[j];
     }
     __syncthreads();
     if (mine && i > j) {
       float s = row[j];
 #pragma unroll
-      for (int k = 0; k < j; ++k) s -= row[k] * Ls[j * 48 + k];
-      row[j] = s / Ls[j * 48 + j];
-      Ls[i * 48 + j] = row[j];
+      for (int k = 0; k < j; ++k) s -= row[k] * Ls[j * D + k];
+      row[j] = s / Ls[j * D + j];
+      Ls[i * D + j] = row[j];
     }
     __syncthreads();
   }
   if (mine)
 #pragma unroll
-    for (int k = 0; k < 48; ++k)
-      if (k < D) L[i * D + k] = k <= i ? row[k] : 0.f;
+    for (int k = 0; k < D; ++k) L[i * D + k] = k <= i ? row[k] : 0.f;
 }
 
 // xi_i = mu_g + L_g z_i for sample i of group g = i / Bg. z from `z` ([B][D]) or,
@@ -447,7 +445,9 @@ cudaError_t launch_sampler_front(const float *mu, const float *sigma, int D, int
                                  float eps, const float *z, unsigned long long seed, int iteration,
                                  float *L_scratch, int *flag, float *xi0, float *samples_out,
                                  cudaStream_t s) {
-  k_cholesky<<<n_dist, 64, 0, s>>>(sigma, D, eps, L_scratch, flag);
+  if (D == 2 * NC) k_cholesky<2 * NC><<<n_dist, 64, 0, s>>>(sigma, eps, L_scratch, flag);
+  else if (D == 3 * NC) k_cholesky<3 * NC><<<n_dist, 64, 0, s>>>(sigma, eps, L_scratch, flag);
+  else return cudaErrorInvalidValue;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sample<<<(B + SAMPLE_WARPS - 1) / SAMPLE_WARPS, 32 * SAMPLE_WARPS, 0, s>>>(
