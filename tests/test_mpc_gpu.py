@@ -16,20 +16,47 @@ def _handle(batch, **kw):
     return tb.from_batch(batch, **kw)
 
 
-def test_three_receding_calls_of_ten_iterations_match_the_oracle():
+def _oracle_sensitivity(batch, iters, rel=1e-7, trials=3):
+    """How far the FP64 oracle's own result after `iters` iterations moves, per
+    trajectory, when its initial coefficients are perturbed at FP32 rounding size
+    (relative 1e-7): the part of any FP32 implementation's error that the method
+    itself amplifies, whatever order its sums are rounded in."""
+    base = am.solve(batch, iters, tol=-1.0)
+    rng = np.random.default_rng(0)
+    worst = np.zeros(batch.n_traj)
+    for _ in range(trials):
+        x0 = batch.xi0 * (1.0 + rel * rng.standard_normal(batch.xi0.shape))
+        o = am.solve(batch, iters, tol=-1.0, xi0=x0)
+        worst = np.maximum(worst, position_error(batch, o["xi"], base["xi"]))
+    return worst
+
+
+@pytest.mark.parametrize("shape", [None, (4, 0, 2)], ids=["one_warp", "two_warp_team"])
+def test_three_receding_calls_of_ten_iterations_match_the_oracle(shape):
     """Each control loop is checked against the oracle's step from the GPU's own state
     before it (coefficients and multipliers as the GPU left them), at the parity bar;
     the oracle's own chain of three loops is followed beside it, where the FP32
-    rounding of each shifted iterate and start state compounds (bound 5e-5 m)."""
+    rounding of each shifted iterate and start state compounds (bound 5e-5 m). Run at
+    one warp per trajectory and with two-warp teams (the shape the MPC bench's trial
+    picks), whose carried multipliers enter through the team kernel. The initial
+    30-iteration solve holds one trajectory (18) that the method itself amplifies: a
+    1e-7 relative change of its start moves the oracle's own result by 2.4e-5 m, so
+    its bar there is twice that measured sensitivity; every trajectory the method
+    does not amplify is held to 1e-5 m."""
     b = scenes.config2(5, n_scenes=6, inits=4)
     executed = np.arange(b.n_problems) * 4 + 1  # the second plan of every scene
     delta = 0.3
     h = _handle(b)
     try:
+        if shape:
+            h.set_launch_shape(*shape)
         h.solve(30, -1.0)
         g = h.get_trajectories()
         o = am.solve(b, 30, tol=-1.0, want_lambda=True)
-        assert position_error(b, g["xi"], o["xi"]).max() <= POS_TOL
+        err0 = position_error(b, g["xi"], o["xi"])
+        sens = _oracle_sensitivity(b, 30)
+        assert np.all(err0 <= np.maximum(POS_TOL, 2.0 * sens)), (err0.max(), sens[np.argmax(err0)])
+        assert np.all(err0[sens < POS_TOL / 4] <= POS_TOL)
         chain_xi, chain_lam, chain_b = o["xi"], o["lam"], b
         cur = b
         for step in range(3):
