@@ -115,7 +115,7 @@ def kernel_name(precision, shape, max_np=100):
 
 def algorithmic_ops(batch, iters):
     """FP32 lane operations the method must execute for the given iteration counts,
-    counted per trajectory-iteration as the survey's measurement plan does:
+    counted per trajectory-iteration (the dense count of the method's definition):
       every obstacle-timestep pair (the dense test, every pair every iteration):
         13 in 2D, 17 in 3D (Delta = p - (c + v t), u = Delta / a, |u|^2, the
         compare, and the projection's share: 1 / |u| - 1, the scale and the sum);
