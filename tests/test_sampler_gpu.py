@@ -286,3 +286,39 @@ def test_selections_break_exact_ties_by_the_lower_index():
         np.testing.assert_array_equal(g["elite_idx"], e_o)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("n_elite", [900, 1500])
+def test_refit_paths_for_large_elite_sets_match_the_oracle(n_elite):
+    """The refit reads the elites from shared memory while they fit: the covariance up
+    to 775 elites of 33 coefficients (weighted and centred copies), the mean up to
+    1241. Beyond, it reads them from global memory; 900 elites take the covariance's
+    global path, 1500 both. The selections are checked exactly and the mean,
+    covariance and best elite against the oracle's refit on the GPU's own keys."""
+    import torch
+    B, D = 4096, 33
+    c3, b, h = _handle(B)
+    cfg = dict(n_inner=5, n_proj=3000, n_elite=n_elite, gamma=1.0, sigma_lr=0.5, eps=1e-6,
+               w_res=1.0, seed=3)
+    mu, sigma, best = _cuda(c3["mu0"]), _cuda(c3["sigma0"]), _cuda(np.zeros(D + 1))
+    mu_in = c3["mu0"].astype(np.float64)
+    sig_in = c3["sigma0"].astype(np.float64)
+    try:
+        tr = dict(projected=torch.zeros(B, D, device="cuda"),
+                  residual=torch.zeros(B, device="cuda"), cost_aug=torch.zeros(B, device="cuda"),
+                  proj_idx=torch.zeros(cfg["n_proj"], dtype=torch.int32, device="cuda"),
+                  elite_idx=torch.zeros(n_elite, dtype=torch.int32, device="cuda"))
+        h.sampler_step(cfg, 0, mu, sigma, best, trace=tr)
+        g = {k: v.cpu().numpy() for k, v in tr.items()}
+        p_o, e_o = priest.select(g["residual"], g["cost_aug"], cfg["n_proj"], n_elite)
+        np.testing.assert_array_equal(g["proj_idx"], p_o)
+        np.testing.assert_array_equal(g["elite_idx"], e_o)
+        m_o, s_o, best_o, bc_o = priest.refit(g["projected"].astype(np.float64),
+                                              g["cost_aug"].astype(np.float64), e_o, mu_in,
+                                              sig_in, cfg["gamma"], cfg["sigma_lr"])
+        np.testing.assert_allclose(mu.cpu().numpy(), m_o, rtol=1e-4, atol=1e-4)
+        np.testing.assert_allclose(sigma.cpu().numpy(), s_o, rtol=1e-3, atol=1e-4)
+        np.testing.assert_array_equal(best.cpu().numpy()[:D], g["projected"][e_o[0]])
+        assert best.cpu().numpy()[D] == g["cost_aug"][e_o[0]]
+    finally:
+        h.close()
