@@ -322,3 +322,48 @@ def test_refit_paths_for_large_elite_sets_match_the_oracle(n_elite):
         assert best.cpu().numpy()[D] == g["cost_aug"][e_o[0]]
     finally:
         h.close()
+
+
+def test_two_dimensional_sampler_step_matches_oracle_stagewise():
+    """The sampler on a 2D projection-mode handle (22 coefficients per sample: the
+    Cholesky's D = 22 form): draws, projection, costs, selections and refit of one
+    outer iteration against the oracle on the GPU's inputs to each stage."""
+    import torch
+    from paper_2408_10731_b300 import trajbatch as tb
+    B, D = 128, 22
+    b = scenes.config2(21, n_scenes=1, inits=B)
+    h = tb.from_batch(b, cost_mode="project")
+    mu0 = scenes.straight_line_coeffs(b.start[0], b.goal[0]).reshape(-1).astype(np.float64)
+    sig0 = 0.5 * np.eye(D) + 0.05 * np.ones((D, D))
+    cfg = dict(n_inner=10, n_proj=math.ceil(0.73 * B), n_elite=math.ceil(0.10 * B), gamma=1.0,
+               sigma_lr=0.5, eps=1e-6, w_res=1.0, seed=0)
+    mu, sigma, best = _cuda(mu0), _cuda(sig0), _cuda(np.zeros(D + 1))
+    z = scenes.normal_draws(77, (B, D))
+    try:
+        tr = dict(samples=torch.zeros(B, D, device="cuda"),
+                  projected=torch.zeros(B, D, device="cuda"),
+                  residual=torch.zeros(B, device="cuda"), cost_aug=torch.zeros(B, device="cuda"),
+                  proj_idx=torch.zeros(cfg["n_proj"], dtype=torch.int32, device="cuda"),
+                  elite_idx=torch.zeros(cfg["n_elite"], dtype=torch.int32, device="cuda"))
+        h.sampler_step(cfg, 0, mu, sigma, best, z=_cuda(z), trace=tr)
+        g = {k: v.cpu().numpy() for k, v in tr.items()}
+        ref = priest.sample(mu0, sig0.astype(np.float32).astype(np.float64), z, cfg["eps"])
+        np.testing.assert_allclose(g["samples"], ref, atol=5e-5, rtol=1e-5)
+        xs = g["samples"].astype(np.float64).reshape(B, 2, 11)
+        o = am.solve(b, cfg["n_inner"], tol=-1.0, cost_mode=1, xi0=xs)
+        err = position_error(b, g["projected"].reshape(B, 2, 11), o["xi"])
+        assert err.max() <= POS_TOL, err.max()
+        r_o, c_o = priest.costs(b, g["projected"].astype(np.float64), o["residual"])
+        np.testing.assert_allclose(g["residual"], r_o, atol=2e-5, rtol=1e-4)
+        np.testing.assert_allclose(g["cost_aug"], c_o, atol=1e-4, rtol=2e-5)
+        p_o, e_o = priest.select(g["residual"], g["cost_aug"], cfg["n_proj"], cfg["n_elite"])
+        np.testing.assert_array_equal(g["proj_idx"], p_o)
+        np.testing.assert_array_equal(g["elite_idx"], e_o)
+        m_o, s_o, _, _ = priest.refit(g["projected"].astype(np.float64),
+                                      g["cost_aug"].astype(np.float64), e_o, mu0,
+                                      sig0.astype(np.float32).astype(np.float64), cfg["gamma"],
+                                      cfg["sigma_lr"])
+        np.testing.assert_allclose(mu.cpu().numpy(), m_o, rtol=1e-4, atol=1e-4)
+        np.testing.assert_allclose(sigma.cpu().numpy(), s_o, rtol=1e-3, atol=1e-4)
+    finally:
+        h.close()
