@@ -246,15 +246,17 @@ def test_receding_step_in_the_tensor_core_forms(prec, bound, capsys):
     assert err.max() <= bound
 
 
-def test_mpc_step_graph_is_bitwise_the_shift_and_solve_calls():
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_mpc_step_graph_is_bitwise_the_shift_and_solve_calls(precision):
     """traj_mpc_step replays the shift, the boundary update and the solve as one CUDA
     graph. Over control loops with the default executed plan, a given one, a new delta
     (the graph captured again) and obstacles replaced between loops (the graph dropped
     with the set-up), it gives bitwise the iterates, multipliers, residuals, iteration
-    counts and statuses of traj_shift_horizon followed by traj_solve."""
+    counts and statuses of traj_shift_horizon followed by traj_solve, with the FP32
+    solve and with the tensor-core one inside the graph."""
     b = scenes.config2(11, n_scenes=6, inits=4)
     new = scenes.config2(12, n_scenes=6, inits=4, n_obstacles=30)
-    h1, h2 = _handle(b), _handle(b)
+    h1, h2 = _handle(b, precision=precision), _handle(b, precision=precision)
     try:
         for h in (h1, h2):
             h.solve(40, 1e-3, stats=False)
