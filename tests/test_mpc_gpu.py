@@ -251,9 +251,10 @@ def test_mpc_step_graph_is_bitwise_the_shift_and_solve_calls(precision):
     """traj_mpc_step replays the shift, the boundary update and the solve as one CUDA
     graph. Over control loops with the default executed plan, a given one, a new delta
     (the graph captured again) and obstacles replaced between loops (the graph dropped
-    with the set-up), it gives bitwise the iterates, multipliers, residuals, iteration
-    counts and statuses of traj_shift_horizon followed by traj_solve, with the FP32
-    solve and with the tensor-core one inside the graph."""
+    with the set-up) and a new launch shape (two-warp teams for FP32), it gives bitwise
+    the iterates, multipliers, residuals, iteration counts and statuses of
+    traj_shift_horizon followed by traj_solve, with the FP32 solve and with the
+    tensor-core one inside the graph."""
     b = scenes.config2(11, n_scenes=6, inits=4)
     new = scenes.config2(12, n_scenes=6, inits=4, n_obstacles=30)
     h1, h2 = _handle(b, precision=precision), _handle(b, precision=precision)
@@ -262,12 +263,16 @@ def test_mpc_step_graph_is_bitwise_the_shift_and_solve_calls(precision):
             h.solve(40, 1e-3, stats=False)
         given = np.arange(b.n_problems) * 4 + 1
         plan = [(0.1, None), (0.1, None), (0.1, given), (0.2, None), ("obstacles", None),
-                (0.2, None), (0.2, given), (0.1, None)]
+                (0.2, None), (0.2, given), ("shape", None), (0.1, None), (0.1, None)]
         for step, (delta, ex) in enumerate(plan):
             if delta == "obstacles":
                 for h in (h1, h2):
                     h.set_obstacles(new.offsets, new.centers, new.semi_axes, new.velocities)
                     h.solve(10, 1e-3, stats=False)
+                continue
+            if delta == "shape":  # the graph is captured again for the new launch shape
+                for h in (h1, h2):
+                    h.set_launch_shape(4, 0, 2 if precision == "fp32" else 1)
                 continue
             h1.shift_horizon(delta, ex)
             h1.solve(10, 1e-3, stats=False)
