@@ -317,8 +317,9 @@ cudaError_t launch_setup_boundary(int n_problems, int levels, const double *d_st
                                   double w_track, const double *kkt64, float *d_constants,
                                   cudaStream_t s) {
   if (n_problems <= 0 || levels <= 0) return cudaSuccess;
+  // small blocks: the FP64 dot products spread over every SM instead of a few
   const long long total = (long long)n_problems * levels * 3 * ROW;
-  k_setup_boundary<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+  k_setup_boundary<<<(unsigned)((total + 31) / 32), 32, 0, s>>>(
       n_problems, levels, d_start, d_goal, d_start_va, dim, w_track, kkt64, d_constants);
   return cudaGetLastError();
 }
@@ -328,9 +329,10 @@ cudaError_t launch_pack_obstacles(int dim, int n_problems, int n_slots, const in
                                   const float *vel, float4 *out, ProblemDev *problems,
                                   cudaStream_t s) {
   if (n_slots <= 0 || n_problems <= 0) return cudaSuccess;
-  k_pack_obstacles<<<(n_slots + 255) / 256, 256, 0, s>>>(dim, n_problems, n_slots, offsets,
-                                                        pair_off, centers, axes, vel, out,
-                                                        problems);
+  // small blocks: the FP64 divisions spread over every SM instead of a few
+  k_pack_obstacles<<<(n_slots + 31) / 32, 32, 0, s>>>(dim, n_problems, n_slots, offsets,
+                                                      pair_off, centers, axes, vel, out,
+                                                      problems);
   return cudaGetLastError();
 }
 
