@@ -367,3 +367,37 @@ def test_two_dimensional_sampler_step_matches_oracle_stagewise():
         np.testing.assert_allclose(sigma.cpu().numpy(), s_o, rtol=1e-3, atol=1e-4)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("n_proj,n_elite", [(128, 1), (1, 1), (128, 128)])
+def test_degenerate_selection_sizes_match_the_oracle(n_proj, n_elite):
+    """Edge sizes of ConstraintEliteSet / EliteSet: every sample a candidate with one
+    elite, a single candidate and elite, and every sample an elite. Selections exact,
+    refit (a single elite: the mean moves toward it and the covariance takes its
+    outer product) against the oracle on the GPU's own keys."""
+    import torch
+    B, D = 128, 33
+    c3, b, h = _handle(B)
+    cfg = dict(n_inner=5, n_proj=n_proj, n_elite=n_elite, gamma=1.0, sigma_lr=0.5, eps=1e-6,
+               w_res=1.0, seed=9)
+    mu, sigma, best = _cuda(c3["mu0"]), _cuda(c3["sigma0"]), _cuda(np.zeros(D + 1))
+    try:
+        tr = dict(projected=torch.zeros(B, D, device="cuda"),
+                  residual=torch.zeros(B, device="cuda"), cost_aug=torch.zeros(B, device="cuda"),
+                  proj_idx=torch.zeros(n_proj, dtype=torch.int32, device="cuda"),
+                  elite_idx=torch.zeros(n_elite, dtype=torch.int32, device="cuda"))
+        h.sampler_step(cfg, 0, mu, sigma, best, trace=tr)
+        g = {k: v.cpu().numpy() for k, v in tr.items()}
+        p_o, e_o = priest.select(g["residual"], g["cost_aug"], n_proj, n_elite)
+        np.testing.assert_array_equal(g["proj_idx"], p_o)
+        np.testing.assert_array_equal(g["elite_idx"], e_o)
+        m_o, s_o, _, _ = priest.refit(g["projected"].astype(np.float64),
+                                      g["cost_aug"].astype(np.float64), e_o,
+                                      c3["mu0"].astype(np.float64),
+                                      c3["sigma0"].astype(np.float64), cfg["gamma"],
+                                      cfg["sigma_lr"])
+        np.testing.assert_allclose(mu.cpu().numpy(), m_o, rtol=1e-4, atol=1e-4)
+        np.testing.assert_allclose(sigma.cpu().numpy(), s_o, rtol=1e-3, atol=1e-4)
+        assert best.cpu().numpy()[D] == g["cost_aug"][e_o[0]]
+    finally:
+        h.close()
