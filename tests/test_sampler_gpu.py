@@ -401,3 +401,35 @@ def test_degenerate_selection_sizes_match_the_oracle(n_proj, n_elite):
         assert best.cpu().numpy()[D] == g["cost_aug"][e_o[0]]
     finally:
         h.close()
+
+
+def test_non_finite_samples_rank_last():
+    """Two draws made NaN by the caller: their samples are NaN, the solve leaves them
+    (non-finite input), their residual ranks as +inf and their cost is NaN, so both
+    selections put them last, as the oracle's stable sort does, and the refit from
+    the remaining elites stays finite."""
+    import torch
+    B, D = 128, 33
+    c3, b, h = _handle(B)
+    cfg = dict(n_inner=5, n_proj=100, n_elite=13, gamma=1.0, sigma_lr=0.5, eps=1e-6, w_res=1.0,
+               seed=0)
+    mu, sigma, best = _cuda(c3["mu0"]), _cuda(c3["sigma0"]), _cuda(np.zeros(D + 1))
+    z = scenes.normal_draws(55, (B, D)).astype(np.float64)
+    z[[17, 90]] = np.nan
+    try:
+        tr = dict(projected=torch.zeros(B, D, device="cuda"),
+                  residual=torch.zeros(B, device="cuda"), cost_aug=torch.zeros(B, device="cuda"),
+                  proj_idx=torch.zeros(cfg["n_proj"], dtype=torch.int32, device="cuda"),
+                  elite_idx=torch.zeros(cfg["n_elite"], dtype=torch.int32, device="cuda"))
+        h.sampler_step(cfg, 0, mu, sigma, best, z=_cuda(z), trace=tr)
+        g = {k: v.cpu().numpy() for k, v in tr.items()}
+        assert np.isinf(g["residual"][[17, 90]]).all()
+        assert not np.isfinite(g["cost_aug"][[17, 90]]).any()
+        p_o, e_o = priest.select(g["residual"], g["cost_aug"], cfg["n_proj"], cfg["n_elite"])
+        np.testing.assert_array_equal(g["proj_idx"], p_o)
+        np.testing.assert_array_equal(g["elite_idx"], e_o)
+        assert 17 not in g["proj_idx"] and 90 not in g["proj_idx"]
+        assert np.all(np.isfinite(mu.cpu().numpy())) and np.all(np.isfinite(sigma.cpu().numpy()))
+        assert np.isfinite(best.cpu().numpy()).all()
+    finally:
+        h.close()
