@@ -882,15 +882,17 @@ traj_status traj_mpc_step(traj_batch *b, double delta, const int *executed, int 
     b->mpc_exec = nullptr;
     b->mpc_valid = false;
     cudaStream_t cs = b->capture_stream;
-    CK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = launch_mpc_shift(sa, cs);
-    if (ce == cudaSuccess && shift_boundary(b, cs) != TRAJ_OK) ce = cudaErrorUnknown;
-    if (ce == cudaSuccess) ce = record_solve(b, a, cs);
-    cudaGraph_t g = nullptr;
-    cudaError_t ee = cudaStreamEndCapture(cs, &g);
-    if (ce == cudaSuccess) ce = ee;
-    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->mpc_exec, g, 0);
-    if (g) cudaGraphDestroy(g);
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      ce = launch_mpc_shift(sa, cs);
+      if (ce == cudaSuccess && shift_boundary(b, cs) != TRAJ_OK) ce = cudaErrorUnknown;
+      if (ce == cudaSuccess) ce = record_solve(b, a, cs);
+      cudaGraph_t g = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(cs, &g);
+      if (ce == cudaSuccess) ce = ee;
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->mpc_exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+    }
     if (ce != cudaSuccess) { // nothing of the step ran: the handle stays as it was
       if (b->mpc_exec) cudaGraphExecDestroy(b->mpc_exec);
       b->mpc_exec = nullptr;
